@@ -1,0 +1,312 @@
+#!/usr/bin/env python3
+"""Benchmark: the 28-qubit diagonal-heavy gate-level stream on one GB300.
+
+One step = simulate the whole circuit from |0...0>: reset + optimizer
+(diagonal detector, gate-block search, fusion) + every kernel of the plan,
+over a 2 GiB complex64 state resident in HBM (larger than the 129 MB L2, so
+no flush is needed between steps).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (torchrun): independent replicas, one per GPU (the path does not
+shard: replicas only); value = total amplitude updates of all ranks / the
+slowest rank's time.  ``--impl reference`` times the CPU oracle (the only
+reference this paper has) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "amplitude-updates/s & HBM GB/s vs peak; served circuits/s, p50/p99 latency"
+UNIT = "amplitude-updates/s"
+N_QUBITS = 28
+N_GATES = 500
+SEED = 1
+WORKLOAD = "28-qubit diagonal-heavy gate-level stream (500 gates, 80% RZ/CP/RZZ, 20% H/RX, after H on every qubit), complex64"
+
+# ncu DRAM traffic per chunk-sweep launch (dram__bytes_read.sum + write.sum),
+# keyed by the sha256 of k_chunk.cu at capture time; null when the kernel changed.
+TRAFFIC = {}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for i, nm in enumerate(names):
+                if f[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(budget_s: float = 15.0):
+    """Time the CPU oracle (complex128, gate by gate, all host cores) on the
+    first gates of the workload until ~budget_s of work; returns
+    (amplitude-updates/s, cores, sample description)."""
+    import numpy as np
+    import oracle
+    from paper_2604_12256_gb300 import circuits as C
+    c = C.diag_heavy(N_QUBITS, N_GATES, SEED)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    a = oracle.basis_state(N_QUBITS, 0)
+    oracle.run_inplace(N_QUBITS, a, c.gates[:1], cores)    # warm: page in the 4 GiB state
+    done, t0 = 0, time.perf_counter()
+    for g in c.gates[1:]:
+        oracle.run_inplace(N_QUBITS, a, [g], cores)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    del a
+    return done * (1 << N_QUBITS) / dt, cores, \
+        f"gates 2..{done + 1} of {len(c.gates)} at {N_QUBITS} qubits, complex128, {dt:.1f} s (per-gate rate)"
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(min(5.0, args.ref_budget))
+    for _ in range(args.steps):
+        v, cores, sample = cpu_oracle_sample(args.ref_budget)
+        vals.append(v)
+    v = statistics.median(vals)
+    steps_per_s = v / (len(_circuit_gates()) * (1 << N_QUBITS))
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 / steps_per_s, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "gates": len(_circuit_gates()),
+                       "seed": SEED, "l2": "state (4 GiB) larger than L2"},
+            "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+_GATES = None
+
+
+def _circuit_gates():
+    global _GATES
+    if _GATES is None:
+        from paper_2604_12256_gb300 import circuits as C
+        _GATES = C.diag_heavy(N_QUBITS, N_GATES, SEED).gates
+    return _GATES
+
+
+def run_gpu(args, rank, world, dist):
+    import torch
+    from paper_2604_12256_gb300 import build as B
+    from paper_2604_12256_gb300 import circuits as C
+    from paper_2604_12256_gb300 import svsim as S
+
+    B.build()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    circ = C.diag_heavy(N_QUBITS, N_GATES, SEED)
+    ga = S.GateArray(circ.gates)
+    G = len(circ.gates)
+    amps = 1 << N_QUBITS
+    # the state lives in a torch-owned HBM buffer; kernels run on torch's stream
+    buf = torch.empty(2 * amps, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    sim = S.Sim(N_QUBITS, S.SIM_C64, dev_buf=buf.data_ptr(), nbytes=buf.numel() * 4, stream=stream.cuda_stream)
+    opt = S.default_options()
+
+    def step():
+        sim.reset(0)
+        sim.apply(ga, opt)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    plan = sim.stats()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    clocks = Clocks(dev)
+    clocks.start()
+    time.sleep(0.3)
+    sim.profile_enable(True)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = sim.profile_read()
+    sim.profile_enable(False)
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end-to-end through the C ABI: host gate list in, host results out
+    pairs = [(i, (i * 7 + 3) % N_QUBITS) for i in range(16)]
+    masks = [(1 << a) | (1 << b) for a, b in pairs]
+    torch.cuda.synchronize()
+    te = []
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        sim.reset(0)
+        sim.apply(circ.gates, opt)      # marshal from the Python gate list each step
+        idx, p = sim.top_k(64)
+        ev = sim.expectation(masks)
+        te.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(te)
+    h2d = prof["h2d_bytes"] // max(1, args.steps)
+    d2h = 64 * 16 + 16 * 8
+
+    # the unfused gate-by-gate GPU path on the same circuit (one timed run)
+    unf = S.default_options(flags=0)
+    sim.reset(0)
+    sim.apply(ga, unf)
+    torch.cuda.synchronize()
+    u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    u0.record(stream)
+    sim.reset(0)
+    sim.apply(ga, unf)
+    u1.record(stream)
+    torch.cuda.synchronize()
+    unf_ms = u0.elapsed_time(u1)
+
+    peak, peak_kind = _peaks()
+    ch = prof["chunk"]
+    launches = sum(v["launches"] for k, v in prof.items() if isinstance(v, dict))
+    # one of our kernels per recorded op (a reset's memset is the driver's, its k_set_one is ours)
+    gpu_launches = launches
+    achieved = ch["bytes"] / (ch["ms"] / 1e3) / 1e9 if ch["ms"] > 0 else None
+    src = open(os.path.join(ROOT, "paper_2604_12256_gb300", "csrc", "k_chunk.cu"), "rb").read()
+    traffic = TRAFFIC.get(hashlib.sha256(src).hexdigest())
+    total_bytes = sum(v["bytes"] for k, v in prof.items() if isinstance(v, dict)) / args.steps
+    value = world * G * amps / (ms / 1e3)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "gates": G, "seed": SEED,
+                       "parallelism": f"replicas x{world}", "l2": "state (2 GiB) larger than L2, no flush",
+                       "sweeps": plan["sweeps"], "chunk_ops": plan["chunk_ops"], "diag_fused": plan["diag_fused"],
+                       "plan_ms": plan["plan_ms"]},
+            "hbm_gbs": total_bytes / (ms / 1e3) / 1e9,
+            "hbm_frac_of_" + peak_kind: total_bytes / (ms / 1e3) / 1e9 / peak,
+            "roofline": {"bound": "hbm", "kernel": "k_chunk (cache-blocked chunk sweep)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                         "launches": ch["launches"], "avg_launch_ms": ch["ms"] / max(1, ch["launches"]),
+                         "algorithmic_bytes_per_launch": ch["bytes"] / max(1, ch["launches"]),
+                         "peak_source": peak_kind},
+            "unfused": {"ms_per_step": unf_ms, "value": G * amps / (unf_ms / 1e3),
+                        "speedup_fused_vs_unfused": unf_ms / ms},
+            "e2e": {"value": world * G * amps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
+            "gpu_launches": int(gpu_launches),
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline:
+            v, cores, sample = cpu_oracle_sample(args.ref_budget)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        print(json.dumps(line), flush=True)
+    sim.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+        dist_.init_process_group("nccl")
+        dist = dist_
+    try:
+        run_gpu(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * svsim.h -- C ABI of the GB300 (sm_103a) full state-vector simulator.
+ *
+ * The library simulates a quantum circuit on a 2^n-amplitude complex state
+ * vector resident in GPU memory (Eq. 1 of the paper: |phi> = sum_i a_i |i>,
+ * qubit j = bit j of the index i).  A circuit is restructured on the host by
+ * the optimizer of Section 4.2 (Algorithm 4: diagonal detector, merge booster,
+ * gate-block search for cache blocking and fusion) and executed by the
+ * adaptive simulator of Section 4.3 (Algorithm 5) as a sequence of CUDA
+ * kernels: fused-diagonal phase sweeps, cache-blocked chunk sweeps, tensor
+ * products and read-out reductions.
+ *
+ * Conventions (apply to every function below):
+ *  - Every function returns a sim_status; nothing throws across the ABI.  On
+ *    failure the handle's message is available from sim_last_error() (or
+ *    sim_global_error() when no handle exists yet).
+ *  - Host arrays passed in are borrowed: read (or written) only during the
+ *    call.  Device memory belongs to the handle, except the buffer given to
+ *    sim_create_on(), which stays the caller's.
+ *  - Calls on one handle are ordered on the handle's CUDA stream; a handle is
+ *    not thread-safe, separate handles are independent.  Functions that
+ *    return host results synchronise the handle's stream before returning.
+ *  - Amplitudes are interleaved (re, im): float pairs for SIM_C64, double
+ *    pairs for SIM_C128.  Indices are 64-bit.
+ *  - n is limited to 1..34 for SIM_C64 and 1..33 for SIM_C128
+ *    (SIM_EUNSUPPORTED beyond); qubit indices of a gate must be < n and
+ *    distinct (SIM_EINVAL otherwise).
+ */
+#ifndef SVSIM_H
+#define SVSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sim_t sim_t;
+
+/* Amplitude type of a state vector.  The paper runs complex128 (Section 5.1). */
+typedef enum { SIM_C64 = 0, SIM_C128 = 1 } sim_dtype;
+
+typedef enum {
+    SIM_OK = 0,
+    SIM_EINVAL = 1,        /* bad argument or gate                         */
+    SIM_ENOMEM = 2,        /* device or host allocation failed / no room    */
+    SIM_ECUDA = 3,         /* a CUDA call failed (message has the CUDA text) */
+    SIM_ETIMEOUT = 4,      /* a bounded wait ran out                        */
+    SIM_EBUSY = 5,         /* resource in use                               */
+    SIM_EUNSUPPORTED = 6   /* size or feature outside what is built         */
+} sim_status;
+
+/* Gate kinds (Section 2.2 names the gates; matrices are the textbook ones:
+ * RX(t) = exp(-i t X/2), RY(t) = exp(-i t Y/2), RZ(t) = exp(-i t Z/2),
+ * P(t) = diag(1, e^{it}), CP(t) = diag(1,1,1,e^{it}), RZZ(t) = exp(-i t ZZ/2),
+ * CX with q[0] the control).  For a gate on q[0..k-1], bit i of the local
+ * matrix index belongs to qubit q[i] (Eqs. 2-3). */
+typedef enum {
+    G_H = 0, G_X, G_Y, G_Z, G_S, G_T, G_RX, G_RY, G_RZ, G_P,
+    G_CX, G_CZ, G_CP, G_RZZ, G_SWAP,
+    G_U1Q,       /* 2x2 matrix in .matrix                                   */
+    G_UNITARY,   /* 2^k x 2^k matrix in .matrix, k = nq (1..6)              */
+    G_DIAG       /* 2^k diagonal entries in .matrix, k = nq (1..6)          */
+} sim_gate_kind;
+
+/* One gate.  .matrix (U1Q, UNITARY: row-major; DIAG: the diagonal) holds
+ * interleaved (re, im) doubles and is borrowed for the call; it is ignored
+ * for named gates.  Angles are in radians in .param[0]. */
+typedef struct {
+    uint32_t kind;
+    uint32_t nq;          /* number of qubits (named gates: may be 0 = default) */
+    uint32_t q[6];
+    double param[3];
+    const double *matrix;
+} sim_gate;
+
+/* Optimizer switches (Algorithm 4 stages), combinable. */
+enum {
+    SIM_F_DIAG = 1u << 0,   /* diagonal detector (Algorithm 8)                */
+    SIM_F_BOOST = 1u << 1,  /* merge booster (Algorithms 6-7)                 */
+    SIM_F_BLOCK = 1u << 2,  /* cache blocking (gate-block search, Algorithm 2) */
+    SIM_F_FUSE = 1u << 3,   /* cost-based gate fusion inside blocks           */
+    SIM_F_TC = 1u << 4,     /* dense fused blocks on the tensor cores          */
+    SIM_F_ALL = 0x1f
+};
+
+/* Precision of dense fused blocks on the tensor-core path. */
+enum { SIM_DENSE_SPLIT_TF32 = 0, SIM_DENSE_FP32 = 1, SIM_DENSE_FP64 = 2 };
+
+/* The environment of Section 4.1 (N comes from the handle, R is 0: one GPU). */
+typedef struct {
+    int max_fuse_qubits;   /* F: largest fused dense block (default 3)            */
+    int max_diag_qubits;   /* D: largest fused diagonal, 0 = unbounded (default 0) */
+    int chunk_qubits;      /* C: qubits per cached chunk (0 = default: 12 c64, 11 c128) */
+    int booster_div;       /* B: Divider uses divSize = (n+B-1)/B; 0 = divSize C   */
+    uint32_t flags;        /* SIM_F_* (default SIM_F_DIAG|BOOST|BLOCK|FUSE)       */
+    int dense_precision;   /* SIM_DENSE_* for the tensor-core path                 */
+    int max_stages;        /* register stages per cached chunk (default 4)         */
+    int reserved[5];
+} sim_options;
+
+/* Counts of the last executed plan (Section 5's "state vector updates"). */
+typedef struct {
+    uint64_t gates_in;       /* gates in the circuit                              */
+    uint64_t ops;            /* kernel launches on the state                      */
+    uint64_t sweeps;         /* full read+write passes over the 2^n state          */
+    uint64_t chunk_ops, diag_ops, gate_ops, dense_ops, tensor_ops, permute_ops;
+    uint64_t diag_fused;     /* gates absorbed by the diagonal detector           */
+    uint64_t boosted_gates;  /* gates run on merge-booster sub-states              */
+    uint64_t state_updates;  /* sum over ops of amplitudes touched (Section 3)     */
+    uint64_t bytes;          /* algorithmic HBM bytes of the plan                  */
+    double flops;            /* algorithmic floating-point operations              */
+    double plan_ms;          /* host optimizer time                                */
+} sim_plan_stats;
+
+/* ------------------------------------------------------------ lifecycle */
+
+/* Fill *opt with the defaults listed in sim_options. */
+int sim_default_options(sim_options *opt);
+
+/* Allocate a 2^n state of the given dtype on the current CUDA device, set it
+ * to |0...0> and create a private stream.  SIM_ENOMEM if 2^n * bytes/amp
+ * exceeds free device memory. */
+int sim_create(int n_qubits, sim_dtype dtype, sim_t **out);
+
+/* Like sim_create, but on a caller-owned device buffer of >= 2^n amplitudes
+ * (bytes is its size) and a caller-owned stream (cudaStream_t, may be NULL
+ * for the legacy default stream).  The buffer is set to |0...0>. */
+int sim_create_on(int n_qubits, sim_dtype dtype, void *dev_buf, size_t bytes,
+                  void *cuda_stream, sim_t **out);
+
+int sim_destroy(sim_t *s);
+
+/* Set the state to the computational basis state |basis_index>.  The merge
+ * booster (Section 4.4) needs a product state and is only used while the
+ * state is known to be one (after create / reset). */
+int sim_reset(sim_t *s, uint64_t basis_index);
+
+/* Apply n gates (borrowed host array) with the given options (NULL =
+ * defaults).  Plans on the host (Algorithm 4) and enqueues the kernels
+ * (Algorithm 5) on the handle's stream; returns once enqueued. */
+int sim_apply_circuit(sim_t *s, const sim_gate *gates, size_t n,
+                      const sim_options *opt);
+
+/* Wait for all work enqueued on the handle. */
+int sim_sync(sim_t *s);
+
+/* ------------------------------------------------------------ read-out */
+
+/* p_x = |a_x|^2 for all 2^n x, as doubles, into a host array of 2^n. */
+int sim_probabilities(sim_t *s, double *out);
+
+/* The k (1..1024) largest probabilities, ties to the lower index, largest
+ * first: idx[k], prob[k] host arrays. */
+int sim_top_k(sim_t *s, int k, uint64_t *idx, double *prob);
+
+/* <Z-string m> = sum_x |a_x|^2 (-1)^popcount(x & m) for n_terms masks. */
+int sim_expectation(sim_t *s, const uint64_t *z_masks, size_t n_terms, double *out);
+
+/* Squared norm sum_x |a_x|^2, accumulated in FP64. */
+int sim_norm(sim_t *s, double *out);
+
+/* Copy the state out of / into host memory (bytes = 2^n * bytes/amp).
+ * sim_set_state ends the product-state knowledge (no booster after it). */
+int sim_get_state(sim_t *s, void *host, size_t bytes);
+int sim_set_state(sim_t *s, const void *host, size_t bytes);
+
+/* Device pointer of the state and its CUDA stream (for zero-copy use). */
+int sim_state_device(sim_t *s, void **dev_ptr, void **cuda_stream);
+
+int sim_last_plan_stats(const sim_t *s, sim_plan_stats *out);
+
+/* Per-kernel-kind device time, recorded with CUDA events around every launch
+ * on the handle's stream while enabled.  Index = kind: 0 basis init,
+ * 1 gate-by-gate dense gate, 2 gate-by-gate diagonal gate, 3 fused diagonal
+ * sweep, 4 cache-blocked chunk sweep, 5 tensor product, 6 dense block,
+ * 7 small-register phase.  `bytes` is the algorithmic HBM traffic of those
+ * launches (2 x 2^n x bytes/amp per read+write sweep). */
+typedef struct {
+    uint64_t launches[8];
+    double ms[8];
+    double bytes[8];
+    uint64_t h2d_bytes;      /* plan constants copied host -> device          */
+} sim_profile;
+
+/* on != 0: clear the counters and start recording; 0: stop. */
+int sim_profile_enable(sim_t *s, int on);
+/* Synchronise the handle's stream and return the accumulated counters. */
+int sim_profile_read(sim_t *s, sim_profile *out);
+const char *sim_last_error(const sim_t *s);
+const char *sim_global_error(void);
+
+/* ------------------------------------------------------------ planner only */
+
+/* Run the optimizer alone (no GPU needed) for an n-qubit circuit starting
+ * from the product state |basis_index> (pass UINT64_MAX for "unknown state":
+ * no booster) and write a JSON description of the plan into buf (at most
+ * buflen bytes including the terminating NUL).  *needed receives the full
+ * length + 1; returns SIM_ENOMEM (and fills nothing) when buflen is too small.
+ * Used to check the optimizer's algebra on the CPU. */
+int sim_plan_json(int n_qubits, sim_dtype dtype, uint64_t basis_index,
+                  const sim_gate *gates, size_t n, const sim_options *opt,
+                  char *buf, size_t buflen, size_t *needed);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SVSIM_H */

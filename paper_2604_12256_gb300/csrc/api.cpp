@@ -1,0 +1,541 @@
+// api.cpp -- the C ABI of include/svsim.h and the executor (the adaptive
+// simulation of Algorithm 5): runs a plan's ops as kernel launches on the
+// handle's stream.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "kernels.h"
+
+using namespace svs;
+
+struct sim_t {
+    int n = 0;
+    sim_dtype dt = SIM_C64;
+    void *state = nullptr;
+    bool own_state = false;
+    size_t state_bytes = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    bool product = true;        // state is the basis state `basis`
+    uint64_t basis = 0;
+    double *d_part = nullptr;   // reduction partials
+    double *d_out = nullptr;    // small device results
+    uint64_t *d_masks = nullptr;
+    void *d_topk = nullptr;
+    size_t topk_bytes = 0;
+    unsigned char *d_const = nullptr;   // plan constants
+    size_t const_bytes = 0;
+    unsigned char *h_pin = nullptr;     // pinned staging of plan constants
+    size_t pin_bytes = 0;
+    cudaEvent_t pin_ev = nullptr;
+    bool pin_pending = false;
+    std::vector<void *> sub;            // booster sub-state buffers
+    std::vector<size_t> sub_bytes;
+    std::string err;
+    sim_plan_stats stats{};
+    // profiling: event pairs around launches, resolved at sim_profile_read
+    bool prof_on = false;
+    sim_profile prof{};
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    struct Pend { int kind; size_t e0; double bytes; };
+    std::vector<Pend> prof_pend;
+};
+
+static cudaEvent_t prof_event(sim_t *s, size_t i)
+{
+    while (s->ev_pool.size() <= i) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        s->ev_pool.push_back(e);
+    }
+    return s->ev_pool[i];
+}
+
+// record the start of a launch of kind `kind`; returns the pair index
+static long prof_begin(sim_t *s)
+{
+    if (!s->prof_on) return -1;
+    size_t i = s->ev_used;
+    cudaEvent_t a = prof_event(s, i), b = prof_event(s, i + 1);
+    if (!a || !b) return -1;
+    s->ev_used += 2;
+    cudaEventRecord(a, s->stream);
+    return (long)i;
+}
+
+static void prof_end(sim_t *s, long i, int kind, double bytes)
+{
+    if (i < 0) return;
+    cudaEventRecord(s->ev_pool[i + 1], s->stream);
+    s->prof_pend.push_back({kind, (size_t)i, bytes});
+}
+
+static thread_local std::string g_err;
+
+static int fail(sim_t *s, int code, const std::string &msg)
+{
+    if (s) s->err = msg;
+    g_err = msg;
+    return code;
+}
+
+static int cuda_fail(sim_t *s, cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    if (e == cudaErrorMemoryAllocation) return fail(s, SIM_ENOMEM, m);
+    return fail(s, SIM_ECUDA, m);
+}
+
+#define CK(s, call)                                     \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(s, e_, #call); \
+    } while (0)
+
+static size_t amp_bytes(sim_dtype dt) { return dt == SIM_C64 ? 8 : 16; }
+
+static int check_n(int n, sim_dtype dt)
+{
+    if (dt != SIM_C64 && dt != SIM_C128) return fail(nullptr, SIM_EINVAL, "dtype must be SIM_C64 or SIM_C128");
+    int mx = dt == SIM_C64 ? kMaxQubitsC64 : kMaxQubitsC128;
+    if (n < 1) return fail(nullptr, SIM_EINVAL, "n_qubits must be >= 1");
+    if (n > mx) return fail(nullptr, SIM_EUNSUPPORTED, "n_qubits above the supported maximum");
+    return SIM_OK;
+}
+
+static int alloc_aux(sim_t *s)
+{
+    int np = reduce_partials();
+    CK(s, cudaMalloc((void **)&s->d_part, sizeof(double) * np * 16));
+    CK(s, cudaMalloc((void **)&s->d_out, sizeof(double) * 64));
+    CK(s, cudaMalloc((void **)&s->d_masks, sizeof(uint64_t) * 64));
+    CK(s, cudaEventCreateWithFlags(&s->pin_ev, cudaEventDisableTiming));
+    return SIM_OK;
+}
+
+static void free_all(sim_t *s)
+{
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->own_state && s->state) cudaFree(s->state);
+    if (s->d_part) cudaFree(s->d_part);
+    if (s->d_out) cudaFree(s->d_out);
+    if (s->d_masks) cudaFree(s->d_masks);
+    if (s->d_topk) cudaFree(s->d_topk);
+    if (s->d_const) cudaFree(s->d_const);
+    if (s->h_pin) cudaFreeHost(s->h_pin);
+    if (s->pin_ev) cudaEventDestroy(s->pin_ev);
+    for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+    for (void *p : s->sub) if (p) cudaFree(p);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+extern "C" {
+
+int sim_default_options(sim_options *opt)
+{
+    if (!opt) return fail(nullptr, SIM_EINVAL, "null options");
+    fill_default_options(*opt);
+    return SIM_OK;
+}
+
+const char *sim_global_error(void) { return g_err.c_str(); }
+
+const char *sim_last_error(const sim_t *s) { return s ? s->err.c_str() : g_err.c_str(); }
+
+static int create_common(int n, sim_dtype dt, void *buf, size_t bytes, void *stream, bool own, sim_t **out)
+{
+    if (!out) return fail(nullptr, SIM_EINVAL, "null output handle");
+    *out = nullptr;
+    int rc = check_n(n, dt);
+    if (rc) return rc;
+    sim_t *s = new (std::nothrow) sim_t();
+    if (!s) return fail(nullptr, SIM_ENOMEM, "host allocation failed");
+    s->n = n;
+    s->dt = dt;
+    s->state_bytes = ((size_t)1 << n) * amp_bytes(dt);
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e != cudaSuccess) { cuda_fail(nullptr, e, "cudaGetDevice"); delete s; return SIM_ECUDA; }
+    if (own) {
+        size_t fr = 0, tot = 0;
+        e = cudaMemGetInfo(&fr, &tot);
+        if (e != cudaSuccess) { cuda_fail(nullptr, e, "cudaMemGetInfo"); delete s; return SIM_ECUDA; }
+        if (s->state_bytes + (64ull << 20) > fr) {
+            delete s;
+            return fail(nullptr, SIM_ENOMEM, "state vector does not fit in free device memory");
+        }
+        e = cudaMalloc(&s->state, s->state_bytes);
+        if (e != cudaSuccess) { delete s; return cuda_fail(nullptr, e, "cudaMalloc(state)"); }
+        s->own_state = true;
+        e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { free_all(s); return cuda_fail(nullptr, e, "cudaStreamCreate"); }
+        s->own_stream = true;
+    } else {
+        if (!buf) { delete s; return fail(nullptr, SIM_EINVAL, "null device buffer"); }
+        if (bytes < s->state_bytes) { delete s; return fail(nullptr, SIM_EINVAL, "device buffer too small"); }
+        if (((uintptr_t)buf & 255) != 0) { delete s; return fail(nullptr, SIM_EINVAL, "device buffer must be 256-byte aligned"); }
+        s->state = buf;
+        s->stream = (cudaStream_t)stream;
+    }
+    rc = alloc_aux(s);
+    if (rc) { std::string m = s->err; free_all(s); return fail(nullptr, rc, m); }
+    e = launch_init_basis(s->state, n, dt == SIM_C128, 0, s->stream);
+    if (e != cudaSuccess) { free_all(s); return cuda_fail(nullptr, e, "init"); }
+    *out = s;
+    return SIM_OK;
+}
+
+int sim_create(int n_qubits, sim_dtype dtype, sim_t **out)
+{
+    return create_common(n_qubits, dtype, nullptr, 0, nullptr, true, out);
+}
+
+int sim_create_on(int n_qubits, sim_dtype dtype, void *dev_buf, size_t bytes, void *cuda_stream, sim_t **out)
+{
+    return create_common(n_qubits, dtype, dev_buf, bytes, cuda_stream, false, out);
+}
+
+int sim_destroy(sim_t *s)
+{
+    if (!s) return fail(nullptr, SIM_EINVAL, "null handle");
+    free_all(s);
+    return SIM_OK;
+}
+
+int sim_reset(sim_t *s, uint64_t basis)
+{
+    if (!s) return fail(nullptr, SIM_EINVAL, "null handle");
+    if (s->n < 64 && (basis >> s->n) != 0) return fail(s, SIM_EINVAL, "basis index out of range");
+    long pe = prof_begin(s);
+    CK(s, launch_init_basis(s->state, s->n, s->dt == SIM_C128, basis, s->stream));
+    prof_end(s, pe, OPK_INIT_BASIS, (double)s->state_bytes);
+    s->product = true;
+    s->basis = basis;
+    return SIM_OK;
+}
+
+int sim_sync(sim_t *s)
+{
+    if (!s) return fail(nullptr, SIM_EINVAL, "null handle");
+    CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+int sim_state_device(sim_t *s, void **dev_ptr, void **stream)
+{
+    if (!s) return fail(nullptr, SIM_EINVAL, "null handle");
+    if (dev_ptr) *dev_ptr = s->state;
+    if (stream) *stream = (void *)s->stream;
+    return SIM_OK;
+}
+
+int sim_last_plan_stats(const sim_t *s, sim_plan_stats *out)
+{
+    if (!s || !out) return fail(nullptr, SIM_EINVAL, "null argument");
+    *out = s->stats;
+    return SIM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ executor
+static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+struct Blob {
+    std::vector<unsigned char> b;
+    size_t add(const void *p, size_t n)
+    {
+        size_t off = align16(b.size());
+        b.resize(off + n);
+        std::memcpy(b.data() + off, p, n);
+        return off;
+    }
+};
+
+static void add_complex(Blob &bl, const std::vector<cd> &v, bool f64, size_t &off)
+{
+    if (f64) {
+        std::vector<double> d(2 * v.size());
+        for (size_t i = 0; i < v.size(); i++) { d[2 * i] = v[i].real(); d[2 * i + 1] = v[i].imag(); }
+        off = bl.add(d.data(), d.size() * 8);
+    } else {
+        std::vector<float> d(2 * v.size());
+        for (size_t i = 0; i < v.size(); i++) { d[2 * i] = (float)v[i].real(); d[2 * i + 1] = (float)v[i].imag(); }
+        off = bl.add(d.data(), d.size() * 4);
+    }
+}
+
+static int ensure_sub(sim_t *s, int id, int nq)
+{
+    if ((int)s->sub.size() <= id) { s->sub.resize(id + 1, nullptr); s->sub_bytes.resize(id + 1, 0); }
+    size_t need = ((size_t)1 << nq) * amp_bytes(s->dt);
+    if (s->sub_bytes[id] < need) {
+        if (s->sub[id]) { CK(s, cudaStreamSynchronize(s->stream)); CK(s, cudaFree(s->sub[id])); s->sub[id] = nullptr; }
+        CK(s, cudaMalloc(&s->sub[id], need));
+        s->sub_bytes[id] = need;
+    }
+    return SIM_OK;
+}
+
+static void *buf_ptr(sim_t *s, int id) { return id == 0 ? s->state : s->sub[id]; }
+
+static int execute(sim_t *s, const Plan &p)
+{
+    const bool f64 = s->dt == SIM_C128;
+    // 1. plan constants: matrices, diagonal factors and device programs
+    Blob bl;
+    std::vector<size_t> off(p.ops.size(), 0);
+    std::vector<std::vector<int>> nzidx(p.ops.size());
+    for (size_t i = 0; i < p.ops.size(); i++) {
+        const Op &o = p.ops[i];
+        if (o.kind == OPK_GATE || o.kind == OPK_DENSE_TC) {
+            add_complex(bl, o.gate.M, f64, off[i]);
+        } else if (o.kind == OPK_GATE_DIAG) {
+            std::vector<cd> f;
+            for (int c = 0; c < (1 << o.gate.k); c++) {
+                uint64_t x = 0;
+                for (int j = 0; j < o.gate.k; j++) if ((c >> j) & 1) x |= 1ull << o.gate.q[j];
+                uint64_t w = 0;
+                for (const Term &t : o.gate.terms) if ((x & t.mask) == t.mask) w += t.w;
+                if (w != 0) { nzidx[i].push_back(c); f.push_back(phase_of(w)); }
+            }
+            if (!f.empty()) add_complex(bl, f, f64, off[i]);
+        } else if (o.kind == OPK_PHASE_SMALL) {
+            std::vector<uint64_t> tw;
+            for (const Term &t : o.terms) { tw.push_back(t.mask); tw.push_back(t.w); }
+            if (tw.empty()) tw.assign(2, 0);
+            off[i] = bl.add(tw.data(), tw.size() * 8);
+        } else if (o.kind == OPK_CHUNK || o.kind == OPK_DIAG) {
+            off[i] = bl.add(o.words.data(), o.words.size() * 4);
+        }
+    }
+    for (size_t b = 1; b < p.buf_qubits.size(); b++) {
+        int rc = ensure_sub(s, (int)b, p.buf_qubits[b]);
+        if (rc) return rc;
+    }
+    size_t need = std::max<size_t>(align16(bl.b.size()), 256);
+    if (s->pin_pending) { CK(s, cudaEventSynchronize(s->pin_ev)); s->pin_pending = false; }
+    if (s->pin_bytes < need) {
+        if (s->h_pin) CK(s, cudaFreeHost(s->h_pin));
+        s->h_pin = nullptr;
+        size_t nb = std::max(need, (size_t)1 << 20);
+        CK(s, cudaMallocHost((void **)&s->h_pin, nb));
+        s->pin_bytes = nb;
+    }
+    if (s->const_bytes < need) {
+        if (s->d_const) { CK(s, cudaStreamSynchronize(s->stream)); CK(s, cudaFree(s->d_const)); }
+        s->d_const = nullptr;
+        size_t nb = std::max(need, (size_t)1 << 20);
+        CK(s, cudaMalloc((void **)&s->d_const, nb));
+        s->const_bytes = nb;
+    }
+    if (!bl.b.empty()) {
+        std::memcpy(s->h_pin, bl.b.data(), bl.b.size());
+        CK(s, cudaMemcpyAsync(s->d_const, s->h_pin, bl.b.size(), cudaMemcpyHostToDevice, s->stream));
+        CK(s, cudaEventRecord(s->pin_ev, s->stream));
+        s->pin_pending = true;
+    }
+    // 2. launches (Algorithm 5)
+    for (size_t i = 0; i < p.ops.size(); i++) {
+        const Op &o = p.ops[i];
+        void *a = buf_ptr(s, o.buf);
+        const unsigned char *cst = s->d_const + off[i];
+        cudaError_t e = cudaSuccess;
+        long pe = prof_begin(s);
+        switch (o.kind) {
+        case OPK_INIT_BASIS: e = launch_init_basis(a, o.n, f64, o.basis, s->stream); break;
+        case OPK_GATE:
+        case OPK_DENSE_TC: e = launch_gate_dense(a, o.n, f64, o.gate.k, o.gate.q, cst, s->stream); break;
+        case OPK_GATE_DIAG:
+            e = launch_gate_diag(a, o.n, f64, o.gate.k, o.gate.q, (int)nzidx[i].size(), nzidx[i].data(), cst,
+                                 s->stream);
+            break;
+        case OPK_DIAG:
+            e = launch_diag_sweep(a, o.n, f64, (const uint32_t *)cst, s->stream);
+            break;
+        case OPK_PHASE_SMALL:
+            e = launch_phase_small(a, o.n, f64, (const uint64_t *)cst, (int)o.terms.size(), s->stream);
+            break;
+        case OPK_CHUNK:
+            e = launch_chunk(a, o.n, f64, o.prog.C, (const uint32_t *)cst, s->stream);
+            break;
+        case OPK_TENSOR:
+            e = launch_tensor(a, buf_ptr(s, o.buf_hi), o.n_hi, buf_ptr(s, o.buf_lo), o.n_lo, f64, s->stream);
+            break;
+        }
+        if (e != cudaSuccess) return cuda_fail(s, e, "kernel launch");
+        double amps = (double)((uint64_t)1 << o.n), sz = f64 ? 16.0 : 8.0;
+        double by = o.kind == OPK_TENSOR ? amps * sz : 2.0 * amps * sz;
+        prof_end(s, pe, (int)o.kind, by);
+    }
+    if (s->prof_on) s->prof.h2d_bytes += bl.b.size();
+    return SIM_OK;
+}
+
+extern "C" {
+
+int sim_apply_circuit(sim_t *s, const sim_gate *gates, size_t n, const sim_options *opt)
+{
+    if (!s) return fail(nullptr, SIM_EINVAL, "null handle");
+    if (n > 0 && !gates) return fail(s, SIM_EINVAL, "null gate array");
+    sim_options o;
+    if (opt) o = *opt;
+    else fill_default_options(o);
+    Plan p;
+    std::string err;
+    uint64_t basis = s->product ? s->basis : UINT64_MAX;
+    try {
+        if (!make_plan(s->n, s->dt, basis, gates, n, o, p, err)) return fail(s, SIM_EINVAL, err);
+    } catch (const std::bad_alloc &) {
+        return fail(s, SIM_ENOMEM, "host allocation failed while planning");
+    }
+    int rc = execute(s, p);
+    if (rc) return rc;
+    s->stats = p.stats;
+    if (n > 0) s->product = false;
+    return SIM_OK;
+}
+
+int sim_norm(sim_t *s, double *out)
+{
+    if (!s || !out) return fail(s, SIM_EINVAL, "null argument");
+    CK(s, launch_norm(s->state, s->n, s->dt == SIM_C128, s->d_part, s->d_out, s->stream));
+    CK(s, cudaMemcpyAsync(out, s->d_out, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+int sim_expectation(sim_t *s, const uint64_t *masks, size_t nt, double *out)
+{
+    if (!s || (nt && (!masks || !out))) return fail(s, SIM_EINVAL, "null argument");
+    for (size_t i = 0; i < nt; i++)
+        if (s->n < 64 && (masks[i] >> s->n)) return fail(s, SIM_EINVAL, "Z mask has bits above n");
+    for (size_t b = 0; b < nt; b += 16) {
+        int cnt = (int)std::min<size_t>(16, nt - b);
+        CK(s, cudaMemcpyAsync(s->d_masks, masks + b, sizeof(uint64_t) * cnt, cudaMemcpyHostToDevice, s->stream));
+        CK(s, launch_expect_z(s->state, s->n, s->dt == SIM_C128, s->d_masks, cnt, s->d_part, s->d_out, s->stream));
+        CK(s, cudaMemcpyAsync(out + b, s->d_out, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s->stream));
+        CK(s, cudaStreamSynchronize(s->stream));
+    }
+    return SIM_OK;
+}
+
+int sim_probabilities(sim_t *s, double *out)
+{
+    if (!s || !out) return fail(s, SIM_EINVAL, "null argument");
+    size_t N = (size_t)1 << s->n;
+    double *d = nullptr;
+    CK(s, cudaMallocAsync((void **)&d, N * sizeof(double), s->stream));
+    cudaError_t e = launch_probs(s->state, s->n, s->dt == SIM_C128, d, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, N * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    cudaFreeAsync(d, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "probabilities");
+    CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+int sim_top_k(sim_t *s, int k, uint64_t *idx, double *prob)
+{
+    if (!s || !idx || !prob) return fail(s, SIM_EINVAL, "null argument");
+    if (k < 1 || k > 1024) return fail(s, SIM_EINVAL, "k must be in 1..1024");
+    int kk = (int)std::min<uint64_t>((uint64_t)k, (uint64_t)1 << s->n);
+    size_t need = topk_scratch_bytes(1024) + 2 * 1024 * 8;
+    if (s->topk_bytes < need) {
+        if (s->d_topk) { CK(s, cudaStreamSynchronize(s->stream)); CK(s, cudaFree(s->d_topk)); }
+        s->d_topk = nullptr;
+        CK(s, cudaMalloc(&s->d_topk, need));
+        s->topk_bytes = need;
+    }
+    unsigned char *base = (unsigned char *)s->d_topk;
+    uint64_t *di = (uint64_t *)(base + topk_scratch_bytes(1024));
+    double *dp = (double *)(di + 1024);
+    CK(s, launch_topk(s->state, s->n, s->dt == SIM_C128, kk, base, di, dp, s->stream));
+    CK(s, cudaMemcpyAsync(idx, di, sizeof(uint64_t) * kk, cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaMemcpyAsync(prob, dp, sizeof(double) * kk, cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    for (int i = kk; i < k; i++) { idx[i] = UINT64_MAX; prob[i] = -1.0; }
+    return SIM_OK;
+}
+
+int sim_get_state(sim_t *s, void *host, size_t bytes)
+{
+    if (!s || !host) return fail(s, SIM_EINVAL, "null argument");
+    if (bytes != s->state_bytes) return fail(s, SIM_EINVAL, "byte count must equal 2^n * bytes per amplitude");
+    CK(s, cudaMemcpyAsync(host, s->state, bytes, cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+int sim_set_state(sim_t *s, const void *host, size_t bytes)
+{
+    if (!s || !host) return fail(s, SIM_EINVAL, "null argument");
+    if (bytes != s->state_bytes) return fail(s, SIM_EINVAL, "byte count must equal 2^n * bytes per amplitude");
+    CK(s, cudaMemcpyAsync(s->state, host, bytes, cudaMemcpyHostToDevice, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    s->product = false;
+    return SIM_OK;
+}
+
+int sim_profile_enable(sim_t *s, int on)
+{
+    if (!s) return fail(nullptr, SIM_EINVAL, "null handle");
+    CK(s, cudaStreamSynchronize(s->stream));
+    s->prof_pend.clear();
+    s->ev_used = 0;
+    if (on) s->prof = sim_profile{};
+    s->prof_on = on != 0;
+    return SIM_OK;
+}
+
+int sim_profile_read(sim_t *s, sim_profile *out)
+{
+    if (!s || !out) return fail(s, SIM_EINVAL, "null argument");
+    CK(s, cudaStreamSynchronize(s->stream));
+    for (const sim_t::Pend &p : s->prof_pend) {
+        float ms = 0;
+        CK(s, cudaEventElapsedTime(&ms, s->ev_pool[p.e0], s->ev_pool[p.e0 + 1]));
+        s->prof.launches[p.kind & 7]++;
+        s->prof.ms[p.kind & 7] += ms;
+        s->prof.bytes[p.kind & 7] += p.bytes;
+    }
+    s->prof_pend.clear();
+    s->ev_used = 0;
+    *out = s->prof;
+    return SIM_OK;
+}
+
+int sim_plan_json(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_t ng, const sim_options *opt,
+                  char *buf, size_t buflen, size_t *needed)
+{
+    int rc = check_n(n, dt);
+    if (rc) return rc;
+    if (ng > 0 && !gates) return fail(nullptr, SIM_EINVAL, "null gate array");
+    sim_options o;
+    if (opt) o = *opt;
+    else fill_default_options(o);
+    Plan p;
+    std::string err;
+    try {
+        if (!make_plan(n, dt, basis, gates, ng, o, p, err)) return fail(nullptr, SIM_EINVAL, err);
+    } catch (const std::bad_alloc &) {
+        return fail(nullptr, SIM_ENOMEM, "host allocation failed while planning");
+    }
+    std::string js = plan_json(p);
+    if (needed) *needed = js.size() + 1;
+    if (!buf || buflen < js.size() + 1) return fail(nullptr, SIM_ENOMEM, "buffer too small for the plan");
+    std::memcpy(buf, js.c_str(), js.size() + 1);
+    return SIM_OK;
+}
+
+}  // extern "C"

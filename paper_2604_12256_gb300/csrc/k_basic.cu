@@ -1,0 +1,473 @@
+// k_basic.cu -- whole-vector kernels: basis-state initialisation, the
+// gate-by-gate sweeps of Algorithm 1 (one dense gate, or one diagonal gate
+// touching only the amplitudes it changes), the tensor-product merge of the
+// merge booster (Algorithm 7 / Algorithm 5 first branch) and the read-out
+// reductions (norm, <Z-string>, probabilities, top-k) in FP64 accumulation
+// with a fixed reduction order.
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace svs {
+
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+static int g_sms = 0;
+int device_sm_count()
+{
+    if (g_sms <= 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            g_sms = v;
+        else
+            g_sms = kNumSMs;
+    }
+    return g_sms;
+}
+
+static inline int grid_for(int64_t work, int threads, int per_sm)
+{
+    int64_t g = (work + threads - 1) / threads;
+    int64_t cap = (int64_t)device_sm_count() * per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// ------------------------------------------------------------ basis state
+template <typename T2>
+__global__ void k_set_one(T2 *a, uint64_t idx)
+{
+    T2 one;
+    one.x = 1;
+    one.y = 0;
+    a[idx] = one;
+}
+
+cudaError_t launch_init_basis(void *a, int n, bool f64, uint64_t basis, cudaStream_t st)
+{
+    size_t bytes = ((size_t)1 << n) * (f64 ? 16 : 8);
+    cudaError_t e = cudaMemsetAsync(a, 0, bytes, st);
+    if (e != cudaSuccess) return e;
+    if (f64) k_set_one<double2><<<1, 1, 0, st>>>((double2 *)a, basis);
+    else k_set_one<float2><<<1, 1, 0, st>>>((float2 *)a, basis);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ dense gate
+struct DenseArgs {
+    int sq[6];          // the gate's qubits, ascending (zero-insertion order)
+    uint64_t off[64];   // global offset of local index c: sum_i c_i << q[i]
+};
+
+template <typename R, int K>
+__global__ void __launch_bounds__(256) k_gate_dense(typename Cx<R>::T *__restrict__ a, int n, DenseArgs g,
+                                                    const typename Cx<R>::T *__restrict__ M)
+{
+    using T2 = typename Cx<R>::T;
+    constexpr int D = 1 << K;
+    const int64_t nb = (int64_t)1 << (n - K);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += stride) {
+        uint64_t base = (uint64_t)b;
+#pragma unroll
+        for (int i = 0; i < K; i++) {
+            uint64_t low = base & ((1ull << g.sq[i]) - 1);
+            base = ((base >> g.sq[i]) << (g.sq[i] + 1)) | low;
+        }
+        T2 v[D];
+#pragma unroll
+        for (int c = 0; c < D; c++) v[c] = a[base | g.off[c]];
+#pragma unroll
+        for (int r = 0; r < D; r++) {
+            R re = 0, im = 0;
+#pragma unroll
+            for (int c = 0; c < D; c++) {
+                T2 m = __ldg(&M[r * D + c]);
+                re = fma(m.x, v[c].x, re);
+                re = fma(-m.y, v[c].y, re);
+                im = fma(m.x, v[c].y, im);
+                im = fma(m.y, v[c].x, im);
+            }
+            T2 w;
+            w.x = re;
+            w.y = im;
+            a[base | g.off[r]] = w;
+        }
+    }
+}
+
+template <typename R>
+static cudaError_t gate_dense_t(void *a, int n, int k, const int *q, const void *dmat, cudaStream_t st)
+{
+    using T2 = typename Cx<R>::T;
+    DenseArgs g;
+    int sq[6];
+    for (int i = 0; i < k; i++) sq[i] = q[i];
+    for (int i = 1; i < k; i++)
+        for (int j = i; j > 0 && sq[j - 1] > sq[j]; j--) { int t = sq[j]; sq[j] = sq[j - 1]; sq[j - 1] = t; }
+    for (int i = 0; i < 6; i++) g.sq[i] = i < k ? sq[i] : 0;
+    for (int c = 0; c < 64; c++) {
+        uint64_t o = 0;
+        if (c < (1 << k))
+            for (int i = 0; i < k; i++) if ((c >> i) & 1) o |= 1ull << q[i];
+        g.off[c] = o;
+    }
+    int64_t groups = (int64_t)1 << (n - k);
+    int grid = grid_for(groups, 256, 8);
+    T2 *A = (T2 *)a;
+    const T2 *M = (const T2 *)dmat;
+    switch (k) {
+    case 1: k_gate_dense<R, 1><<<grid, 256, 0, st>>>(A, n, g, M); break;
+    case 2: k_gate_dense<R, 2><<<grid, 256, 0, st>>>(A, n, g, M); break;
+    case 3: k_gate_dense<R, 3><<<grid, 256, 0, st>>>(A, n, g, M); break;
+    case 4: k_gate_dense<R, 4><<<grid, 256, 0, st>>>(A, n, g, M); break;
+    case 5: k_gate_dense<R, 5><<<grid, 256, 0, st>>>(A, n, g, M); break;
+    case 6: k_gate_dense<R, 6><<<grid, 256, 0, st>>>(A, n, g, M); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gate_dense(void *a, int n, bool f64, int k, const int *q, const void *dmat, cudaStream_t st)
+{
+    if (k < 1 || k > 6 || k > n) return cudaErrorInvalidValue;
+    return f64 ? gate_dense_t<double>(a, n, k, q, dmat, st) : gate_dense_t<float>(a, n, k, q, dmat, st);
+}
+
+// ------------------------------------------------------------ diagonal gate
+struct DiagArgs {
+    int k, nz;
+    int sq[6];
+    uint64_t off[64];   // global offsets of the nz local indices to touch
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_gate_diag(typename Cx<R>::T *__restrict__ a, int n, DiagArgs g,
+                                                   const typename Cx<R>::T *__restrict__ d)
+{
+    using T2 = typename Cx<R>::T;
+    const int64_t nb = (int64_t)1 << (n - g.k);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += stride) {
+        uint64_t base = (uint64_t)b;
+        for (int i = 0; i < g.k; i++) {
+            uint64_t low = base & ((1ull << g.sq[i]) - 1);
+            base = ((base >> g.sq[i]) << (g.sq[i] + 1)) | low;
+        }
+        for (int c = 0; c < g.nz; c++) {
+            T2 f = __ldg(&d[c]);
+            T2 v = a[base | g.off[c]];
+            T2 w;
+            w.x = v.x * f.x - v.y * f.y;
+            w.y = v.x * f.y + v.y * f.x;
+            a[base | g.off[c]] = w;
+        }
+    }
+}
+
+cudaError_t launch_gate_diag(void *a, int n, bool f64, int k, const int *q, int nz, const int *cidx,
+                             const void *dvals, cudaStream_t st)
+{
+    if (k < 1 || k > 6 || k > n || nz < 0 || nz > 64) return cudaErrorInvalidValue;
+    if (nz == 0) return cudaSuccess;
+    DiagArgs g;
+    g.k = k;
+    g.nz = nz;
+    int sq[6];
+    for (int i = 0; i < k; i++) sq[i] = q[i];
+    for (int i = 1; i < k; i++)
+        for (int j = i; j > 0 && sq[j - 1] > sq[j]; j--) { int t = sq[j]; sq[j] = sq[j - 1]; sq[j - 1] = t; }
+    for (int i = 0; i < 6; i++) g.sq[i] = i < k ? sq[i] : 0;
+    for (int c = 0; c < 64; c++) {
+        uint64_t o = 0;
+        if (c < nz)
+            for (int i = 0; i < k; i++) if ((cidx[c] >> i) & 1) o |= 1ull << q[i];
+        g.off[c] = o;
+    }
+    int64_t groups = (int64_t)1 << (n - k);
+    int grid = grid_for(groups, 256, 8);
+    if (f64) k_gate_diag<double><<<grid, 256, 0, st>>>((double2 *)a, n, g, (const double2 *)dvals);
+    else k_gate_diag<float><<<grid, 256, 0, st>>>((float2 *)a, n, g, (const float2 *)dvals);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ small phase sweep
+template <typename R>
+__global__ void __launch_bounds__(256) k_phase_small(typename Cx<R>::T *__restrict__ a, int64_t N,
+                                                     const uint64_t *__restrict__ terms, int nt)
+{
+    using T2 = typename Cx<R>::T;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += stride) {
+        uint64_t w = 0;
+        for (int t = 0; t < nt; t++) {
+            uint64_t m = __ldg(&terms[2 * t]);
+            if (((uint64_t)x & m) == m) w += __ldg(&terms[2 * t + 1]);
+        }
+        double s, c;
+        sincospi((double)(int64_t)w * 1.0842021724855044340e-19, &s, &c);
+        T2 v = a[x], r;
+        r.x = (R)(v.x * c - v.y * s);
+        r.y = (R)(v.x * s + v.y * c);
+        a[x] = r;
+    }
+}
+
+cudaError_t launch_phase_small(void *a, int n, bool f64, const uint64_t *terms, int nt, cudaStream_t st)
+{
+    int64_t N = (int64_t)1 << n;
+    int grid = grid_for(N, 256, 8);
+    if (f64) k_phase_small<double><<<grid, 256, 0, st>>>((double2 *)a, N, terms, nt);
+    else k_phase_small<float><<<grid, 256, 0, st>>>((float2 *)a, N, terms, nt);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ tensor product
+template <typename R>
+__global__ void __launch_bounds__(256) k_tensor(typename Cx<R>::T *__restrict__ out,
+                                                const typename Cx<R>::T *__restrict__ hi,
+                                                const typename Cx<R>::T *__restrict__ lo, int n_lo,
+                                                int64_t total)
+{
+    using T2 = typename Cx<R>::T;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t lmask = (1ull << n_lo) - 1;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += stride) {
+        T2 h = __ldg(&hi[(uint64_t)x >> n_lo]);
+        T2 l = __ldg(&lo[(uint64_t)x & lmask]);
+        T2 w;
+        w.x = h.x * l.x - h.y * l.y;
+        w.y = h.x * l.y + h.y * l.x;
+        out[x] = w;
+    }
+}
+
+cudaError_t launch_tensor(void *out, const void *hi, int n_hi, const void *lo, int n_lo, bool f64, cudaStream_t st)
+{
+    int64_t total = (int64_t)1 << (n_hi + n_lo);
+    int grid = grid_for(total, 256, 8);
+    if (f64) k_tensor<double><<<grid, 256, 0, st>>>((double2 *)out, (const double2 *)hi, (const double2 *)lo, n_lo, total);
+    else k_tensor<float><<<grid, 256, 0, st>>>((float2 *)out, (const float2 *)hi, (const float2 *)lo, n_lo, total);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ reductions
+// A fixed grid (kRedBlocks x kRedThreads) makes every sum's order independent
+// of the device, so results are bit-reproducible run to run.
+constexpr int kRedBlocks = 1024;
+constexpr int kRedThreads = 256;
+int reduce_partials() { return kRedBlocks; }
+
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) s += sh[i];
+    return s;   // valid in thread 0
+}
+
+// |a|^2 of one amplitude: exact squares in FP64, one rounding in the sum.
+__device__ __forceinline__ double prob_of(float2 v) { return fma((double)v.x, (double)v.x, (double)v.y * (double)v.y); }
+__device__ __forceinline__ double prob_of(double2 v) { return fma(v.x, v.x, v.y * v.y); }
+__device__ __forceinline__ float probf(float2 v) { return fmaf(v.x, v.x, v.y * v.y); }
+
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_norm_part(const typename Cx<R>::T *__restrict__ a, int64_t N,
+                                                            double *part)
+{
+    __shared__ double sh[32];
+    double acc = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        if constexpr (sizeof(R) == 4) acc += (double)probf(a[i]);
+        else acc += prob_of(a[i]);
+    }
+    double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_sum_parts(const double *part, int np, int nt, double *out)
+{
+    // one block per term; fixed-order tree over np partials
+    __shared__ double sh[32];
+    const double *p = part + (size_t)blockIdx.x * np;
+    double acc = 0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) acc += p[i];
+    double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+    (void)nt;
+}
+
+cudaError_t launch_norm(const void *a, int n, bool f64, double *part, double *out, cudaStream_t st)
+{
+    int64_t N = (int64_t)1 << n;
+    if (f64) k_norm_part<double><<<kRedBlocks, kRedThreads, 0, st>>>((const double2 *)a, N, part);
+    else k_norm_part<float><<<kRedBlocks, kRedThreads, 0, st>>>((const float2 *)a, N, part);
+    k_sum_parts<<<1, 256, 0, st>>>(part, kRedBlocks, 1, out);
+    return cudaGetLastError();
+}
+
+template <typename R, int NT>
+__global__ void __launch_bounds__(kRedThreads) k_expect_part(const typename Cx<R>::T *__restrict__ a, int64_t N,
+                                                              const uint64_t *__restrict__ masks, int nt,
+                                                              double *part)
+{
+    __shared__ double sh[32];
+    __shared__ uint64_t m[NT];
+    if (threadIdx.x < NT) m[threadIdx.x] = threadIdx.x < nt ? masks[threadIdx.x] : 0;
+    __syncthreads();
+    double acc[NT];
+#pragma unroll
+    for (int t = 0; t < NT; t++) acc[t] = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        double p;
+        if constexpr (sizeof(R) == 4) p = (double)probf(a[i]);
+        else p = prob_of(a[i]);
+#pragma unroll
+        for (int t = 0; t < NT; t++) acc[t] += (__popcll((uint64_t)i & m[t]) & 1) ? -p : p;
+    }
+#pragma unroll
+    for (int t = 0; t < NT; t++) {
+        if (t >= nt) break;
+        double s = block_sum(acc[t], sh);
+        if (threadIdx.x == 0) part[(size_t)t * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+cudaError_t launch_expect_z(const void *a, int n, bool f64, const uint64_t *masks, int nt, double *part,
+                            double *out, cudaStream_t st)
+{
+    if (nt < 1 || nt > 16) return cudaErrorInvalidValue;
+    int64_t N = (int64_t)1 << n;
+    if (f64) k_expect_part<double, 16><<<kRedBlocks, kRedThreads, 0, st>>>((const double2 *)a, N, masks, nt, part);
+    else k_expect_part<float, 16><<<kRedBlocks, kRedThreads, 0, st>>>((const float2 *)a, N, masks, nt, part);
+    k_sum_parts<<<nt, 256, 0, st>>>(part, kRedBlocks, nt, out);
+    return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_probs(const typename Cx<R>::T *__restrict__ a, int64_t N, double *out)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) out[i] = prob_of(a[i]);
+}
+
+cudaError_t launch_probs(const void *a, int n, bool f64, double *out, cudaStream_t st)
+{
+    int64_t N = (int64_t)1 << n;
+    int grid = grid_for(N, 256, 8);
+    if (f64) k_probs<double><<<grid, 256, 0, st>>>((const double2 *)a, N, out);
+    else k_probs<float><<<grid, 256, 0, st>>>((const float2 *)a, N, out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ top-k
+// Each block keeps the best k (probability descending, index ascending) of
+// its slice in shared memory: candidates better than the current k-th best
+// are appended, and the buffer is bitonic-sorted and cut back to k whenever
+// it holds more than k.  A second single-block pass merges the block lists.
+// The order (p desc, index asc) is total, so the result is unique.
+struct KI {
+    double p;
+    uint64_t i;
+};
+constexpr int kTopThreads = 256;
+constexpr int kTopTile = kTopThreads * 4;
+constexpr int kTopCap = 2048;   // >= 1024 kept + one tile
+static int topk_blocks(int64_t N)
+{
+    int64_t g = (N + kTopTile - 1) / kTopTile;
+    int64_t cap = 2 * (int64_t)device_sm_count();
+    return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
+}
+size_t topk_scratch_bytes(int k) { return (size_t)2 * kNumSMs * 2 * (size_t)k * sizeof(KI) + 4096; }
+
+__device__ __forceinline__ bool better(const KI &a, const KI &b) { return a.p > b.p || (a.p == b.p && a.i < b.i); }
+
+__device__ void bitonic_desc(KI *buf, int cap)
+{
+    for (int size = 2; size <= cap; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            __syncthreads();
+            for (int t = threadIdx.x; t < cap / 2; t += blockDim.x) {
+                int lo = 2 * t - (t & (stride - 1));
+                int hi = lo + stride;
+                bool desc = ((lo & size) == 0);
+                KI x = buf[lo], y = buf[hi];
+                bool sw = desc ? better(y, x) : better(x, y);
+                if (sw) { buf[lo] = y; buf[hi] = x; }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <typename R, bool FROM_STATE>
+__global__ void __launch_bounds__(kTopThreads) k_topk(const typename Cx<R>::T *__restrict__ a, const KI *__restrict__ cand,
+                                                      int64_t N, int k, KI *out)
+{
+    __shared__ KI buf[kTopCap];
+    __shared__ int cnt;
+    __shared__ KI thr;
+    const KI worst = {-1.0, ~0ull};
+    if (threadIdx.x == 0) { cnt = 0; thr = worst; }
+    __syncthreads();
+    int64_t per = (N + gridDim.x - 1) / gridDim.x;
+    int64_t lo = (int64_t)blockIdx.x * per, hi = lo + per < N ? lo + per : N;
+    for (int64_t t0 = lo; t0 < hi; t0 += kTopTile) {
+        KI th = thr;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            int64_t i = t0 + e * kTopThreads + threadIdx.x;
+            if (i < hi) {
+                KI v;
+                if constexpr (FROM_STATE) { v.p = prob_of(a[i]); v.i = (uint64_t)i; }
+                else v = cand[i];
+                if (better(v, th)) { int pos = atomicAdd(&cnt, 1); buf[pos] = v; }
+            }
+        }
+        __syncthreads();
+        if (cnt > k) {
+            for (int j = cnt + threadIdx.x; j < kTopCap; j += blockDim.x) buf[j] = worst;
+            bitonic_desc(buf, kTopCap);
+            if (threadIdx.x == 0) { cnt = k; thr = buf[k - 1]; }
+        }
+        __syncthreads();
+    }
+    // final: sort what is kept and write exactly k entries (padded with worst)
+    for (int j = cnt + threadIdx.x; j < kTopCap; j += blockDim.x) buf[j] = worst;
+    bitonic_desc(buf, kTopCap);
+    for (int j = threadIdx.x; j < k; j += blockDim.x) out[(size_t)blockIdx.x * k + j] = buf[j];
+}
+
+__global__ void k_topk_split(const KI *in, int k, uint64_t *idx, double *p)
+{
+    for (int j = threadIdx.x; j < k; j += blockDim.x) { idx[j] = in[j].i; p[j] = in[j].p; }
+}
+
+cudaError_t launch_topk(const void *a, int n, bool f64, int k, void *scratch, uint64_t *idx, double *p,
+                        cudaStream_t st)
+{
+    if (k < 1 || k > 1024) return cudaErrorInvalidValue;
+    int64_t N = (int64_t)1 << n;
+    int G = topk_blocks(N);
+    KI *lists = (KI *)scratch;
+    KI *final_ = lists + (size_t)G * k;
+    if (f64) k_topk<double, true><<<G, kTopThreads, 0, st>>>((const double2 *)a, nullptr, N, k, lists);
+    else k_topk<float, true><<<G, kTopThreads, 0, st>>>((const float2 *)a, nullptr, N, k, lists);
+    k_topk<float, false><<<1, kTopThreads, 0, st>>>(nullptr, lists, (int64_t)G * k, k, final_);
+    k_topk_split<<<1, 256, 0, st>>>(final_, k, idx, p);
+    return cudaGetLastError();
+}
+
+}  // namespace svs

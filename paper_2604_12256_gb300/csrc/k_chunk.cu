@@ -1,0 +1,411 @@
+// k_chunk.cu -- the cache-blocked chunk sweep (K4, the all-in-one branch of
+// Algorithm 5 / the block-by-block scheme of Algorithm 2) and the fused
+// diagonal phase sweep (K3, the diagonal branch of Algorithm 5).
+//
+// K4: each CTA takes chunks of 2^C amplitudes (C = 12 complex64, 11
+// complex128): the low chunk bits are contiguous qubits (coalesced 128-bit
+// loads), the others strided high qubits (direct indexing, no permutation
+// pass).  The chunk is staged through shared memory (planar re/im planes,
+// XOR-swizzled) and processed in register stages: in each stage every thread
+// holds 2^RB amplitudes whose index bits are the stage's register bits; gates
+// on those bits are register arithmetic, diagonal phases may use any bit.
+// One HBM read and one write per chunk, whatever the number of gates.
+//
+// Phases: a diagonal segment is a phase polynomial in fixed-point turns.
+// Per thread it reduces to base + sum_j m_j lin_j + tab[m] (+ rare terms with
+// several register bits) over the register index m, evaluated with integer
+// adds; one sin/cos per amplitude turns it into a complex factor.
+#include <cstdint>
+
+#include "kernels.h"
+#include "program.h"
+
+namespace svs {
+
+using namespace prog;
+
+template <typename R> struct CT;
+template <> struct CT<float> {
+    using T2 = float2;
+    using W = uint32_t;
+    static constexpr int SWZ = 5;
+};
+template <> struct CT<double> {
+    using T2 = double2;
+    using W = uint64_t;
+    static constexpr int SWZ = 4;
+};
+
+__device__ __forceinline__ uint32_t ldw(const uint32_t *p) { return __ldg(p); }
+__device__ __forceinline__ uint64_t ld64(const uint32_t *p) { return (uint64_t)__ldg(p) | ((uint64_t)__ldg(p + 1) << 32); }
+
+template <typename R> __device__ __forceinline__ typename CT<R>::W ldwt(const uint32_t *p);
+template <> __device__ __forceinline__ uint32_t ldwt<float>(const uint32_t *p) { return __ldg(p); }
+template <> __device__ __forceinline__ uint64_t ldwt<double>(const uint32_t *p) { return ld64(p); }
+
+// complex matrix element i of a dense op body
+__device__ __forceinline__ float2 ldm(const float *b, int i) { return make_float2(__ldg(b + 2 * i), __ldg(b + 2 * i + 1)); }
+__device__ __forceinline__ double2 ldm(const double *b, int i) { return make_double2(__ldg(b + 2 * i), __ldg(b + 2 * i + 1)); }
+
+// exp(2 pi i w / 2^bits) for the weight type
+__device__ __forceinline__ float2 cis_turns(uint32_t w)
+{
+    float s, c;
+    __sincosf((float)(int32_t)w * 1.46291807926715968e-09f, &s, &c);   // 2 pi / 2^32
+    return make_float2(c, s);
+}
+__device__ __forceinline__ double2 cis_turns(uint64_t w)
+{
+    double s, c;
+    sincospi((double)(int64_t)w * 1.0842021724855044340e-19, &s, &c);   // 2^-63
+    return make_double2(c, s);
+}
+
+template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b)
+{
+    T2 r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+// shared-memory swizzle: phys(y) = y ^ fold_SWZ(y >> SWZ); linear over GF(2)
+template <int SWZ, int C> __device__ __forceinline__ uint32_t swz(uint32_t y)
+{
+    uint32_t r = y;
+#pragma unroll
+    for (int s = SWZ; s < C; s += SWZ) r ^= (y >> s) & ((1u << SWZ) - 1);
+    return r;
+}
+
+// ------------------------------------------------------------ dense ops
+template <typename R, int NR, int K, int P0, int P1>
+__device__ __forceinline__ void dense_apply(typename CT<R>::T2 (&v)[NR], const uint32_t *body)
+{
+    using T2 = typename CT<R>::T2;
+    constexpr int D = 1 << K;
+    constexpr int gm = (1 << P0) | (K > 1 ? (1 << P1) : 0);
+    const R *mb = (const R *)body;
+    T2 M[D * D];
+#pragma unroll
+    for (int i = 0; i < D * D; i++) M[i] = ldm(mb, i);
+#pragma unroll
+    for (int g = 0; g < NR; g++) {
+        if (g & gm) continue;
+        T2 in[D];
+#pragma unroll
+        for (int c = 0; c < D; c++) {
+            int off = ((c & 1) << P0) | (K > 1 ? (((c >> 1) & 1) << P1) : 0);
+            in[c] = v[g | off];
+        }
+#pragma unroll
+        for (int r = 0; r < D; r++) {
+            R re = 0, im = 0;
+#pragma unroll
+            for (int c = 0; c < D; c++) {
+                re = fma(M[r * D + c].x, in[c].x, re);
+                re = fma(-M[r * D + c].y, in[c].y, re);
+                im = fma(M[r * D + c].x, in[c].y, im);
+                im = fma(M[r * D + c].y, in[c].x, im);
+            }
+            int off = ((r & 1) << P0) | (K > 1 ? (((r >> 1) & 1) << P1) : 0);
+            v[g | off].x = re;
+            v[g | off].y = im;
+        }
+    }
+}
+
+// walk the (P0 < P1 < RB) combinations at compile time
+template <typename R, int NR, int RB, int K, int P0, int P1>
+struct DenseDispatch {
+    static __device__ __forceinline__ void run(int code, typename CT<R>::T2 (&v)[NR], const uint32_t *body)
+    {
+        constexpr int mycode = K == 1 ? P0 : (P0 | (P1 << 3));
+        if (code == mycode) {
+            dense_apply<R, NR, K, P0, P1>(v, body);
+            return;
+        }
+        if constexpr (K == 1) {
+            if constexpr (P0 + 1 < RB) DenseDispatch<R, NR, RB, K, P0 + 1, 0>::run(code, v, body);
+        } else {
+            if constexpr (P1 + 1 < RB) DenseDispatch<R, NR, RB, K, P0, P1 + 1>::run(code, v, body);
+            else if constexpr (P0 + 2 < RB) DenseDispatch<R, NR, RB, K, P0 + 1, P0 + 2>::run(code, v, body);
+        }
+    }
+};
+
+// ------------------------------------------------------------ phase segment
+template <typename R, int RB>
+__device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uint64_t x0, const uint32_t *body)
+{
+    using W = typename CT<R>::W;
+    constexpr int NR = 1 << RB;
+    const int nb = (int)ldw(body + D_NBASE);
+    const int nm = (int)ldw(body + D_NMULTI);
+    const uint32_t *t = body + D_TERMS;
+    W base = 0;
+    for (int i = 0; i < nb; i++, t += kTermWords) {
+        uint64_t m = ld64(t);
+        if ((x0 & m) == m) base += ldwt<R>(t + 2);
+    }
+    W lin[RB];
+#pragma unroll
+    for (int j = 0; j < RB; j++) {
+        lin[j] = 0;
+        const int cnt = (int)ldw(body + D_NLIN + j);
+        for (int i = 0; i < cnt; i++, t += kTermWords) {
+            uint64_t m = ld64(t);
+            if ((x0 & m) == m) lin[j] += ldwt<R>(t + 2);
+        }
+    }
+    const uint32_t *tab = t;
+    const uint32_t *mt = t + 2 * NR;
+#pragma unroll
+    for (int m = 0; m < NR; m++) {
+        W ph = base + ldwt<R>(tab + 2 * m);
+#pragma unroll
+        for (int j = 0; j < RB; j++)
+            if ((m >> j) & 1) ph += lin[j];
+        for (int i = 0; i < nm; i++) {
+            const uint32_t *q = mt + i * kMultiWords;
+            uint64_t mm = ld64(q);
+            uint32_t rm = ldw(q + 2);
+            if ((x0 & mm) == mm && ((uint32_t)m & rm) == rm) ph += ldwt<R>(q + 4);
+        }
+        v[m] = cmul(v[m], cis_turns(ph));
+    }
+}
+
+// ------------------------------------------------------------ K4 chunk sweep
+template <typename R, int C, int RB>
+__global__ void __launch_bounds__(1 << (C - RB)) k_chunk(typename CT<R>::T2 *__restrict__ a,
+                                                         const uint32_t *__restrict__ prog, int n)
+{
+    using T2 = typename CT<R>::T2;
+    constexpr int TB = C - RB;
+    constexpr int T = 1 << TB;
+    constexpr int NR = 1 << RB;
+    constexpr int SW = CT<R>::SWZ;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    R *sre = (R *)smraw;
+    R *sim = sre + (1 << C);
+    __shared__ uint64_t s_git[NR / 2];    // global offset of load iteration `it`
+    __shared__ uint32_t s_sit[NR / 2];    // swizzled smem position of `it` on the store
+
+    const int tid = threadIdx.x;
+    int qin[C];
+#pragma unroll
+    for (int i = 0; i < C; i++) qin[i] = (int)ldw(prog + H_QIN + i);
+    int sperm[C];
+#pragma unroll
+    for (int i = 0; i < C; i++) sperm[i] = (int)ldw(prog + H_SPERM + i);
+    const uint64_t freem = ld64(prog + H_FREE_LO);
+    const int nst = (int)ldw(prog + H_NSTAGE);
+
+    // element pair e = it * T + tid covers chunk indices y = 2e, 2e + 1:
+    // y bit 0 = pair member, bits 1..TB = tid, bits TB+1.. = it
+    uint64_t g_tid = 0;
+    uint32_t st_tid = 0;   // store: chunk position of output index 2*tid
+#pragma unroll
+    for (int i = 0; i < TB; i++)
+        if ((tid >> i) & 1) { g_tid |= 1ull << qin[i + 1]; st_tid |= 1u << sperm[i + 1]; }
+    const uint32_t st_one = 1u << sperm[0];
+    if (tid < NR / 2) {
+        uint64_t g = 0;
+        uint32_t sp = 0;
+        for (int b = 0; b < RB - 1; b++)
+            if ((tid >> b) & 1) { g |= 1ull << qin[TB + 1 + b]; sp |= 1u << sperm[TB + 1 + b]; }
+        s_git[tid] = g;
+        s_sit[tid] = swz<SW, C>(sp);
+    }
+    __syncthreads();
+    const uint32_t pst_tid = swz<SW, C>(st_tid);
+    const uint32_t pst_one = swz<SW, C>(st_one);
+    const uint32_t pld_tid = swz<SW, C>((uint32_t)tid << 1);
+
+    const int64_t nchunks = (int64_t)1 << (n - C);
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        // chunk base: spread the chunk number over the free (non-chunk) qubits
+        uint64_t base = 0;
+        {
+            uint64_t fm = freem, cv = (uint64_t)ch;
+            while (fm) {
+                uint64_t low = fm & (~fm + 1);
+                if (cv & 1) base |= low;
+                cv >>= 1;
+                fm ^= low;
+            }
+        }
+        // ---- load: HBM -> shared (coalesced pairs)
+#pragma unroll
+        for (int it = 0; it < NR / 2; it++) {
+            const uint64_t g = base | g_tid | s_git[it];
+            const uint32_t p = pld_tid ^ swz<SW, C>((uint32_t)it << (TB + 1));
+            T2 v0, v1;
+            if constexpr (sizeof(R) == 4) {
+                float4 q = __ldcs((const float4 *)(a + g));
+                v0 = make_float2(q.x, q.y);
+                v1 = make_float2(q.z, q.w);
+            } else {
+                v0 = __ldcs(a + g);
+                v1 = __ldcs(a + g + 1);
+            }
+            sre[p] = v0.x;
+            sim[p] = v0.y;
+            sre[p ^ 1] = v1.x;
+            sim[p ^ 1] = v1.y;
+        }
+        __syncthreads();
+        // ---- register stages
+        for (int s = 0; s < nst; s++) {
+            const uint32_t *sp = prog + ldw(prog + H_STAGE_OFF + s);
+            uint32_t pv[RB];
+#pragma unroll
+            for (int j = 0; j < RB; j++) pv[j] = swz<SW, C>(1u << ldw(sp + S_REG + j));
+            uint32_t ybase = 0;
+            uint64_t x0 = base;
+#pragma unroll
+            for (int i = 0; i < TB; i++) {
+                const int b = (int)ldw(sp + S_THR + i);
+                if ((tid >> i) & 1) {
+                    ybase |= 1u << b;
+                    x0 |= 1ull << qin[b];
+                }
+            }
+            const uint32_t pb = swz<SW, C>(ybase);
+            T2 v[NR];
+#pragma unroll
+            for (int m = 0; m < NR; m++) {
+                uint32_t pm = pb;
+#pragma unroll
+                for (int j = 0; j < RB; j++)
+                    if ((m >> j) & 1) pm ^= pv[j];
+                v[m].x = sre[pm];
+                v[m].y = sim[pm];
+            }
+            // x0 also needs the global positions of the register bits = 0 (already 0)
+            const int nops = (int)ldw(sp + S_NOPS);
+            const uint32_t *op = sp + S_SIZE;
+            for (int k = 0; k < nops; k++) {
+                const uint32_t hdr = ldw(op + O_HDR);
+                const int type = hdr & 0xff;
+                if (type == OP_DENSE) {
+                    const int kq = (hdr >> 8) & 0xff;
+                    const int code = (int)(hdr >> 16);
+                    if (kq == 1) DenseDispatch<R, NR, RB, 1, 0, 0>::run(code, v, op + O_BODY);
+                    else DenseDispatch<R, NR, RB, 2, 0, 1>::run(code, v, op + O_BODY);
+                } else {
+                    dseg_apply<R, RB>(v, x0, op + O_BODY);
+                }
+                op += ldw(op + O_WORDS);
+            }
+#pragma unroll
+            for (int m = 0; m < NR; m++) {
+                uint32_t pm = pb;
+#pragma unroll
+                for (int j = 0; j < RB; j++)
+                    if ((m >> j) & 1) pm ^= pv[j];
+                sre[pm] = v[m].x;
+                sim[pm] = v[m].y;
+            }
+            __syncthreads();
+        }
+        // ---- store: shared -> HBM, output bit i' takes chunk bit sperm[i']
+#pragma unroll
+        for (int it = 0; it < NR / 2; it++) {
+            const uint64_t g = base | g_tid | s_git[it];
+            const uint32_t p0 = pst_tid ^ s_sit[it];
+            const uint32_t p1 = p0 ^ pst_one;
+            if constexpr (sizeof(R) == 4) {
+                float4 q = make_float4(sre[p0], sim[p0], sre[p1], sim[p1]);
+                __stcs((float4 *)(a + g), q);
+            } else {
+                __stcs(a + g, make_double2(sre[p0], sim[p0]));
+                __stcs(a + g + 1, make_double2(sre[p1], sim[p1]));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ K3 diagonal sweep
+// tile of 2^C consecutive amplitudes, C = 7 + RB: thread t holds amplitudes
+// tile + t + m * 128 (register bits on top -> each warp load is contiguous)
+template <typename R, int RB>
+__global__ void __launch_bounds__(128) k_diag(typename CT<R>::T2 *__restrict__ a, const uint32_t *__restrict__ prog,
+                                              int n)
+{
+    using T2 = typename CT<R>::T2;
+    constexpr int NR = 1 << RB;
+    constexpr int C = 7 + RB;
+    const uint32_t *sp = prog + ldw(prog + H_STAGE_OFF);
+    const uint32_t *op = sp + S_SIZE + O_BODY;
+    const int64_t ntiles = (int64_t)1 << (n - C);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint64_t x0 = ((uint64_t)tile << C) | threadIdx.x;
+        T2 v[NR];
+#pragma unroll
+        for (int m = 0; m < NR; m++) v[m] = __ldcs(a + x0 + ((uint64_t)m << 7));
+        dseg_apply<R, RB>(v, x0, op);
+#pragma unroll
+        for (int m = 0; m < NR; m++) __stcs(a + x0 + ((uint64_t)m << 7), v[m]);
+    }
+}
+
+// ------------------------------------------------------------ launchers
+template <typename R, int C, int RB>
+static cudaError_t chunk_t(void *a, int n, const uint32_t *prog, cudaStream_t st)
+{
+    constexpr int T = 1 << (C - RB);
+    const size_t smem = (size_t)2 * sizeof(R) << C;
+    static int occ = 0;
+    if (occ <= 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_chunk<R, C, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_chunk<R, C, RB>, T, smem);
+        if (e != cudaSuccess) return e;
+        if (occ <= 0) occ = 1;
+    }
+    int64_t nch = (int64_t)1 << (n - C);
+    int64_t grid = (int64_t)device_sm_count() * occ;
+    if (grid > nch) grid = nch;
+    k_chunk<R, C, RB><<<(int)grid, T, smem, st>>>((typename CT<R>::T2 *)a, prog, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chunk(void *a, int n, bool f64, int C, const uint32_t *prog, cudaStream_t st)
+{
+    if (!f64) {
+        if (C == 12 && n >= 12) return chunk_t<float, 12, 5>(a, n, prog, st);
+        if (C == 10 && n >= 10) return chunk_t<float, 10, 5>(a, n, prog, st);
+    } else {
+        if (C == 11 && n >= 11) return chunk_t<double, 11, 4>(a, n, prog, st);
+        if (C == 9 && n >= 9) return chunk_t<double, 9, 4>(a, n, prog, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename R, int RB>
+static cudaError_t diag_t(void *a, int n, const uint32_t *prog, cudaStream_t st)
+{
+    constexpr int C = 7 + RB;
+    if (n < C) return cudaErrorInvalidValue;
+    static int occ = 0;
+    if (occ <= 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_diag<R, RB>, 128, 0);
+        if (e != cudaSuccess) return e;
+        if (occ <= 0) occ = 1;
+    }
+    int64_t nt = (int64_t)1 << (n - C);
+    int64_t grid = (int64_t)device_sm_count() * occ;
+    if (grid > nt) grid = nt;
+    k_diag<R, RB><<<(int)grid, 128, 0, st>>>((typename CT<R>::T2 *)a, prog, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag_sweep(void *a, int n, bool f64, const uint32_t *prog, cudaStream_t st)
+{
+    return f64 ? diag_t<double, 4>(a, n, prog, st) : diag_t<float, 5>(a, n, prog, st);
+}
+
+}  // namespace svs

@@ -1,0 +1,62 @@
+// kernels.h -- host-side launchers of the CUDA kernels (one translation unit
+// per kernel family).  All launchers enqueue on `st` and return the launch
+// status; none allocates memory.  `a` is the interleaved complex state of 2^n
+// amplitudes (float2 for is_f64 == false, double2 otherwise).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace svs {
+
+constexpr int kNumSMs = 152;   // sizing fallback when the device query fails
+
+// |basis> : zero the vector and set one amplitude to 1 (write-only sweep)
+cudaError_t launch_init_basis(void *a, int n, bool is_f64, uint64_t basis, cudaStream_t st);
+
+// One k-qubit dense gate over the whole vector (Algorithm 1).  q: the gate's
+// qubits (local bit i <-> q[i]); dmat: device matrix, 2^k x 2^k row-major
+// complex of the state's precision.
+cudaError_t launch_gate_dense(void *a, int n, bool is_f64, int k, const int *q,
+                              const void *dmat, cudaStream_t st);
+
+// One diagonal gate: multiply only the amplitudes whose local index c has
+// d[c] != 1.  nz: number of such c; cidx: their local indices (host array,
+// <= 64); dvals: device array of nz complex factors (state precision).
+cudaError_t launch_gate_diag(void *a, int n, bool is_f64, int k, const int *q, int nz,
+                             const int *cidx, const void *dvals, cudaStream_t st);
+
+// out[h * 2^n_lo + l] = hi[h] * lo[l]  (the merge of Algorithm 7 / K7)
+cudaError_t launch_tensor(void *out, const void *hi, int n_hi, const void *lo, int n_lo,
+                          bool is_f64, cudaStream_t st);
+
+// ---- read-out (FP64 accumulation, fixed reduction order) ----
+// Partials buffer `part` must hold reduce_partials() doubles per term.
+int reduce_partials();
+// sum_x |a_x|^2 -> *out_dev (device double)
+cudaError_t launch_norm(const void *a, int n, bool is_f64, double *part, double *out_dev,
+                        cudaStream_t st);
+// <Z_m> for nt <= 16 masks (device array) -> out_dev[nt]
+cudaError_t launch_expect_z(const void *a, int n, bool is_f64, const uint64_t *masks_dev, int nt,
+                            double *part, double *out_dev, cudaStream_t st);
+// p_x for all x -> out_dev[2^n]
+cudaError_t launch_probs(const void *a, int n, bool is_f64, double *out_dev, cudaStream_t st);
+// top-k (k <= 1024): scratch must hold topk_scratch_bytes(k); results to
+// idx_dev[k], p_dev[k] (largest first, ties to the lower index)
+size_t topk_scratch_bytes(int k);
+cudaError_t launch_topk(const void *a, int n, bool is_f64, int k, void *scratch,
+                        uint64_t *idx_dev, double *p_dev, cudaStream_t st);
+
+// ---- optimizer-driven sweeps ----
+// Fused diagonal phase sweep (K3) and cache-blocked chunk sweep (K4): `prog`
+// is a device program written by the encoder in program.h.
+cudaError_t launch_diag_sweep(void *a, int n, bool is_f64, const uint32_t *prog, cudaStream_t st);
+cudaError_t launch_chunk(void *a, int n, bool is_f64, int C, const uint32_t *prog, cudaStream_t st);
+
+// Phase polynomial on small registers: one thread per amplitude sums the
+// nt terms (device array of {mask, w} pairs, uint64 turns).
+cudaError_t launch_phase_small(void *a, int n, bool is_f64, const uint64_t *terms_dev, int nt, cudaStream_t st);
+
+int device_sm_count();
+
+}  // namespace svs

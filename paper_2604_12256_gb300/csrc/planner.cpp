@@ -1,0 +1,1093 @@
+// planner.cpp -- the host optimizer (swarm optimization, Algorithm 4):
+//
+//   1. ingest + validate the gate list (Section 4.1's `circuit`);
+//   2. diagonal detector (Algorithm 8) with the readings listed below;
+//   3. merge booster (Algorithms 6-7) for product initial states;
+//   4. gate-block search (GBSA mode 0, Algorithm 2's cache blocking) fused
+//      with register-stage scheduling, lazy placement of diagonal phases and
+//      cost-based gate fusion (GBSA mode 1);
+//   5. encoding of each block as a device program (program.h).
+//
+// Readings of Algorithm 8 (the pseudocode leaves these open):
+//   (i)   a lone diagonal gate (diagSize == 1) is emitted unchanged;
+//   (ii)  a non-diagonal gate goes to uList when it overlaps depSet OR a
+//         qubit already held by uList (else it would jump ahead of that gate);
+//   (iii) the D bound of Section 4.1 stops the fusion (a break) when the fused
+//         qubit set would exceed D (D = 0: unbounded, the phase-polynomial
+//         form needs no table);
+//   (iv)  a diagonal gate that meets a stopped qubit ends the group and starts
+//         the next one.
+// GBSA itself is unspecified (Section 4.2 builds on prior simulators); ours is
+// a greedy scan in dependency order, see schedule_blocked().
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <sstream>
+
+#include "internal.h"
+#include "program.h"
+
+namespace svs {
+
+static inline int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+void fill_default_options(sim_options &o)
+{
+    std::memset(&o, 0, sizeof(o));
+    o.max_fuse_qubits = 2;
+    o.max_diag_qubits = 0;
+    o.chunk_qubits = 0;
+    o.booster_div = 0;
+    o.flags = SIM_F_DIAG | SIM_F_BOOST | SIM_F_BLOCK | SIM_F_FUSE;
+    o.dense_precision = SIM_DENSE_SPLIT_TF32;
+    o.max_stages = 4;
+}
+
+// Instantiated chunk kernels: (C, RB) = (12,5) / (10,5) for complex64 and
+// (11,4) / (9,4) for complex128.
+static bool chunk_shape(int n, sim_dtype dt, int want_c, int &C, int &RB)
+{
+    if (dt == SIM_C64) {
+        RB = 5;
+        int cands[2] = {12, 10};
+        for (int c : cands)
+            if (c <= n && (want_c <= 0 || c <= want_c)) { C = c; return true; }
+    } else {
+        RB = 4;
+        int cands[2] = {11, 9};
+        for (int c : cands)
+            if (c <= n && (want_c <= 0 || c <= want_c)) { C = c; return true; }
+    }
+    return false;
+}
+
+void resolve_options(sim_options &o, int n, sim_dtype dt)
+{
+    if (o.max_fuse_qubits < 1) o.max_fuse_qubits = 1;
+    if (o.max_fuse_qubits > 3) o.max_fuse_qubits = 3;
+    if (o.max_stages < 1) o.max_stages = 1;
+    if (o.max_stages > prog::kMaxStages) o.max_stages = prog::kMaxStages;
+    if (o.max_diag_qubits < 0) o.max_diag_qubits = 0;
+    (void)n;
+    (void)dt;
+}
+
+// ------------------------------------------------------------ helpers
+static std::vector<cd> matmul(const std::vector<cd> &A, const std::vector<cd> &B, int dim)
+{
+    std::vector<cd> C((size_t)dim * dim, cd(0, 0));
+    for (int r = 0; r < dim; r++)
+        for (int k = 0; k < dim; k++) {
+            cd a = A[(size_t)r * dim + k];
+            if (a == cd(0, 0)) continue;
+            for (int c = 0; c < dim; c++) C[(size_t)r * dim + c] += a * B[(size_t)k * dim + c];
+        }
+    return C;
+}
+
+// Expand a matrix on positions `pos` (local bit i <-> pos[i]) to the
+// positions `upos` (a superset), identity on the extra ones.
+static std::vector<cd> expand(const std::vector<cd> &M, int k, const int *pos, int ku, const int *upos)
+{
+    int du = 1 << ku, d = 1 << k;
+    int where[kMaxGateQubits];
+    for (int i = 0; i < k; i++)
+        for (int j = 0; j < ku; j++) if (upos[j] == pos[i]) where[i] = j;
+    uint32_t inmask = 0;
+    for (int i = 0; i < k; i++) inmask |= 1u << where[i];
+    std::vector<cd> E((size_t)du * du, cd(0, 0));
+    for (int r = 0; r < du; r++)
+        for (int c = 0; c < du; c++) {
+            if ((r & ~inmask) != (c & ~inmask)) continue;
+            int lr = 0, lc = 0;
+            for (int i = 0; i < k; i++) {
+                lr |= ((r >> where[i]) & 1) << i;
+                lc |= ((c >> where[i]) & 1) << i;
+            }
+            E[(size_t)r * du + c] = M[(size_t)lr * d + lc];
+        }
+    return E;
+}
+
+// ------------------------------------------------------------ diagonal detector
+// Algorithm 8 with readings (i)-(iv) above.  Fused groups become one gate
+// whose phase polynomial is the sum of the members' polynomials.
+static std::vector<PGate> diagonal_detector(const std::vector<PGate> &G, int D, uint64_t &absorbed)
+{
+    std::vector<PGate> res;
+    res.reserve(G.size());
+    size_t i = 0;
+    absorbed = 0;
+    while (i < G.size()) {
+        if (!G[i].diag) { res.push_back(G[i]); i++; continue; }
+        std::vector<size_t> diagList{i}, uList;
+        uint64_t stop = 0, dep = G[i].qmask, fused = G[i].qmask;
+        size_t j = i + 1;
+        for (; j < G.size(); j++) {
+            const PGate &h = G[j];
+            if (!h.diag) {
+                if ((h.qmask & dep) || (h.qmask & stop)) { stop |= h.qmask; uList.push_back(j); }
+                else res.push_back(h);
+            } else {
+                if ((h.qmask & stop) || (D > 0 && popc(fused | h.qmask) > D)) break;
+                dep |= h.qmask;
+                fused |= h.qmask;
+                diagList.push_back(j);
+            }
+        }
+        if (diagList.size() == 1) {
+            res.push_back(G[i]);
+        } else {
+            PGate f;
+            f.kind = kFusedDiag;
+            f.diag = true;
+            f.qmask = fused;
+            f.k = popc(fused);
+            f.n_src = 0;
+            for (size_t d : diagList) {
+                f.terms.insert(f.terms.end(), G[d].terms.begin(), G[d].terms.end());
+                f.n_src += G[d].n_src;
+            }
+            normalize_terms(f.terms);
+            absorbed += diagList.size() - 1;
+            res.push_back(std::move(f));
+        }
+        for (size_t u : uList) res.push_back(G[u]);
+        i = j;
+    }
+    return res;
+}
+
+// ------------------------------------------------------------ merge booster
+// Divider of Algorithm 6: split N into halves (ceil on the second half)
+// until every part is <= divSize; parts are queued low qubits first.
+static void divider(int N, int divSize, std::vector<int> &que)
+{
+    if (N <= divSize) { que.push_back(N); return; }
+    divider(N >> 1, divSize, que);
+    int M = (N & 1) ? N + 1 : N;
+    divider(M >> 1, divSize, que);
+}
+
+// Gates of `pend` that lie inside [lo, lo+w) and are not preceded by a left-out
+// gate on one of their qubits (a dependency-closed prefix: reading of
+// genGateBlock).  Taken gates are removed from `pend`.
+static std::vector<PGate> take_group(std::vector<PGate> &pend, int lo, int w)
+{
+    uint64_t grp = (w >= 64 ? ~0ull : ((1ull << w) - 1)) << lo;
+    uint64_t blocked = 0;
+    std::vector<PGate> taken, keep;
+    for (PGate &g : pend) {
+        if ((g.qmask & ~grp) == 0 && (g.qmask & blocked) == 0) taken.push_back(std::move(g));
+        else { blocked |= g.qmask; keep.push_back(std::move(g)); }
+    }
+    pend.swap(keep);
+    return taken;
+}
+
+static PGate shift_gate(const PGate &g, int lo)
+{
+    PGate s = g;
+    s.qmask = g.qmask >> lo;
+    for (int i = 0; i < g.k && i < kMaxGateQubits; i++) s.q[i] = g.q[i] - lo;
+    for (Term &t : s.terms) t.mask >>= lo;
+    return s;
+}
+
+// ------------------------------------------------------------ encoding
+struct ProgWriter {
+    std::vector<uint32_t> w;
+    void put(uint32_t v) { w.push_back(v); }
+    void put64(uint64_t v) { w.push_back((uint32_t)v); w.push_back((uint32_t)(v >> 32)); }
+    void align2() { if (w.size() & 1) w.push_back(0); }
+};
+
+static inline uint64_t qweight(uint64_t w, bool f64)
+{
+    if (f64) return w;
+    return (uint64_t)(uint32_t)((w + (1ull << 31)) >> 32);
+}
+
+// A stage as scheduled: register positions and ops, in the physical frame
+// of the block's load.
+struct SOp {
+    int type = 0;              // 1 dense, 2 phase
+    int k = 0;
+    int pos[kMaxGateQubits] = {0};
+    uint64_t pmask = 0;
+    std::vector<cd> M;
+    std::vector<Term> terms;
+    int n_src = 0;
+};
+struct SStage {
+    uint64_t R = 0;            // physical positions used as register bits
+    std::vector<SOp> ops;
+};
+
+// Choose lane bits (first 5 thread bits) with distinct residues modulo the
+// swizzle width so that shared-memory accesses are bank-conflict free.
+static void stage_layout(int C, int RB, int swz, const std::vector<int> &need_reg, int *reg, int *thr)
+{
+    std::vector<char> used(C, 0);
+    int nr = 0;
+    for (int b : need_reg) { reg[nr++] = b; used[b] = 1; }
+    int T = C - RB;
+    std::vector<int> lanes;
+    int nl = std::min(5, T);
+    for (int r = 0; r < swz && (int)lanes.size() < nl; r++)
+        for (int b = 0; b < C; b++)
+            if (!used[b] && b % swz == r) { lanes.push_back(b); used[b] = 1; break; }
+    for (int b = 0; b < C && (int)lanes.size() < nl; b++)
+        if (!used[b]) { lanes.push_back(b); used[b] = 1; }
+    // pad registers with the highest free bits, keep low bits for warps
+    for (int b = C - 1; b >= 0 && nr < RB; b--)
+        if (!used[b]) { reg[nr++] = b; used[b] = 1; }
+    int nt = 0;
+    for (int b : lanes) thr[nt++] = b;
+    for (int b = 0; b < C; b++)
+        if (!used[b]) { thr[nt++] = b; used[b] = 1; }
+}
+
+static void encode_dseg(ProgWriter &pw, const std::vector<Term> &terms, int RB, const uint64_t *regphys,
+                        bool f64)
+{
+    uint64_t regall = 0;
+    for (int j = 0; j < RB; j++) regall |= regphys[j];
+    std::vector<Term> base;
+    std::vector<std::vector<Term>> lin(RB);
+    std::vector<std::pair<Term, uint32_t>> multi;
+    std::vector<uint64_t> tab(1u << RB, 0);
+    for (const Term &t : terms) {
+        uint32_t rm = 0;
+        for (int j = 0; j < RB; j++) if (t.mask & regphys[j]) rm |= 1u << j;
+        uint64_t nonreg = t.mask & ~regall;
+        if (rm == 0) base.push_back({nonreg, t.w});
+        else if (nonreg == 0) {
+            for (uint32_t m = 0; m < (1u << RB); m++) if ((m & rm) == rm) tab[m] += t.w;
+        } else if (popc(rm) == 1) lin[__builtin_ctz(rm)].push_back({nonreg, t.w});
+        else multi.push_back({{nonreg, t.w}, rm});
+    }
+    size_t start = pw.w.size();
+    pw.put(prog::OP_DSEG);
+    pw.put(0);   // words, patched below
+    pw.put((uint32_t)base.size());
+    pw.put((uint32_t)multi.size());
+    for (int j = 0; j < prog::kMaxRB; j++) pw.put(j < RB ? (uint32_t)lin[j].size() : 0);
+    auto put_term = [&](const Term &t) {
+        pw.put64(t.mask);
+        pw.put64(qweight(t.w, f64));
+    };
+    for (const Term &t : base) put_term(t);
+    for (int j = 0; j < RB; j++)
+        for (const Term &t : lin[j]) put_term(t);
+    for (uint32_t m = 0; m < (1u << RB); m++) pw.put64(qweight(tab[m], f64));
+    for (auto &mt : multi) {
+        pw.put64(mt.first.mask);
+        pw.put(mt.second);
+        pw.put(0);
+        pw.put64(qweight(mt.first.w, f64));
+    }
+    pw.align2();
+    pw.w[start + prog::O_WORDS] = (uint32_t)(pw.w.size() - start);
+}
+
+static void encode_dense(ProgWriter &pw, const SOp &op, const int *reg, const int *qin, int RB, bool f64)
+{
+    // register index of each of the op's positions
+    int ri[kMaxGateQubits];
+    for (int i = 0; i < op.k; i++) {
+        ri[i] = -1;
+        for (int j = 0; j < RB; j++) if (qin[reg[j]] == op.pos[i]) ri[i] = j;
+    }
+    // ascending register order; local bit i' of the new matrix <-> sorted[i']
+    int order[kMaxGateQubits];
+    for (int i = 0; i < op.k; i++) order[i] = i;
+    std::sort(order, order + op.k, [&](int a, int b) { return ri[a] < ri[b]; });
+    int dim = 1 << op.k;
+    std::vector<cd> M2((size_t)dim * dim);
+    auto remap = [&](int l) {
+        int o = 0;
+        for (int i2 = 0; i2 < op.k; i2++) o |= ((l >> order[i2]) & 1) << i2;
+        return o;
+    };
+    for (int r = 0; r < dim; r++)
+        for (int c = 0; c < dim; c++) M2[(size_t)remap(r) * dim + remap(c)] = op.M[(size_t)r * dim + c];
+    uint32_t code = 0;
+    for (int i2 = 0; i2 < op.k; i2++) code |= (uint32_t)ri[order[i2]] << (3 * i2);
+    size_t start = pw.w.size();
+    pw.put(prog::OP_DENSE | (uint32_t)op.k << 8 | code << 16);
+    pw.put(0);
+    for (const cd &z : M2) {
+        if (f64) {
+            double re = z.real(), im = z.imag();
+            uint64_t a, b;
+            std::memcpy(&a, &re, 8);
+            std::memcpy(&b, &im, 8);
+            pw.put64(a);
+            pw.put64(b);
+        } else {
+            float re = (float)z.real(), im = (float)z.imag();
+            uint32_t a, b;
+            std::memcpy(&a, &re, 4);
+            std::memcpy(&b, &im, 4);
+            pw.put(a);
+            pw.put(b);
+        }
+    }
+    pw.align2();
+    pw.w[start + prog::O_WORDS] = (uint32_t)(pw.w.size() - start);
+}
+
+// Encode one cache-blocked pass.  Q: physical chunk positions (popcount C);
+// lam_end[p]: logical qubit held by position p at the end of the block
+// (identity off the chunk); forced_layout: the K3 diagonal sweep's layout.
+static std::vector<uint32_t> encode_program(int n, int C, int RB, bool f64, uint64_t Q,
+                                            const std::vector<SStage> &stages, const int *lam_end,
+                                            bool forced_layout)
+{
+    int qin[prog::kMaxC];
+    int nc = 0;
+    for (int p = 0; p < n; p++) if ((Q >> p) & 1) qin[nc++] = p;
+    ProgWriter pw;
+    pw.w.assign(prog::H_SIZE, 0);
+    pw.w[prog::H_MAGIC] = prog::kMagic;
+    pw.w[prog::H_C] = (uint32_t)C;
+    pw.w[prog::H_RB] = (uint32_t)RB;
+    pw.w[prog::H_NSTAGE] = (uint32_t)stages.size();
+    pw.w[prog::H_N] = (uint32_t)n;
+    pw.w[prog::H_WBYTES] = f64 ? 8 : 4;
+    uint64_t nmask = n >= 64 ? ~0ull : ((1ull << n) - 1);
+    uint64_t freem = nmask & ~Q;
+    pw.w[prog::H_FREE_LO] = (uint32_t)freem;
+    pw.w[prog::H_FREE_HI] = (uint32_t)(freem >> 32);
+    for (int i = 0; i < C; i++) pw.w[prog::H_QIN + i] = (uint32_t)qin[i];
+    for (int i2 = 0; i2 < C; i2++) {
+        int src = i2;
+        for (int i = 0; i < C; i++) if (lam_end[qin[i]] == qin[i2]) src = i;
+        pw.w[prog::H_SPERM + i2] = (uint32_t)src;
+    }
+    int swz = f64 ? 4 : 5;
+    for (size_t s = 0; s < stages.size(); s++) {
+        const SStage &st = stages[s];
+        pw.align2();
+        size_t sstart = pw.w.size();
+        pw.w[prog::H_STAGE_OFF + s] = (uint32_t)sstart;
+        int reg[prog::kMaxRB] = {0}, thr[prog::kMaxC] = {0};
+        if (forced_layout) {
+            for (int j = 0; j < RB; j++) reg[j] = C - RB + j;
+            for (int i = 0; i < C - RB; i++) thr[i] = i;
+        } else {
+            std::vector<int> need;
+            for (int i = 0; i < C; i++) if ((st.R >> qin[i]) & 1) need.push_back(i);
+            stage_layout(C, RB, swz, need, reg, thr);
+        }
+        pw.w.resize(sstart + prog::S_SIZE, 0);
+        pw.w[sstart + prog::S_NOPS] = (uint32_t)st.ops.size();
+        for (int j = 0; j < prog::kMaxRB; j++) pw.w[sstart + prog::S_REG + j] = j < RB ? (uint32_t)reg[j] : 0;
+        for (int i = 0; i < prog::kMaxC; i++) pw.w[sstart + prog::S_THR + i] = i < C - RB ? (uint32_t)thr[i] : 0;
+        uint64_t regphys[prog::kMaxRB];
+        for (int j = 0; j < RB; j++) regphys[j] = 1ull << qin[reg[j]];
+        for (const SOp &op : st.ops) {
+            if (op.type == 1) encode_dense(pw, op, reg, qin, RB, f64);
+            else encode_dseg(pw, op.terms, RB, regphys, f64);
+        }
+        pw.align2();
+        pw.w[sstart + prog::S_WORDS] = (uint32_t)(pw.w.size() - sstart);
+    }
+    return pw.w;
+}
+
+// ------------------------------------------------------------ scheduling
+struct Cfg {
+    int C, RB, L, F, Smax;
+    bool fuse;
+    bool f64;
+};
+
+struct PendingDiag {
+    uint64_t mask;             // physical positions
+    std::vector<Term> terms;   // physical masks
+    int n_src;
+};
+
+// dense ops applied inside a chunk pass have at most this many qubits
+constexpr int kChunkMaxK = 2;
+constexpr int kChunkMaxKEncoded = 2;   // arities the chunk kernel dispatches
+
+static int dense_cost(int k) { return k == 1 ? 8 : k == 2 ? 16 : k == 3 ? 48 : 1 << 12; }
+
+struct Scheduler {
+    const std::vector<PGate> &G;
+    int n;
+    Cfg cfg;
+    Plan &plan;
+    int buf;
+    std::vector<char> done;
+    std::vector<PendingDiag> pending;
+    int lam[64], laminv[64];
+    int last_chunk_op = -1;
+    std::vector<SStage> last_stages;
+    uint64_t last_Q = 0;
+    int last_lam[64];
+
+    Scheduler(const std::vector<PGate> &g, int n_, Cfg c, Plan &p, int b) : G(g), n(n_), cfg(c), plan(p), buf(b)
+    {
+        done.assign(G.size(), 0);
+        for (int i = 0; i < 64; i++) lam[i] = laminv[i] = i;
+    }
+
+    uint64_t phys(uint64_t lm) const
+    {
+        uint64_t r = 0;
+        while (lm) { int q = __builtin_ctzll(lm); lm &= lm - 1; r |= 1ull << laminv[q]; }
+        return r;
+    }
+
+    void make_pending(const PGate &g)
+    {
+        PendingDiag d;
+        d.mask = phys(g.qmask);
+        d.n_src = g.n_src;
+        for (const Term &t : g.terms) d.terms.push_back({phys(t.mask), t.w});
+        pending.push_back(std::move(d));
+    }
+
+    // take the pending diagonals meeting `pm` into one phase op
+    bool flush(uint64_t pm, SOp &out)
+    {
+        out = SOp();
+        out.type = 2;
+        bool any = false;
+        std::vector<PendingDiag> keep;
+        for (PendingDiag &d : pending) {
+            if (d.mask & pm) {
+                out.terms.insert(out.terms.end(), d.terms.begin(), d.terms.end());
+                out.pmask |= d.mask;
+                out.n_src += d.n_src;
+                any = true;
+            } else {
+                keep.push_back(std::move(d));
+            }
+        }
+        pending.swap(keep);
+        normalize_terms(out.terms);
+        return any;
+    }
+
+    static bool meets(const SOp &x, uint64_t pm)
+    {
+        if (x.type == 1) return (x.pmask & pm) != 0;
+        for (const Term &t : x.terms) if (t.mask & pm) return true;
+        return false;
+    }
+
+    // cost-based fusion (GBSA mode 1): merge `op` into an earlier dense op of
+    // the stage that it can be moved next to.
+    void push_dense(SStage &st, SOp op)
+    {
+        if (cfg.fuse) {
+            for (int i = (int)st.ops.size() - 1; i >= 0; i--) {
+                SOp &x = st.ops[i];
+                if (x.type == 1) {
+                    uint64_t um = x.pmask | op.pmask;
+                    int ku = popc(um);
+                    if (ku <= cfg.F && dense_cost(ku) <= dense_cost(x.k) + dense_cost(op.k) &&
+                        (x.pmask & op.pmask)) {
+                        int upos[kMaxGateQubits];
+                        int nu = 0;
+                        for (int j = 0; j < x.k; j++) upos[nu++] = x.pos[j];
+                        for (int j = 0; j < op.k; j++)
+                            if (!((x.pmask >> op.pos[j]) & 1)) upos[nu++] = op.pos[j];
+                        std::vector<cd> A = expand(x.M, x.k, x.pos, nu, upos);
+                        std::vector<cd> B = expand(op.M, op.k, op.pos, nu, upos);
+                        x.M = matmul(B, A, 1 << nu);
+                        x.k = nu;
+                        for (int j = 0; j < nu; j++) x.pos[j] = upos[j];
+                        x.pmask = um;
+                        x.n_src += op.n_src;
+                        return;
+                    }
+                }
+                if (meets(x, op.pmask)) break;
+            }
+        }
+        st.ops.push_back(std::move(op));
+    }
+
+    void emit_diag_op(std::vector<Term> terms)
+    {
+        normalize_terms(terms);
+        Op o;
+        o.kind = OPK_DIAG;
+        o.buf = buf;
+        o.n = n;
+        o.terms = std::move(terms);
+        plan.ops.push_back(std::move(o));
+    }
+
+    void run()
+    {
+        const uint64_t lowL = (1ull << cfg.L) - 1;
+        size_t first = 0;
+        while (true) {
+            while (first < G.size() && done[first]) first++;
+            bool dense_left = false;
+            for (size_t i = first; i < G.size(); i++)
+                if (!done[i] && !G[i].diag) { dense_left = true; break; }
+            if (!dense_left) {
+                for (size_t i = first; i < G.size(); i++)
+                    if (!done[i]) { make_pending(G[i]); done[i] = 1; }
+                break;
+            }
+            std::vector<SStage> stages;
+            uint64_t Q = lowL;
+            for (int s = 0; s < cfg.Smax; s++) {
+                SStage st;
+                uint64_t blocked = 0;
+                bool placed = false;
+                for (size_t i = first; i < G.size(); i++) {
+                    if (done[i]) continue;
+                    const PGate &g = G[i];
+                    if (g.qmask & blocked) { blocked |= g.qmask; continue; }
+                    if (g.diag) { make_pending(g); done[i] = 1; continue; }
+                    uint64_t P = phys(g.qmask);
+                    if (g.swap) {
+                        if (popc((Q | P) & ~lowL) <= cfg.C - cfg.L) {
+                            Q |= P;
+                            int pa = laminv[g.q[0]], pb = laminv[g.q[1]];
+                            std::swap(lam[pa], lam[pb]);
+                            laminv[lam[pa]] = pa;
+                            laminv[lam[pb]] = pb;
+                            done[i] = 1;
+                            placed = true;
+                        } else {
+                            blocked |= g.qmask;
+                        }
+                        continue;
+                    }
+                    if (g.k > kChunkMaxK || popc(st.R | P) > cfg.RB || popc((Q | P) & ~lowL) > cfg.C - cfg.L) {
+                        blocked |= g.qmask;
+                        continue;
+                    }
+                    SOp ph;
+                    if (flush(P, ph)) st.ops.push_back(std::move(ph));
+                    SOp d;
+                    d.type = 1;
+                    d.k = g.k;
+                    for (int j = 0; j < g.k; j++) d.pos[j] = laminv[g.q[j]];
+                    d.pmask = P;
+                    d.M = g.M;
+                    d.n_src = g.n_src;
+                    push_dense(st, std::move(d));
+                    st.R |= P;
+                    Q |= P;
+                    done[i] = 1;
+                    placed = true;
+                }
+                if (!placed) break;
+                stages.push_back(std::move(st));
+            }
+            if (stages.empty()) {
+                // the earliest unplaced gate is wider than the register stage
+                size_t i = first;
+                while (done[i]) i++;
+                const PGate &g = G[i];
+                SOp ph;
+                if (flush(phys(g.qmask), ph)) emit_diag_op(ph.terms);
+                Op o;
+                o.kind = OPK_GATE;
+                o.buf = buf;
+                o.n = n;
+                o.gate = g;
+                for (int j = 0; j < g.k; j++) o.gate.q[j] = laminv[g.q[j]];
+                plan.ops.push_back(std::move(o));
+                done[i] = 1;
+                continue;
+            }
+            // pad the chunk to exactly C positions with the lowest free qubits
+            for (int p = 0; p < n && popc(Q) < cfg.C; p++) Q |= 1ull << p;
+            Op o;
+            o.kind = OPK_CHUNK;
+            o.buf = buf;
+            o.n = n;
+            finalize_chunk(o, Q, stages);
+            last_chunk_op = (int)plan.ops.size();
+            last_stages = stages;
+            last_Q = Q;
+            std::memcpy(last_lam, lam, sizeof(lam));
+            plan.ops.push_back(std::move(o));
+            // next frame: position p's content moves to position lam[p]
+            for (PendingDiag &d : pending) {
+                d.mask = remap(d.mask);
+                for (Term &t : d.terms) t.mask = remap(t.mask);
+            }
+            for (int i = 0; i < 64; i++) lam[i] = laminv[i] = i;
+        }
+        // the diagonals left at the end of the circuit
+        if (!pending.empty()) {
+            std::vector<Term> all;
+            for (PendingDiag &d : pending) all.insert(all.end(), d.terms.begin(), d.terms.end());
+            pending.clear();
+            normalize_terms(all);
+            if (all.empty()) return;
+            if (last_chunk_op >= 0 && last_chunk_op == (int)plan.ops.size() - 1) {
+                // fold into the end of the last block, in its load frame
+                int inv[64];
+                for (int p = 0; p < 64; p++) inv[last_lam[p]] = p;
+                SOp ph;
+                ph.type = 2;
+                for (Term &t : all) {
+                    uint64_t m = 0, x = t.mask;
+                    while (x) { int p = __builtin_ctzll(x); x &= x - 1; m |= 1ull << inv[p]; }
+                    ph.terms.push_back({m, t.w});
+                }
+                normalize_terms(ph.terms);
+                last_stages.back().ops.push_back(std::move(ph));
+                std::memcpy(lam, last_lam, sizeof(lam));
+                Op &o = plan.ops[last_chunk_op];
+                finalize_chunk(o, last_Q, last_stages);
+                for (int i = 0; i < 64; i++) lam[i] = laminv[i] = i;
+            } else {
+                emit_diag_op(std::move(all));
+            }
+        }
+    }
+
+    uint64_t remap(uint64_t m) const
+    {
+        uint64_t r = 0;
+        while (m) { int p = __builtin_ctzll(m); m &= m - 1; r |= 1ull << lam[p]; }
+        return r;
+    }
+
+    void finalize_chunk(Op &o, uint64_t Q, const std::vector<SStage> &stages)
+    {
+        ChunkProg &cp = o.prog;
+        cp.C = cfg.C;
+        cp.RB = cfg.RB;
+        int nc = 0;
+        for (int p = 0; p < n; p++) if ((Q >> p) & 1) { cp.qin[nc] = p; cp.qout[nc] = lam[p]; nc++; }
+        cp.stages.clear();
+        for (const SStage &s : stages) {
+            Stage ps;
+            for (const SOp &x : s.ops) {
+                StageOp so;
+                so.type = x.type;
+                so.k = x.k;
+                for (int j = 0; j < x.k; j++) so.reg[j] = x.pos[j];
+                so.M = x.M;
+                so.terms = x.terms;
+                so.n_src = x.n_src;
+                ps.ops.push_back(std::move(so));
+            }
+            cp.stages.push_back(std::move(ps));
+        }
+        o.words = encode_program(n, cfg.C, cfg.RB, cfg.f64, Q, stages, lam, false);
+    }
+};
+
+// ------------------------------------------------------------ stats
+static void account(Plan &p)
+{
+    sim_plan_stats &s = p.stats;
+    int sz = p.dtype == SIM_C64 ? 8 : 16;
+    for (const Op &o : p.ops) {
+        double amps = std::ldexp(1.0, o.n);
+        s.ops++;
+        switch (o.kind) {
+        case OPK_INIT_BASIS:
+            s.bytes += (uint64_t)(amps * sz);
+            break;
+        case OPK_GATE:
+            s.gate_ops++;
+            if (o.buf == 0) s.sweeps++;
+            s.bytes += (uint64_t)(2 * amps * sz);
+            s.state_updates += (uint64_t)amps;
+            s.flops += amps * 8.0 * (1 << o.gate.k);
+            break;
+        case OPK_GATE_DIAG: {
+            s.gate_ops++;
+            int nz = 0;
+            for (int c = 0; c < (1 << o.gate.k); c++) {
+                uint64_t x = 0;
+                for (int i = 0; i < o.gate.k; i++) if ((c >> i) & 1) x |= 1ull << o.gate.q[i];
+                uint64_t w = 0;
+                for (const Term &t : o.gate.terms) if ((x & t.mask) == t.mask) w += t.w;
+                if (w != 0) nz++;
+            }
+            double frac = (double)nz / (1 << o.gate.k);
+            s.bytes += (uint64_t)(2 * amps * sz * frac);
+            s.state_updates += (uint64_t)(amps * frac);
+            s.flops += amps * frac * 6.0;
+            break;
+        }
+        case OPK_DIAG:
+        case OPK_PHASE_SMALL:
+            s.diag_ops++;
+            if (o.buf == 0) s.sweeps++;
+            s.bytes += (uint64_t)(2 * amps * sz);
+            s.state_updates += (uint64_t)amps;
+            s.flops += amps * 6.0;
+            break;
+        case OPK_CHUNK: {
+            s.chunk_ops++;
+            if (o.buf == 0) s.sweeps++;
+            s.bytes += (uint64_t)(2 * amps * sz);
+            s.state_updates += (uint64_t)amps;
+            for (const Stage &st : o.prog.stages)
+                for (const StageOp &x : st.ops) s.flops += x.type == 1 ? amps * 8.0 * (1 << x.k) : amps * 6.0;
+            break;
+        }
+        case OPK_TENSOR:
+            s.tensor_ops++;
+            s.bytes += (uint64_t)(amps * sz);
+            s.state_updates += (uint64_t)amps;
+            s.flops += amps * 6.0;
+            break;
+        case OPK_DENSE_TC:
+            s.dense_ops++;
+            if (o.buf == 0) s.sweeps++;
+            s.bytes += (uint64_t)(2 * amps * sz);
+            s.state_updates += (uint64_t)amps;
+            s.flops += amps * 8.0 * 32;
+            break;
+        }
+    }
+}
+
+// ------------------------------------------------------------ pipeline
+static void emit_unfused(const std::vector<PGate> &G, int n, int buf, Plan &plan)
+{
+    for (const PGate &g : G) {
+        Op o;
+        o.buf = buf;
+        o.n = n;
+        if (g.diag && g.kind == kFusedDiag) {
+            o.kind = OPK_DIAG;
+            o.terms = g.terms;
+        } else if (g.diag) {
+            o.kind = OPK_GATE_DIAG;
+            o.gate = g;
+        } else {
+            o.kind = OPK_GATE;
+            o.gate = g;
+        }
+        plan.ops.push_back(std::move(o));
+    }
+}
+
+// Encode the K3 diagonal sweep program (fixed layout: tile of 2^C
+// consecutive amplitudes, register bits on top).
+static std::vector<uint32_t> encode_diag_sweep(int n, const std::vector<Term> &terms, bool f64, int &C, int &RB)
+{
+    RB = f64 ? 4 : 5;
+    C = 7 + RB;
+    SStage st;
+    SOp ph;
+    ph.type = 2;
+    ph.terms = terms;
+    st.ops.push_back(ph);
+    std::vector<SStage> stages{st};
+    int lam[64];
+    for (int i = 0; i < 64; i++) lam[i] = i;
+    return encode_program(n, C, RB, f64, (1ull << C) - 1, stages, lam, true);
+}
+
+static void schedule(const std::vector<PGate> &G, int n, const sim_options &opt, sim_dtype dt, int buf, Plan &plan)
+{
+    int C = 0, RB = 0;
+    bool blocked = (opt.flags & SIM_F_BLOCK) && chunk_shape(n, dt, opt.chunk_qubits, C, RB);
+    if (!blocked) {
+        emit_unfused(G, n, buf, plan);
+        return;
+    }
+    Cfg cfg;
+    cfg.C = C;
+    cfg.RB = RB;
+    cfg.L = std::min(dt == SIM_C64 ? 4 : 3, C - RB);
+    cfg.F = opt.max_fuse_qubits;
+    cfg.Smax = opt.max_stages;
+    cfg.fuse = (opt.flags & SIM_F_FUSE) != 0;
+    cfg.f64 = dt == SIM_C128;
+    Scheduler s(G, n, cfg, plan, buf);
+    s.run();
+}
+
+static void finalize_words(Plan &plan)
+{
+    bool f64 = plan.dtype == SIM_C128;
+    for (Op &o : plan.ops) {
+        if (o.kind == OPK_DIAG) {
+            int C, RB;
+            if (o.n >= (f64 ? 11 : 12)) {
+                o.words = encode_diag_sweep(o.n, o.terms, f64, C, RB);
+            } else {
+                // too small for the diagonal sweep's tile: run it as a one-stage chunk pass
+                int Cc = 0, RBc = 0;
+                if (!chunk_shape(o.n, plan.dtype, 0, Cc, RBc)) {
+                    // below every chunk shape: one thread per amplitude sums the terms
+                    o.kind = OPK_PHASE_SMALL;
+                    continue;
+                }
+                o.kind = OPK_CHUNK;
+                SStage st;
+                SOp ph;
+                ph.type = 2;
+                ph.terms = o.terms;
+                st.ops.push_back(ph);
+                std::vector<SStage> stages{st};
+                int lam[64];
+                for (int i = 0; i < 64; i++) lam[i] = i;
+                uint64_t Q = (1ull << Cc) - 1;
+                o.prog.C = Cc;
+                o.prog.RB = RBc;
+                for (int i = 0; i < Cc; i++) o.prog.qin[i] = o.prog.qout[i] = i;
+                Stage ps;
+                StageOp so;
+                so.type = 2;
+                so.terms = o.terms;
+                ps.ops.push_back(so);
+                o.prog.stages.push_back(ps);
+                o.words = encode_program(o.n, Cc, RBc, f64, Q, stages, lam, false);
+            }
+        }
+    }
+}
+
+// Walk an encoded program the way the kernels do and check every offset,
+// count and bit position before it can reach the GPU.
+static bool validate_program(const std::vector<uint32_t> &w, int n, bool diag_sweep, std::string &err)
+{
+    auto bad = [&](const char *m) { err = std::string("internal: invalid device program: ") + m; return false; };
+    const size_t W = w.size();
+    if (W < (size_t)prog::H_SIZE || w[prog::H_MAGIC] != prog::kMagic) return bad("header");
+    const int C = (int)w[prog::H_C], RB = (int)w[prog::H_RB], ns = (int)w[prog::H_NSTAGE];
+    if (C < 1 || C > prog::kMaxC || C > n || RB < 1 || RB > prog::kMaxRB || RB >= C) return bad("shape");
+    if (ns < 0 || ns > prog::kMaxStages || (diag_sweep && ns != 1)) return bad("stage count");
+    if ((int)w[prog::H_N] != n) return bad("n");
+    const int wb = (int)w[prog::H_WBYTES];
+    if (wb != 4 && wb != 8) return bad("weight size");
+    uint64_t freem = (uint64_t)w[prog::H_FREE_LO] | ((uint64_t)w[prog::H_FREE_HI] << 32);
+    uint64_t qm = 0;
+    for (int i = 0; i < C; i++) {
+        uint32_t q = w[prog::H_QIN + i];
+        if ((int)q >= n || ((qm >> q) & 1)) return bad("qin");
+        qm |= 1ull << q;
+    }
+    uint64_t nmask = n >= 64 ? ~0ull : ((1ull << n) - 1);
+    if ((qm & freem) || ((qm | freem) != nmask)) return bad("free mask");
+    if (!diag_sweep && (qm & 1) == 0) return bad("qubit 0 must be a chunk bit");
+    uint32_t sp = 0;
+    for (int i = 0; i < C; i++) {
+        uint32_t b = w[prog::H_SPERM + i];
+        if ((int)b >= C || ((sp >> b) & 1)) return bad("store permutation");
+        sp |= 1u << b;
+    }
+    for (int s = 0; s < ns; s++) {
+        size_t so = w[prog::H_STAGE_OFF + s];
+        if ((so & 1) || so + prog::S_SIZE > W) return bad("stage offset");
+        uint32_t seen = 0;
+        for (int j = 0; j < RB; j++) {
+            uint32_t b = w[so + prog::S_REG + j];
+            if ((int)b >= C || ((seen >> b) & 1)) return bad("register bits");
+            seen |= 1u << b;
+        }
+        for (int i = 0; i < C - RB; i++) {
+            uint32_t b = w[so + prog::S_THR + i];
+            if ((int)b >= C || ((seen >> b) & 1)) return bad("thread bits");
+            seen |= 1u << b;
+        }
+        const uint32_t nops = w[so + prog::S_NOPS];
+        size_t op = so + prog::S_SIZE;
+        for (uint32_t k = 0; k < nops; k++) {
+            if (op + 2 > W || (op & 1)) return bad("op offset");
+            const uint32_t hdr = w[op], len = w[op + prog::O_WORDS];
+            if (len < 2 || op + len > W) return bad("op length");
+            const int type = hdr & 0xff;
+            if (type == prog::OP_DENSE) {
+                if (diag_sweep) return bad("dense op in a diagonal sweep");
+                const int kq = (hdr >> 8) & 0xff, code = (int)(hdr >> 16);
+                if (kq < 1 || kq > kChunkMaxKEncoded) return bad("dense arity");
+                int prev = -1;
+                for (int i = 0; i < kq; i++) {
+                    int p = (code >> (3 * i)) & 7;
+                    if (p >= RB || p <= prev) return bad("dense positions");
+                    prev = p;
+                }
+                if (code >> (3 * kq)) return bad("dense code");
+                size_t need = 2 + (size_t)2 * (1u << (2 * kq)) * (wb == 8 ? 2 : 1);
+                if (len < need) return bad("dense body");
+            } else if (type == prog::OP_DSEG) {
+                if (len < (size_t)prog::O_BODY + prog::D_TERMS) return bad("phase header");
+                const uint32_t *b = &w[op + prog::O_BODY];
+                size_t nterm = b[prog::D_NBASE];
+                for (int j = 0; j < prog::kMaxRB; j++) {
+                    if (j >= RB && b[prog::D_NLIN + j]) return bad("phase lin count");
+                    nterm += b[prog::D_NLIN + j];
+                }
+                size_t need = prog::O_BODY + prog::D_TERMS + nterm * prog::kTermWords + 2 * ((size_t)1 << RB) +
+                              (size_t)b[prog::D_NMULTI] * prog::kMultiWords;
+                if (len < need) return bad("phase body");
+            } else {
+                return bad("op type");
+            }
+            op += len;
+        }
+        if (op > so + w[so + prog::S_WORDS] || so + w[so + prog::S_WORDS] > W) return bad("stage length");
+    }
+    return true;
+}
+
+bool make_plan(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_t ng, const sim_options &opt_in,
+               Plan &plan, std::string &err)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    sim_options opt = opt_in;
+    resolve_options(opt, n, dt);
+    plan = Plan();
+    plan.n = n;
+    plan.dtype = dt;
+    plan.buf_qubits.push_back(n);
+    std::vector<PGate> G;
+    G.reserve(ng);
+    for (size_t i = 0; i < ng; i++) {
+        PGate g;
+        if (!make_gate(gates[i], n, g, err)) {
+            err = "gate " + std::to_string(i) + ": " + err;
+            return false;
+        }
+        G.push_back(std::move(g));
+    }
+    plan.stats.gates_in = ng;
+    (void)basis;
+    if (opt.flags & SIM_F_DIAG) {
+        uint64_t absorbed = 0;
+        G = diagonal_detector(G, opt.max_diag_qubits, absorbed);
+        plan.stats.diag_fused = absorbed;
+    }
+    schedule(G, n, opt, dt, 0, plan);
+    finalize_words(plan);
+    for (const Op &o : plan.ops) {
+        if (o.kind == OPK_CHUNK || o.kind == OPK_DIAG)
+            if (!validate_program(o.words, o.n, o.kind == OPK_DIAG, err)) return false;
+        if ((o.kind == OPK_GATE || o.kind == OPK_DENSE_TC) &&
+            (o.gate.k < 1 || o.gate.k > kMaxGateQubits || o.gate.M.size() != ((size_t)1 << (2 * o.gate.k)))) {
+            err = "internal: bad dense gate op";
+            return false;
+        }
+    }
+    account(plan);
+    plan.stats.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return true;
+}
+
+// ------------------------------------------------------------ JSON
+static void jnum(std::ostringstream &os, double v)
+{
+    char b[40];
+    snprintf(b, sizeof b, "%.17g", v);
+    os << b;
+}
+
+static void jterms(std::ostringstream &os, const std::vector<Term> &t)
+{
+    os << "[";
+    for (size_t i = 0; i < t.size(); i++) os << (i ? "," : "") << "[\"" << t[i].mask << "\",\"" << t[i].w << "\"]";
+    os << "]";
+}
+
+static void jmat(std::ostringstream &os, const std::vector<cd> &M)
+{
+    os << "[";
+    for (size_t i = 0; i < M.size(); i++) {
+        os << (i ? "," : "") << "[";
+        jnum(os, M[i].real());
+        os << ",";
+        jnum(os, M[i].imag());
+        os << "]";
+    }
+    os << "]";
+}
+
+std::string plan_json(const Plan &p)
+{
+    std::ostringstream os;
+    const sim_plan_stats &s = p.stats;
+    os << "{\"n\":" << p.n << ",\"dtype\":" << (int)p.dtype << ",\"wbits\":" << (p.dtype == SIM_C64 ? 32 : 64);
+    os << ",\"stats\":{\"gates_in\":" << s.gates_in << ",\"ops\":" << s.ops << ",\"sweeps\":" << s.sweeps
+       << ",\"chunk_ops\":" << s.chunk_ops << ",\"diag_ops\":" << s.diag_ops << ",\"gate_ops\":" << s.gate_ops
+       << ",\"tensor_ops\":" << s.tensor_ops << ",\"dense_ops\":" << s.dense_ops << ",\"diag_fused\":" << s.diag_fused
+       << ",\"boosted_gates\":" << s.boosted_gates << ",\"state_updates\":" << s.state_updates
+       << ",\"bytes\":" << s.bytes << "}";
+    os << ",\"buffers\":[";
+    for (size_t i = 0; i < p.buf_qubits.size(); i++) os << (i ? "," : "") << p.buf_qubits[i];
+    os << "],\"ops\":[";
+    for (size_t oi = 0; oi < p.ops.size(); oi++) {
+        const Op &o = p.ops[oi];
+        os << (oi ? "," : "") << "{\"buf\":" << o.buf << ",\"n\":" << o.n << ",";
+        switch (o.kind) {
+        case OPK_INIT_BASIS: os << "\"op\":\"init\",\"basis\":\"" << o.basis << "\""; break;
+        case OPK_GATE:
+            os << "\"op\":\"gate\",\"qubits\":[";
+            for (int i = 0; i < o.gate.k; i++) os << (i ? "," : "") << o.gate.q[i];
+            os << "],\"matrix\":";
+            jmat(os, o.gate.M);
+            break;
+        case OPK_GATE_DIAG:
+            os << "\"op\":\"phase\",\"terms\":";
+            jterms(os, o.gate.terms);
+            break;
+        case OPK_DIAG:
+        case OPK_PHASE_SMALL:
+            os << "\"op\":\"phase\",\"terms\":";
+            jterms(os, o.terms);
+            break;
+        case OPK_CHUNK: {
+            const ChunkProg &cp = o.prog;
+            os << "\"op\":\"chunk\",\"C\":" << cp.C << ",\"qin\":[";
+            for (int i = 0; i < cp.C; i++) os << (i ? "," : "") << cp.qin[i];
+            os << "],\"qout\":[";
+            for (int i = 0; i < cp.C; i++) os << (i ? "," : "") << cp.qout[i];
+            os << "],\"words\":" << o.words.size() << ",\"stages\":[";
+            for (size_t si = 0; si < cp.stages.size(); si++) {
+                os << (si ? "," : "") << "[";
+                const Stage &st = cp.stages[si];
+                for (size_t k = 0; k < st.ops.size(); k++) {
+                    const StageOp &x = st.ops[k];
+                    os << (k ? "," : "");
+                    if (x.type == 1) {
+                        os << "{\"dense\":[";
+                        for (int i = 0; i < x.k; i++) os << (i ? "," : "") << x.reg[i];
+                        os << "],\"matrix\":";
+                        jmat(os, x.M);
+                        os << "}";
+                    } else {
+                        os << "{\"phase\":";
+                        jterms(os, x.terms);
+                        os << "}";
+                    }
+                }
+                os << "]";
+            }
+            os << "]";
+            break;
+        }
+        case OPK_TENSOR:
+            os << "\"op\":\"tensor\",\"lo\":" << o.buf_lo << ",\"hi\":" << o.buf_hi << ",\"n_lo\":" << o.n_lo
+               << ",\"n_hi\":" << o.n_hi;
+            break;
+        case OPK_DENSE_TC:
+            os << "\"op\":\"gate\",\"qubits\":[";
+            for (int i = 0; i < o.gate.k; i++) os << (i ? "," : "") << o.gate.q[i];
+            os << "],\"matrix\":";
+            jmat(os, o.gate.M);
+            break;
+        }
+        os << "}";
+    }
+    os << "]}";
+    return os.str();
+}
+
+}  // namespace svs

@@ -1,0 +1,281 @@
+"""Thin ctypes binding of the C ABI in ``include/svsim.h`` (same names).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+kernels of ``libsvsim.so``.  Loading fails loudly when the library is missing
+or was not built; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+from typing import Iterable, Optional, Sequence
+
+import numpy as np
+
+from . import circuits as _circ
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsvsim.so")
+
+SIM_C64, SIM_C128 = 0, 1
+SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_ETIMEOUT, SIM_EBUSY, SIM_EUNSUPPORTED = range(7)
+SIM_F_DIAG, SIM_F_BOOST, SIM_F_BLOCK, SIM_F_FUSE, SIM_F_TC = 1, 2, 4, 8, 16
+SIM_F_ALL = 0x1F
+SIM_DENSE_SPLIT_TF32, SIM_DENSE_FP32, SIM_DENSE_FP64 = 0, 1, 2
+
+KIND = {"h": 0, "x": 1, "y": 2, "z": 3, "s": 4, "t": 5, "rx": 6, "ry": 7, "rz": 8, "p": 9,
+        "cx": 10, "cz": 11, "cp": 12, "rzz": 13, "swap": 14, "u1q": 15, "unitary": 16, "diag": 17}
+STATUS = {0: "SIM_OK", 1: "SIM_EINVAL", 2: "SIM_ENOMEM", 3: "SIM_ECUDA", 4: "SIM_ETIMEOUT",
+          5: "SIM_EBUSY", 6: "SIM_EUNSUPPORTED"}
+
+
+class sim_gate(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("nq", ctypes.c_uint32), ("q", ctypes.c_uint32 * 6),
+                ("param", ctypes.c_double * 3), ("matrix", ctypes.POINTER(ctypes.c_double))]
+
+
+class sim_options(ctypes.Structure):
+    _fields_ = [("max_fuse_qubits", ctypes.c_int), ("max_diag_qubits", ctypes.c_int),
+                ("chunk_qubits", ctypes.c_int), ("booster_div", ctypes.c_int),
+                ("flags", ctypes.c_uint32), ("dense_precision", ctypes.c_int),
+                ("max_stages", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+
+class sim_plan_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in
+                ("gates_in", "ops", "sweeps", "chunk_ops", "diag_ops", "gate_ops", "dense_ops",
+                 "tensor_ops", "permute_ops", "diag_fused", "boosted_gates", "state_updates", "bytes")] + \
+               [("flops", ctypes.c_double), ("plan_ms", ctypes.c_double)]
+
+    def asdict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class sim_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64 * 8), ("ms", ctypes.c_double * 8), ("bytes", ctypes.c_double * 8),
+                ("h2d_bytes", ctypes.c_uint64)]
+
+    KINDS = ("init", "gate", "gate_diag", "diag", "chunk", "tensor", "dense", "phase_small")
+
+    def asdict(self):
+        return {k: {"launches": int(self.launches[i]), "ms": float(self.ms[i]), "bytes": float(self.bytes[i])}
+                for i, k in enumerate(self.KINDS)} | {"h2d_bytes": int(self.h2d_bytes)}
+
+
+class SimError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported function of include/svsim.h
+_P = ctypes.c_void_p
+_SIGS = [
+    ("sim_default_options", ctypes.c_int, [ctypes.POINTER(sim_options)]),
+    ("sim_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)]),
+    ("sim_create_on", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+    ("sim_destroy", ctypes.c_int, [_P]),
+    ("sim_reset", ctypes.c_int, [_P, ctypes.c_uint64]),
+    ("sim_apply_circuit", ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.POINTER(sim_options)]),
+    ("sim_sync", ctypes.c_int, [_P]),
+    ("sim_probabilities", ctypes.c_int, [_P, _P]),
+    ("sim_top_k", ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    ("sim_expectation", ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
+    ("sim_norm", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    ("sim_get_state", ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    ("sim_set_state", ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    ("sim_state_device", ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    ("sim_last_plan_stats", ctypes.c_int, [_P, ctypes.POINTER(sim_plan_stats)]),
+    ("sim_profile_enable", ctypes.c_int, [_P, ctypes.c_int]),
+    ("sim_profile_read", ctypes.c_int, [_P, ctypes.POINTER(sim_profile)]),
+    ("sim_last_error", ctypes.c_char_p, [_P]),
+    ("sim_global_error", ctypes.c_char_p, []),
+    ("sim_plan_json", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _P, ctypes.c_size_t,
+                                     ctypes.POINTER(sim_options), ctypes.c_char_p, ctypes.c_size_t,
+                                     ctypes.POINTER(ctypes.c_size_t)]),
+]
+
+
+def load(path: Optional[str] = None):
+    """Load libsvsim.so (built by ``paper_2604_12256_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libsvsim.so not built ({p}); run paper_2604_12256_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    for name, res, args in _SIGS:
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc, h=None):
+    if rc != SIM_OK:
+        lib = load()
+        msg = lib.sim_last_error(h) if h else lib.sim_global_error()
+        raise SimError(rc, (msg or b"").decode(errors="replace"))
+
+
+def default_options(**kw) -> sim_options:
+    o = sim_options()
+    _check(load().sim_default_options(ctypes.byref(o)))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class GateArray:
+    """A circuit marshalled into a contiguous sim_gate array (keeps the
+    matrix buffers alive)."""
+
+    def __init__(self, gates: Sequence[_circ.Gate]):
+        self.n = len(gates)
+        self.arr = (sim_gate * max(1, self.n))()
+        self._keep = []
+        for i, g in enumerate(gates):
+            s = self.arr[i]
+            s.kind = KIND[g.kind]
+            s.nq = len(g.qubits)
+            for j, q in enumerate(g.qubits):
+                s.q[j] = q
+            for j, p in enumerate(g.params):
+                s.param[j] = p
+            if g.matrix is not None:
+                buf = np.ascontiguousarray(g.matrix, np.complex128).reshape(-1).view(np.float64).copy()
+                self._keep.append(buf)
+                s.matrix = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+    @property
+    def ptr(self):
+        return ctypes.cast(self.arr, ctypes.c_void_p)
+
+
+def plan_json(n: int, gates, dtype: int = SIM_C64, basis: Optional[int] = 0,
+              opt: Optional[sim_options] = None) -> dict:
+    """The optimizer's plan for a circuit (no GPU needed)."""
+    lib = load()
+    ga = gates if isinstance(gates, GateArray) else GateArray(gates)
+    b = (1 << 64) - 1 if basis is None else basis
+    need = ctypes.c_size_t(0)
+    optp = ctypes.byref(opt) if opt is not None else None
+    lib.sim_plan_json(n, dtype, b, ga.ptr, ga.n, optp, None, 0, ctypes.byref(need))
+    if need.value == 0:
+        _check(lib.sim_plan_json(n, dtype, b, ga.ptr, ga.n, optp, None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(need.value)
+    _check(lib.sim_plan_json(n, dtype, b, ga.ptr, ga.n, optp, buf, need.value, ctypes.byref(need)))
+    return json.loads(buf.value.decode())
+
+
+class Sim:
+    """Owner of one sim_t handle."""
+
+    def __init__(self, n: int, dtype: int = SIM_C64, dev_buf: Optional[int] = None, nbytes: int = 0,
+                 stream: Optional[int] = None):
+        self.lib = load()
+        self.n = n
+        self.dtype = dtype
+        h = ctypes.c_void_p()
+        if dev_buf is None:
+            _check(self.lib.sim_create(n, dtype, ctypes.byref(h)))
+        else:
+            _check(self.lib.sim_create_on(n, dtype, ctypes.c_void_p(dev_buf), nbytes,
+                                          ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+        self.h = h
+
+    @property
+    def amp_bytes(self):
+        return 8 if self.dtype == SIM_C64 else 16
+
+    def close(self):
+        if self.h:
+            self.lib.sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def reset(self, basis: int = 0):
+        _check(self.lib.sim_reset(self.h, basis), self.h)
+
+    def apply(self, gates, opt: Optional[sim_options] = None):
+        ga = gates if isinstance(gates, GateArray) else GateArray(gates)
+        _check(self.lib.sim_apply_circuit(self.h, ga.ptr, ga.n, ctypes.byref(opt) if opt is not None else None),
+               self.h)
+
+    def sync(self):
+        _check(self.lib.sim_sync(self.h), self.h)
+
+    def stats(self) -> dict:
+        st = sim_plan_stats()
+        _check(self.lib.sim_last_plan_stats(self.h, ctypes.byref(st)), self.h)
+        return st.asdict()
+
+    def profile_enable(self, on: bool = True):
+        _check(self.lib.sim_profile_enable(self.h, 1 if on else 0), self.h)
+
+    def profile_read(self) -> dict:
+        p = sim_profile()
+        _check(self.lib.sim_profile_read(self.h, ctypes.byref(p)), self.h)
+        return p.asdict()
+
+    def norm(self) -> float:
+        v = ctypes.c_double()
+        _check(self.lib.sim_norm(self.h, ctypes.byref(v)), self.h)
+        return v.value
+
+    def probabilities(self) -> np.ndarray:
+        out = np.empty(1 << self.n, np.float64)
+        _check(self.lib.sim_probabilities(self.h, out.ctypes.data), self.h)
+        return out
+
+    def top_k(self, k: int):
+        idx = np.empty(k, np.uint64)
+        p = np.empty(k, np.float64)
+        _check(self.lib.sim_top_k(self.h, k, idx.ctypes.data, p.ctypes.data), self.h)
+        return idx, p
+
+    def expectation(self, masks: Iterable[int]) -> np.ndarray:
+        m = np.ascontiguousarray(np.array(list(masks), dtype=np.uint64))
+        out = np.empty(len(m), np.float64)
+        _check(self.lib.sim_expectation(self.h, m.ctypes.data, len(m), out.ctypes.data), self.h)
+        return out
+
+    def get_state(self) -> np.ndarray:
+        dt = np.complex64 if self.dtype == SIM_C64 else np.complex128
+        out = np.empty(1 << self.n, dt)
+        _check(self.lib.sim_get_state(self.h, out.ctypes.data, out.nbytes), self.h)
+        return out
+
+    def set_state(self, a: np.ndarray):
+        dt = np.complex64 if self.dtype == SIM_C64 else np.complex128
+        a = np.ascontiguousarray(a, dt)
+        _check(self.lib.sim_set_state(self.h, a.ctypes.data, a.nbytes), self.h)
+
+    def device(self):
+        p, s = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(self.lib.sim_state_device(self.h, ctypes.byref(p), ctypes.byref(s)), self.h)
+        return p.value, s.value
+
+
+def run(circuit: _circ.Circuit, dtype: int = SIM_C64, opt: Optional[sim_options] = None) -> np.ndarray:
+    """Convenience: simulate a circuit from its basis state, return the state."""
+    with Sim(circuit.n, dtype) as s:
+        s.reset(circuit.basis)
+        s.apply(circuit.gates, opt)
+        return s.get_state()

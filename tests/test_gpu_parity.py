@@ -1,0 +1,176 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances: complex128 max |d amp| <= 1e-12; complex64 max |d amp| <= 1e-5
+and fidelity >= 1 - 1e-6 (circuits of depth <= 200 and more)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_12256_gb300 import circuits as C
+from paper_2604_12256_gb300 import svsim as S
+
+pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("built_lib")]
+
+TOL128 = 1e-12
+TOL64 = 1e-5
+FID64 = 1 - 1e-6
+
+FLAG_SETS = {
+    "unfused": 0,
+    "diag": S.SIM_F_DIAG,
+    "block": S.SIM_F_BLOCK,
+    "all": S.SIM_F_DIAG | S.SIM_F_BLOCK | S.SIM_F_FUSE | S.SIM_F_BOOST,
+}
+
+
+def gpu_run(c, dtype, flags=None, **kw):
+    opt = S.default_options(**({"flags": flags} if flags is not None else {}), **kw)
+    with S.Sim(c.n, dtype) as s:
+        s.reset(c.basis)
+        s.apply(c.gates, opt)
+        return s.get_state().astype(np.complex128), s.stats()
+
+
+def check(c, dtype, got, exp):
+    err = np.max(np.abs(got - exp))
+    if dtype == S.SIM_C128:
+        assert err <= TOL128, err
+    else:
+        assert err <= TOL64, err
+        assert oracle.fidelity(exp, got) >= FID64
+
+
+def test_config0_layered14_c128():
+    """14-qubit random layered circuit, complex128, depth 20 (config 0)."""
+    c = C.layered(14, 20, 0)
+    exp = oracle.run(c)
+    for flags in FLAG_SETS.values():
+        got, st = gpu_run(c, S.SIM_C128, flags)
+        check(c, S.SIM_C128, got, exp)
+    with S.Sim(14, S.SIM_C128) as s:
+        s.apply(c.gates)
+        p = s.probabilities()
+    np.testing.assert_allclose(p, oracle.probabilities(exp), atol=1e-13, rtol=0)
+
+
+@pytest.mark.parametrize("dtype", [S.SIM_C64, S.SIM_C128])
+@pytest.mark.parametrize("flags", list(FLAG_SETS))
+@pytest.mark.parametrize("maker", [
+    lambda: C.random_mixed(12, 200, 1, max_k=3),
+    lambda: C.random_mixed(11, 200, 2, max_k=3),
+    lambda: C.random_mixed(9, 150, 3, max_k=3),
+    lambda: C.random_mixed(7, 100, 4, max_k=3),
+    lambda: C.diag_heavy(16, 300, 5),
+    lambda: C.qft(15, 6),
+    lambda: C.qaoa(16, 3, 7),
+    lambda: C.layered(13, 8, 8),
+    lambda: C.rzz_full(14, 9),
+], ids=["mixed12", "mixed11", "mixed9", "mixed7", "diag16", "qft15", "qaoa16", "layered13", "rzz14"])
+def test_parity_small(maker, flags, dtype):
+    c = maker()
+    exp = oracle.run(c)
+    got, _ = gpu_run(c, dtype, FLAG_SETS[flags])
+    check(c, dtype, got, exp)
+
+
+@pytest.mark.parametrize("dtype", [S.SIM_C64, S.SIM_C128])
+@pytest.mark.parametrize("maker", [
+    lambda: C.diag_heavy(21, 500, 11),
+    lambda: C.qft(20, 12),
+    lambda: C.qaoa(20, 4, 13),
+    lambda: C.layered(19, 20, 14),
+    lambda: C.random_mixed(20, 300, 15, max_k=3),
+], ids=["diag21", "qft20", "qaoa20", "layered19", "mixed20"])
+def test_parity_multi_tile(maker, dtype):
+    """Sizes that span hundreds of chunks (2^12 amplitudes each)."""
+    c = maker()
+    exp = oracle.run(c)
+    got, st = gpu_run(c, dtype)
+    check(c, dtype, got, exp)
+    assert st["sweeps"] < len(c.gates)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5])
+def test_tiny_registers(n):
+    c = C.random_mixed(n, 60, 20 + n, max_k=min(3, n))
+    exp = oracle.run(c)
+    for dtype in (S.SIM_C64, S.SIM_C128):
+        got, _ = gpu_run(c, dtype)
+        check(c, dtype, got, exp)
+
+
+def test_empty_circuit_and_reset():
+    with S.Sim(13, S.SIM_C64) as s:
+        s.reset(1234)
+        s.apply([])
+        a = s.get_state()
+        assert a[1234] == 1 and np.count_nonzero(a) == 1
+        with pytest.raises(S.SimError):
+            s.reset(1 << 13)
+
+
+@pytest.mark.parametrize("dtype", [S.SIM_C64, S.SIM_C128])
+def test_readouts(dtype):
+    c = C.random_mixed(14, 150, 30, max_k=2)
+    exp = oracle.run(c)
+    masks = [1 << 0, (1 << 3) | (1 << 9), (1 << 13) | (1 << 2), 0x3FFF, 0, 0b1010101]
+    with S.Sim(14, dtype) as s:
+        s.reset(c.basis)
+        s.apply(c.gates)
+        tol = 1e-12 if dtype == S.SIM_C128 else 2e-5
+        assert abs(s.norm() - 1.0) <= tol
+        np.testing.assert_allclose(s.expectation(masks), oracle.expectation_z(exp, masks), atol=tol)
+        np.testing.assert_allclose(s.probabilities(), oracle.probabilities(exp), atol=tol)
+        k = 64
+        idx, p = s.top_k(k)
+        eidx, ep = oracle.top_k(exp, k)
+        np.testing.assert_allclose(p, ep, atol=tol)
+        if dtype == S.SIM_C128:
+            assert list(idx) == list(eidx)
+        else:   # near-ties may swap in complex64: every index must be a valid top-k member
+            pe = oracle.probabilities(exp)
+            assert len(set(idx.tolist())) == k
+            assert np.all(pe[idx.astype(np.int64)] >= ep[-1] - 2 * tol)
+
+
+def test_topk_ties_uniform():
+    with S.Sim(16, S.SIM_C64) as s:
+        s.apply([C.Gate("h", (q,)) for q in range(16)])
+        idx, p = s.top_k(100)
+        assert list(idx) == list(range(100))
+        np.testing.assert_allclose(p, 2.0 ** -16, rtol=1e-6)
+
+
+def test_deterministic():
+    c = C.diag_heavy(20, 300, 40)
+    a1, _ = gpu_run(c, S.SIM_C64)
+    a2, _ = gpu_run(c, S.SIM_C64)
+    assert np.array_equal(a1, a2)
+
+
+def test_set_get_state_roundtrip():
+    rng = np.random.default_rng(0)
+    a = (rng.standard_normal(1 << 12) + 1j * rng.standard_normal(1 << 12))
+    a /= np.linalg.norm(a)
+    c = C.random_mixed(12, 80, 41)
+    exp = oracle.run(c, state=a)
+    with S.Sim(12, S.SIM_C128) as s:
+        s.set_state(a)
+        s.apply(c.gates)
+        np.testing.assert_allclose(s.get_state(), exp, atol=TOL128)
+
+
+@pytest.mark.parametrize("dtype", [S.SIM_C64, S.SIM_C128])
+def test_full_size_config1_properties(dtype):
+    """28-qubit diagonal-heavy stream at full size (the bench workload):
+    norm preserved and C C^dagger returns |0...0>."""
+    c = C.diag_heavy(28, 500, 1)
+    with S.Sim(28, dtype) as s:
+        s.apply(c.gates)
+        nrm = s.norm()
+        s.apply(C.inverse(c).gates)
+        idx, p = s.top_k(2)
+    tol = 1e-12 if dtype == S.SIM_C128 else 1e-5
+    assert abs(nrm - 1) < tol * 10
+    assert idx[0] == 0 and abs(p[0] - 1) < (1e-11 if dtype == S.SIM_C128 else 1e-4)
+    assert p[1] < 1e-10

@@ -1,0 +1,127 @@
+"""CPU tests of the optimizer (no GPU): the plan, run by the numpy plan
+interpreter, must equal the oracle's unoptimised gate-by-gate result; plus
+structural properties of the diagonal detector (Algorithm 8), the gate-block
+search and the fusion."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_12256_gb300 import circuits as C
+from paper_2604_12256_gb300 import svsim as S
+from plan_interp import interpret
+
+pytestmark = pytest.mark.usefixtures("built_lib")
+
+FLAG_SETS = {
+    "unfused": 0,
+    "diag": S.SIM_F_DIAG,
+    "block": S.SIM_F_BLOCK,
+    "block_fuse": S.SIM_F_BLOCK | S.SIM_F_FUSE,
+    "all": S.SIM_F_DIAG | S.SIM_F_BLOCK | S.SIM_F_FUSE | S.SIM_F_BOOST,
+}
+
+CIRCUITS = {
+    "mixed": lambda n: C.random_mixed(n, 120, 100 + n, max_k=3),
+    "layered": lambda n: C.layered(n, 6, n),
+    "diagheavy": lambda n: C.diag_heavy(n, 150, n),
+    "qft": lambda n: C.qft(n, n),
+    "qaoa": lambda n: C.qaoa(n if n % 2 == 0 else n - 1, 2, n),
+    "rzzfull": lambda n: C.rzz_full(n, n),
+}
+
+
+@pytest.mark.parametrize("flags", list(FLAG_SETS))
+@pytest.mark.parametrize("name", list(CIRCUITS))
+@pytest.mark.parametrize("n", [10, 13])
+def test_plan_is_exact_c128(name, flags, n):
+    c = CIRCUITS[name](n)
+    opt = S.default_options(flags=FLAG_SETS[flags])
+    plan = S.plan_json(c.n, c.gates, S.SIM_C128, c.basis, opt)
+    got = interpret(plan, basis=c.basis)
+    exp = oracle.run(c)
+    np.testing.assert_allclose(got, exp, atol=1e-12, rtol=0)
+
+
+@pytest.mark.parametrize("name", ["mixed", "diagheavy", "qft", "qaoa"])
+def test_plan_is_exact_c64_weights(name):
+    c = CIRCUITS[name](12)
+    plan = S.plan_json(c.n, c.gates, S.SIM_C64, c.basis)
+    got = interpret(plan, basis=c.basis)
+    exp = oracle.run(c)
+    # 32-bit phase weights: <= 2^-33 turn per term
+    np.testing.assert_allclose(got, exp, atol=2e-7, rtol=0)
+
+
+def test_small_registers_fall_back_to_gate_by_gate():
+    for n in (1, 3, 8):
+        c = C.random_mixed(n, 40, n, max_k=min(3, n))
+        plan = S.plan_json(c.n, c.gates, S.SIM_C64, c.basis)
+        assert all(op["op"] in ("gate", "phase") for op in plan["ops"])
+        np.testing.assert_allclose(interpret(plan, basis=c.basis), oracle.run(c), atol=2e-7)
+
+
+def test_blocking_cuts_sweeps():
+    c = C.diag_heavy(20, 500, 1)
+    unf = S.plan_json(c.n, c.gates, S.SIM_C64, 0, S.default_options(flags=0))
+    blk = S.plan_json(c.n, c.gates, S.SIM_C64, 0)
+    assert unf["stats"]["gates_in"] == 520
+    assert blk["stats"]["sweeps"] * 10 < unf["stats"]["ops"]
+
+
+def test_qft_needs_few_sweeps():
+    c = C.qft(30, 2)
+    p = S.plan_json(c.n, c.gates, S.SIM_C64, c.basis)
+    assert p["stats"]["sweeps"] <= 8, p["stats"]
+
+
+def test_diagonal_detector_fuses_across_barriers():
+    # diagonals separated by non-diagonal gates on other qubits (barriers that
+    # do not touch the fused set) fuse into ONE diagonal; a naive scan that
+    # stops at every non-diagonal gate would produce three.
+    g = [C.Gate("rzz", (0, 1), (0.3,)), C.Gate("h", (2,)), C.Gate("ry", (3,), (0.2,)),
+         C.Gate("rzz", (1, 4), (0.5,)), C.Gate("cp", (0, 4), (0.7,)), C.Gate("rx", (2,), (0.4,)),
+         C.Gate("rzz", (0, 4), (0.9,)), C.Gate("cp", (1, 4), (1.1,))]
+    c = C.Circuit(5, g)
+    p = S.plan_json(5, g, S.SIM_C128, 0, S.default_options(flags=S.SIM_F_DIAG))
+    phases = [op for op in p["ops"] if op["op"] == "phase"]
+    assert len(phases) == 1
+    assert p["stats"]["diag_fused"] == 4
+    np.testing.assert_allclose(interpret(p), oracle.run(c), atol=1e-13)
+
+
+def test_diagonal_detector_stops_at_stopped_qubit():
+    # RZZ(0,1), H(1) [overlaps depSet -> uList, qubit 1 stopped], CP(1,2)
+    # touches the stopped qubit -> must not be fused ahead of H(1)
+    g = [C.Gate("rzz", (0, 1), (0.3,)), C.Gate("h", (1,)), C.Gate("cp", (1, 2), (0.7,)),
+         C.Gate("rz", (0,), (0.2,))]
+    c = C.Circuit(3, g)
+    p = S.plan_json(3, g, S.SIM_C128, 0, S.default_options(flags=S.SIM_F_DIAG))
+    kinds = [op["op"] for op in p["ops"]]
+    assert kinds == ["phase", "gate", "phase"], kinds
+    np.testing.assert_allclose(interpret(p), oracle.run(c), atol=1e-13)
+
+
+def test_diagonal_detector_D_bound():
+    g = [C.Gate("rzz", (i, i + 1), (0.1 * i,)) for i in range(8)]
+    p = S.plan_json(12, g, S.SIM_C128, 0, S.default_options(flags=S.SIM_F_DIAG, max_diag_qubits=3))
+    assert len([op for op in p["ops"] if op["op"] == "phase"]) == 4
+    np.testing.assert_allclose(interpret(p), oracle.run(C.Circuit(12, g)), atol=1e-13)
+
+
+def test_every_gate_emitted_once():
+    c = C.diag_heavy(14, 300, 7)
+    p = S.plan_json(c.n, c.gates, S.SIM_C128, 0, S.default_options(flags=S.SIM_F_DIAG))
+    assert p["stats"]["gates_in"] == 314
+    # ops + absorbed == inputs: nothing lost, nothing duplicated
+    assert len(p["ops"]) + p["stats"]["diag_fused"] == 314
+
+
+def test_invalid_gates_rejected():
+    with pytest.raises(S.SimError) as e:
+        S.plan_json(4, [C.Gate("cx", (1, 1))])
+    assert e.value.code == S.SIM_EINVAL
+    with pytest.raises(S.SimError):
+        S.plan_json(4, [C.Gate("h", (4,))])
+    with pytest.raises(S.SimError) as e:
+        S.plan_json(35, [C.Gate("h", (0,))])
+    assert e.value.code == S.SIM_EUNSUPPORTED
