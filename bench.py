@@ -283,6 +283,7 @@ def run_gpu(args, rank, world, dist):
 
 
 def main():
+    global N_QUBITS, WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -290,7 +291,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--qubits", type=int, default=N_QUBITS,
+                    help="same workload on fewer qubits (small cases for ncu captures)")
     args = ap.parse_args()
+    if args.qubits != N_QUBITS:
+        WORKLOAD = WORKLOAD.replace(f"{N_QUBITS}-qubit", f"{args.qubits}-qubit")
+        N_QUBITS = args.qubits
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

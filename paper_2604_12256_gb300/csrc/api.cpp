@@ -26,6 +26,7 @@ struct sim_t {
     bool own_stream = false;
     int device = 0;
     bool product = true;        // state is the basis state `basis`
+    bool reset_pending = true;  // |basis> not yet written (lazy: a booster plan overwrites it)
     uint64_t basis = 0;
     double *d_part = nullptr;   // reduction partials
     double *d_out = nullptr;    // small device results
@@ -141,6 +142,17 @@ static void free_all(sim_t *s)
     delete s;
 }
 
+// write the pending |basis> (sim_reset is lazy)
+static int materialize(sim_t *s)
+{
+    if (!s->reset_pending) return SIM_OK;
+    long pe = prof_begin(s);
+    CK(s, launch_init_basis(s->state, s->n, s->dt == SIM_C128, s->basis, s->stream));
+    prof_end(s, pe, OPK_INIT_BASIS, (double)s->state_bytes);
+    s->reset_pending = false;
+    return SIM_OK;
+}
+
 extern "C" {
 
 int sim_default_options(sim_options *opt)
@@ -190,8 +202,8 @@ static int create_common(int n, sim_dtype dt, void *buf, size_t bytes, void *str
     }
     rc = alloc_aux(s);
     if (rc) { std::string m = s->err; free_all(s); return fail(nullptr, rc, m); }
-    e = launch_init_basis(s->state, n, dt == SIM_C128, 0, s->stream);
-    if (e != cudaSuccess) { free_all(s); return cuda_fail(nullptr, e, "init"); }
+    s->reset_pending = true;
+    s->basis = 0;
     *out = s;
     return SIM_OK;
 }
@@ -217,17 +229,16 @@ int sim_reset(sim_t *s, uint64_t basis)
 {
     if (!s) return fail(nullptr, SIM_EINVAL, "null handle");
     if (s->n < 64 && (basis >> s->n) != 0) return fail(s, SIM_EINVAL, "basis index out of range");
-    long pe = prof_begin(s);
-    CK(s, launch_init_basis(s->state, s->n, s->dt == SIM_C128, basis, s->stream));
-    prof_end(s, pe, OPK_INIT_BASIS, (double)s->state_bytes);
     s->product = true;
     s->basis = basis;
+    s->reset_pending = true;
     return SIM_OK;
 }
 
 int sim_sync(sim_t *s)
 {
     if (!s) return fail(nullptr, SIM_EINVAL, "null handle");
+    if (int rc = materialize(s)) return rc;
     CK(s, cudaStreamSynchronize(s->stream));
     return SIM_OK;
 }
@@ -235,6 +246,7 @@ int sim_sync(sim_t *s)
 int sim_state_device(sim_t *s, void **dev_ptr, void **stream)
 {
     if (!s) return fail(nullptr, SIM_EINVAL, "null handle");
+    if (int rc = materialize(s)) return rc;
     if (dev_ptr) *dev_ptr = s->state;
     if (stream) *stream = (void *)s->stream;
     return SIM_OK;
@@ -293,6 +305,17 @@ static void *buf_ptr(sim_t *s, int id) { return id == 0 ? s->state : s->sub[id];
 static int execute(sim_t *s, const Plan &p)
 {
     const bool f64 = s->dt == SIM_C128;
+    if (s->reset_pending) {
+        // a booster plan writes the whole state with its final tensor product
+        // before anything reads it; otherwise write |basis> first
+        bool overwritten = false;
+        for (const Op &o : p.ops)
+            if (o.buf == 0) { overwritten = o.kind == OPK_TENSOR; break; }
+        if (!overwritten) {
+            if (int rc = materialize(s)) return rc;
+        }
+        s->reset_pending = false;
+    }
     // 1. plan constants: matrices, diagonal factors and device programs
     Blob bl;
     std::vector<size_t> off(p.ops.size(), 0);
@@ -410,6 +433,7 @@ int sim_apply_circuit(sim_t *s, const sim_gate *gates, size_t n, const sim_optio
 int sim_norm(sim_t *s, double *out)
 {
     if (!s || !out) return fail(s, SIM_EINVAL, "null argument");
+    if (int rc = materialize(s)) return rc;
     CK(s, launch_norm(s->state, s->n, s->dt == SIM_C128, s->d_part, s->d_out, s->stream));
     CK(s, cudaMemcpyAsync(out, s->d_out, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CK(s, cudaStreamSynchronize(s->stream));
@@ -421,6 +445,7 @@ int sim_expectation(sim_t *s, const uint64_t *masks, size_t nt, double *out)
     if (!s || (nt && (!masks || !out))) return fail(s, SIM_EINVAL, "null argument");
     for (size_t i = 0; i < nt; i++)
         if (s->n < 64 && (masks[i] >> s->n)) return fail(s, SIM_EINVAL, "Z mask has bits above n");
+    if (int rc = materialize(s)) return rc;
     for (size_t b = 0; b < nt; b += 16) {
         int cnt = (int)std::min<size_t>(16, nt - b);
         CK(s, cudaMemcpyAsync(s->d_masks, masks + b, sizeof(uint64_t) * cnt, cudaMemcpyHostToDevice, s->stream));
@@ -434,6 +459,7 @@ int sim_expectation(sim_t *s, const uint64_t *masks, size_t nt, double *out)
 int sim_probabilities(sim_t *s, double *out)
 {
     if (!s || !out) return fail(s, SIM_EINVAL, "null argument");
+    if (int rc = materialize(s)) return rc;
     size_t N = (size_t)1 << s->n;
     double *d = nullptr;
     CK(s, cudaMallocAsync((void **)&d, N * sizeof(double), s->stream));
@@ -449,6 +475,7 @@ int sim_top_k(sim_t *s, int k, uint64_t *idx, double *prob)
 {
     if (!s || !idx || !prob) return fail(s, SIM_EINVAL, "null argument");
     if (k < 1 || k > 1024) return fail(s, SIM_EINVAL, "k must be in 1..1024");
+    if (int rc = materialize(s)) return rc;
     int kk = (int)std::min<uint64_t>((uint64_t)k, (uint64_t)1 << s->n);
     size_t need = topk_scratch_bytes(1024) + 2 * 1024 * 8;
     if (s->topk_bytes < need) {
@@ -472,6 +499,7 @@ int sim_get_state(sim_t *s, void *host, size_t bytes)
 {
     if (!s || !host) return fail(s, SIM_EINVAL, "null argument");
     if (bytes != s->state_bytes) return fail(s, SIM_EINVAL, "byte count must equal 2^n * bytes per amplitude");
+    if (int rc = materialize(s)) return rc;
     CK(s, cudaMemcpyAsync(host, s->state, bytes, cudaMemcpyDeviceToHost, s->stream));
     CK(s, cudaStreamSynchronize(s->stream));
     return SIM_OK;
@@ -481,6 +509,7 @@ int sim_set_state(sim_t *s, const void *host, size_t bytes)
 {
     if (!s || !host) return fail(s, SIM_EINVAL, "null argument");
     if (bytes != s->state_bytes) return fail(s, SIM_EINVAL, "byte count must equal 2^n * bytes per amplitude");
+    s->reset_pending = false;
     CK(s, cudaMemcpyAsync(s->state, host, bytes, cudaMemcpyHostToDevice, s->stream));
     CK(s, cudaStreamSynchronize(s->stream));
     s->product = false;

@@ -111,6 +111,7 @@ struct Plan {
     sim_dtype dtype = SIM_C64;
     std::vector<Op> ops;
     std::vector<int> buf_qubits;   // qubit count of each buffer id (0 = state)
+    std::vector<int> booster_queue;   // Divider output (Algorithm 6), empty if unused
     sim_plan_stats stats{};
 };
 

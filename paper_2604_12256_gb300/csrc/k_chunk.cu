@@ -52,7 +52,9 @@ __device__ __forceinline__ float2 cis_turns(uint32_t w)
 {
     float s, c;
     __sincosf((float)(int32_t)w * 1.46291807926715968e-09f, &s, &c);   // 2 pi / 2^32
-    return make_float2(c, s);
+    // one Newton step towards |c + i s| = 1 so that phases do not bias the norm
+    const float f = fmaf(-0.5f, fmaf(c, c, s * s), 1.5f);
+    return make_float2(c * f, s * f);
 }
 __device__ __forceinline__ double2 cis_turns(uint64_t w)
 {
@@ -267,9 +269,10 @@ __global__ void __launch_bounds__(1 << (C - RB)) k_chunk(typename CT<R>::T2 *__r
 #pragma unroll
             for (int i = 0; i < TB; i++) {
                 const int b = (int)ldw(sp + S_THR + i);
+                const int gb = (int)ldw(sp + S_GTHR + i);
                 if ((tid >> i) & 1) {
                     ybase |= 1u << b;
-                    x0 |= 1ull << qin[b];
+                    x0 |= 1ull << gb;
                 }
             }
             const uint32_t pb = swz<SW, C>(ybase);

@@ -386,6 +386,8 @@ static std::vector<uint32_t> encode_program(int n, int C, int RB, bool f64, uint
         pw.w[sstart + prog::S_NOPS] = (uint32_t)st.ops.size();
         for (int j = 0; j < prog::kMaxRB; j++) pw.w[sstart + prog::S_REG + j] = j < RB ? (uint32_t)reg[j] : 0;
         for (int i = 0; i < prog::kMaxC; i++) pw.w[sstart + prog::S_THR + i] = i < C - RB ? (uint32_t)thr[i] : 0;
+        for (int i = 0; i < prog::kMaxC; i++)
+            pw.w[sstart + prog::S_GTHR + i] = i < C - RB ? (uint32_t)qin[thr[i]] : 0;
         uint64_t regphys[prog::kMaxRB];
         for (int j = 0; j < RB; j++) regphys[j] = 1ull << qin[reg[j]];
         for (const SOp &op : st.ops) {
@@ -814,6 +816,85 @@ static void schedule(const std::vector<PGate> &G, int n, const sim_options &opt,
     s.run();
 }
 
+// Merge booster (Algorithm 7 with the Divider of Algorithm 6).  The state is
+// the product basis state |basis>; qubits are split into contiguous groups
+// (low qubits first).  Each group simulates the dependency-closed prefix of
+// gates that stay inside it on its own 2^w sub-state; groups then merge
+// pairwise by tensor products (the higher range is the left factor) and the
+// merged groups take their next prefixes, until one group spans all n
+// qubits.  Returns the gates left for the full state.  Readings: 0-based
+// qubit ranges; an odd group is carried up unmerged; divSize = (n+B-1)/B
+// when B > 0, else the chunk width (every leaf fits one cached chunk).
+static void run_booster(std::vector<PGate> &pend, int n, const sim_options &opt, sim_dtype dt, uint64_t basis,
+                        Plan &plan)
+{
+    int def_div = dt == SIM_C64 ? 12 : 11;
+    int divSize = opt.booster_div > 0 ? (n + opt.booster_div - 1) / opt.booster_div : def_div;
+    if (divSize < 1) divSize = 1;
+    std::vector<int> que;
+    divider(n, divSize, que);
+    if (que.size() < 2) return;
+    plan.booster_queue = que;
+    struct Grp {
+        int lo, w, buf;
+    };
+    std::vector<Grp> groups;
+    int lo = 0;
+    for (int w : que) {
+        plan.buf_qubits.push_back(w);
+        Grp g{lo, w, (int)plan.buf_qubits.size() - 1};
+        Op o;
+        o.kind = OPK_INIT_BASIS;
+        o.buf = g.buf;
+        o.n = w;
+        o.basis = (basis >> lo) & ((1ull << w) - 1);
+        plan.ops.push_back(std::move(o));
+        groups.push_back(g);
+        lo += w;
+    }
+    while (groups.size() > 1) {
+        // generation step: every group's entanglement-free prefix
+        for (const Grp &g : groups) {
+            std::vector<PGate> sub = take_group(pend, g.lo, g.w);
+            if (sub.empty()) continue;
+            for (PGate &x : sub) {
+                plan.stats.boosted_gates += x.n_src;
+                x = shift_gate(x, g.lo);
+            }
+            if (opt.flags & SIM_F_DIAG) {
+                uint64_t absorbed = 0;
+                sub = diagonal_detector(sub, opt.max_diag_qubits, absorbed);
+                plan.stats.diag_fused += absorbed;
+            }
+            schedule(sub, g.w, opt, dt, g.buf, plan);
+        }
+        // merge step: pairwise tensor products, the last merge writes the state
+        std::vector<Grp> next;
+        const bool final_merge = groups.size() == 2;
+        for (size_t i = 0; i + 1 < groups.size(); i += 2) {
+            const Grp &a = groups[i], &b = groups[i + 1];
+            int w = a.w + b.w;
+            int nb = 0;
+            if (!final_merge) {
+                plan.buf_qubits.push_back(w);
+                nb = (int)plan.buf_qubits.size() - 1;
+            }
+            Op o;
+            o.kind = OPK_TENSOR;
+            o.buf = nb;
+            o.n = w;
+            o.buf_lo = a.buf;
+            o.n_lo = a.w;
+            o.buf_hi = b.buf;
+            o.n_hi = b.w;
+            plan.ops.push_back(std::move(o));
+            next.push_back({a.lo, w, nb});
+        }
+        if (groups.size() & 1) next.push_back(groups.back());
+        groups.swap(next);
+    }
+}
+
 static void finalize_words(Plan &plan)
 {
     bool f64 = plan.dtype == SIM_C128;
@@ -896,6 +977,7 @@ static bool validate_program(const std::vector<uint32_t> &w, int n, bool diag_sw
         for (int i = 0; i < C - RB; i++) {
             uint32_t b = w[so + prog::S_THR + i];
             if ((int)b >= C || ((seen >> b) & 1)) return bad("thread bits");
+            if (w[so + prog::S_GTHR + i] != w[prog::H_QIN + b]) return bad("thread bit positions");
             seen |= 1u << b;
         }
         const uint32_t nops = w[so + prog::S_NOPS];
@@ -960,11 +1042,12 @@ bool make_plan(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_
         G.push_back(std::move(g));
     }
     plan.stats.gates_in = ng;
-    (void)basis;
+    // Algorithm 4, machine level: booster, diagonal detector, blocking + fusion
+    if ((opt.flags & SIM_F_BOOST) && basis != UINT64_MAX && ng > 0) run_booster(G, n, opt, dt, basis, plan);
     if (opt.flags & SIM_F_DIAG) {
         uint64_t absorbed = 0;
         G = diagonal_detector(G, opt.max_diag_qubits, absorbed);
-        plan.stats.diag_fused = absorbed;
+        plan.stats.diag_fused += absorbed;
     }
     schedule(G, n, opt, dt, 0, plan);
     finalize_words(plan);
@@ -1022,6 +1105,8 @@ std::string plan_json(const Plan &p)
        << ",\"bytes\":" << s.bytes << "}";
     os << ",\"buffers\":[";
     for (size_t i = 0; i < p.buf_qubits.size(); i++) os << (i ? "," : "") << p.buf_qubits[i];
+    os << "],\"booster_queue\":[";
+    for (size_t i = 0; i < p.booster_queue.size(); i++) os << (i ? "," : "") << p.booster_queue[i];
     os << "],\"ops\":[";
     for (size_t oi = 0; oi < p.ops.size(); oi++) {
         const Op &o = p.ops[oi];

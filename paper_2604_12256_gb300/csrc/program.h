@@ -47,7 +47,8 @@ enum : int {
     S_WORDS = 1,
     S_REG = 2,                 // kMaxRB words
     S_THR = S_REG + kMaxRB,    // kMaxC words
-    S_SIZE = S_THR + kMaxC     // even
+    S_GTHR = S_THR + kMaxC,    // kMaxC words: physical qubit of thread bit i (= qin[thr[i]])
+    S_SIZE = S_GTHR + kMaxC    // even
 };
 
 // op header

@@ -31,13 +31,25 @@ def gpu_run(c, dtype, flags=None, **kw):
         return s.get_state().astype(np.complex128), s.stats()
 
 
+def fidelity(a, b):
+    """|<a|b>|^2 / (<a|a><b|b>): the overlap of the two states as quantum
+    states.  complex64 gate matrices are not exactly unitary (H's 1/sqrt2
+    rounds to 0.70710677, shrinking ||psi||^2 by ~3e-8 per gate), so the
+    norm drift is checked separately (NORM64) from the state's direction."""
+    return float(abs(np.vdot(a, b)) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real))
+
+
+NORM64 = 2e-5
+
+
 def check(c, dtype, got, exp):
     err = np.max(np.abs(got - exp))
     if dtype == S.SIM_C128:
         assert err <= TOL128, err
     else:
         assert err <= TOL64, err
-        assert oracle.fidelity(exp, got) >= FID64
+        assert fidelity(exp, got) >= FID64
+        assert abs(np.vdot(got, got).real - 1.0) <= NORM64
 
 
 def test_config0_layered14_c128():
