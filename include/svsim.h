@@ -172,15 +172,17 @@ int sim_state_device(sim_t *s, void **dev_ptr, void **cuda_stream);
 int sim_last_plan_stats(const sim_t *s, sim_plan_stats *out);
 
 /* Per-kernel-kind device time, recorded with CUDA events around every launch
- * on the handle's stream while enabled.  Index = kind: 0 basis init,
+ * on the handle's stream while enabled.  Index = kind for launches on the
+ * state, 8 + kind for launches on merge-booster sub-states: 0 basis init,
  * 1 gate-by-gate dense gate, 2 gate-by-gate diagonal gate, 3 fused diagonal
  * sweep, 4 cache-blocked chunk sweep, 5 tensor product, 6 dense block,
  * 7 small-register phase.  `bytes` is the algorithmic HBM traffic of those
- * launches (2 x 2^n x bytes/amp per read+write sweep). */
+ * launches (2 x 2^n x bytes/amp per read+write sweep, 2^n x bytes/amp for a
+ * write-only tensor product or basis init). */
 typedef struct {
-    uint64_t launches[8];
-    double ms[8];
-    double bytes[8];
+    uint64_t launches[16];
+    double ms[16];
+    double bytes[16];
     uint64_t h2d_bytes;      /* plan constants copied host -> device          */
 } sim_profile;
 

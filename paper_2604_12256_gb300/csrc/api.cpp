@@ -13,6 +13,7 @@
 
 #include "internal.h"
 #include "kernels.h"
+#include "program.h"
 
 using namespace svs;
 
@@ -385,13 +386,15 @@ static int execute(sim_t *s, const Plan &p)
                                  s->stream);
             break;
         case OPK_DIAG:
-            e = launch_diag_sweep(a, o.n, f64, (const uint32_t *)cst, s->stream);
+            e = launch_diag_sweep(a, o.n, f64, (const uint32_t *)cst, prog::smem_bytes(o.words.data(), true),
+                                  s->stream);
             break;
         case OPK_PHASE_SMALL:
             e = launch_phase_small(a, o.n, f64, (const uint64_t *)cst, (int)o.terms.size(), s->stream);
             break;
         case OPK_CHUNK:
-            e = launch_chunk(a, o.n, f64, o.prog.C, (const uint32_t *)cst, s->stream);
+            e = launch_chunk(a, o.n, f64, o.prog.C, (const uint32_t *)cst, prog::smem_bytes(o.words.data(), false),
+                             s->stream);
             break;
         case OPK_TENSOR:
             e = launch_tensor(a, buf_ptr(s, o.buf_hi), o.n_hi, buf_ptr(s, o.buf_lo), o.n_lo, f64, s->stream);
@@ -399,8 +402,8 @@ static int execute(sim_t *s, const Plan &p)
         }
         if (e != cudaSuccess) return cuda_fail(s, e, "kernel launch");
         double amps = (double)((uint64_t)1 << o.n), sz = f64 ? 16.0 : 8.0;
-        double by = o.kind == OPK_TENSOR ? amps * sz : 2.0 * amps * sz;
-        prof_end(s, pe, (int)o.kind, by);
+        double by = (o.kind == OPK_TENSOR || o.kind == OPK_INIT_BASIS) ? amps * sz : 2.0 * amps * sz;
+        prof_end(s, pe, (int)o.kind + (o.buf ? 8 : 0), by);
     }
     if (s->prof_on) s->prof.h2d_bytes += bl.b.size();
     return SIM_OK;
@@ -534,9 +537,9 @@ int sim_profile_read(sim_t *s, sim_profile *out)
     for (const sim_t::Pend &p : s->prof_pend) {
         float ms = 0;
         CK(s, cudaEventElapsedTime(&ms, s->ev_pool[p.e0], s->ev_pool[p.e0 + 1]));
-        s->prof.launches[p.kind & 7]++;
-        s->prof.ms[p.kind & 7] += ms;
-        s->prof.bytes[p.kind & 7] += p.bytes;
+        s->prof.launches[p.kind & 15]++;
+        s->prof.ms[p.kind & 15] += ms;
+        s->prof.bytes[p.kind & 15] += p.bytes;
     }
     s->prof_pend.clear();
     s->ev_used = 0;

@@ -88,9 +88,17 @@ __device__ __forceinline__ void dense_apply(typename CT<R>::T2 (&v)[NR], const u
     constexpr int D = 1 << K;
     constexpr int gm = (1 << P0) | (K > 1 ? (1 << P1) : 0);
     const R *mb = (const R *)body;
-    T2 M[D * D];
+    // K = 1: the matrix stays in registers; K = 2: its 16 entries are re-read
+    // (L1 broadcast) for every group to keep register pressure down
+    T2 M1[K == 1 ? 4 : 1];
+    if constexpr (K == 1) {
 #pragma unroll
-    for (int i = 0; i < D * D; i++) M[i] = ldm(mb, i);
+        for (int i = 0; i < 4; i++) M1[i] = ldm(mb, i);
+    }
+    auto M = [&](int i) -> T2 {
+        if constexpr (K == 1) return M1[i];
+        else return ldm(mb, i);
+    };
 #pragma unroll
     for (int g = 0; g < NR; g++) {
         if (g & gm) continue;
@@ -105,10 +113,11 @@ __device__ __forceinline__ void dense_apply(typename CT<R>::T2 (&v)[NR], const u
             R re = 0, im = 0;
 #pragma unroll
             for (int c = 0; c < D; c++) {
-                re = fma(M[r * D + c].x, in[c].x, re);
-                re = fma(-M[r * D + c].y, in[c].y, re);
-                im = fma(M[r * D + c].x, in[c].y, im);
-                im = fma(M[r * D + c].y, in[c].x, im);
+                const T2 mrc = M(r * D + c);
+                re = fma(mrc.x, in[c].x, re);
+                re = fma(-mrc.y, in[c].y, re);
+                im = fma(mrc.x, in[c].y, im);
+                im = fma(mrc.y, in[c].x, im);
             }
             int off = ((r & 1) << P0) | (K > 1 ? (((r >> 1) & 1) << P1) : 0);
             v[g | off].x = re;
@@ -117,35 +126,86 @@ __device__ __forceinline__ void dense_apply(typename CT<R>::T2 (&v)[NR], const u
     }
 }
 
+// 2x2 matrices with all-real entries (H, RY): 4 flops per amplitude;
+// real diagonal and imaginary off-diagonal (RX): likewise
+template <typename R, int NR, int P, int SUB>
+__device__ __forceinline__ void dense1_special(typename CT<R>::T2 (&v)[NR], const uint32_t *body)
+{
+    const R *mb = (const R *)body;
+    // entry i of the row-major 2x2 matrix is (mb[2i], mb[2i+1])
+    const R a = __ldg(mb + (SUB == DS_REAL ? 0 : 0));
+    const R b = __ldg(mb + (SUB == DS_REAL ? 2 : 3));
+    const R c = __ldg(mb + (SUB == DS_REAL ? 4 : 5));
+    const R d = __ldg(mb + (SUB == DS_REAL ? 6 : 6));
+#pragma unroll
+    for (int g = 0; g < NR; g++) {
+        if (g & (1 << P)) continue;
+        const auto x0 = v[g], x1 = v[g | (1 << P)];
+        if constexpr (SUB == DS_REAL) {
+            v[g].x = fma(a, x0.x, b * x1.x);
+            v[g].y = fma(a, x0.y, b * x1.y);
+            v[g | (1 << P)].x = fma(c, x0.x, d * x1.x);
+            v[g | (1 << P)].y = fma(c, x0.y, d * x1.y);
+        } else {   // [[a, i b], [i c, d]]
+            v[g].x = fma(a, x0.x, -b * x1.y);
+            v[g].y = fma(a, x0.y, b * x1.x);
+            v[g | (1 << P)].x = fma(-c, x0.y, d * x1.x);
+            v[g | (1 << P)].y = fma(c, x0.x, d * x1.y);
+        }
+    }
+}
+
 // walk the (P0 < P1 < RB) combinations at compile time
 template <typename R, int NR, int RB, int K, int P0, int P1>
 struct DenseDispatch {
-    static __device__ __forceinline__ void run(int code, typename CT<R>::T2 (&v)[NR], const uint32_t *body)
+    static __device__ __forceinline__ void run(int code, int sub, typename CT<R>::T2 (&v)[NR], const uint32_t *body)
     {
         constexpr int mycode = K == 1 ? P0 : (P0 | (P1 << 3));
         if (code == mycode) {
-            dense_apply<R, NR, K, P0, P1>(v, body);
+            if constexpr (K == 1) {
+                if (sub == DS_REAL) dense1_special<R, NR, P0, DS_REAL>(v, body);
+                else if (sub == DS_RX) dense1_special<R, NR, P0, DS_RX>(v, body);
+                else dense_apply<R, NR, K, P0, P1>(v, body);
+            } else {
+                dense_apply<R, NR, K, P0, P1>(v, body);
+            }
             return;
         }
         if constexpr (K == 1) {
-            if constexpr (P0 + 1 < RB) DenseDispatch<R, NR, RB, K, P0 + 1, 0>::run(code, v, body);
+            if constexpr (P0 + 1 < RB) DenseDispatch<R, NR, RB, K, P0 + 1, 0>::run(code, sub, v, body);
         } else {
-            if constexpr (P1 + 1 < RB) DenseDispatch<R, NR, RB, K, P0, P1 + 1>::run(code, v, body);
-            else if constexpr (P0 + 2 < RB) DenseDispatch<R, NR, RB, K, P0 + 1, P0 + 2>::run(code, v, body);
+            if constexpr (P1 + 1 < RB) DenseDispatch<R, NR, RB, K, P0, P1 + 1>::run(code, sub, v, body);
+            else if constexpr (P0 + 2 < RB) DenseDispatch<R, NR, RB, K, P0 + 1, P0 + 2>::run(code, sub, v, body);
         }
     }
 };
 
+// index of the lowest set bit; folds to a constant for unrolled loop indices
+__host__ __device__ __forceinline__ constexpr int low_bit(int k)
+{
+    int j = 0;
+    while (j < 31 && !((k >> j) & 1)) j++;
+    return j;
+}
+
 // ------------------------------------------------------------ phase segment
-template <typename R, int RB>
-__device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uint64_t x0, const uint32_t *body)
+// Shared sums of a launch: cta_ph[d * S + s] (per chunk) and
+// thr_ph[(d * S + s) * T + tid] (per thread, segments d < nhoist), S = 1 + RB.
+template <typename R, int RB, int T>
+__device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uint64_t x0, const uint32_t *body,
+                                           const typename CT<R>::W *cta_ph, const typename CT<R>::W *thr_ph,
+                                           int nhoist, int tid)
 {
     using W = typename CT<R>::W;
     constexpr int NR = 1 << RB;
+    constexpr int S = 1 + RB;
+    const int d = (int)ldw(body + D_INDEX);
+    const bool hoisted = d < nhoist;
     const int nb = (int)ldw(body + D_NBASE);
     const int nm = (int)ldw(body + D_NMULTI);
     const uint32_t *t = body + D_TERMS;
-    W base = 0;
+    W base = cta_ph[d * S];
+    if (hoisted) base += thr_ph[(d * S) * T + tid];
     for (int i = 0; i < nb; i++, t += kTermWords) {
         uint64_t m = ld64(t);
         if ((x0 & m) == m) base += ldwt<R>(t + 2);
@@ -153,7 +213,8 @@ __device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uin
     W lin[RB];
 #pragma unroll
     for (int j = 0; j < RB; j++) {
-        lin[j] = 0;
+        lin[j] = cta_ph[d * S + 1 + j];
+        if (hoisted) lin[j] += thr_ph[(d * S + 1 + j) * T + tid];
         const int cnt = (int)ldw(body + D_NLIN + j);
         for (int i = 0; i < cnt; i++, t += kTermWords) {
             uint64_t m = ld64(t);
@@ -162,19 +223,66 @@ __device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uin
     }
     const uint32_t *tab = t;
     const uint32_t *mt = t + 2 * NR;
+    const int pivot = (int)ldw(body + D_PIVOT);
+    const bool tabnz = (ldw(body + D_FLAGS) & 1) != 0;
+    // walk the register index in Gray-code order: one add per amplitude
+    W ph = base;
 #pragma unroll
-    for (int m = 0; m < NR; m++) {
-        W ph = base + ldwt<R>(tab + 2 * m);
-#pragma unroll
-        for (int j = 0; j < RB; j++)
+    for (int k = 0; k < NR; k++) {
+        const int m = k ^ (k >> 1);
+        if (k > 0) {
+            const int j = low_bit(k);   // the bit that flips from k-1 to k (k is a constant here)
             if ((m >> j) & 1) ph += lin[j];
+            else ph -= lin[j];
+        }
+        if (pivot >= 0 && !((m >> pivot) & 1)) continue;   // phase 0 here
+        W p = ph;
+        if (tabnz) p += ldwt<R>(tab + 2 * m);
         for (int i = 0; i < nm; i++) {
             const uint32_t *q = mt + i * kMultiWords;
             uint64_t mm = ld64(q);
             uint32_t rm = ldw(q + 2);
-            if ((x0 & mm) == mm && ((uint32_t)m & rm) == rm) ph += ldwt<R>(q + 4);
+            if ((x0 & mm) == mm && ((uint32_t)m & rm) == rm) p += ldwt<R>(q + 4);
         }
-        v[m] = cmul(v[m], cis_turns(ph));
+        v[m] = cmul(v[m], cis_turns(p));
+    }
+}
+
+// Per-thread sums of the thread table (once per launch; each thread owns its
+// column, so no synchronisation is needed before its own use).
+template <typename R, int T>
+__device__ __forceinline__ void thread_sums(const uint32_t *prog, typename CT<R>::W *thr_ph, int nslots, int tid)
+{
+    using W = typename CT<R>::W;
+    for (int i = 0; i < nslots; i++) thr_ph[i * T + tid] = 0;
+    const uint32_t *tt = prog + ldw(prog + H_THR_OFF);
+    const int nt = (int)ldw(prog + H_NTHR);
+    for (int i = 0; i < nt; i++, tt += kThrWords) {
+        const uint32_t tm = ldw(tt + 1);
+        if (((uint32_t)tid & tm) == tm) thr_ph[ldw(tt) * T + tid] += ldwt<R>(tt + 2);
+    }
+}
+
+__device__ __forceinline__ void add_atomic(uint32_t *p, uint32_t v) { atomicAdd((unsigned int *)p, (unsigned int)v); }
+__device__ __forceinline__ void add_atomic(uint64_t *p, uint64_t v)
+{
+    atomicAdd((unsigned long long *)p, (unsigned long long)v);
+}
+
+// Per-chunk sums of the CTA table for chunk base `base` (block-wide; integer
+// adds are exact, so the atomics' order does not matter).
+template <typename R, int T>
+__device__ __forceinline__ void cta_sums(const uint32_t *prog, typename CT<R>::W *cta_ph, int nslots, uint64_t base,
+                                         int tid)
+{
+    for (int i = tid; i < nslots; i += T) cta_ph[i] = 0;
+    __syncthreads();
+    const uint32_t *ct = prog + ldw(prog + H_CTA_OFF);
+    const int nc = (int)ldw(prog + H_NCTA);
+    for (int i = tid; i < nc; i += T) {
+        const uint32_t *e = ct + i * kCtaWords;
+        const uint64_t m = ld64(e + 2);
+        if ((base & m) == m) add_atomic(&cta_ph[ldw(e)], ldwt<R>(e + 4));
     }
 }
 
@@ -184,13 +292,19 @@ __global__ void __launch_bounds__(1 << (C - RB)) k_chunk(typename CT<R>::T2 *__r
                                                          const uint32_t *__restrict__ prog, int n)
 {
     using T2 = typename CT<R>::T2;
+    using W = typename CT<R>::W;
     constexpr int TB = C - RB;
     constexpr int T = 1 << TB;
     constexpr int NR = 1 << RB;
     constexpr int SW = CT<R>::SWZ;
+    constexpr int S = 1 + RB;
     extern __shared__ __align__(16) unsigned char smraw[];
     R *sre = (R *)smraw;
     R *sim = sre + (1 << C);
+    W *cta_ph = (W *)(sim + (1 << C));
+    const int nd = (int)ldw(prog + H_NDSEG);
+    const int nhoist = (int)ldw(prog + H_NHOIST);
+    W *thr_ph = cta_ph + nd * S;
     __shared__ uint64_t s_git[NR / 2];    // global offset of load iteration `it`
     __shared__ uint32_t s_sit[NR / 2];    // swizzled smem position of `it` on the store
 
@@ -215,11 +329,13 @@ __global__ void __launch_bounds__(1 << (C - RB)) k_chunk(typename CT<R>::T2 *__r
     if (tid < NR / 2) {
         uint64_t g = 0;
         uint32_t sp = 0;
+#pragma unroll
         for (int b = 0; b < RB - 1; b++)
             if ((tid >> b) & 1) { g |= 1ull << qin[TB + 1 + b]; sp |= 1u << sperm[TB + 1 + b]; }
         s_git[tid] = g;
         s_sit[tid] = swz<SW, C>(sp);
     }
+    thread_sums<R, T>(prog, thr_ph, nhoist * S, tid);
     __syncthreads();
     const uint32_t pst_tid = swz<SW, C>(st_tid);
     const uint32_t pst_one = swz<SW, C>(st_one);
@@ -238,6 +354,7 @@ __global__ void __launch_bounds__(1 << (C - RB)) k_chunk(typename CT<R>::T2 *__r
                 fm ^= low;
             }
         }
+        cta_sums<R, T>(prog, cta_ph, nd * S, base, tid);
         // ---- load: HBM -> shared (coalesced pairs)
 #pragma unroll
         for (int it = 0; it < NR / 2; it++) {
@@ -286,25 +403,31 @@ __global__ void __launch_bounds__(1 << (C - RB)) k_chunk(typename CT<R>::T2 *__r
                 v[m].x = sre[pm];
                 v[m].y = sim[pm];
             }
-            // x0 also needs the global positions of the register bits = 0 (already 0)
             const int nops = (int)ldw(sp + S_NOPS);
             const uint32_t *op = sp + S_SIZE;
             for (int k = 0; k < nops; k++) {
                 const uint32_t hdr = ldw(op + O_HDR);
                 const int type = hdr & 0xff;
                 if (type == OP_DENSE) {
-                    const int kq = (hdr >> 8) & 0xff;
+                    const int kq = (hdr >> 8) & 0xf;
+                    const int sub = (hdr >> 12) & 0xf;
                     const int code = (int)(hdr >> 16);
-                    if (kq == 1) DenseDispatch<R, NR, RB, 1, 0, 0>::run(code, v, op + O_BODY);
-                    else DenseDispatch<R, NR, RB, 2, 0, 1>::run(code, v, op + O_BODY);
+                    if (kq == 1) DenseDispatch<R, NR, RB, 1, 0, 0>::run(code, sub, v, op + O_BODY);
+                    else DenseDispatch<R, NR, RB, 2, 0, 1>::run(code, sub, v, op + O_BODY);
                 } else {
-                    dseg_apply<R, RB>(v, x0, op + O_BODY);
+                    dseg_apply<R, RB, T>(v, x0, op + O_BODY, cta_ph, thr_ph, nhoist, tid);
                 }
                 op += ldw(op + O_WORDS);
             }
+            // make the compiler rebuild the 2^RB addresses here instead of
+            // keeping them live across the ops (register pressure)
+            uint32_t pbw = pb;
+            asm volatile("" : "+r"(pbw));
+#pragma unroll
+            for (int j = 0; j < RB; j++) asm volatile("" : "+r"(pv[j]));
 #pragma unroll
             for (int m = 0; m < NR; m++) {
-                uint32_t pm = pb;
+                uint32_t pm = pbw;
 #pragma unroll
                 for (int j = 0; j < RB; j++)
                     if ((m >> j) & 1) pm ^= pv[j];
@@ -339,76 +462,96 @@ __global__ void __launch_bounds__(128) k_diag(typename CT<R>::T2 *__restrict__ a
                                               int n)
 {
     using T2 = typename CT<R>::T2;
+    using W = typename CT<R>::W;
     constexpr int NR = 1 << RB;
     constexpr int C = 7 + RB;
+    constexpr int S = 1 + RB;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    W *cta_ph = (W *)smraw;
+    const int nd = (int)ldw(prog + H_NDSEG);
+    const int nhoist = (int)ldw(prog + H_NHOIST);
+    W *thr_ph = cta_ph + nd * S;
+    const int tid = threadIdx.x;
     const uint32_t *sp = prog + ldw(prog + H_STAGE_OFF);
     const uint32_t *op = sp + S_SIZE + O_BODY;
+    thread_sums<R, 128>(prog, thr_ph, nhoist * S, tid);
     const int64_t ntiles = (int64_t)1 << (n - C);
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint64_t x0 = ((uint64_t)tile << C) | threadIdx.x;
+        const uint64_t base = (uint64_t)tile << C;
+        cta_sums<R, 128>(prog, cta_ph, nd * S, base, tid);
+        __syncthreads();
+        const uint64_t x0 = base | (uint64_t)tid;
         T2 v[NR];
 #pragma unroll
         for (int m = 0; m < NR; m++) v[m] = __ldcs(a + x0 + ((uint64_t)m << 7));
-        dseg_apply<R, RB>(v, x0, op);
+        dseg_apply<R, RB, 128>(v, x0, op, cta_ph, thr_ph, nhoist, tid);
 #pragma unroll
         for (int m = 0; m < NR; m++) __stcs(a + x0 + ((uint64_t)m << 7), v[m]);
+        __syncthreads();
     }
 }
 
 // ------------------------------------------------------------ launchers
+static constexpr int kMaxSmem = 200 * 1024;
+
+template <typename K>
+static cudaError_t sized_grid(K kern, int threads, size_t smem, int64_t work, int &grid)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ <= 0) return cudaErrorInvalidConfiguration;
+    int64_t g = (int64_t)device_sm_count() * occ;
+    grid = (int)(g < work ? g : work);
+    return cudaSuccess;
+}
+
 template <typename R, int C, int RB>
-static cudaError_t chunk_t(void *a, int n, const uint32_t *prog, cudaStream_t st)
+static cudaError_t chunk_t(void *a, int n, const uint32_t *prog, size_t smem, cudaStream_t st)
 {
     constexpr int T = 1 << (C - RB);
-    const size_t smem = (size_t)2 * sizeof(R) << C;
-    static int occ = 0;
-    if (occ <= 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_chunk<R, C, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_chunk<R, C, RB>, T, smem);
-        if (e != cudaSuccess) return e;
-        if (occ <= 0) occ = 1;
-    }
-    int64_t nch = (int64_t)1 << (n - C);
-    int64_t grid = (int64_t)device_sm_count() * occ;
-    if (grid > nch) grid = nch;
-    k_chunk<R, C, RB><<<(int)grid, T, smem, st>>>((typename CT<R>::T2 *)a, prog, n);
+    int grid = 0;
+    cudaError_t e = sized_grid(k_chunk<R, C, RB>, T, smem, (int64_t)1 << (n - C), grid);
+    if (e != cudaSuccess) return e;
+    k_chunk<R, C, RB><<<grid, T, smem, st>>>((typename CT<R>::T2 *)a, prog, n);
     return cudaGetLastError();
 }
 
-cudaError_t launch_chunk(void *a, int n, bool f64, int C, const uint32_t *prog, cudaStream_t st)
+cudaError_t launch_chunk(void *a, int n, bool f64, int C, const uint32_t *prog, size_t smem, cudaStream_t st)
 {
+    if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
     if (!f64) {
-        if (C == 12 && n >= 12) return chunk_t<float, 12, 5>(a, n, prog, st);
-        if (C == 10 && n >= 10) return chunk_t<float, 10, 5>(a, n, prog, st);
+        if (C == 12 && n >= 12) return chunk_t<float, 12, 5>(a, n, prog, smem, st);
+        if (C == 10 && n >= 10) return chunk_t<float, 10, 5>(a, n, prog, smem, st);
     } else {
-        if (C == 11 && n >= 11) return chunk_t<double, 11, 4>(a, n, prog, st);
-        if (C == 9 && n >= 9) return chunk_t<double, 9, 4>(a, n, prog, st);
+        if (C == 11 && n >= 11) return chunk_t<double, 11, 4>(a, n, prog, smem, st);
+        if (C == 9 && n >= 9) return chunk_t<double, 9, 4>(a, n, prog, smem, st);
     }
     return cudaErrorInvalidValue;
 }
 
 template <typename R, int RB>
-static cudaError_t diag_t(void *a, int n, const uint32_t *prog, cudaStream_t st)
+static cudaError_t diag_t(void *a, int n, const uint32_t *prog, size_t smem, cudaStream_t st)
 {
     constexpr int C = 7 + RB;
     if (n < C) return cudaErrorInvalidValue;
-    static int occ = 0;
-    if (occ <= 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_diag<R, RB>, 128, 0);
-        if (e != cudaSuccess) return e;
-        if (occ <= 0) occ = 1;
-    }
-    int64_t nt = (int64_t)1 << (n - C);
-    int64_t grid = (int64_t)device_sm_count() * occ;
-    if (grid > nt) grid = nt;
-    k_diag<R, RB><<<(int)grid, 128, 0, st>>>((typename CT<R>::T2 *)a, prog, n);
+    int grid = 0;
+    cudaError_t e = sized_grid(k_diag<R, RB>, 128, smem, (int64_t)1 << (n - C), grid);
+    if (e != cudaSuccess) return e;
+    k_diag<R, RB><<<grid, 128, smem, st>>>((typename CT<R>::T2 *)a, prog, n);
     return cudaGetLastError();
 }
 
-cudaError_t launch_diag_sweep(void *a, int n, bool f64, const uint32_t *prog, cudaStream_t st)
+cudaError_t launch_diag_sweep(void *a, int n, bool f64, const uint32_t *prog, size_t smem, cudaStream_t st)
 {
-    return f64 ? diag_t<double, 4>(a, n, prog, st) : diag_t<float, 5>(a, n, prog, st);
+    if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
+    return f64 ? diag_t<double, 4>(a, n, prog, smem, st) : diag_t<float, 5>(a, n, prog, smem, st);
 }
 
 }  // namespace svs

@@ -249,31 +249,91 @@ static void stage_layout(int C, int RB, int swz, const std::vector<int> &need_re
         if (!used[b]) { thr[nt++] = b; used[b] = 1; }
 }
 
-static void encode_dseg(ProgWriter &pw, const std::vector<Term> &terms, int RB, const uint64_t *regphys,
-                        bool f64)
+// Context of one phase segment: where the register and thread bits sit in
+// this stage, the segment's number and the launch-wide term tables.
+struct DsegCtx {
+    int RB = 0, TB = 0;
+    bool f64 = false;
+    const uint64_t *regphys = nullptr;   // physical bit of register bit j
+    const int *gthr = nullptr;           // physical qubit of thread bit i
+    uint64_t freem = 0;                  // chunk-selecting qubits
+    int d = 0;                           // segment number
+    bool hoist = false;                  // thread-only terms go to the thread table
+    std::vector<uint32_t> *cta = nullptr, *thr = nullptr;
+};
+
+// Split a segment's terms: slot terms (no register bit: slot 0; one register
+// bit j: slot 1 + j) go to the CTA table when they only test chunk-selecting
+// qubits, to the thread table when they only test thread bits (and the
+// segment is hoisted), else stay in the body; register-only terms fold into
+// the 2^RB table; terms with several register bits stay in the body.
+static void encode_dseg(ProgWriter &pw, const std::vector<Term> &terms, const DsegCtx &cx)
 {
-    uint64_t regall = 0;
-    for (int j = 0; j < RB; j++) regall |= regphys[j];
+    const int RB = cx.RB;
+    const bool f64 = cx.f64;
+    uint64_t regall = 0, thrall = 0;
+    for (int j = 0; j < RB; j++) regall |= cx.regphys[j];
+    for (int i = 0; i < cx.TB; i++) thrall |= 1ull << cx.gthr[i];
     std::vector<Term> base;
     std::vector<std::vector<Term>> lin(RB);
     std::vector<std::pair<Term, uint32_t>> multi;
     std::vector<uint64_t> tab(1u << RB, 0);
+    const uint32_t S = 1 + RB;
+    auto to_tables = [&](uint32_t slot, uint64_t nonreg, uint64_t w) {
+        const uint64_t mt = nonreg & thrall, mc = nonreg & ~thrall;
+        if (mt == 0) {
+            cx.cta->push_back(cx.d * S + slot);
+            cx.cta->push_back(0);
+            cx.cta->push_back((uint32_t)mc);
+            cx.cta->push_back((uint32_t)(mc >> 32));
+            uint64_t q = qweight(w, f64);
+            cx.cta->push_back((uint32_t)q);
+            cx.cta->push_back((uint32_t)(q >> 32));
+            return true;
+        }
+        if (mc == 0 && cx.hoist) {
+            uint32_t tm = 0;
+            for (int i = 0; i < cx.TB; i++) if ((mt >> cx.gthr[i]) & 1) tm |= 1u << i;
+            cx.thr->push_back(cx.d * S + slot);
+            cx.thr->push_back(tm);
+            uint64_t q = qweight(w, f64);
+            cx.thr->push_back((uint32_t)q);
+            cx.thr->push_back((uint32_t)(q >> 32));
+            return true;
+        }
+        return false;
+    };
+    uint32_t common = (1u << RB) - 1;
     for (const Term &t : terms) {
         uint32_t rm = 0;
-        for (int j = 0; j < RB; j++) if (t.mask & regphys[j]) rm |= 1u << j;
+        for (int j = 0; j < RB; j++) if (t.mask & cx.regphys[j]) rm |= 1u << j;
+        common &= rm;
         uint64_t nonreg = t.mask & ~regall;
-        if (rm == 0) base.push_back({nonreg, t.w});
-        else if (nonreg == 0) {
+        if (rm == 0) {
+            if (!to_tables(0, nonreg, t.w)) base.push_back({nonreg, t.w});
+        } else if (nonreg == 0) {
             for (uint32_t m = 0; m < (1u << RB); m++) if ((m & rm) == rm) tab[m] += t.w;
-        } else if (popc(rm) == 1) lin[__builtin_ctz(rm)].push_back({nonreg, t.w});
-        else multi.push_back({{nonreg, t.w}, rm});
+        } else if (popc(rm) == 1) {
+            int j = __builtin_ctz(rm);
+            if (!to_tables(1 + j, nonreg, t.w)) lin[j].push_back({nonreg, t.w});
+        } else {
+            multi.push_back({{nonreg, t.w}, rm});
+        }
     }
+    // a register bit shared by every term: amplitudes without it keep phase 0
+    const int pivot = terms.empty() || common == 0 ? -1 : __builtin_ctz(common);
+    bool tabnz = false;
+    for (uint64_t x : tab) if (qweight(x, f64) != 0) tabnz = true;
     size_t start = pw.w.size();
     pw.put(prog::OP_DSEG);
     pw.put(0);   // words, patched below
     pw.put((uint32_t)base.size());
     pw.put((uint32_t)multi.size());
     for (int j = 0; j < prog::kMaxRB; j++) pw.put(j < RB ? (uint32_t)lin[j].size() : 0);
+    pw.put((uint32_t)pivot);
+    pw.put(tabnz ? 1u : 0u);
+    pw.put((uint32_t)cx.d);
+    pw.put(0);
     auto put_term = [&](const Term &t) {
         pw.put64(t.mask);
         pw.put64(qweight(t.w, f64));
@@ -315,8 +375,22 @@ static void encode_dense(ProgWriter &pw, const SOp &op, const int *reg, const in
         for (int c = 0; c < dim; c++) M2[(size_t)remap(r) * dim + remap(c)] = op.M[(size_t)r * dim + c];
     uint32_t code = 0;
     for (int i2 = 0; i2 < op.k; i2++) code |= (uint32_t)ri[order[i2]] << (3 * i2);
+    // 2x2 structure after rounding to the state precision: all-real entries
+    // (H, RY) or real diagonal with imaginary off-diagonal (RX) need half the
+    // arithmetic of a general complex matrix
+    uint32_t sub = prog::DS_GENERAL;
+    if (op.k == 1) {
+        auto rz = [&](double v) { return f64 ? v == 0.0 : (float)v == 0.0f; };
+        bool real = true, rx = true;
+        for (int i = 0; i < 4; i++) {
+            if (!rz(M2[i].imag())) real = false;
+            bool diag = (i == 0 || i == 3);
+            if (diag ? !rz(M2[i].imag()) : !rz(M2[i].real())) rx = false;
+        }
+        sub = real ? prog::DS_REAL : rx ? prog::DS_RX : prog::DS_GENERAL;
+    }
     size_t start = pw.w.size();
-    pw.put(prog::OP_DENSE | (uint32_t)op.k << 8 | code << 16);
+    pw.put(prog::OP_DENSE | (uint32_t)op.k << 8 | sub << 12 | code << 16);
     pw.put(0);
     for (const cd &z : M2) {
         if (f64) {
@@ -338,6 +412,9 @@ static void encode_dense(ProgWriter &pw, const SOp &op, const int *reg, const in
     pw.align2();
     pw.w[start + prog::O_WORDS] = (uint32_t)(pw.w.size() - start);
 }
+
+// shared-memory budget of the per-thread term table of one launch
+constexpr size_t kThreadTableBytes = 40 * 1024;
 
 // Encode one cache-blocked pass.  Q: physical chunk positions (popcount C);
 // lam_end[p]: logical qubit held by position p at the end of the block
@@ -368,6 +445,15 @@ static std::vector<uint32_t> encode_program(int n, int C, int RB, bool f64, uint
         pw.w[prog::H_SPERM + i2] = (uint32_t)src;
     }
     int swz = f64 ? 4 : 5;
+    // phase segments whose thread-only terms are summed once per launch:
+    // as many as fit the shared-memory budget of the thread table
+    int nseg = 0;
+    for (const SStage &st : stages)
+        for (const SOp &op : st.ops) nseg += op.type == 2;
+    const size_t per_seg = (size_t)(1 + RB) * ((size_t)1 << (C - RB)) * (f64 ? 8 : 4);
+    const int nhoist = (int)std::min<size_t>((size_t)nseg, kThreadTableBytes / per_seg);
+    int nd = 0;
+    std::vector<uint32_t> cta, thr_t;
     for (size_t s = 0; s < stages.size(); s++) {
         const SStage &st = stages[s];
         pw.align2();
@@ -390,13 +476,39 @@ static std::vector<uint32_t> encode_program(int n, int C, int RB, bool f64, uint
             pw.w[sstart + prog::S_GTHR + i] = i < C - RB ? (uint32_t)qin[thr[i]] : 0;
         uint64_t regphys[prog::kMaxRB];
         for (int j = 0; j < RB; j++) regphys[j] = 1ull << qin[reg[j]];
+        int gthr[prog::kMaxC];
+        for (int i = 0; i < C - RB; i++) gthr[i] = qin[thr[i]];
         for (const SOp &op : st.ops) {
-            if (op.type == 1) encode_dense(pw, op, reg, qin, RB, f64);
-            else encode_dseg(pw, op.terms, RB, regphys, f64);
+            if (op.type == 1) {
+                encode_dense(pw, op, reg, qin, RB, f64);
+            } else {
+                DsegCtx cx;
+                cx.RB = RB;
+                cx.TB = C - RB;
+                cx.f64 = f64;
+                cx.regphys = regphys;
+                cx.gthr = gthr;
+                cx.freem = freem;
+                cx.d = nd;
+                cx.hoist = nd < nhoist;
+                cx.cta = &cta;
+                cx.thr = &thr_t;
+                encode_dseg(pw, op.terms, cx);
+                nd++;
+            }
         }
         pw.align2();
         pw.w[sstart + prog::S_WORDS] = (uint32_t)(pw.w.size() - sstart);
     }
+    pw.align2();
+    pw.w[prog::H_NDSEG] = (uint32_t)nd;
+    pw.w[prog::H_NHOIST] = (uint32_t)nhoist;
+    pw.w[prog::H_CTA_OFF] = (uint32_t)pw.w.size();
+    pw.w[prog::H_NCTA] = (uint32_t)(cta.size() / prog::kCtaWords);
+    pw.w.insert(pw.w.end(), cta.begin(), cta.end());
+    pw.w[prog::H_THR_OFF] = (uint32_t)pw.w.size();
+    pw.w[prog::H_NTHR] = (uint32_t)(thr_t.size() / prog::kThrWords);
+    pw.w.insert(pw.w.end(), thr_t.begin(), thr_t.end());
     return pw.w;
 }
 
@@ -446,13 +558,19 @@ struct Scheduler {
         return r;
     }
 
+    // A ready diagonal gate is split into its monomials: each monomial is a
+    // diagonal operator on its own qubits only, so it commutes with every gate
+    // that misses them and is flushed just before the first gate that does
+    // not (the global-phase monomial floats to the end of the circuit).
     void make_pending(const PGate &g)
     {
-        PendingDiag d;
-        d.mask = phys(g.qmask);
-        d.n_src = g.n_src;
-        for (const Term &t : g.terms) d.terms.push_back({phys(t.mask), t.w});
-        pending.push_back(std::move(d));
+        for (const Term &t : g.terms) {
+            PendingDiag d;
+            d.mask = phys(t.mask);
+            d.n_src = 0;
+            d.terms.push_back({d.mask, t.w});
+            pending.push_back(std::move(d));
+        }
     }
 
     // take the pending diagonals meeting `pm` into one phase op
@@ -633,6 +751,22 @@ struct Scheduler {
             pending.clear();
             normalize_terms(all);
             if (all.empty()) return;
+            if (all.size() == 1 && all[0].mask == 0 && last_chunk_op >= 0 &&
+                last_chunk_op == (int)plan.ops.size() - 1) {
+                // only a global phase is left: scale the last dense matrix by it
+                for (int s = (int)last_stages.size() - 1; s >= 0; s--) {
+                    for (int k = (int)last_stages[s].ops.size() - 1; k >= 0; k--) {
+                        SOp &x = last_stages[s].ops[k];
+                        if (x.type != 1) continue;
+                        cd f = phase_of(all[0].w);
+                        for (cd &z : x.M) z *= f;
+                        std::memcpy(lam, last_lam, sizeof(lam));
+                        finalize_chunk(plan.ops[last_chunk_op], last_Q, last_stages);
+                        for (int i = 0; i < 64; i++) lam[i] = laminv[i] = i;
+                        return;
+                    }
+                }
+            }
             if (last_chunk_op >= 0 && last_chunk_op == (int)plan.ops.size() - 1) {
                 // fold into the end of the last block, in its load frame
                 int inv[64];
@@ -965,6 +1099,21 @@ static bool validate_program(const std::vector<uint32_t> &w, int n, bool diag_sw
         if ((int)b >= C || ((sp >> b) & 1)) return bad("store permutation");
         sp |= 1u << b;
     }
+    // launch-wide term tables
+    const uint32_t ND = w[prog::H_NDSEG], NH = w[prog::H_NHOIST], S = 1 + RB, TB = C - RB;
+    if (ND > (uint32_t)prog::kMaxDseg || NH > ND) return bad("segment counts");
+    if (prog::smem_bytes(w.data(), diag_sweep) > 200 * 1024) return bad("shared memory");
+    {
+        size_t co = w[prog::H_CTA_OFF], cn = w[prog::H_NCTA], to = w[prog::H_THR_OFF], tn = w[prog::H_NTHR];
+        if (co + cn * prog::kCtaWords > W || to + tn * prog::kThrWords > W) return bad("term tables");
+        for (size_t i = 0; i < cn; i++)
+            if (w[co + i * prog::kCtaWords] >= ND * S) return bad("CTA table slot");
+        for (size_t i = 0; i < tn; i++) {
+            if (w[to + i * prog::kThrWords] >= NH * S) return bad("thread table slot");
+            if (w[to + i * prog::kThrWords + 1] >> TB) return bad("thread table mask");
+        }
+    }
+    uint32_t nseg_seen = 0;
     for (int s = 0; s < ns; s++) {
         size_t so = w[prog::H_STAGE_OFF + s];
         if ((so & 1) || so + prog::S_SIZE > W) return bad("stage offset");
@@ -989,8 +1138,9 @@ static bool validate_program(const std::vector<uint32_t> &w, int n, bool diag_sw
             const int type = hdr & 0xff;
             if (type == prog::OP_DENSE) {
                 if (diag_sweep) return bad("dense op in a diagonal sweep");
-                const int kq = (hdr >> 8) & 0xff, code = (int)(hdr >> 16);
+                const int kq = (hdr >> 8) & 0xf, code = (int)(hdr >> 16), sub = (hdr >> 12) & 0xf;
                 if (kq < 1 || kq > kChunkMaxKEncoded) return bad("dense arity");
+                if (sub > prog::DS_RX || (sub != prog::DS_GENERAL && kq != 1)) return bad("dense subtype");
                 int prev = -1;
                 for (int i = 0; i < kq; i++) {
                     int p = (code >> (3 * i)) & 7;
@@ -1003,6 +1153,9 @@ static bool validate_program(const std::vector<uint32_t> &w, int n, bool diag_sw
             } else if (type == prog::OP_DSEG) {
                 if (len < (size_t)prog::O_BODY + prog::D_TERMS) return bad("phase header");
                 const uint32_t *b = &w[op + prog::O_BODY];
+                if ((int32_t)b[prog::D_PIVOT] < -1 || (int32_t)b[prog::D_PIVOT] >= RB) return bad("phase pivot");
+                if (b[prog::D_FLAGS] > 1) return bad("phase flags");
+                if (b[prog::D_INDEX] != nseg_seen++) return bad("phase segment number");
                 size_t nterm = b[prog::D_NBASE];
                 for (int j = 0; j < prog::kMaxRB; j++) {
                     if (j >= RB && b[prog::D_NLIN + j]) return bad("phase lin count");

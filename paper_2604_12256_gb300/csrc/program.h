@@ -38,8 +38,24 @@ enum : int {
     H_QIN = 8,           // kMaxC words
     H_SPERM = H_QIN + kMaxC,
     H_STAGE_OFF = H_SPERM + kMaxC,   // kMaxStages words
-    H_SIZE = H_STAGE_OFF + kMaxStages
+    // Phase segments are numbered 0..ND-1.  Their terms on chunk-selecting
+    // (free) qubits only are summed once per chunk (CTA table); terms on
+    // thread bits only are summed once per launch per thread (thread table,
+    // for segments < NHOIST); the rest stay in the segment body.
+    H_NDSEG = H_STAGE_OFF + kMaxStages,
+    H_NHOIST,
+    H_CTA_OFF,           // CTA table: word offset, count (kCtaWords each)
+    H_NCTA,
+    H_THR_OFF,           // thread table: word offset, count (kThrWords each)
+    H_NTHR,
+    H_SIZE
 };
+// CTA-table entry: slot (= d * (1 + RB) + s, s = 0 base / 1 + j linear in
+// register bit j), 0, mask_lo, mask_hi, w_lo, w_hi
+constexpr int kCtaWords = 6;
+// thread-table entry: slot, mask over the thread-index bits, w_lo, w_hi
+constexpr int kThrWords = 4;
+constexpr int kMaxDseg = 64;
 
 // stage
 enum : int {
@@ -61,14 +77,31 @@ enum : int {
     D_NBASE = 0,          // terms on thread/chunk bits only
     D_NMULTI = 1,         // terms with >= 2 register bits and other bits
     D_NLIN = 2,           // kMaxRB counts: terms with register bit j and other bits
-    D_TERMS = D_NLIN + kMaxRB   // even
+    D_PIVOT = D_NLIN + kMaxRB,   // register bit present in every term, or -1:
+                                 // then only amplitudes with that bit set change
+    D_FLAGS = D_PIVOT + 1,       // bit 0: the register-only table is not all zero
+    D_INDEX = D_FLAGS + 1,       // segment number d
+    D_PAD = D_INDEX + 1,
+    D_TERMS = D_PAD + 1          // even
 };
+// dense op subtypes (hdr bits 12..15), for k = 1
+enum : int { DS_GENERAL = 0, DS_REAL = 1, DS_RX = 2 };
 // term (4 words): mask_lo, mask_hi, w_lo, w_hi   (mask over physical qubits,
 //                 register bits removed; w: uint32 in w_lo or uint64)
 // then reg table: 2^RB entries x 2 words (phase of the register-only terms)
 // multi term (6 words): mask_lo, mask_hi, regmask, 0, w_lo, w_hi
 constexpr int kTermWords = 4;
 constexpr int kMultiWords = 6;
+
+// Dynamic shared memory of a launch of this program: the chunk's re/im planes
+// (chunk kernel only), the per-chunk CTA sums and the per-thread sums.
+inline size_t smem_bytes(const uint32_t *w, bool diag_sweep)
+{
+    const size_t C = w[H_C], RB = w[H_RB], wb = w[H_WBYTES];
+    const size_t T = (size_t)1 << (C - RB), S = 1 + RB;
+    const size_t planes = diag_sweep ? 0 : 2 * ((size_t)1 << C) * wb;
+    return planes + (size_t)w[H_NDSEG] * S * wb + (size_t)w[H_NHOIST] * S * T * wb;
+}
 
 }  // namespace prog
 }  // namespace svs

@@ -53,14 +53,19 @@ class sim_plan_stats(ctypes.Structure):
 
 
 class sim_profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_uint64 * 8), ("ms", ctypes.c_double * 8), ("bytes", ctypes.c_double * 8),
+    _fields_ = [("launches", ctypes.c_uint64 * 16), ("ms", ctypes.c_double * 16), ("bytes", ctypes.c_double * 16),
                 ("h2d_bytes", ctypes.c_uint64)]
 
     KINDS = ("init", "gate", "gate_diag", "diag", "chunk", "tensor", "dense", "phase_small")
 
     def asdict(self):
-        return {k: {"launches": int(self.launches[i]), "ms": float(self.ms[i]), "bytes": float(self.bytes[i])}
-                for i, k in enumerate(self.KINDS)} | {"h2d_bytes": int(self.h2d_bytes)}
+        d = {}
+        for i, k in enumerate(self.KINDS):
+            d[k] = {"launches": int(self.launches[i]), "ms": float(self.ms[i]), "bytes": float(self.bytes[i])}
+            d["sub_" + k] = {"launches": int(self.launches[8 + i]), "ms": float(self.ms[8 + i]),
+                             "bytes": float(self.bytes[8 + i])}
+        d["h2d_bytes"] = int(self.h2d_bytes)
+        return d
 
 
 class SimError(RuntimeError):
