@@ -176,6 +176,8 @@ def run_gpu(args, rank, world, dist):
     stream = torch.cuda.current_stream()
     sim = S.Sim(N_QUBITS, S.SIM_C64, dev_buf=buf.data_ptr(), nbytes=buf.numel() * 4, stream=stream.cuda_stream)
     opt = S.default_options()
+    if args.register_bits:
+        opt.register_bits = args.register_bits
 
     def step():
         sim.reset(0)
@@ -291,6 +293,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--register-bits", type=int, default=0,
+                    help="chunk bits per thread in the cache-blocked kernel (0 = library default)")
     ap.add_argument("--qubits", type=int, default=N_QUBITS,
                     help="same workload on fewer qubits (small cases for ncu captures)")
     args = ap.parse_args()

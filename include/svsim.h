@@ -97,7 +97,8 @@ typedef struct {
     uint32_t flags;        /* SIM_F_* (default SIM_F_DIAG|BOOST|BLOCK|FUSE)       */
     int dense_precision;   /* SIM_DENSE_* for the tensor-core path                 */
     int max_stages;        /* register stages per cached chunk (default 4)         */
-    int reserved[5];
+    int register_bits;     /* chunk bits held in registers per thread (0 = default) */
+    int reserved[4];
 } sim_options;
 
 /* Counts of the last executed plan (Section 5's "state vector updates"). */

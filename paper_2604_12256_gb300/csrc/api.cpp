@@ -393,7 +393,8 @@ static int execute(sim_t *s, const Plan &p)
             e = launch_phase_small(a, o.n, f64, (const uint64_t *)cst, (int)o.terms.size(), s->stream);
             break;
         case OPK_CHUNK:
-            e = launch_chunk(a, o.n, f64, o.prog.C, (const uint32_t *)cst, prog::smem_bytes(o.words.data(), false),
+            e = launch_chunk(a, o.n, f64, o.prog.C, o.prog.RB, (const uint32_t *)cst,
+                             prog::smem_bytes(o.words.data(), false),
                              s->stream);
             break;
         case OPK_TENSOR:

@@ -36,16 +36,30 @@ template <> struct CT<double> {
     static constexpr int SWZ = 4;
 };
 
-__device__ __forceinline__ uint32_t ldw(const uint32_t *p) { return __ldg(p); }
-__device__ __forceinline__ uint64_t ld64(const uint32_t *p) { return (uint64_t)__ldg(p) | ((uint64_t)__ldg(p + 1) << 32); }
+// Program words are read from the CTA's shared-memory copy of the program.
+__device__ __forceinline__ uint32_t ldw(const uint32_t *p) { return *p; }
+__device__ __forceinline__ uint64_t ld64(const uint32_t *p) { return (uint64_t)p[0] | ((uint64_t)p[1] << 32); }
+
+using namespace prog;
 
 template <typename R> __device__ __forceinline__ typename CT<R>::W ldwt(const uint32_t *p);
-template <> __device__ __forceinline__ uint32_t ldwt<float>(const uint32_t *p) { return __ldg(p); }
+template <> __device__ __forceinline__ uint32_t ldwt<float>(const uint32_t *p) { return *p; }
 template <> __device__ __forceinline__ uint64_t ldwt<double>(const uint32_t *p) { return ld64(p); }
 
 // complex matrix element i of a dense op body
-__device__ __forceinline__ float2 ldm(const float *b, int i) { return make_float2(__ldg(b + 2 * i), __ldg(b + 2 * i + 1)); }
-__device__ __forceinline__ double2 ldm(const double *b, int i) { return make_double2(__ldg(b + 2 * i), __ldg(b + 2 * i + 1)); }
+__device__ __forceinline__ float2 ldm(const float *b, int i) { return make_float2(b[2 * i], b[2 * i + 1]); }
+__device__ __forceinline__ double2 ldm(const double *b, int i) { return make_double2(b[2 * i], b[2 * i + 1]); }
+
+// stage the program (H_WORDS words, 16-byte aligned in both spaces) in shared memory
+template <int T>
+__device__ __forceinline__ void stage_program(const uint32_t *__restrict__ g, uint32_t *s, int tid)
+{
+    const int nw = (int)__ldg(g + H_WORDS);
+    const uint4 *g4 = (const uint4 *)g;
+    uint4 *s4 = (uint4 *)s;
+    for (int i = tid; i < (nw >> 2); i += T) s4[i] = __ldg(g4 + i);
+    for (int i = (nw & ~3) + tid; i < nw; i += T) s[i] = __ldg(g + i);
+}
 
 // exp(2 pi i w / 2^bits) for the weight type
 __device__ __forceinline__ float2 cis_turns(uint32_t w)
@@ -133,10 +147,11 @@ __device__ __forceinline__ void dense1_special(typename CT<R>::T2 (&v)[NR], cons
 {
     const R *mb = (const R *)body;
     // entry i of the row-major 2x2 matrix is (mb[2i], mb[2i+1])
-    const R a = __ldg(mb + (SUB == DS_REAL ? 0 : 0));
-    const R b = __ldg(mb + (SUB == DS_REAL ? 2 : 3));
-    const R c = __ldg(mb + (SUB == DS_REAL ? 4 : 5));
-    const R d = __ldg(mb + (SUB == DS_REAL ? 6 : 6));
+    // (the op body is in the shared-memory copy of the program: plain loads)
+    const R a = mb[0];
+    const R b = mb[SUB == DS_REAL ? 2 : 3];
+    const R c = mb[SUB == DS_REAL ? 4 : 5];
+    const R d = mb[6];
 #pragma unroll
     for (int g = 0; g < NR; g++) {
         if (g & (1 << P)) continue;
@@ -223,21 +238,35 @@ __device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uin
     }
     const uint32_t *tab = t;
     const uint32_t *mt = t + 2 * NR;
-    const int pivot = (int)ldw(body + D_PIVOT);
+    // (the pivot bit of the segment header is not used here: applying
+    // cis(0) = 1 to the amplitudes it would skip is exact)
     const bool tabnz = (ldw(body + D_FLAGS) & 1) != 0;
-    // walk the register index in Gray-code order: one add per amplitude
+    if (nm == 0 && !tabnz) {
+        // the common case: walk the register index in Gray-code order, one
+        // add per amplitude
+        W ph = base;
+#pragma unroll
+        for (int k = 0; k < NR; k++) {
+            const int m = k ^ (k >> 1);
+            if (k > 0) {
+                const int j = low_bit(k);   // the bit that flips from k-1 to k (k is a constant here)
+                if ((m >> j) & 1) ph += lin[j];
+                else ph -= lin[j];
+            }
+            v[m] = cmul(v[m], cis_turns(ph));
+        }
+        return;
+    }
     W ph = base;
 #pragma unroll
     for (int k = 0; k < NR; k++) {
         const int m = k ^ (k >> 1);
         if (k > 0) {
-            const int j = low_bit(k);   // the bit that flips from k-1 to k (k is a constant here)
+            const int j = low_bit(k);
             if ((m >> j) & 1) ph += lin[j];
             else ph -= lin[j];
         }
-        if (pivot >= 0 && !((m >> pivot) & 1)) continue;   // phase 0 here
-        W p = ph;
-        if (tabnz) p += ldwt<R>(tab + 2 * m);
+        W p = ph + ldwt<R>(tab + 2 * m);
         for (int i = 0; i < nm; i++) {
             const uint32_t *q = mt + i * kMultiWords;
             uint64_t mm = ld64(q);
@@ -288,8 +317,8 @@ __device__ __forceinline__ void cta_sums(const uint32_t *prog, typename CT<R>::W
 
 // ------------------------------------------------------------ K4 chunk sweep
 template <typename R, int C, int RB>
-__global__ void __launch_bounds__(1 << (C - RB)) k_chunk(typename CT<R>::T2 *__restrict__ a,
-                                                         const uint32_t *__restrict__ prog, int n)
+__global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 2 : 8) k_chunk(typename CT<R>::T2 *__restrict__ a,
+                                                         const uint32_t *__restrict__ gprog, int n)
 {
     using T2 = typename CT<R>::T2;
     using W = typename CT<R>::W;
@@ -301,14 +330,17 @@ __global__ void __launch_bounds__(1 << (C - RB)) k_chunk(typename CT<R>::T2 *__r
     extern __shared__ __align__(16) unsigned char smraw[];
     R *sre = (R *)smraw;
     R *sim = sre + (1 << C);
-    W *cta_ph = (W *)(sim + (1 << C));
+    uint32_t *prog = (uint32_t *)(sim + (1 << C));
+    const int tid = threadIdx.x;
+    stage_program<T>(gprog, prog, tid);
+    __syncthreads();
     const int nd = (int)ldw(prog + H_NDSEG);
     const int nhoist = (int)ldw(prog + H_NHOIST);
-    W *thr_ph = cta_ph + nd * S;
+    W *cta_ph = (W *)(prog + ((ldw(prog + H_WORDS) + 3) & ~3u));
+    W *thr_ph = (W *)((unsigned char *)cta_ph + (((size_t)nd * S * sizeof(W) + 15) & ~(size_t)15));
     __shared__ uint64_t s_git[NR / 2];    // global offset of load iteration `it`
     __shared__ uint32_t s_sit[NR / 2];    // swizzled smem position of `it` on the store
 
-    const int tid = threadIdx.x;
     int qin[C];
 #pragma unroll
     for (int i = 0; i < C; i++) qin[i] = (int)ldw(prog + H_QIN + i);
@@ -336,63 +368,83 @@ __global__ void __launch_bounds__(1 << (C - RB)) k_chunk(typename CT<R>::T2 *__r
         s_sit[tid] = swz<SW, C>(sp);
     }
     thread_sums<R, T>(prog, thr_ph, nhoist * S, tid);
+    // this thread's part of every stage's layout (the same for all chunks)
+    uint64_t *s_x0 = (uint64_t *)((unsigned char *)thr_ph + (((size_t)nhoist * S * T * sizeof(W) + 15) & ~(size_t)15));
+    uint32_t *s_pb = (uint32_t *)(s_x0 + (size_t)nst * T);
+    for (int s = 0; s < nst; s++) {
+        const uint32_t *sp = prog + ldw(prog + H_STAGE_OFF + s);
+        uint32_t ybase = 0;
+        uint64_t x0t = 0;
+        for (int i = 0; i < TB; i++) {
+            if ((tid >> i) & 1) {
+                ybase |= 1u << ldw(sp + S_THR + i);
+                x0t |= 1ull << ldw(sp + S_GTHR + i);
+            }
+        }
+        s_x0[s * T + tid] = x0t;
+        s_pb[s * T + tid] = swz<SW, C>(ybase);
+    }
     __syncthreads();
     const uint32_t pst_tid = swz<SW, C>(st_tid);
     const uint32_t pst_one = swz<SW, C>(st_one);
     const uint32_t pld_tid = swz<SW, C>((uint32_t)tid << 1);
 
     const int64_t nchunks = (int64_t)1 << (n - C);
-    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        // chunk base: spread the chunk number over the free (non-chunk) qubits
-        uint64_t base = 0;
-        {
-            uint64_t fm = freem, cv = (uint64_t)ch;
-            while (fm) {
-                uint64_t low = fm & (~fm + 1);
-                if (cv & 1) base |= low;
-                cv >>= 1;
-                fm ^= low;
-            }
+    // chunk base: spread the chunk number over the free (non-chunk) qubits
+    auto chunk_base = [&](int64_t chn) {
+        uint64_t b = 0, fm = freem, cv = (uint64_t)chn;
+        while (fm) {
+            uint64_t low = fm & (~fm + 1);
+            if (cv & 1) b |= low;
+            cv >>= 1;
+            fm ^= low;
         }
-        cta_sums<R, T>(prog, cta_ph, nd * S, base, tid);
-        // ---- load: HBM -> shared (coalesced pairs)
+        return b;
+    };
+    // coalesced loads of one chunk's amplitude pairs into registers
+    auto load_regs = [&](T2 (&dst)[NR], uint64_t b) {
 #pragma unroll
         for (int it = 0; it < NR / 2; it++) {
-            const uint64_t g = base | g_tid | s_git[it];
-            const uint32_t p = pld_tid ^ swz<SW, C>((uint32_t)it << (TB + 1));
-            T2 v0, v1;
+            const uint64_t g = b | g_tid | s_git[it];
             if constexpr (sizeof(R) == 4) {
                 float4 q = __ldcs((const float4 *)(a + g));
-                v0 = make_float2(q.x, q.y);
-                v1 = make_float2(q.z, q.w);
+                dst[2 * it] = make_float2(q.x, q.y);
+                dst[2 * it + 1] = make_float2(q.z, q.w);
             } else {
-                v0 = __ldcs(a + g);
-                v1 = __ldcs(a + g + 1);
+                dst[2 * it] = __ldcs(a + g);
+                dst[2 * it + 1] = __ldcs(a + g + 1);
             }
-            sre[p] = v0.x;
-            sim[p] = v0.y;
-            sre[p ^ 1] = v1.x;
-            sim[p ^ 1] = v1.y;
         }
+    };
+    // register double buffer: the next chunk's amplitudes are in flight
+    // while this chunk goes through its stages
+    T2 pf[NR];
+    int64_t ch = blockIdx.x;
+    uint64_t base = chunk_base(ch);
+    if (ch < nchunks) load_regs(pf, base);
+    for (; ch < nchunks; ch += gridDim.x) {
+        // ---- the prefetched chunk -> shared
+#pragma unroll
+        for (int it = 0; it < NR / 2; it++) {
+            const uint32_t p = pld_tid ^ swz<SW, C>((uint32_t)it << (TB + 1));
+            sre[p] = pf[2 * it].x;
+            sim[p] = pf[2 * it].y;
+            sre[p ^ 1] = pf[2 * it + 1].x;
+            sim[p ^ 1] = pf[2 * it + 1].y;
+        }
+        cta_sums<R, T>(prog, cta_ph, nd * S, base, tid);
         __syncthreads();
+        const int64_t nch = ch + gridDim.x;
+        const uint64_t nbase = nch < nchunks ? chunk_base(nch) : 0;
+        if (nch < nchunks) load_regs(pf, nbase);
         // ---- register stages
         for (int s = 0; s < nst; s++) {
             const uint32_t *sp = prog + ldw(prog + H_STAGE_OFF + s);
             uint32_t pv[RB];
 #pragma unroll
-            for (int j = 0; j < RB; j++) pv[j] = swz<SW, C>(1u << ldw(sp + S_REG + j));
-            uint32_t ybase = 0;
-            uint64_t x0 = base;
-#pragma unroll
-            for (int i = 0; i < TB; i++) {
-                const int b = (int)ldw(sp + S_THR + i);
-                const int gb = (int)ldw(sp + S_GTHR + i);
-                if ((tid >> i) & 1) {
-                    ybase |= 1u << b;
-                    x0 |= 1ull << gb;
-                }
-            }
-            const uint32_t pb = swz<SW, C>(ybase);
+            for (int j = 0; j < RB; j++) pv[j] = ldw(sp + S_PV + j);
+            const uint64_t x0 = base | s_x0[s * T + tid];
+            const uint32_t pb = s_pb[s * T + tid];
             T2 v[NR];
 #pragma unroll
             for (int m = 0; m < NR; m++) {
@@ -451,6 +503,7 @@ __global__ void __launch_bounds__(1 << (C - RB)) k_chunk(typename CT<R>::T2 *__r
             }
         }
         __syncthreads();
+        base = nbase;
     }
 }
 
@@ -458,7 +511,7 @@ __global__ void __launch_bounds__(1 << (C - RB)) k_chunk(typename CT<R>::T2 *__r
 // tile of 2^C consecutive amplitudes, C = 7 + RB: thread t holds amplitudes
 // tile + t + m * 128 (register bits on top -> each warp load is contiguous)
 template <typename R, int RB>
-__global__ void __launch_bounds__(128) k_diag(typename CT<R>::T2 *__restrict__ a, const uint32_t *__restrict__ prog,
+__global__ void __launch_bounds__(128) k_diag(typename CT<R>::T2 *__restrict__ a, const uint32_t *__restrict__ gprog,
                                               int n)
 {
     using T2 = typename CT<R>::T2;
@@ -467,11 +520,14 @@ __global__ void __launch_bounds__(128) k_diag(typename CT<R>::T2 *__restrict__ a
     constexpr int C = 7 + RB;
     constexpr int S = 1 + RB;
     extern __shared__ __align__(16) unsigned char smraw[];
-    W *cta_ph = (W *)smraw;
+    uint32_t *prog = (uint32_t *)smraw;
+    const int tid = threadIdx.x;
+    stage_program<128>(gprog, prog, tid);
+    __syncthreads();
     const int nd = (int)ldw(prog + H_NDSEG);
     const int nhoist = (int)ldw(prog + H_NHOIST);
-    W *thr_ph = cta_ph + nd * S;
-    const int tid = threadIdx.x;
+    W *cta_ph = (W *)(prog + ((ldw(prog + H_WORDS) + 3) & ~3u));
+    W *thr_ph = (W *)((unsigned char *)cta_ph + (((size_t)nd * S * sizeof(W) + 15) & ~(size_t)15));
     const uint32_t *sp = prog + ldw(prog + H_STAGE_OFF);
     const uint32_t *op = sp + S_SIZE + O_BODY;
     thread_sums<R, 128>(prog, thr_ph, nhoist * S, tid);
@@ -494,10 +550,10 @@ __global__ void __launch_bounds__(128) k_diag(typename CT<R>::T2 *__restrict__ a
 // ------------------------------------------------------------ launchers
 static constexpr int kMaxSmem = 200 * 1024;
 
+// `attr` is per kernel instantiation (kernels of one signature share K)
 template <typename K>
-static cudaError_t sized_grid(K kern, int threads, size_t smem, int64_t work, int &grid)
+static cudaError_t sized_grid(K kern, bool &attr, int threads, size_t smem, int64_t work, int &grid)
 {
-    static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
         if (e != cudaSuccess) return e;
@@ -516,22 +572,25 @@ template <typename R, int C, int RB>
 static cudaError_t chunk_t(void *a, int n, const uint32_t *prog, size_t smem, cudaStream_t st)
 {
     constexpr int T = 1 << (C - RB);
+    static bool attr = false;
     int grid = 0;
-    cudaError_t e = sized_grid(k_chunk<R, C, RB>, T, smem, (int64_t)1 << (n - C), grid);
+    cudaError_t e = sized_grid(k_chunk<R, C, RB>, attr, T, smem, (int64_t)1 << (n - C), grid);
     if (e != cudaSuccess) return e;
     k_chunk<R, C, RB><<<grid, T, smem, st>>>((typename CT<R>::T2 *)a, prog, n);
     return cudaGetLastError();
 }
 
-cudaError_t launch_chunk(void *a, int n, bool f64, int C, const uint32_t *prog, size_t smem, cudaStream_t st)
+cudaError_t launch_chunk(void *a, int n, bool f64, int C, int RB, const uint32_t *prog, size_t smem,
+                         cudaStream_t st)
 {
     if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
     if (!f64) {
-        if (C == 12 && n >= 12) return chunk_t<float, 12, 5>(a, n, prog, smem, st);
-        if (C == 10 && n >= 10) return chunk_t<float, 10, 5>(a, n, prog, smem, st);
+        if (C == 12 && RB == 5 && n >= 12) return chunk_t<float, 12, 5>(a, n, prog, smem, st);
+        if (C == 12 && RB == 4 && n >= 12) return chunk_t<float, 12, 4>(a, n, prog, smem, st);
+        if (C == 10 && RB == 5 && n >= 10) return chunk_t<float, 10, 5>(a, n, prog, smem, st);
     } else {
-        if (C == 11 && n >= 11) return chunk_t<double, 11, 4>(a, n, prog, smem, st);
-        if (C == 9 && n >= 9) return chunk_t<double, 9, 4>(a, n, prog, smem, st);
+        if (C == 11 && RB == 4 && n >= 11) return chunk_t<double, 11, 4>(a, n, prog, smem, st);
+        if (C == 9 && RB == 4 && n >= 9) return chunk_t<double, 9, 4>(a, n, prog, smem, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -541,8 +600,9 @@ static cudaError_t diag_t(void *a, int n, const uint32_t *prog, size_t smem, cud
 {
     constexpr int C = 7 + RB;
     if (n < C) return cudaErrorInvalidValue;
+    static bool attr = false;
     int grid = 0;
-    cudaError_t e = sized_grid(k_diag<R, RB>, 128, smem, (int64_t)1 << (n - C), grid);
+    cudaError_t e = sized_grid(k_diag<R, RB>, attr, 128, smem, (int64_t)1 << (n - C), grid);
     if (e != cudaSuccess) return e;
     k_diag<R, RB><<<grid, 128, smem, st>>>((typename CT<R>::T2 *)a, prog, n);
     return cudaGetLastError();

@@ -52,7 +52,8 @@ cudaError_t launch_topk(const void *a, int n, bool is_f64, int k, void *scratch,
 // is a device program written by the encoder in program.h.
 // `smem` = prog::smem_bytes() of the program (dynamic shared memory).
 cudaError_t launch_diag_sweep(void *a, int n, bool is_f64, const uint32_t *prog, size_t smem, cudaStream_t st);
-cudaError_t launch_chunk(void *a, int n, bool is_f64, int C, const uint32_t *prog, size_t smem, cudaStream_t st);
+cudaError_t launch_chunk(void *a, int n, bool is_f64, int C, int RB, const uint32_t *prog, size_t smem,
+                         cudaStream_t st);
 
 // Phase polynomial on small registers: one thread per amplitude sums the
 // nt terms (device array of {mask, w} pairs, uint64 turns).

@@ -44,11 +44,16 @@ void fill_default_options(sim_options &o)
     o.max_stages = 4;
 }
 
-// Instantiated chunk kernels: (C, RB) = (12,5) / (10,5) for complex64 and
-// (11,4) / (9,4) for complex128.
-static bool chunk_shape(int n, sim_dtype dt, int want_c, int &C, int &RB)
+// Instantiated chunk kernels: (C, RB) = (12,5) / (10,5) / (12,4) for
+// complex64 and (11,4) / (9,4) for complex128.
+static bool chunk_shape(int n, sim_dtype dt, int want_c, int want_rb, int &C, int &RB)
 {
     if (dt == SIM_C64) {
+        if (want_rb != 5 && n >= 12 && (want_c <= 0 || want_c >= 12)) {
+            C = 12;
+            RB = 4;
+            return true;
+        }
         RB = 5;
         int cands[2] = {12, 10};
         for (int c : cands)
@@ -414,7 +419,7 @@ static void encode_dense(ProgWriter &pw, const SOp &op, const int *reg, const in
 }
 
 // shared-memory budget of the per-thread term table of one launch
-constexpr size_t kThreadTableBytes = 40 * 1024;
+constexpr size_t kThreadTableBytes = 24 * 1024;
 
 // Encode one cache-blocked pass.  Q: physical chunk positions (popcount C);
 // lam_end[p]: logical qubit held by position p at the end of the block
@@ -474,6 +479,8 @@ static std::vector<uint32_t> encode_program(int n, int C, int RB, bool f64, uint
         for (int i = 0; i < prog::kMaxC; i++) pw.w[sstart + prog::S_THR + i] = i < C - RB ? (uint32_t)thr[i] : 0;
         for (int i = 0; i < prog::kMaxC; i++)
             pw.w[sstart + prog::S_GTHR + i] = i < C - RB ? (uint32_t)qin[thr[i]] : 0;
+        for (int j = 0; j < prog::kMaxRB; j++)
+            pw.w[sstart + prog::S_PV + j] = j < RB ? prog::swizzle(1u << reg[j], C, swz) : 0;
         uint64_t regphys[prog::kMaxRB];
         for (int j = 0; j < RB; j++) regphys[j] = 1ull << qin[reg[j]];
         int gthr[prog::kMaxC];
@@ -509,6 +516,8 @@ static std::vector<uint32_t> encode_program(int n, int C, int RB, bool f64, uint
     pw.w[prog::H_THR_OFF] = (uint32_t)pw.w.size();
     pw.w[prog::H_NTHR] = (uint32_t)(thr_t.size() / prog::kThrWords);
     pw.w.insert(pw.w.end(), thr_t.begin(), thr_t.end());
+    pw.align2();
+    pw.w[prog::H_WORDS] = (uint32_t)pw.w.size();
     return pw.w;
 }
 
@@ -595,6 +604,13 @@ struct Scheduler {
         return any;
     }
 
+    bool pending_meets(uint64_t pm) const
+    {
+        for (const PendingDiag &d : pending)
+            if (d.mask & pm) return true;
+        return false;
+    }
+
     static bool meets(const SOp &x, uint64_t pm)
     {
         if (x.type == 1) return (x.pmask & pm) != 0;
@@ -664,46 +680,73 @@ struct Scheduler {
             uint64_t Q = lowL;
             for (int s = 0; s < cfg.Smax; s++) {
                 SStage st;
-                uint64_t blocked = 0;
                 bool placed = false;
-                for (size_t i = first; i < G.size(); i++) {
-                    if (done[i]) continue;
-                    const PGate &g = G[i];
-                    if (g.qmask & blocked) { blocked |= g.qmask; continue; }
-                    if (g.diag) { make_pending(g); done[i] = 1; continue; }
-                    uint64_t P = phys(g.qmask);
-                    if (g.swap) {
-                        if (popc((Q | P) & ~lowL) <= cfg.C - cfg.L) {
-                            Q |= P;
-                            int pa = laminv[g.q[0]], pb = laminv[g.q[1]];
-                            std::swap(lam[pa], lam[pb]);
-                            laminv[lam[pa]] = pa;
-                            laminv[lam[pb]] = pb;
-                            done[i] = 1;
-                            placed = true;
-                        } else {
-                            blocked |= g.qmask;
+                // Layers: place every gate that needs no pending phase; when a
+                // gate does need one, flush ALL pending phases at once (they
+                // are all ready) and scan again.  One phase segment per layer.
+                while (true) {
+                    uint64_t blocked = 0;
+                    bool need_flush = false;
+                    for (size_t i = first; i < G.size(); i++) {
+                        if (done[i]) continue;
+                        const PGate &g = G[i];
+                        if (g.qmask & blocked) { blocked |= g.qmask; continue; }
+                        if (g.diag) { make_pending(g); done[i] = 1; continue; }
+                        uint64_t P = phys(g.qmask);
+                        if (g.swap) {
+                            // a relabelling: pending phases live in the physical
+                            // frame, so they commute with it
+                            if (popc((Q | P) & ~lowL) <= cfg.C - cfg.L) {
+                                Q |= P;
+                                int pa = laminv[g.q[0]], pb = laminv[g.q[1]];
+                                std::swap(lam[pa], lam[pb]);
+                                laminv[lam[pa]] = pa;
+                                laminv[lam[pb]] = pb;
+                                done[i] = 1;
+                                placed = true;
+                            } else {
+                                blocked |= g.qmask;
+                            }
+                            continue;
                         }
-                        continue;
+                        if (g.k > kChunkMaxK || popc(st.R | P) > cfg.RB ||
+                            popc((Q | P) & ~lowL) > cfg.C - cfg.L) {
+                            blocked |= g.qmask;
+                            continue;
+                        }
+                        if (pending_meets(P)) {
+                            need_flush = true;
+                            blocked |= g.qmask;
+                            continue;
+                        }
+                        SOp d;
+                        d.type = 1;
+                        d.k = g.k;
+                        for (int j = 0; j < g.k; j++) d.pos[j] = laminv[g.q[j]];
+                        d.pmask = P;
+                        d.M = g.M;
+                        d.n_src = g.n_src;
+                        push_dense(st, std::move(d));
+                        st.R |= P;
+                        Q |= P;
+                        done[i] = 1;
+                        placed = true;
                     }
-                    if (g.k > kChunkMaxK || popc(st.R | P) > cfg.RB || popc((Q | P) & ~lowL) > cfg.C - cfg.L) {
-                        blocked |= g.qmask;
-                        continue;
-                    }
+                    if (!need_flush) break;
                     SOp ph;
-                    if (flush(P, ph)) st.ops.push_back(std::move(ph));
-                    SOp d;
-                    d.type = 1;
-                    d.k = g.k;
-                    for (int j = 0; j < g.k; j++) d.pos[j] = laminv[g.q[j]];
-                    d.pmask = P;
-                    d.M = g.M;
-                    d.n_src = g.n_src;
-                    push_dense(st, std::move(d));
-                    st.R |= P;
-                    Q |= P;
-                    done[i] = 1;
-                    placed = true;
+                    flush(~0ull, ph);
+                    st.ops.push_back(std::move(ph));
+                }
+                // a trailing flush with no gate after it goes back to pending
+                if (!st.ops.empty() && st.ops.back().type == 2) {
+                    for (const Term &t : st.ops.back().terms) {
+                        PendingDiag d;
+                        d.mask = t.mask;
+                        d.n_src = 0;
+                        d.terms.push_back(t);
+                        pending.push_back(std::move(d));
+                    }
+                    st.ops.pop_back();
                 }
                 if (!placed) break;
                 stages.push_back(std::move(st));
@@ -933,7 +976,7 @@ static std::vector<uint32_t> encode_diag_sweep(int n, const std::vector<Term> &t
 static void schedule(const std::vector<PGate> &G, int n, const sim_options &opt, sim_dtype dt, int buf, Plan &plan)
 {
     int C = 0, RB = 0;
-    bool blocked = (opt.flags & SIM_F_BLOCK) && chunk_shape(n, dt, opt.chunk_qubits, C, RB);
+    bool blocked = (opt.flags & SIM_F_BLOCK) && chunk_shape(n, dt, opt.chunk_qubits, opt.register_bits, C, RB);
     if (!blocked) {
         emit_unfused(G, n, buf, plan);
         return;
@@ -1040,7 +1083,7 @@ static void finalize_words(Plan &plan)
             } else {
                 // too small for the diagonal sweep's tile: run it as a one-stage chunk pass
                 int Cc = 0, RBc = 0;
-                if (!chunk_shape(o.n, plan.dtype, 0, Cc, RBc)) {
+                if (!chunk_shape(o.n, plan.dtype, 0, 0, Cc, RBc)) {
                     // below every chunk shape: one thread per amplitude sums the terms
                     o.kind = OPK_PHASE_SMALL;
                     continue;
@@ -1077,6 +1120,7 @@ static bool validate_program(const std::vector<uint32_t> &w, int n, bool diag_sw
     auto bad = [&](const char *m) { err = std::string("internal: invalid device program: ") + m; return false; };
     const size_t W = w.size();
     if (W < (size_t)prog::H_SIZE || w[prog::H_MAGIC] != prog::kMagic) return bad("header");
+    if (w[prog::H_WORDS] != W || (W & 1)) return bad("program length");
     const int C = (int)w[prog::H_C], RB = (int)w[prog::H_RB], ns = (int)w[prog::H_NSTAGE];
     if (C < 1 || C > prog::kMaxC || C > n || RB < 1 || RB > prog::kMaxRB || RB >= C) return bad("shape");
     if (ns < 0 || ns > prog::kMaxStages || (diag_sweep && ns != 1)) return bad("stage count");
@@ -1127,6 +1171,9 @@ static bool validate_program(const std::vector<uint32_t> &w, int n, bool diag_sw
             uint32_t b = w[so + prog::S_THR + i];
             if ((int)b >= C || ((seen >> b) & 1)) return bad("thread bits");
             if (w[so + prog::S_GTHR + i] != w[prog::H_QIN + b]) return bad("thread bit positions");
+            if (i < RB && w[so + prog::S_PV + i] !=
+                              prog::swizzle(1u << w[so + prog::S_REG + i], C, w[prog::H_WBYTES] == 8 ? 4 : 5))
+                return bad("register offsets");
             seen |= 1u << b;
         }
         const uint32_t nops = w[so + prog::S_NOPS];

@@ -48,6 +48,8 @@ enum : int {
     H_NCTA,
     H_THR_OFF,           // thread table: word offset, count (kThrWords each)
     H_NTHR,
+    H_WORDS,             // total words of the program (it is staged in shared memory)
+    H_PAD,
     H_SIZE
 };
 // CTA-table entry: slot (= d * (1 + RB) + s, s = 0 base / 1 + j linear in
@@ -64,8 +66,20 @@ enum : int {
     S_REG = 2,                 // kMaxRB words
     S_THR = S_REG + kMaxRB,    // kMaxC words
     S_GTHR = S_THR + kMaxC,    // kMaxC words: physical qubit of thread bit i (= qin[thr[i]])
-    S_SIZE = S_GTHR + kMaxC    // even
+    S_PV = S_GTHR + kMaxC,     // kMaxRB words: swizzled shared-memory offset of register bit j
+    S_SIZE = S_PV + kMaxRB     // even
 };
+
+// Shared-memory swizzle of the chunk planes: element y lives at
+// y ^ fold(y >> sw), folding sw-bit groups into the low bits (sw = 5 for
+// float planes, 4 for double).  Linear over GF(2), so offsets of disjoint bit
+// sets combine by XOR.
+inline uint32_t swizzle(uint32_t y, int C, int sw)
+{
+    uint32_t r = y;
+    for (int s = sw; s < C; s += sw) r ^= (y >> s) & ((1u << sw) - 1);
+    return r;
+}
 
 // op header
 enum : int { OP_DENSE = 1, OP_DSEG = 2 };
@@ -100,7 +114,12 @@ inline size_t smem_bytes(const uint32_t *w, bool diag_sweep)
     const size_t C = w[H_C], RB = w[H_RB], wb = w[H_WBYTES];
     const size_t T = (size_t)1 << (C - RB), S = 1 + RB;
     const size_t planes = diag_sweep ? 0 : 2 * ((size_t)1 << C) * wb;
-    return planes + (size_t)w[H_NDSEG] * S * wb + (size_t)w[H_NHOIST] * S * T * wb;
+    const size_t progw = ((size_t)w[H_WORDS] * 4 + 15) & ~(size_t)15;
+    // per-thread stage layouts (chunk kernel): thread part of x0 and of the
+    // swizzled register-block offset for every stage
+    const size_t layouts = diag_sweep ? 0 : (size_t)w[H_NSTAGE] * T * 12;
+    return planes + progw + (((size_t)w[H_NDSEG] * S * wb + 15) & ~(size_t)15) +
+           (((size_t)w[H_NHOIST] * S * T * wb + 15) & ~(size_t)15) + layouts;
 }
 
 }  // namespace prog

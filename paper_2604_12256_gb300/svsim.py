@@ -39,7 +39,7 @@ class sim_options(ctypes.Structure):
     _fields_ = [("max_fuse_qubits", ctypes.c_int), ("max_diag_qubits", ctypes.c_int),
                 ("chunk_qubits", ctypes.c_int), ("booster_div", ctypes.c_int),
                 ("flags", ctypes.c_uint32), ("dense_precision", ctypes.c_int),
-                ("max_stages", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("max_stages", ctypes.c_int), ("register_bits", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class sim_plan_stats(ctypes.Structure):
