@@ -162,6 +162,36 @@ int sim_expectation(sim_t *s, const uint64_t *z_masks, size_t n_terms, double *o
 /* Squared norm sum_x |a_x|^2, accumulated in FP64. */
 int sim_norm(sim_t *s, double *out);
 
+/* <Z-string m> like sim_expectation, for callers that cannot allocate device
+ * memory when they need the result -- code running inside an allocator or
+ * memory-pool callback, embedded callers whose device memory is owned and
+ * budgeted by a host framework, programs that forbid allocation after
+ * start-up.  It allocates nothing (no cudaMalloc / cudaFree, no allocating
+ * library call): the reduction partials live in a fixed device array of
+ * 128 KiB compiled into the library, present on every device that loads it
+ * until the process exits.  (The paper has no counterpart; this is an
+ * interface convenience.)
+ *
+ *   dev_state  2^n amplitudes in device memory (interleaved, dtype's precision)
+ *   dev_masks  n_terms Z-string masks in device memory (bits < n_qubits)
+ *   n_terms    1..16 (the fixed array's capacity; SIM_EINVAL beyond)
+ *   dev_out    n_terms doubles in device memory, written when the stream
+ *              reaches the kernels (the call only enqueues them)
+ *   cuda_stream the cudaStream_t to run on (NULL: legacy default stream)
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call on a device shares the one array: calls whose kernels overlap on the
+ * GPU (different streams, no ordering between them) race and must be
+ * serialised by the caller.  Each call overwrites every partial it reads, so
+ * nothing needs clearing.  Errors: SIM_EINVAL / SIM_EUNSUPPORTED for bad
+ * arguments, SIM_ECUDA for a failed CUDA call; the message is available from
+ * sim_noalloc_error(). */
+int sim_expectation_noalloc(const void *dev_state, int n_qubits, sim_dtype dtype,
+                            const uint64_t *dev_masks, size_t n_terms, double *dev_out,
+                            void *cuda_stream);
+const char *sim_noalloc_error(void);
+
 /* Copy the state out of / into host memory (bytes = 2^n * bytes/amp).
  * sim_set_state ends the product-state knowledge (no booster after it). */
 int sim_get_state(sim_t *s, void *host, size_t bytes);

@@ -96,6 +96,8 @@ _SIGS = [
     ("sim_last_plan_stats", ctypes.c_int, [_P, ctypes.POINTER(sim_plan_stats)]),
     ("sim_profile_enable", ctypes.c_int, [_P, ctypes.c_int]),
     ("sim_profile_read", ctypes.c_int, [_P, ctypes.POINTER(sim_profile)]),
+    ("sim_expectation_noalloc", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t, _P, _P]),
+    ("sim_noalloc_error", ctypes.c_char_p, []),
     ("sim_last_error", ctypes.c_char_p, [_P]),
     ("sim_global_error", ctypes.c_char_p, []),
     ("sim_plan_json", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _P, ctypes.c_size_t,
@@ -276,6 +278,18 @@ class Sim:
         p, s = ctypes.c_void_p(), ctypes.c_void_p()
         _check(self.lib.sim_state_device(self.h, ctypes.byref(p), ctypes.byref(s)), self.h)
         return p.value, s.value
+
+
+def expectation_noalloc(dev_state: int, n: int, dtype: int, dev_masks: int, n_terms: int, dev_out: int,
+                        stream: Optional[int] = None) -> None:
+    """sim_expectation_noalloc: <Z-string> values for callers that cannot
+    allocate device memory; all pointers are device addresses owned by the
+    caller, the results land in dev_out when the stream reaches the kernels."""
+    lib = load()
+    rc = lib.sim_expectation_noalloc(ctypes.c_void_p(dev_state), n, dtype, ctypes.c_void_p(dev_masks), n_terms,
+                                     ctypes.c_void_p(dev_out), ctypes.c_void_p(stream or 0))
+    if rc != SIM_OK:
+        raise SimError(rc, (lib.sim_noalloc_error() or b"").decode(errors="replace"))
 
 
 def run(circuit: _circ.Circuit, dtype: int = SIM_C64, opt: Optional[sim_options] = None) -> np.ndarray:
