@@ -77,6 +77,34 @@ __device__ __forceinline__ double2 cis_turns(uint64_t w)
     return make_double2(c, s);
 }
 
+// packed f32x2 arithmetic (sm_100+): a 64-bit register pair holds (re, im)
+using u64 = unsigned long long;
+__device__ __forceinline__ u64 pk2(float lo, float hi)
+{
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ u64 pk(float2 v) { return pk2(v.x, v.y); }
+__device__ __forceinline__ float2 upk(u64 r)
+{
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c)
+{
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ u64 fmul2(u64 a, u64 b)
+{
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b)
 {
     T2 r;
@@ -102,6 +130,24 @@ __device__ __forceinline__ void dense_apply(typename CT<R>::T2 (&v)[NR], const u
     constexpr int D = 1 << K;
     constexpr int gm = (1 << P0) | (K > 1 ? (1 << P1) : 0);
     const R *mb = (const R *)body;
+    if constexpr (sizeof(R) == 4 && K == 1) {
+        // complex64 2x2: m x = (mr, mr) * x + (-mi, mi) * (x.im, x.re), packed
+        u64 Mr[4], Mi[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            Mr[i] = pk2(mb[2 * i], mb[2 * i]);
+            Mi[i] = pk2(-mb[2 * i + 1], mb[2 * i + 1]);
+        }
+#pragma unroll
+        for (int g = 0; g < NR; g++) {
+            if (g & gm) continue;
+            const float2 y0 = v[g], y1 = v[g | (1 << P0)];
+            const u64 x0 = pk(y0), x1 = pk(y1), s0 = pk2(y0.y, y0.x), s1 = pk2(y1.y, y1.x);
+            v[g] = upk(ffma2(s0, Mi[0], ffma2(x0, Mr[0], ffma2(s1, Mi[1], fmul2(x1, Mr[1])))));
+            v[g | (1 << P0)] = upk(ffma2(s0, Mi[2], ffma2(x0, Mr[2], ffma2(s1, Mi[3], fmul2(x1, Mr[3])))));
+        }
+        return;
+    }
     // K = 1: the matrix stays in registers; K = 2: its 16 entries are re-read
     // (L1 broadcast) for every group to keep register pressure down
     T2 M1[K == 1 ? 4 : 1];
@@ -152,6 +198,31 @@ __device__ __forceinline__ void dense1_special(typename CT<R>::T2 (&v)[NR], cons
     const R b = mb[SUB == DS_REAL ? 2 : 3];
     const R c = mb[SUB == DS_REAL ? 4 : 5];
     const R d = mb[6];
+    if constexpr (sizeof(R) == 4) {
+        // complex64: one packed f32x2 op updates (re, im) together
+        if constexpr (SUB == DS_REAL) {
+            const u64 A = pk2(a, a), B = pk2(b, b), Cc = pk2(c, c), D = pk2(d, d);
+#pragma unroll
+            for (int g = 0; g < NR; g++) {
+                if (g & (1 << P)) continue;
+                const u64 x0 = pk(v[g]), x1 = pk(v[g | (1 << P)]);
+                v[g] = upk(ffma2(x0, A, fmul2(x1, B)));
+                v[g | (1 << P)] = upk(ffma2(x0, Cc, fmul2(x1, D)));
+            }
+        } else {   // [[a, i b], [i c, d]]: a x0 + i b x1, i c x0 + d x1
+            const u64 A = pk2(a, a), D = pk2(d, d), B = pk2(-b, b), Cc = pk2(-c, c);
+#pragma unroll
+            for (int g = 0; g < NR; g++) {
+                if (g & (1 << P)) continue;
+                const float2 y0 = v[g], y1 = v[g | (1 << P)];
+                const u64 x0 = pk(y0), x1 = pk(y1);
+                const u64 s0 = pk2(y0.y, y0.x), s1 = pk2(y1.y, y1.x);   // i x = (-im, re) via the signs
+                v[g] = upk(ffma2(x0, A, fmul2(s1, B)));
+                v[g | (1 << P)] = upk(ffma2(x1, D, fmul2(s0, Cc)));
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int g = 0; g < NR; g++) {
         if (g & (1 << P)) continue;
@@ -340,6 +411,7 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 2 : 8) k_chunk(
     W *thr_ph = (W *)((unsigned char *)cta_ph + (((size_t)nd * S * sizeof(W) + 15) & ~(size_t)15));
     __shared__ uint64_t s_git[NR / 2];    // global offset of load iteration `it`
     __shared__ uint32_t s_sit[NR / 2];    // swizzled smem position of `it` on the store
+    __shared__ uint64_t s_dep[768];       // chunk number byte k -> its free-qubit bits
 
     int qin[C];
 #pragma unroll
@@ -368,6 +440,19 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 2 : 8) k_chunk(
         s_sit[tid] = swz<SW, C>(sp);
     }
     thread_sums<R, T>(prog, thr_ph, nhoist * S, tid);
+    // deposit tables: entry 256 k + i = the chunk-number bits i << 8k spread
+    // over the free qubits (n - C <= 22 < 24 bits)
+    for (int e = tid; e < 768; e += T) {
+        const int k = e >> 8;
+        uint64_t b = 0, fm = freem, cv = (uint64_t)(e & 255) << (8 * k);
+        while (fm) {
+            uint64_t low = fm & (~fm + 1);
+            if (cv & 1) b |= low;
+            cv >>= 1;
+            fm ^= low;
+        }
+        s_dep[e] = b;
+    }
     // this thread's part of every stage's layout (the same for all chunks)
     uint64_t *s_x0 = (uint64_t *)((unsigned char *)thr_ph + (((size_t)nhoist * S * T * sizeof(W) + 15) & ~(size_t)15));
     uint32_t *s_pb = (uint32_t *)(s_x0 + (size_t)nst * T);
@@ -391,15 +476,10 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 2 : 8) k_chunk(
 
     const int64_t nchunks = (int64_t)1 << (n - C);
     // chunk base: spread the chunk number over the free (non-chunk) qubits
+    // (deposit is linear over disjoint input bytes: three 256-entry tables)
     auto chunk_base = [&](int64_t chn) {
-        uint64_t b = 0, fm = freem, cv = (uint64_t)chn;
-        while (fm) {
-            uint64_t low = fm & (~fm + 1);
-            if (cv & 1) b |= low;
-            cv >>= 1;
-            fm ^= low;
-        }
-        return b;
+        const uint64_t c = (uint64_t)chn;
+        return s_dep[c & 255] | s_dep[256 + ((c >> 8) & 255)] | s_dep[512 + ((c >> 16) & 255)];
     };
     // coalesced loads of one chunk's amplitude pairs into registers
     auto load_regs = [&](T2 (&dst)[NR], uint64_t b) {
