@@ -38,7 +38,11 @@ WORKLOAD = "28-qubit diagonal-heavy gate-level stream (500 gates, 80% RZ/CP/RZZ,
 
 # ncu DRAM traffic per chunk-sweep launch (dram__bytes_read.sum + write.sum),
 # keyed by the sha256 of k_chunk.cu at capture time; null when the kernel changed.
-TRAFFIC = {}
+TRAFFIC_PER_AMP = {
+    # profiles/k_chunk_diagheavy_25q.md: 475.6 MB per 2^25-amplitude launch;
+    # a sweep's traffic grows with the amplitudes it processes
+    "31c90410b3be81eee0a16191da362476d0f0d9a3afe9db3a91fa0f1bb6b115b9": 475.6e6 / 2 ** 25,
+}
 
 
 def _peaks():
@@ -250,7 +254,8 @@ def run_gpu(args, rank, world, dist):
     gpu_launches = launches
     achieved = ch["bytes"] / (ch["ms"] / 1e3) / 1e9 if ch["ms"] > 0 else None
     src = open(os.path.join(ROOT, "paper_2604_12256_gb300", "csrc", "k_chunk.cu"), "rb").read()
-    traffic = TRAFFIC.get(hashlib.sha256(src).hexdigest())
+    tpa = TRAFFIC_PER_AMP.get(hashlib.sha256(src).hexdigest())
+    traffic = tpa * amps if tpa is not None else None
     total_bytes = sum(v["bytes"] for k, v in prof.items() if isinstance(v, dict)) / args.steps
     value = world * G * amps / (ms / 1e3)
     if rank == 0:

@@ -277,7 +277,8 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 
 // |a|^2 of one amplitude: exact squares in FP64, one rounding in the sum.
 __device__ __forceinline__ double prob_of(float2 v) { return fma((double)v.x, (double)v.x, (double)v.y * (double)v.y); }
-__device__ __forceinline__ double prob_of(double2 v) { return fma(v.x, v.x, v.y * v.y); }
+// (no contraction: each square rounded, then the sum -- the plain definition)
+__device__ __forceinline__ double prob_of(double2 v) { return __dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y)); }
 __device__ __forceinline__ float probf(float2 v) { return fmaf(v.x, v.x, v.y * v.y); }
 
 template <typename R>
@@ -329,12 +330,28 @@ __global__ void __launch_bounds__(kRedThreads) k_expect_part(const typename Cx<R
 #pragma unroll
     for (int t = 0; t < NT; t++) acc[t] = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-        double p;
-        if constexpr (sizeof(R) == 4) p = (double)probf(a[i]);
-        else p = prob_of(a[i]);
+    if constexpr (sizeof(R) == 4) {
+        // complex64: FP32 sums over batches of 32 amplitudes, FP64 across
+        // batches (the FP64 rate of this part is far below its FP32 rate)
+        int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        while (i < N) {
+            float acc32[NT];
 #pragma unroll
-        for (int t = 0; t < NT; t++) acc[t] += (__popcll((uint64_t)i & m[t]) & 1) ? -p : p;
+            for (int t = 0; t < NT; t++) acc32[t] = 0.f;
+            for (int b = 0; b < 32 && i < N; b++, i += stride) {
+                const float p = probf(a[i]);
+#pragma unroll
+                for (int t = 0; t < NT; t++) acc32[t] += (__popcll((uint64_t)i & m[t]) & 1) ? -p : p;
+            }
+#pragma unroll
+            for (int t = 0; t < NT; t++) acc[t] += (double)acc32[t];
+        }
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+            const double p = prob_of(a[i]);
+#pragma unroll
+            for (int t = 0; t < NT; t++) acc[t] += (__popcll((uint64_t)i & m[t]) & 1) ? -p : p;
+        }
     }
 #pragma unroll
     for (int t = 0; t < NT; t++) {
@@ -426,18 +443,30 @@ __global__ void __launch_bounds__(kTopThreads) k_topk(const typename Cx<R>::T *_
     int64_t lo = (int64_t)blockIdx.x * per, hi = lo + per < N ? lo + per : N;
     for (int64_t t0 = lo; t0 < hi; t0 += kTopTile) {
         KI th = thr;
+        // complex64: a float pre-filter (rounded down by a margin far above
+        // its rounding error) skips the FP64 probability of clear losers
+        const float thf = th.p > 0 ? __double2float_rd(th.p * (1.0 - 1e-5)) : -1.0f;
 #pragma unroll
         for (int e = 0; e < 4; e++) {
             int64_t i = t0 + e * kTopThreads + threadIdx.x;
             if (i < hi) {
                 KI v;
-                if constexpr (FROM_STATE) { v.p = prob_of(a[i]); v.i = (uint64_t)i; }
-                else v = cand[i];
+                if constexpr (FROM_STATE) {
+                    const auto z = a[i];
+                    if constexpr (sizeof(R) == 4) {
+                        if (fmaf(z.x, z.x, z.y * z.y) < thf) continue;
+                    }
+                    v.p = prob_of(z);
+                    v.i = (uint64_t)i;
+                } else {
+                    v = cand[i];
+                }
                 if (better(v, th)) { int pos = atomicAdd(&cnt, 1); buf[pos] = v; }
             }
         }
         __syncthreads();
-        if (cnt > k) {
+        // sort and cut back to k only when another tile might not fit
+        if (cnt > kTopCap - kTopTile) {
             for (int j = cnt + threadIdx.x; j < kTopCap; j += blockDim.x) buf[j] = worst;
             bitonic_desc(buf, kTopCap);
             if (threadIdx.x == 0) { cnt = k; thr = buf[k - 1]; }

@@ -145,6 +145,26 @@ def test_readouts(dtype):
             assert np.all(pe[idx.astype(np.int64)] >= ep[-1] - 2 * tol)
 
 
+@pytest.mark.parametrize("dtype", [S.SIM_C64, S.SIM_C128])
+@pytest.mark.parametrize("k", [1, 64, 1000])
+def test_topk_large_random_state(dtype, k):
+    """Top-k over 2^21 amplitudes (many blocks, the float pre-filter and the
+    merge pass): the same probabilities as the oracle's definition, exactly,
+    and the same indices (ties to the lower index)."""
+    n = 21
+    rng = np.random.default_rng(k)
+    a = (rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)) * (rng.random(1 << n) ** 3)
+    a /= np.linalg.norm(a)
+    a[[5, 77, 123456]] = a[999]          # exact ties
+    with S.Sim(n, dtype) as s:
+        s.set_state(a)
+        ref = s.get_state().astype(np.complex128)   # the values the GPU holds
+        idx, p = s.top_k(k)
+    eidx, ep = oracle.top_k(ref, k)
+    assert list(idx) == list(eidx)
+    np.testing.assert_array_equal(p, ep)
+
+
 def test_topk_ties_uniform():
     with S.Sim(16, S.SIM_C64) as s:
         s.apply([C.Gate("h", (q,)) for q in range(16)])
