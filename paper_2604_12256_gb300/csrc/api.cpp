@@ -32,6 +32,7 @@ struct sim_t {
     double *d_part = nullptr;   // reduction partials
     double *d_out = nullptr;    // small device results
     uint64_t *d_masks = nullptr;
+    int *d_status = nullptr;    // set by kernels whose bounded waits gave up
     void *d_topk = nullptr;
     size_t topk_bytes = 0;
     unsigned char *d_const = nullptr;   // plan constants
@@ -121,6 +122,8 @@ static int alloc_aux(sim_t *s)
     CK(s, cudaMalloc((void **)&s->d_part, sizeof(double) * np * 16));
     CK(s, cudaMalloc((void **)&s->d_out, sizeof(double) * 64));
     CK(s, cudaMalloc((void **)&s->d_masks, sizeof(uint64_t) * 64));
+    CK(s, cudaMalloc((void **)&s->d_status, sizeof(int)));
+    CK(s, cudaMemset(s->d_status, 0, sizeof(int)));
     CK(s, cudaEventCreateWithFlags(&s->pin_ev, cudaEventDisableTiming));
     return SIM_OK;
 }
@@ -133,6 +136,7 @@ static void free_all(sim_t *s)
     if (s->d_part) cudaFree(s->d_part);
     if (s->d_out) cudaFree(s->d_out);
     if (s->d_masks) cudaFree(s->d_masks);
+    if (s->d_status) cudaFree(s->d_status);
     if (s->d_topk) cudaFree(s->d_topk);
     if (s->d_const) cudaFree(s->d_const);
     if (s->h_pin) cudaFreeHost(s->h_pin);
@@ -144,6 +148,18 @@ static void free_all(sim_t *s)
 }
 
 // write the pending |basis> (sim_reset is lazy)
+// after a synchronisation: report (and clear) a kernel's timed-out wait
+static int check_status(sim_t *s)
+{
+    int st = 0;
+    CK(s, cudaMemcpy(&st, s->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) {
+        CK(s, cudaMemset(s->d_status, 0, sizeof(int)));
+        return fail(s, SIM_ETIMEOUT, "a kernel's bounded wait for the tensor cores timed out; results are invalid");
+    }
+    return SIM_OK;
+}
+
 static int materialize(sim_t *s)
 {
     if (!s->reset_pending) return SIM_OK;
@@ -241,7 +257,7 @@ int sim_sync(sim_t *s)
     if (!s) return fail(nullptr, SIM_EINVAL, "null handle");
     if (int rc = materialize(s)) return rc;
     CK(s, cudaStreamSynchronize(s->stream));
-    return SIM_OK;
+    return check_status(s);
 }
 
 int sim_state_device(sim_t *s, void **dev_ptr, void **stream)
@@ -323,7 +339,9 @@ static int execute(sim_t *s, const Plan &p)
     std::vector<std::vector<int>> nzidx(p.ops.size());
     for (size_t i = 0; i < p.ops.size(); i++) {
         const Op &o = p.ops[i];
-        if (o.kind == OPK_GATE || o.kind == OPK_DENSE_TC) {
+        if (o.kind == OPK_DENSE_TC) {
+            add_complex(bl, o.gate.M, true, off[i]);   // FP64; the kernels round as their arithmetic needs
+        } else if (o.kind == OPK_GATE) {
             add_complex(bl, o.gate.M, f64, off[i]);
         } else if (o.kind == OPK_GATE_DIAG) {
             std::vector<cd> f;
@@ -380,7 +398,9 @@ static int execute(sim_t *s, const Plan &p)
         switch (o.kind) {
         case OPK_INIT_BASIS: e = launch_init_basis(a, o.n, f64, o.basis, s->stream); break;
         case OPK_GATE:
-        case OPK_DENSE_TC: e = launch_gate_dense(a, o.n, f64, o.gate.k, o.gate.q, cst, s->stream); break;
+        case OPK_DENSE_TC:
+            e = launch_dense5(a, o.n, f64, o.precision, o.gate.q, cst, s->d_status, s->stream);
+            break;
         case OPK_GATE_DIAG:
             e = launch_gate_diag(a, o.n, f64, o.gate.k, o.gate.q, (int)nzidx[i].size(), nzidx[i].data(), cst,
                                  s->stream);
@@ -441,7 +461,7 @@ int sim_norm(sim_t *s, double *out)
     CK(s, launch_norm(s->state, s->n, s->dt == SIM_C128, s->d_part, s->d_out, s->stream));
     CK(s, cudaMemcpyAsync(out, s->d_out, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CK(s, cudaStreamSynchronize(s->stream));
-    return SIM_OK;
+    return check_status(s);
 }
 
 int sim_expectation(sim_t *s, const uint64_t *masks, size_t nt, double *out)
@@ -472,7 +492,7 @@ int sim_probabilities(sim_t *s, double *out)
     cudaFreeAsync(d, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "probabilities");
     CK(s, cudaStreamSynchronize(s->stream));
-    return SIM_OK;
+    return check_status(s);
 }
 
 int sim_top_k(sim_t *s, int k, uint64_t *idx, double *prob)
@@ -506,7 +526,7 @@ int sim_get_state(sim_t *s, void *host, size_t bytes)
     if (int rc = materialize(s)) return rc;
     CK(s, cudaMemcpyAsync(host, s->state, bytes, cudaMemcpyDeviceToHost, s->stream));
     CK(s, cudaStreamSynchronize(s->stream));
-    return SIM_OK;
+    return check_status(s);
 }
 
 int sim_set_state(sim_t *s, const void *host, size_t bytes)

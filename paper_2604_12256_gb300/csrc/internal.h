@@ -104,6 +104,7 @@ struct Op {
     ChunkProg prog;                // CHUNK
     int buf_lo = 0, buf_hi = 0, n_lo = 0, n_hi = 0;   // TENSOR: buf <- hi (x) lo
     std::vector<uint32_t> words;   // CHUNK / DIAG: encoded device program
+    int precision = 0;             // DENSE_TC: SIM_DENSE_* arithmetic
 };
 
 struct Plan {

@@ -74,6 +74,8 @@ void resolve_options(sim_options &o, int n, sim_dtype dt)
     if (o.max_stages < 1) o.max_stages = 1;
     if (o.max_stages > prog::kMaxStages) o.max_stages = prog::kMaxStages;
     if (o.max_diag_qubits < 0) o.max_diag_qubits = 0;
+    // dense-block mode: fused diagonals must fit a 5-qubit block
+    if ((o.flags & SIM_F_TC) && (o.max_diag_qubits == 0 || o.max_diag_qubits > 5)) o.max_diag_qubits = 5;
     (void)n;
     (void)dt;
 }
@@ -973,8 +975,91 @@ static std::vector<uint32_t> encode_diag_sweep(int n, const std::vector<Term> &t
     return encode_program(n, C, RB, f64, (1ull << C) - 1, stages, lam, true);
 }
 
+// Dense-block mode (tensor-core path): GBSA in fusion mode over the whole
+// circuit -- greedy in dependency order, each block collects every gate that
+// fits a set of at most 5 qubits, and its 32 x 32 unitary is composed in FP64
+// (gates applied in order).  Blocks narrower than 5 qubits are widened with
+// idle qubits so that every block is one 5-qubit dense sweep.
+static void schedule_dense_blocks(const std::vector<PGate> &G, int n, int precision, int buf, Plan &plan)
+{
+    const int K = n < 5 ? n : 5;
+    std::vector<char> done(G.size(), 0);
+    size_t first = 0;
+    while (true) {
+        while (first < G.size() && done[first]) first++;
+        if (first >= G.size()) break;
+        uint64_t S = 0, blocked = 0;
+        std::vector<size_t> members;
+        for (size_t i = first; i < G.size(); i++) {
+            if (done[i]) continue;
+            const PGate &g = G[i];
+            if (g.qmask & blocked) { blocked |= g.qmask; continue; }
+            if (popc(S | g.qmask) <= K) {
+                S |= g.qmask;
+                members.push_back(i);
+                done[i] = 1;
+            } else {
+                blocked |= g.qmask;
+            }
+        }
+        if (members.empty()) {
+            // a single gate wider than the block: apply it on its own
+            const PGate &g = G[first];
+            Op o;
+            o.buf = buf;
+            o.n = n;
+            if (g.diag) { o.kind = OPK_DIAG; o.terms = g.terms; }
+            else { o.kind = OPK_GATE; o.gate = g; }
+            plan.ops.push_back(std::move(o));
+            done[first] = 1;
+            continue;
+        }
+        for (int p = 0; p < n && popc(S) < K; p++) S |= 1ull << p;
+        int qs[kMaxGateQubits], kq = 0;
+        for (int p = 0; p < n; p++) if ((S >> p) & 1) qs[kq++] = p;
+        const int dim = 1 << kq;
+        std::vector<cd> U((size_t)dim * dim, cd(0, 0));
+        for (int i = 0; i < dim; i++) U[(size_t)i * dim + i] = 1;
+        int nsrc = 0;
+        for (size_t mi : members) {
+            const PGate &g = G[mi];
+            nsrc += g.n_src;
+            if (g.diag) {
+                // scale row r by the phase of the basis state it stands for
+                for (int r = 0; r < dim; r++) {
+                    uint64_t x = 0;
+                    for (int b = 0; b < kq; b++) if ((r >> b) & 1) x |= 1ull << qs[b];
+                    uint64_t w = 0;
+                    for (const Term &t : g.terms) if ((x & t.mask) == t.mask) w += t.w;
+                    cd f = phase_of(w);
+                    for (int c = 0; c < dim; c++) U[(size_t)r * dim + c] *= f;
+                }
+            } else {
+                std::vector<cd> E = expand(g.M, g.k, g.q, kq, qs);
+                U = matmul(E, U, dim);
+            }
+        }
+        Op o;
+        o.kind = kq == 5 ? OPK_DENSE_TC : OPK_GATE;
+        o.buf = buf;
+        o.n = n;
+        o.gate.kind = kFusedDense;
+        o.gate.k = kq;
+        for (int b = 0; b < kq; b++) o.gate.q[b] = qs[b];
+        o.gate.qmask = S;
+        o.gate.M = std::move(U);
+        o.gate.n_src = nsrc;
+        o.precision = precision;
+        plan.ops.push_back(std::move(o));
+    }
+}
+
 static void schedule(const std::vector<PGate> &G, int n, const sim_options &opt, sim_dtype dt, int buf, Plan &plan)
 {
+    if ((opt.flags & SIM_F_TC) && n >= 5) {
+        schedule_dense_blocks(G, n, dt == SIM_C128 ? SIM_DENSE_FP64 : opt.dense_precision, buf, plan);
+        return;
+    }
     int C = 0, RB = 0;
     bool blocked = (opt.flags & SIM_F_BLOCK) && chunk_shape(n, dt, opt.chunk_qubits, opt.register_bits, C, RB);
     if (!blocked) {

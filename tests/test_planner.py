@@ -125,3 +125,15 @@ def test_invalid_gates_rejected():
     with pytest.raises(S.SimError) as e:
         S.plan_json(35, [C.Gate("h", (0,))])
     assert e.value.code == S.SIM_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("maker", [lambda: C.layered(12, 6, 1), lambda: C.random_mixed(11, 120, 3, max_k=3),
+                                   lambda: C.qft(10, 2), lambda: C.diag_heavy(12, 100, 4)])
+def test_dense_block_plans_are_exact(maker):
+    c = maker()
+    opt = S.default_options(flags=S.SIM_F_TC | S.SIM_F_DIAG)
+    p = S.plan_json(c.n, c.gates, S.SIM_C128, c.basis, opt)
+    assert p["stats"]["dense_ops"] > 0
+    assert all(op["op"] in ("gate", "phase") for op in p["ops"])
+    assert all(len(op["qubits"]) == 5 for op in p["ops"] if op["op"] == "gate")
+    np.testing.assert_allclose(interpret(p, basis=c.basis), oracle.run(c), atol=1e-12)
