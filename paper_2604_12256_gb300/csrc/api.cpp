@@ -235,6 +235,27 @@ int sim_create_on(int n_qubits, sim_dtype dtype, void *dev_buf, size_t bytes, vo
     return create_common(n_qubits, dtype, dev_buf, bytes, cuda_stream, false, out);
 }
 
+}  // extern "C"
+
+int svs_rebind(sim_t *s, int n, sim_dtype dt, void *buf, size_t bytes)
+{
+    if (!s || s->own_state) return fail(s, SIM_EINVAL, "rebind needs a handle on a caller buffer");
+    int rc = check_n(n, dt);
+    if (rc) return rc;
+    const size_t need = ((size_t)1 << n) * amp_bytes(dt);
+    if (!buf || bytes < need) return fail(s, SIM_EINVAL, "buffer too small");
+    s->n = n;
+    s->dt = dt;
+    s->state = buf;
+    s->state_bytes = need;
+    s->product = true;
+    s->basis = 0;
+    s->reset_pending = true;
+    return SIM_OK;
+}
+
+extern "C" {
+
 int sim_destroy(sim_t *s)
 {
     if (!s) return fail(nullptr, SIM_EINVAL, "null handle");
@@ -397,7 +418,7 @@ static int execute(sim_t *s, const Plan &p)
         long pe = prof_begin(s);
         switch (o.kind) {
         case OPK_INIT_BASIS: e = launch_init_basis(a, o.n, f64, o.basis, s->stream); break;
-        case OPK_GATE:
+        case OPK_GATE: e = launch_gate_dense(a, o.n, f64, o.gate.k, o.gate.q, cst, s->stream); break;
         case OPK_DENSE_TC:
             e = launch_dense5(a, o.n, f64, o.precision, o.gate.q, cst, s->d_status, s->stream);
             break;
