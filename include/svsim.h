@@ -236,6 +236,62 @@ int sim_plan_json(int n_qubits, sim_dtype dtype, uint64_t basis_index,
                   const sim_gate *gates, size_t n, const sim_options *opt,
                   char *buf, size_t buflen, size_t *needed);
 
+/* ------------------------------------------------------------ serving */
+/* A request loop with continuous batching (not in the paper; the serving
+ * pattern around its simulator).  Requests are admitted as they arrive:
+ * circuits small enough for one CTA's shared memory (n <= 13 complex64,
+ * n <= 12 complex128, gates of <= 3 qubits, top_k <= 128) are packed into
+ * one kernel launch, one CTA per circuit, state kept on chip; larger ones run
+ * the full optimizer + kernel pipeline on one of n_streams worker streams,
+ * admitted only while the sum of their state footprints (2^n x bytes/amp)
+ * stays within hbm_budget.  Batches and worker streams overlap on the GPU. */
+typedef struct srv_t srv_t;
+
+typedef struct {
+    int n_qubits;
+    sim_dtype dtype;
+    const sim_gate *gates;     /* copied by srv_submit (matrices included) */
+    size_t n_gates;
+    uint64_t basis;            /* initial basis state */
+    int top_k;                 /* 0..1024 largest probabilities to return   */
+    const uint64_t *z_masks;   /* copied; <Z-string> values to return       */
+    size_t n_masks;            /* 0..64                                     */
+} srv_request;
+
+typedef struct {
+    int status;                /* SIM_OK or the request's error code        */
+    int top_k;
+    int n_masks;
+    int path;                  /* 0 shared-memory batch, 1 full-state pipeline */
+    uint64_t top_idx[1024];    /* ties to the lower index, largest first    */
+    double top_p[1024];
+    double expect[64];
+    double latency_ms;         /* submit -> result ready                   */
+    double queue_ms;           /* submit -> start of its GPU work          */
+} srv_result;
+
+typedef struct {
+    uint64_t submitted, completed, failed;
+    uint64_t batched, batches; /* requests run by batch launches, launches  */
+    double p50_ms, p99_ms, mean_ms, max_ms;   /* latency of completed requests */
+    double elapsed_s;          /* first submit -> last completion           */
+    double circuits_per_s;
+    size_t hbm_budget, hbm_peak;   /* admitted state bytes: budget and peak */
+} srv_stats;
+
+/* Start a server on the current device.  n_streams worker streams (>= 1)
+ * for full-state requests plus one batch stream. */
+int srv_create(size_t hbm_budget_bytes, int n_streams, srv_t **out);
+/* Queue a request (copied).  SIM_EINVAL for malformed requests, SIM_ENOMEM
+ * when its state alone exceeds the budget.  *ticket identifies it. */
+int srv_submit(srv_t *s, const srv_request *req, uint64_t *ticket);
+/* Wait up to timeout_ms (-1: forever) for a ticket's result; SIM_ETIMEOUT if
+ * it is not ready.  A returned result releases the ticket. */
+int srv_poll(srv_t *s, uint64_t ticket, srv_result *out, int timeout_ms);
+int srv_get_stats(srv_t *s, srv_stats *out);
+/* Finish the queued work, stop the threads, free everything. */
+int srv_destroy(srv_t *s);
+
 #ifdef __cplusplus
 }
 #endif

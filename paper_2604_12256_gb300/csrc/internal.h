@@ -120,6 +120,20 @@ struct Plan {
 bool make_plan(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_t ng,
                const sim_options &opt, Plan &plan, std::string &err);
 std::string plan_json(const Plan &p);
+
+// Serving: ops of the one-CTA batch kernel (batch.h) for a small circuit --
+// the diagonal detector's fused phases and dense gates of <= 3 qubits.
+// Returns false (err set) for invalid gates or wider dense gates.
+bool make_batch_ops(int n, sim_dtype dt, const sim_gate *gates, size_t ng, std::vector<uint32_t> &words, int &nops,
+                    std::string &err, bool &too_wide);
+
+}  // namespace svs
+
+// Point an existing handle at another state buffer / size (serving workers
+// reuse one handle and one buffer); the state becomes |0...0> (lazily).
+int svs_rebind(sim_t *s, int n, sim_dtype dt, void *dev_buf, size_t bytes);
+
+namespace svs {
 void fill_default_options(sim_options &o);
 void resolve_options(sim_options &o, int n, sim_dtype dt);
 

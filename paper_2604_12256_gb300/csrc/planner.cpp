@@ -1306,6 +1306,71 @@ static bool validate_program(const std::vector<uint32_t> &w, int n, bool diag_sw
     return true;
 }
 
+bool make_batch_ops(int n, sim_dtype dt, const sim_gate *gates, size_t ng, std::vector<uint32_t> &words, int &nops,
+                    std::string &err, bool &too_wide)
+{
+    too_wide = false;
+    std::vector<PGate> G;
+    G.reserve(ng);
+    for (size_t i = 0; i < ng; i++) {
+        PGate g;
+        if (!make_gate(gates[i], n, g, err)) {
+            err = "gate " + std::to_string(i) + ": " + err;
+            return false;
+        }
+        if (!g.diag && g.k > 3) {
+            too_wide = true;
+            err = "dense gate wider than 3 qubits";
+            return false;
+        }
+        G.push_back(std::move(g));
+    }
+    uint64_t absorbed = 0;
+    G = diagonal_detector(G, 0, absorbed);
+    const bool f64 = dt == SIM_C128;
+    nops = 0;
+    for (const PGate &g : G) {
+        const size_t start = words.size();
+        if (g.diag) {
+            if (g.terms.size() > 16000) { err = "phase polynomial too long for the batch path"; too_wide = true; return false; }
+            words.push_back(2);   // BOP_PHASE; length patched below
+            words.push_back((uint32_t)g.terms.size());
+            for (const Term &t : g.terms) {
+                words.push_back((uint32_t)t.mask);
+                words.push_back((uint32_t)(t.mask >> 32));
+                words.push_back((uint32_t)t.w);
+                words.push_back((uint32_t)(t.w >> 32));
+            }
+            words[start] |= (uint32_t)(words.size() - start) << 16;
+        } else {
+            words.push_back(1u | (uint32_t)g.k << 8);   // BOP_DENSE
+            for (int i = 0; i < 3; i++) words.push_back(i < g.k ? (uint32_t)g.q[i] : 0u);
+            for (const cd &z : g.M) {
+                if (f64) {
+                    double re = z.real(), im = z.imag();
+                    uint64_t a, b;
+                    std::memcpy(&a, &re, 8);
+                    std::memcpy(&b, &im, 8);
+                    words.push_back((uint32_t)a);
+                    words.push_back((uint32_t)(a >> 32));
+                    words.push_back((uint32_t)b);
+                    words.push_back((uint32_t)(b >> 32));
+                } else {
+                    float re = (float)z.real(), im = (float)z.imag();
+                    uint32_t a, b;
+                    std::memcpy(&a, &re, 4);
+                    std::memcpy(&b, &im, 4);
+                    words.push_back(a);
+                    words.push_back(b);
+                }
+            }
+            words[start] |= (uint32_t)(words.size() - start) << 16;
+        }
+        nops++;
+    }
+    return true;
+}
+
 bool make_plan(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_t ng, const sim_options &opt_in,
                Plan &plan, std::string &err)
 {

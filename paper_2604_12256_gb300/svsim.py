@@ -97,6 +97,11 @@ _SIGS = [
     ("sim_profile_enable", ctypes.c_int, [_P, ctypes.c_int]),
     ("sim_profile_read", ctypes.c_int, [_P, ctypes.POINTER(sim_profile)]),
     ("sim_expectation_noalloc", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t, _P, _P]),
+    ("srv_create", ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_P)]),
+    ("srv_submit", ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    ("srv_poll", ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.c_int]),
+    ("srv_get_stats", ctypes.c_int, [_P, _P]),
+    ("srv_destroy", ctypes.c_int, [_P]),
     ("sim_noalloc_error", ctypes.c_char_p, []),
     ("sim_last_error", ctypes.c_char_p, [_P]),
     ("sim_global_error", ctypes.c_char_p, []),
@@ -278,6 +283,73 @@ class Sim:
         p, s = ctypes.c_void_p(), ctypes.c_void_p()
         _check(self.lib.sim_state_device(self.h, ctypes.byref(p), ctypes.byref(s)), self.h)
         return p.value, s.value
+
+
+class srv_request(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int), ("dtype", ctypes.c_int), ("gates", ctypes.c_void_p),
+                ("n_gates", ctypes.c_size_t), ("basis", ctypes.c_uint64), ("top_k", ctypes.c_int),
+                ("z_masks", ctypes.c_void_p), ("n_masks", ctypes.c_size_t)]
+
+
+class srv_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("top_k", ctypes.c_int), ("n_masks", ctypes.c_int), ("path", ctypes.c_int),
+                ("top_idx", ctypes.c_uint64 * 1024), ("top_p", ctypes.c_double * 1024),
+                ("expect", ctypes.c_double * 64), ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double)]
+
+
+class srv_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in ("submitted", "completed", "failed", "batched", "batches")] + \
+               [(f, ctypes.c_double) for f in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "elapsed_s",
+                                              "circuits_per_s")] + \
+               [("hbm_budget", ctypes.c_size_t), ("hbm_peak", ctypes.c_size_t)]
+
+    def asdict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Server:
+    """srv_* binding: a continuous-batching request loop on the GPU."""
+
+    def __init__(self, hbm_budget: int, n_streams: int = 2):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        _check(self.lib.srv_create(ctypes.c_size_t(hbm_budget), n_streams, ctypes.byref(h)))
+        self.h = h
+
+    def submit(self, circuit: _circ.Circuit, top_k: int = 64, masks: Sequence[int] = (),
+               dtype: int = SIM_C64) -> int:
+        ga = GateArray(circuit.gates)
+        m = np.ascontiguousarray(np.array(list(masks), dtype=np.uint64)) if len(masks) else None
+        req = srv_request(circuit.n, dtype, ctypes.cast(ga.arr, ctypes.c_void_p), ga.n, circuit.basis, top_k,
+                          m.ctypes.data if m is not None else None, 0 if m is None else len(m))
+        t = ctypes.c_uint64()
+        _check(self.lib.srv_submit(self.h, ctypes.byref(req), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1) -> dict:
+        r = srv_result()
+        rc = self.lib.srv_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(r), timeout_ms)
+        if rc != SIM_OK:
+            raise SimError(rc, "srv_poll")
+        return {"status": r.status, "path": r.path, "latency_ms": r.latency_ms, "queue_ms": r.queue_ms,
+                "top_idx": np.array(r.top_idx[:r.top_k], dtype=np.uint64),
+                "top_p": np.array(r.top_p[:r.top_k]), "expect": np.array(r.expect[:r.n_masks])}
+
+    def stats(self) -> dict:
+        st = srv_stats()
+        _check(self.lib.srv_get_stats(self.h, ctypes.byref(st)))
+        return st.asdict()
+
+    def close(self):
+        if self.h:
+            self.lib.srv_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def expectation_noalloc(dev_state: int, n: int, dtype: int, dev_masks: int, n_terms: int, dev_out: int,

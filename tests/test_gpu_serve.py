@@ -1,0 +1,96 @@
+"""Serving loop (srv_*): continuous batching of requests on one GPU.
+
+Each result must be the same alone and in a concurrent mix (within the
+complex64 tolerance; the kernels are deterministic, so in practice bit-equal),
+agree with the oracle, and the admission / timeout / error paths must report
+what they say."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_12256_gb300 import circuits as C
+from paper_2604_12256_gb300 import svsim as S
+
+pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("built_lib")]
+GiB = 1 << 30
+
+
+def mix(seed, count, n_lo=10, n_hi=20):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        fam = i % 4
+        s = int(rng.integers(1 << 30))
+        c = [C.layered(n, int(rng.integers(2, 8)), s), C.diag_heavy(n, 6 * n, s), C.qft(n, s),
+             C.qaoa(n if n % 2 == 0 else n - 1, 2, s)][fam]
+        pairs = [tuple(int(v) for v in rng.choice(c.n, 2, replace=False)) for _ in range(16)]
+        out.append((c, [(1 << a) | (1 << b) for a, b in pairs]))
+    return out
+
+
+def test_results_same_alone_and_in_mix():
+    reqs = mix(1, 32)
+    with S.Server(8 * GiB, n_streams=3) as srv:
+        tickets = [srv.submit(c, 64, m) for c, m in reqs]     # all in flight together
+        mixed = [srv.poll(t) for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["batched"] > 0 and st["batches"] < st["batched"]          # small ones shared launches
+    assert any(r["path"] == 1 for r in mixed)                             # large ones on worker streams
+    for (c, m), r in zip(reqs, mixed):
+        with S.Server(8 * GiB, n_streams=1) as srv:
+            alone = srv.poll(srv.submit(c, 64, m))
+        assert r["status"] == 0 and alone["status"] == 0
+        assert alone["path"] == r["path"]
+        np.testing.assert_allclose(r["expect"], alone["expect"], atol=1e-5, rtol=0)
+        np.testing.assert_allclose(r["top_p"], alone["top_p"], atol=1e-5, rtol=0)
+        assert np.array_equal(r["top_idx"], alone["top_idx"])
+
+
+@pytest.mark.parametrize("dtype,tol", [(S.SIM_C64, 2e-5), (S.SIM_C128, 1e-12)])
+def test_results_match_oracle(dtype, tol):
+    reqs = mix(2, 12, 10, 13 if dtype == S.SIM_C64 else 12) + mix(3, 4, 14, 16)
+    with S.Server(8 * GiB, n_streams=2) as srv:
+        res = [srv.poll(srv.submit(c, 32, m, dtype)) for c, m in reqs]
+    for (c, m), r in zip(reqs, res):
+        assert r["status"] == 0
+        exp = oracle.run(c)
+        np.testing.assert_allclose(r["expect"], oracle.expectation_z(exp, m), atol=tol,
+                                   err_msg=f"{c.name} path {r['path']}")
+        eidx, ep = oracle.top_k(exp, 32)
+        np.testing.assert_allclose(r["top_p"], ep, atol=tol)
+        # near-ties may swap in complex64: check each index's true probability
+        pe = oracle.probabilities(exp)
+        assert np.all(pe[r["top_idx"].astype(np.int64)] >= ep[-1] - 2 * tol)
+
+
+@pytest.mark.parametrize("n", [10, 15])
+def test_known_states_both_paths(n):
+    """|+> on qubit 0 (batch path at n = 10, full path at n = 15): <Z_0> = 0,
+    <Z_1> = 1, top-2 = indices 0, 1 with probability 1/2 each."""
+    c = C.Circuit(n, [C.Gate("h", (0,))])
+    with S.Server(1 << 30, n_streams=1) as srv:
+        r = srv.poll(srv.submit(c, 2, [1, 2, 3]))
+    assert r["status"] == 0 and r["path"] == (0 if n <= 13 else 1)
+    np.testing.assert_allclose(r["expect"], [0.0, 1.0, 0.0], atol=1e-6)
+    assert list(r["top_idx"]) == [0, 1]
+    np.testing.assert_allclose(r["top_p"], [0.5, 0.5], atol=1e-6)
+
+
+def test_admission_timeout_and_errors():
+    with S.Server(1 << 20, n_streams=1) as srv:        # 1 MiB budget
+        with pytest.raises(S.SimError) as e:
+            srv.submit(C.layered(18, 2, 1))                # 2 MiB state: never admissible
+        assert e.value.code == S.SIM_ENOMEM
+        bad = C.Circuit(12, [C.Gate("cx", (3, 3))])
+        r = srv.poll(srv.submit(bad, 8))
+        assert r["status"] == S.SIM_EINVAL
+        big = C.diag_heavy(16, 4000, 5)                    # 512 KiB, long: still running at t=0
+        t = srv.submit(big, 8)
+        with pytest.raises(S.SimError) as e:
+            srv.poll(t, 0)
+        assert e.value.code == S.SIM_ETIMEOUT
+        assert srv.poll(t, -1)["status"] == 0
+        with pytest.raises(S.SimError):
+            srv.poll(t, 0)                                 # released
