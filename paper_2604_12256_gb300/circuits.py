@@ -79,14 +79,32 @@ def haar_unitary(rng: np.random.Generator, dim: int) -> np.ndarray:
     return q * (d / np.abs(d))[None, :]
 
 
+def haar_u2_batch(rng: np.random.Generator, count: int) -> np.ndarray:
+    """``count`` Haar-random 2x2 unitaries, shape (count, 2, 2): the QR
+    factorisation of complex Ginibre matrices whose R has a positive real
+    diagonal, the unique one that Mezzadri's phase correction selects, so Q is
+    Haar distributed as in :func:`haar_u2`.  In two dimensions it is closed
+    form: q0 = z0 / |z0|, and q1 is the unit vector orthogonal to q0,
+    (-conj(q0[1]), conj(q0[0])), times the phase that makes r11 = q1^H z1 real
+    and positive."""
+    z = (rng.standard_normal((count, 2, 2)) + 1j * rng.standard_normal((count, 2, 2))) / math.sqrt(2.0)
+    c0, c1 = z[:, :, 0], z[:, :, 1]
+    q0 = c0 / np.linalg.norm(c0, axis=1)[:, None]
+    a, b = q0[:, 0], q0[:, 1]
+    w = a * c1[:, 1] - b * c1[:, 0]          # (-conj b, conj a)^H z1
+    q1 = (w / np.abs(w))[:, None] * np.stack([-b.conj(), a.conj()], axis=1)
+    return np.stack([q0, q1], axis=2)
+
+
 def layered(n: int, depth: int, seed: int = 0) -> Circuit:
     """Random layered circuit: every layer puts a Haar U(2) on each qubit, then
     CZ on (0,1),(2,3),... in even layers and (1,2),(3,4),... in odd ones."""
     rng = np.random.default_rng(seed)
     gates: List[Gate] = []
     for layer in range(depth):
+        us = haar_u2_batch(rng, n)
         for q in range(n):
-            gates.append(Gate("u1q", (q,), matrix=haar_u2(rng)))
+            gates.append(Gate("u1q", (q,), matrix=us[q]))
         start = 0 if layer % 2 == 0 else 1
         for q in range(start, n - 1, 2):
             gates.append(Gate("cz", (q, q + 1)))
