@@ -203,11 +203,13 @@ def run_gpu(args, rank, world, dist):
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0 = S.kernel_launches()
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    gpu_launches = S.kernel_launches() - k0
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
     prof = sim.profile_read()
@@ -249,9 +251,6 @@ def run_gpu(args, rank, world, dist):
 
     peak, peak_kind = _peaks()
     ch = prof["chunk"]
-    launches = sum(v["launches"] for k, v in prof.items() if isinstance(v, dict))
-    # one of our kernels per recorded op (a reset's memset is the driver's, its k_set_one is ours)
-    gpu_launches = launches
     achieved = ch["bytes"] / (ch["ms"] / 1e3) / 1e9 if ch["ms"] > 0 else None
     src = open(os.path.join(ROOT, "paper_2604_12256_gb300", "csrc", "k_chunk.cu"), "rb").read()
     tpa = TRAFFIC_PER_AMP.get(hashlib.sha256(src).hexdigest())
@@ -289,6 +288,143 @@ def run_gpu(args, rank, world, dist):
     sim.close()
 
 
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))] if xs else None
+
+
+def run_serve(args, rank, world, dist):
+    """Serving stream: requests of 10-26 qubits, depth 10-200, families
+    layered / diagonal-heavy / QFT / QAOA, each returning the top-64
+    probabilities and 16 <Z_i Z_j>, complex64.  Measured: the serial
+    one-circuit-at-a-time capacity through sim_* handles, then the server
+    (srv_*: continuous batching, admission by state footprint) under Poisson
+    arrivals at 0.5 / 0.8 / 1.2 x that capacity and with every request
+    queued at once (saturated).  Gate lists are marshalled before timing."""
+    import numpy as np
+    import torch
+    from paper_2604_12256_gb300 import build as B
+    from paper_2604_12256_gb300 import circuits as C
+    from paper_2604_12256_gb300 import svsim as S
+
+    B.build()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    R = args.requests
+    reqs = C.serving_stream(R, 1.0, seed=4 + rank)          # unit-rate arrivals, rescaled below
+    arr1 = [r.arrival_s for r in reqs]
+    gas = [S.GateArray(r.circuit.gates) for r in reqs]
+    masks = [[int(m) for m in C.z_masks(r.z_pairs)] for r in reqs]
+    h2d = sum(g.n for g in gas) * ctypes_sizeof_gate(S) / R
+    d2h = 64 * 16 + 16 * 8
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # serial capacity: one handle per qubit count, one request at a time
+    sims = {}
+    for n in sorted({r.circuit.n for r in reqs}):
+        sims[n] = S.Sim(n, S.SIM_C64)
+    ser = [None] * R
+
+    def serial(i):
+        r = reqs[i]
+        sm = sims[r.circuit.n]
+        sm.reset(r.circuit.basis)
+        sm.apply(gas[i])
+        idx, p = sm.top_k(64)
+        ser[i] = (idx, p, sm.expectation(masks[i]))
+
+    for i in range(min(R, 32)):
+        serial(i)
+    torch.cuda.synchronize()
+    clocks = Clocks(dev)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    k0 = S.kernel_launches()
+    t0 = time.perf_counter()
+    svc = []
+    for i in range(R):
+        a = time.perf_counter()
+        serial(i)
+        svc.append((time.perf_counter() - a) * 1e3)
+    serial_s = time.perf_counter() - t0
+    serial_launches = S.kernel_launches() - k0
+    serial_cps = R / serial_s
+    for sm in sims.values():
+        sm.close()
+
+    budget = int(args.budget_gib * (1 << 30))
+
+    def serve(rate_hz):
+        """rate_hz None: everything queued at t = 0."""
+        with S.Server(budget, n_streams=args.streams) as srv:
+            tk = [0] * R
+            k0 = S.kernel_launches()
+            t0 = time.perf_counter()
+            for i in range(R):
+                if rate_hz is not None:
+                    wait = t0 + arr1[i] / rate_hz - time.perf_counter()
+                    if wait > 0:
+                        time.sleep(wait)
+                tk[i] = srv.submit_array(gas[i], reqs[i].circuit.n, reqs[i].circuit.basis, 64, masks[i])
+            res = [srv.poll(t) for t in tk]
+            wall = time.perf_counter() - t0
+            st = srv.stats()
+            kl = S.kernel_launches() - k0
+        dexp = max(float(np.max(np.abs(r["expect"] - ser[i][2]))) for i, r in enumerate(res))
+        dp = max(float(np.max(np.abs(r["top_p"] - ser[i][1]))) for i, r in enumerate(res))
+        return {"offered_hz": rate_hz, "circuits_per_s": R / wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                "mean_ms": st["mean_ms"], "max_ms": st["max_ms"], "failed": int(st["failed"]),
+                "batched": int(st["batched"]), "batch_launches": int(st["batches"]),
+                "hbm_peak_gib": st["hbm_peak"] / 2 ** 30, "kernel_launches": int(kl),
+                "max_abs_diff_vs_serial": {"expect": dexp, "top_p": dp}}
+
+    sat = serve(None)
+    pois = []
+    for f in (0.5, 0.8, 1.2):
+        d = serve(f * serial_cps)
+        d["load"] = f
+        pois.append(d)
+    clk = clocks.stop()
+    value = sat["circuits_per_s"]
+    if dist is not None:
+        t = torch.tensor([R / value], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        value = world * R / float(t.item())
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "circuits/s", "n_gpus": world, "steps": R,
+            "warmup": min(R, 32), "ms_per_step": 1e3 / sat["circuits_per_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": f"serving stream: {R} requests, qubits uniform 10-26, depth uniform 10-200, "
+                                   "family uniform over layered / diagonal-heavy / QFT / QAOA, top-64 "
+                                   "probabilities + 16 <Z_i Z_j> each, complex64",
+                       "requests": R, "worker_streams": args.streams, "hbm_budget_gib": args.budget_gib,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "states up to 512 MiB; no flush (requests run back to back as in service)"},
+            "saturated": sat,
+            "poisson": pois,
+            "serial": {"circuits_per_s": serial_cps, "p50_ms": _pct(svc, 0.5), "p99_ms": _pct(svc, 0.99),
+                       "kernel_launches": int(serial_launches),
+                       "note": "one request at a time through sim_* handles (one per qubit count); "
+                               "latency = service time, no queueing"},
+            "speedup_vs_serial": value / world / serial_cps,
+            "e2e": {"value": value, "unit": "circuits/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(sat["kernel_launches"]),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def ctypes_sizeof_gate(S):
+    import ctypes
+    return ctypes.sizeof(S.sim_gate)
+
+
 def main():
     global N_QUBITS, WORKLOAD
     ap = argparse.ArgumentParser()
@@ -300,6 +436,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--register-bits", type=int, default=0,
                     help="chunk bits per thread in the cache-blocked kernel (0 = library default)")
+    ap.add_argument("--serve", action="store_true",
+                    help="time the serving loop on a Poisson request stream instead")
+    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--streams", type=int, default=4, help="serving worker streams")
+    ap.add_argument("--budget-gib", type=float, default=32.0, help="serving HBM budget for admitted states")
     ap.add_argument("--qubits", type=int, default=N_QUBITS,
                     help="same workload on fewer qubits (small cases for ncu captures)")
     args = ap.parse_args()
@@ -317,7 +458,7 @@ def main():
         dist_.init_process_group("nccl")
         dist = dist_
     try:
-        run_gpu(args, rank, world, dist)
+        (run_serve if args.serve else run_gpu)(args, rank, world, dist)
     finally:
         if dist is not None:
             dist.destroy_process_group()

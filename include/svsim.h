@@ -221,6 +221,10 @@ typedef struct {
 int sim_profile_enable(sim_t *s, int on);
 /* Synchronise the handle's stream and return the accumulated counters. */
 int sim_profile_read(sim_t *s, sim_profile *out);
+/* Kernels this library has launched in this process, over all handles,
+ * servers and threads (a launch that failed to enqueue is not counted).  A
+ * diagnostic with no counterpart in the paper; never fails. */
+uint64_t sim_kernel_launches(void);
 const char *sim_last_error(const sim_t *s);
 const char *sim_global_error(void);
 

@@ -147,7 +147,6 @@ static void free_all(sim_t *s)
     delete s;
 }
 
-// write the pending |basis> (sim_reset is lazy)
 // after a synchronisation: report (and clear) a kernel's timed-out wait
 static int check_status(sim_t *s)
 {
@@ -160,6 +159,7 @@ static int check_status(sim_t *s)
     return SIM_OK;
 }
 
+// write the pending |basis> (sim_reset is lazy)
 static int materialize(sim_t *s)
 {
     if (!s->reset_pending) return SIM_OK;
@@ -180,6 +180,8 @@ int sim_default_options(sim_options *opt)
 }
 
 const char *sim_global_error(void) { return g_err.c_str(); }
+
+uint64_t sim_kernel_launches(void) { return launches_total(); }
 
 const char *sim_last_error(const sim_t *s) { return s ? s->err.c_str() : g_err.c_str(); }
 

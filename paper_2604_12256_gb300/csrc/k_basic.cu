@@ -4,11 +4,22 @@
 // merge booster (Algorithm 7 / Algorithm 5 first branch) and the read-out
 // reductions (norm, <Z-string>, probabilities, top-k) in FP64 accumulation
 // with a fixed reduction order.
+#include <atomic>
 #include <cstdint>
 
 #include "kernels.h"
 
 namespace svs {
+
+static std::atomic<uint64_t> g_launches{0};
+
+cudaError_t counted(cudaError_t e, int kernels)
+{
+    if (e == cudaSuccess) g_launches.fetch_add((uint64_t)kernels, std::memory_order_relaxed);
+    return e;
+}
+
+uint64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 template <typename R> struct Cx;
 template <> struct Cx<float> { using T = float2; };
@@ -54,7 +65,7 @@ cudaError_t launch_init_basis(void *a, int n, bool f64, uint64_t basis, cudaStre
     if (e != cudaSuccess) return e;
     if (f64) k_set_one<double2><<<1, 1, 0, st>>>((double2 *)a, basis);
     else k_set_one<float2><<<1, 1, 0, st>>>((float2 *)a, basis);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), 1);
 }
 
 // ------------------------------------------------------------ dense gate
@@ -129,7 +140,7 @@ static cudaError_t gate_dense_t(void *a, int n, int k, const int *q, const void 
     case 6: k_gate_dense<R, 6><<<grid, 256, 0, st>>>(A, n, g, M); break;
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), 1);
 }
 
 cudaError_t launch_gate_dense(void *a, int n, bool f64, int k, const int *q, const void *dmat, cudaStream_t st)
@@ -192,7 +203,7 @@ cudaError_t launch_gate_diag(void *a, int n, bool f64, int k, const int *q, int 
     int grid = grid_for(groups, 256, 8);
     if (f64) k_gate_diag<double><<<grid, 256, 0, st>>>((double2 *)a, n, g, (const double2 *)dvals);
     else k_gate_diag<float><<<grid, 256, 0, st>>>((float2 *)a, n, g, (const float2 *)dvals);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), 1);
 }
 
 // ------------------------------------------------------------ small phase sweep
@@ -223,7 +234,7 @@ cudaError_t launch_phase_small(void *a, int n, bool f64, const uint64_t *terms, 
     int grid = grid_for(N, 256, 8);
     if (f64) k_phase_small<double><<<grid, 256, 0, st>>>((double2 *)a, N, terms, nt);
     else k_phase_small<float><<<grid, 256, 0, st>>>((float2 *)a, N, terms, nt);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), 1);
 }
 
 // ------------------------------------------------------------ tensor product
@@ -252,7 +263,7 @@ cudaError_t launch_tensor(void *out, const void *hi, int n_hi, const void *lo, i
     int grid = grid_for(total, 256, 8);
     if (f64) k_tensor<double><<<grid, 256, 0, st>>>((double2 *)out, (const double2 *)hi, (const double2 *)lo, n_lo, total);
     else k_tensor<float><<<grid, 256, 0, st>>>((float2 *)out, (const float2 *)hi, (const float2 *)lo, n_lo, total);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), 1);
 }
 
 // ------------------------------------------------------------ reductions
@@ -314,7 +325,7 @@ cudaError_t launch_norm(const void *a, int n, bool f64, double *part, double *ou
     if (f64) k_norm_part<double><<<kRedBlocks, kRedThreads, 0, st>>>((const double2 *)a, N, part);
     else k_norm_part<float><<<kRedBlocks, kRedThreads, 0, st>>>((const float2 *)a, N, part);
     k_sum_parts<<<1, 256, 0, st>>>(part, kRedBlocks, 1, out);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), 2);
 }
 
 template <typename R, int NT>
@@ -369,7 +380,7 @@ cudaError_t launch_expect_z(const void *a, int n, bool f64, const uint64_t *mask
     if (f64) k_expect_part<double, 16><<<kRedBlocks, kRedThreads, 0, st>>>((const double2 *)a, N, masks, nt, part);
     else k_expect_part<float, 16><<<kRedBlocks, kRedThreads, 0, st>>>((const float2 *)a, N, masks, nt, part);
     k_sum_parts<<<nt, 256, 0, st>>>(part, kRedBlocks, nt, out);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), 2);
 }
 
 template <typename R>
@@ -385,7 +396,7 @@ cudaError_t launch_probs(const void *a, int n, bool f64, double *out, cudaStream
     int grid = grid_for(N, 256, 8);
     if (f64) k_probs<double><<<grid, 256, 0, st>>>((const double2 *)a, N, out);
     else k_probs<float><<<grid, 256, 0, st>>>((const float2 *)a, N, out);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), 1);
 }
 
 // ------------------------------------------------------------ top-k
@@ -496,7 +507,7 @@ cudaError_t launch_topk(const void *a, int n, bool f64, int k, void *scratch, ui
     else k_topk<float, true><<<G, kTopThreads, 0, st>>>((const float2 *)a, nullptr, N, k, lists);
     k_topk<float, false><<<1, kTopThreads, 0, st>>>(nullptr, lists, (int64_t)G * k, k, final_);
     k_topk_split<<<1, 256, 0, st>>>(final_, k, idx, p);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), 3);
 }
 
 }  // namespace svs

@@ -197,7 +197,7 @@ cudaError_t launch_batch(const BatchReq *reqs_dev, int nreq, int max_n, const ui
     }
     if (f64) k_batch<double><<<nreq, kBatchThreads, smem, st>>>(reqs_dev, blob_dev, outs_dev);
     else k_batch<float><<<nreq, kBatchThreads, smem, st>>>(reqs_dev, blob_dev, outs_dev);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), 1);
 }
 
 }  // namespace svs

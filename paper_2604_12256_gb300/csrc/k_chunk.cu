@@ -388,7 +388,7 @@ __device__ __forceinline__ void cta_sums(const uint32_t *prog, typename CT<R>::W
 
 // ------------------------------------------------------------ K4 chunk sweep
 template <typename R, int C, int RB>
-__global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 2 : 8) k_chunk(typename CT<R>::T2 *__restrict__ a,
+__global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(typename CT<R>::T2 *__restrict__ a,
                                                          const uint32_t *__restrict__ gprog, int n)
 {
     using T2 = typename CT<R>::T2;
@@ -496,14 +496,14 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 2 : 8) k_chunk(
             }
         }
     };
-    // register double buffer: the next chunk's amplitudes are in flight
-    // while this chunk goes through its stages
-    T2 pf[NR];
+    // no register double buffer: without one the kernel fits in 80 registers
+    // and three CTAs per SM, whose loads overlap each other's stages
     int64_t ch = blockIdx.x;
     uint64_t base = chunk_base(ch);
-    if (ch < nchunks) load_regs(pf, base);
     for (; ch < nchunks; ch += gridDim.x) {
-        // ---- the prefetched chunk -> shared
+        T2 pf[NR];
+        load_regs(pf, base);
+        // ---- the chunk -> shared
 #pragma unroll
         for (int it = 0; it < NR / 2; it++) {
             const uint32_t p = pld_tid ^ swz<SW, C>((uint32_t)it << (TB + 1));
@@ -516,7 +516,6 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 2 : 8) k_chunk(
         __syncthreads();
         const int64_t nch = ch + gridDim.x;
         const uint64_t nbase = nch < nchunks ? chunk_base(nch) : 0;
-        if (nch < nchunks) load_regs(pf, nbase);
         // ---- register stages
         for (int s = 0; s < nst; s++) {
             const uint32_t *sp = prog + ldw(prog + H_STAGE_OFF + s);
@@ -657,7 +656,7 @@ static cudaError_t chunk_t(void *a, int n, const uint32_t *prog, size_t smem, cu
     cudaError_t e = sized_grid(k_chunk<R, C, RB>, attr, T, smem, (int64_t)1 << (n - C), grid);
     if (e != cudaSuccess) return e;
     k_chunk<R, C, RB><<<grid, T, smem, st>>>((typename CT<R>::T2 *)a, prog, n);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), 1);
 }
 
 cudaError_t launch_chunk(void *a, int n, bool f64, int C, int RB, const uint32_t *prog, size_t smem,
@@ -685,7 +684,7 @@ static cudaError_t diag_t(void *a, int n, const uint32_t *prog, size_t smem, cud
     cudaError_t e = sized_grid(k_diag<R, RB>, attr, 128, smem, (int64_t)1 << (n - C), grid);
     if (e != cudaSuccess) return e;
     k_diag<R, RB><<<grid, 128, smem, st>>>((typename CT<R>::T2 *)a, prog, n);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), 1);
 }
 
 cudaError_t launch_diag_sweep(void *a, int n, bool f64, const uint32_t *prog, size_t smem, cudaStream_t st)

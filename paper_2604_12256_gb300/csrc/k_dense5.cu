@@ -318,7 +318,7 @@ cudaError_t launch_dense5(void *a, int n, bool f64, int precision, const int *q,
     if (f64) {
         int grid = (int)std::min<int64_t>((ncol + 127) / 128, (int64_t)device_sm_count() * 8);
         k_dense5_fma<double><<<grid, 128, 0, st>>>((double2 *)a, n, g, (const double2 *)U64);
-        return cudaGetLastError();
+        return counted(cudaGetLastError(), 1);
     }
     if (precision == 0) {   // split-TF32 on the tensor cores
         static bool attr = false;
@@ -332,11 +332,11 @@ cudaError_t launch_dense5(void *a, int n, bool f64, int precision, const int *q,
         // two CTAs per SM: 2 x 64 TMEM columns, 2 x ~97 KB shared memory
         int grid = (int)std::min<int64_t>(tiles, (int64_t)device_sm_count() * 2);
         k_dense5_tc<<<grid, kTcCols, smem, st>>>((float2 *)a, n, g, (const double2 *)U64, status);
-        return cudaGetLastError();
+        return counted(cudaGetLastError(), 1);
     }
     int grid = (int)std::min<int64_t>((ncol + 127) / 128, (int64_t)device_sm_count() * 8);
     k_dense5_fma<float><<<grid, 128, 0, st>>>((float2 *)a, n, g, (const double2 *)U64);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), 1);
 }
 
 }  // namespace svs

@@ -11,6 +11,11 @@ namespace svs {
 
 constexpr int kNumSMs = 152;   // sizing fallback when the device query fails
 
+// Kernels launched by this library in this process: every launcher adds the
+// number of kernels it enqueued when the launch succeeded.
+cudaError_t counted(cudaError_t e, int kernels);
+uint64_t launches_total();
+
 // |basis> : zero the vector and set one amplitude to 1 (write-only sweep)
 cudaError_t launch_init_basis(void *a, int n, bool is_f64, uint64_t basis, cudaStream_t st);
 

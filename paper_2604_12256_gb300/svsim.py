@@ -96,6 +96,7 @@ _SIGS = [
     ("sim_last_plan_stats", ctypes.c_int, [_P, ctypes.POINTER(sim_plan_stats)]),
     ("sim_profile_enable", ctypes.c_int, [_P, ctypes.c_int]),
     ("sim_profile_read", ctypes.c_int, [_P, ctypes.POINTER(sim_profile)]),
+    ("sim_kernel_launches", ctypes.c_uint64, []),
     ("sim_expectation_noalloc", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t, _P, _P]),
     ("srv_create", ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_P)]),
     ("srv_submit", ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
@@ -318,9 +319,13 @@ class Server:
 
     def submit(self, circuit: _circ.Circuit, top_k: int = 64, masks: Sequence[int] = (),
                dtype: int = SIM_C64) -> int:
-        ga = GateArray(circuit.gates)
+        return self.submit_array(GateArray(circuit.gates), circuit.n, circuit.basis, top_k, masks, dtype)
+
+    def submit_array(self, ga: "GateArray", n: int, basis: int = 0, top_k: int = 64, masks: Sequence[int] = (),
+                     dtype: int = SIM_C64) -> int:
+        """Queue an already marshalled gate list (the server copies it)."""
         m = np.ascontiguousarray(np.array(list(masks), dtype=np.uint64)) if len(masks) else None
-        req = srv_request(circuit.n, dtype, ctypes.cast(ga.arr, ctypes.c_void_p), ga.n, circuit.basis, top_k,
+        req = srv_request(n, dtype, ctypes.cast(ga.arr, ctypes.c_void_p), ga.n, basis, top_k,
                           m.ctypes.data if m is not None else None, 0 if m is None else len(m))
         t = ctypes.c_uint64()
         _check(self.lib.srv_submit(self.h, ctypes.byref(req), ctypes.byref(t)))
@@ -350,6 +355,11 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+def kernel_launches() -> int:
+    """sim_kernel_launches: kernels this library has launched in this process."""
+    return int(load().sim_kernel_launches())
 
 
 def expectation_noalloc(dev_state: int, n: int, dtype: int, dev_masks: int, n_terms: int, dev_out: int,
