@@ -41,7 +41,7 @@ WORKLOAD = "28-qubit diagonal-heavy gate-level stream (500 gates, 80% RZ/CP/RZZ,
 TRAFFIC_PER_AMP = {
     # profiles/k_chunk_diagheavy_25q.md: 475.6 MB per 2^25-amplitude launch;
     # a sweep's traffic grows with the amplitudes it processes
-    "31c90410b3be81eee0a16191da362476d0f0d9a3afe9db3a91fa0f1bb6b115b9": 475.6e6 / 2 ** 25,
+    ("k_chunk.cu", "31c90410b3be81eee0a16191da362476d0f0d9a3afe9db3a91fa0f1bb6b115b9", ""): 475.6e6 / 2 ** 25,
 }
 
 
@@ -106,27 +106,39 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_sample(budget_s: float = 15.0):
+PRECISIONS = {"tf32x3": 0, "fp32": 1, "fp64": 2}
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # SMs x FP32 lanes x FMA x max SM clock
+FP64_PEAK_TFLOPS = 1.25                                # GB300 nominal FP64 (non-tensor) rate
+
+
+def _workload_circuit(args, n):
+    from paper_2604_12256_gb300 import circuits as C
+    if args.workload == "layered-dense":
+        return C.layered(n, 20, 0)
+    return C.diag_heavy(n, N_GATES, SEED)
+
+
+def cpu_oracle_sample(args, budget_s: float = 15.0):
     """Time the CPU oracle (complex128, gate by gate, all host cores) on the
     first gates of the workload until ~budget_s of work; returns
-    (amplitude-updates/s, cores, sample description)."""
-    import numpy as np
+    (amplitude-updates/s, cores, sample description).  States above 28
+    qubits are sampled at 28 qubits (the oracle's host memory)."""
     import oracle
-    from paper_2604_12256_gb300 import circuits as C
-    c = C.diag_heavy(N_QUBITS, N_GATES, SEED)
+    n = min(N_QUBITS, 28)
+    c = _workload_circuit(args, n)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    a = oracle.basis_state(N_QUBITS, 0)
-    oracle.run_inplace(N_QUBITS, a, c.gates[:1], cores)    # warm: page in the 4 GiB state
+    a = oracle.basis_state(n, 0)
+    oracle.run_inplace(n, a, c.gates[:1], cores)    # warm: page in the state
     done, t0 = 0, time.perf_counter()
     for g in c.gates[1:]:
-        oracle.run_inplace(N_QUBITS, a, [g], cores)
+        oracle.run_inplace(n, a, [g], cores)
         done += 1
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
     del a
-    return done * (1 << N_QUBITS) / dt, cores, \
-        f"gates 2..{done + 1} of {len(c.gates)} at {N_QUBITS} qubits, complex128, {dt:.1f} s (per-gate rate)"
+    return done * (1 << n) / dt, cores, \
+        f"gates 2..{done + 1} of {len(c.gates)} at {n} qubits, complex128, {dt:.1f} s (per-gate rate)"
 
 
 def run_reference(args, rank, world):
@@ -134,52 +146,47 @@ def run_reference(args, rank, world):
         return
     vals = []
     for _ in range(args.warmup):
-        cpu_oracle_sample(min(5.0, args.ref_budget))
+        cpu_oracle_sample(args, min(5.0, args.ref_budget))
     for _ in range(args.steps):
-        v, cores, sample = cpu_oracle_sample(args.ref_budget)
+        v, cores, sample = cpu_oracle_sample(args, args.ref_budget)
         vals.append(v)
     v = statistics.median(vals)
-    steps_per_s = v / (len(_circuit_gates()) * (1 << N_QUBITS))
+    G = len(_workload_circuit(args, N_QUBITS).gates)
+    steps_per_s = v / (G * (1 << N_QUBITS))
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 / steps_per_s, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "gates": len(_circuit_gates()),
-                       "seed": SEED, "l2": "state (4 GiB) larger than L2"},
+            "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "gates": G,
+                       "seed": SEED, "l2": "state larger than L2"},
             "impl": "reference",
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-_GATES = None
-
-
-def _circuit_gates():
-    global _GATES
-    if _GATES is None:
-        from paper_2604_12256_gb300 import circuits as C
-        _GATES = C.diag_heavy(N_QUBITS, N_GATES, SEED).gates
-    return _GATES
-
-
 def run_gpu(args, rank, world, dist):
     import torch
     from paper_2604_12256_gb300 import build as B
-    from paper_2604_12256_gb300 import circuits as C
     from paper_2604_12256_gb300 import svsim as S
 
     B.build()
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    circ = C.diag_heavy(N_QUBITS, N_GATES, SEED)
+    dense = args.workload == "layered-dense"
+    dt = S.SIM_C128 if args.dtype == "c128" else S.SIM_C64
+    s_amp = 16 if dt == S.SIM_C128 else 8
+    circ = _workload_circuit(args, N_QUBITS)
     ga = S.GateArray(circ.gates)
     G = len(circ.gates)
     amps = 1 << N_QUBITS
     # the state lives in a torch-owned HBM buffer; kernels run on torch's stream
-    buf = torch.empty(2 * amps, dtype=torch.float32, device="cuda")
+    buf = torch.empty(amps * s_amp // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    sim = S.Sim(N_QUBITS, S.SIM_C64, dev_buf=buf.data_ptr(), nbytes=buf.numel() * 4, stream=stream.cuda_stream)
+    sim = S.Sim(N_QUBITS, dt, dev_buf=buf.data_ptr(), nbytes=buf.numel() * 4, stream=stream.cuda_stream)
     opt = S.default_options()
+    if dense:
+        opt.flags = S.SIM_F_TC | S.SIM_F_DIAG
+        opt.dense_precision = PRECISIONS[args.precision]
     if args.register_bits:
         opt.register_bits = args.register_bits
 
@@ -236,53 +243,71 @@ def run_gpu(args, rank, world, dist):
     h2d = prof["h2d_bytes"] // max(1, args.steps)
     d2h = 64 * 16 + 16 * 8
 
-    # the unfused gate-by-gate GPU path on the same circuit (one timed run)
-    unf = S.default_options(flags=0)
-    sim.reset(0)
-    sim.apply(ga, unf)
-    torch.cuda.synchronize()
-    u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    u0.record(stream)
-    sim.reset(0)
-    sim.apply(ga, unf)
-    u1.record(stream)
-    torch.cuda.synchronize()
-    unf_ms = u0.elapsed_time(u1)
+    unfused = None
+    if not args.no_unfused:
+        # the unfused gate-by-gate GPU path on the same circuit (one timed run)
+        unf = S.default_options(flags=0)
+        sim.reset(0)
+        sim.apply(ga, unf)
+        torch.cuda.synchronize()
+        u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u0.record(stream)
+        sim.reset(0)
+        sim.apply(ga, unf)
+        u1.record(stream)
+        torch.cuda.synchronize()
+        unf_ms = u0.elapsed_time(u1)
+        unfused = {"ms_per_step": unf_ms, "value": G * amps / (unf_ms / 1e3), "speedup_fused_vs_unfused": unf_ms / ms}
 
     peak, peak_kind = _peaks()
-    ch = prof["chunk"]
-    achieved = ch["bytes"] / (ch["ms"] / 1e3) / 1e9 if ch["ms"] > 0 else None
-    src = open(os.path.join(ROOT, "paper_2604_12256_gb300", "csrc", "k_chunk.cu"), "rb").read()
-    tpa = TRAFFIC_PER_AMP.get(hashlib.sha256(src).hexdigest())
+    kind = "dense" if dense else "chunk"
+    kp = prof[kind]
+    nl = max(1, kp["launches"])
+    avg_ms = kp["ms"] / nl
+    bytes_per_launch = kp["bytes"] / nl
+    kname = "k_dense5_tc (dense 5-qubit block, tcgen05 split-TF32)" if dense and args.precision == "tf32x3" \
+        and dt == S.SIM_C64 else ("k_dense5_fma (dense 5-qubit block, CUDA cores)" if dense
+                                  else "k_chunk (cache-blocked chunk sweep)")
+    ksrc = "k_dense5.cu" if dense else "k_chunk.cu"
+    src = open(os.path.join(ROOT, "paper_2604_12256_gb300", "csrc", ksrc), "rb").read()
+    tpa = TRAFFIC_PER_AMP.get((ksrc, hashlib.sha256(src).hexdigest(), args.precision if dense else ""))
     traffic = tpa * amps if tpa is not None else None
+    if dense and (args.precision != "tf32x3" or dt == S.SIM_C128):
+        # 32 complex multiply-adds per amplitude: 256 real flops
+        fp64 = args.precision == "fp64" or dt == S.SIM_C128
+        pk = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+        achieved = 256.0 * amps / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                "frac": achieved / pk, "traffic": traffic,
+                "peak_source": "FP64 nominal rate" if fp64 else "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    else:
+        achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9 if kp["ms"] > 0 else None
+        roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic, "peak_source": peak_kind}
+    roof.update({"launches": kp["launches"], "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": bytes_per_launch})
     total_bytes = sum(v["bytes"] for k, v in prof.items() if isinstance(v, dict)) / args.steps
     value = world * G * amps / (ms / 1e3)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "gates": G, "seed": SEED,
-                       "parallelism": f"replicas x{world}", "l2": "state (2 GiB) larger than L2, no flush",
-                       "sweeps": plan["sweeps"], "chunk_ops": plan["chunk_ops"], "diag_fused": plan["diag_fused"],
-                       "plan_ms": plan["plan_ms"]},
+            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "gates": G,
+                       "seed": 0 if dense else SEED, "parallelism": f"replicas x{world}",
+                       "l2": f"state ({amps * s_amp / 2 ** 30:g} GiB) larger than L2, no flush",
+                       "sweeps": plan["sweeps"], "chunk_ops": plan["chunk_ops"], "dense_ops": plan["dense_ops"],
+                       "diag_fused": plan["diag_fused"], "plan_ms": plan["plan_ms"]},
             "hbm_gbs": total_bytes / (ms / 1e3) / 1e9,
             "hbm_frac_of_" + peak_kind: total_bytes / (ms / 1e3) / 1e9 / peak,
-            "roofline": {"bound": "hbm", "kernel": "k_chunk (cache-blocked chunk sweep)",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                         "launches": ch["launches"], "avg_launch_ms": ch["ms"] / max(1, ch["launches"]),
-                         "algorithmic_bytes_per_launch": ch["bytes"] / max(1, ch["launches"]),
-                         "peak_source": peak_kind},
-            "unfused": {"ms_per_step": unf_ms, "value": G * amps / (unf_ms / 1e3),
-                        "speedup_fused_vs_unfused": unf_ms / ms},
+            "roofline": roof,
+            "unfused": unfused,
             "e2e": {"value": world * G * amps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
             "gpu_launches": int(gpu_launches),
             "clocks": clk,
         }
         if not args.no_cpu_baseline:
-            v, cores, sample = cpu_oracle_sample(args.ref_budget)
+            v, cores, sample = cpu_oracle_sample(args, args.ref_budget)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
         print(json.dumps(line), flush=True)
     sim.close()
@@ -436,17 +461,32 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--register-bits", type=int, default=0,
                     help="chunk bits per thread in the cache-blocked kernel (0 = library default)")
+    ap.add_argument("--workload", default="diag-heavy", choices=["diag-heavy", "layered-dense"],
+                    help="diag-heavy: the 28-qubit gate-level stream; layered-dense: depth-20 layered "
+                         "circuit in dense 5-qubit blocks (34 qubits complex64 / 33 complex128 by default)")
+    ap.add_argument("--precision", default="tf32x3", choices=sorted(PRECISIONS),
+                    help="dense-block arithmetic for --workload layered-dense")
+    ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--no-unfused", action="store_true", help="skip the gate-by-gate comparison run")
     ap.add_argument("--serve", action="store_true",
                     help="time the serving loop on a Poisson request stream instead")
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--streams", type=int, default=4, help="serving worker streams")
     ap.add_argument("--budget-gib", type=float, default=32.0, help="serving HBM budget for admitted states")
-    ap.add_argument("--qubits", type=int, default=N_QUBITS,
-                    help="same workload on fewer qubits (small cases for ncu captures)")
+    ap.add_argument("--qubits", type=int, default=0,
+                    help="qubits of the workload (0: its default; smaller for ncu captures)")
     args = ap.parse_args()
-    if args.qubits != N_QUBITS:
+    if args.workload == "layered-dense":
+        n = args.qubits or (33 if args.dtype == "c128" else 34)
+        WORKLOAD = (f"{n}-qubit random layered circuit, depth 20 (Haar U(2) on every qubit, CZ brickwork), "
+                    f"fused into dense 5-qubit blocks ({args.precision if args.dtype == 'c64' else 'fp64'}), "
+                    f"{'complex128' if args.dtype == 'c128' else 'complex64'}")
+        N_QUBITS = n
+    elif args.qubits and args.qubits != N_QUBITS:
         WORKLOAD = WORKLOAD.replace(f"{N_QUBITS}-qubit", f"{args.qubits}-qubit")
         N_QUBITS = args.qubits
+    if args.dtype == "c128" and args.workload == "diag-heavy":
+        WORKLOAD = WORKLOAD.replace("complex64", "complex128")
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

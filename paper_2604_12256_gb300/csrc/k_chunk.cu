@@ -274,8 +274,12 @@ __host__ __device__ __forceinline__ constexpr int low_bit(int k)
     return j;
 }
 
+// log2 of a power of two
+__host__ __device__ __forceinline__ constexpr int log2_of(int x) { return low_bit(x); }
+
 // ------------------------------------------------------------ phase segment
-// Shared sums of a launch: cta_ph[d * S + s] (per chunk) and
+// Shared sums of a launch: cta_ph[d * SC + s] (per chunk; SC = 1 + RB + TB,
+// slots 1 + RB + i are coefficients of thread bit i) and
 // thr_ph[(d * S + s) * T + tid] (per thread, segments d < nhoist), S = 1 + RB.
 template <typename R, int RB, int T>
 __device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uint64_t x0, const uint32_t *body,
@@ -285,12 +289,17 @@ __device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uin
     using W = typename CT<R>::W;
     constexpr int NR = 1 << RB;
     constexpr int S = 1 + RB;
+    constexpr int TB = log2_of(T);
+    constexpr int SC = (int)cta_slots(RB, TB);
     const int d = (int)ldw(body + D_INDEX);
     const bool hoisted = d < nhoist;
     const int nb = (int)ldw(body + D_NBASE);
     const int nm = (int)ldw(body + D_NMULTI);
     const uint32_t *t = body + D_TERMS;
-    W base = cta_ph[d * S];
+    W base = cta_ph[d * SC];
+#pragma unroll
+    for (int i = 0; i < TB; i++)
+        if ((tid >> i) & 1) base += cta_ph[d * SC + 1 + RB + i];
     if (hoisted) base += thr_ph[(d * S) * T + tid];
     for (int i = 0; i < nb; i++, t += kTermWords) {
         uint64_t m = ld64(t);
@@ -299,7 +308,7 @@ __device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uin
     W lin[RB];
 #pragma unroll
     for (int j = 0; j < RB; j++) {
-        lin[j] = cta_ph[d * S + 1 + j];
+        lin[j] = cta_ph[d * SC + 1 + j];
         if (hoisted) lin[j] += thr_ph[(d * S + 1 + j) * T + tid];
         const int cnt = (int)ldw(body + D_NLIN + j);
         for (int i = 0; i < cnt; i++, t += kTermWords) {
@@ -398,6 +407,7 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
     constexpr int NR = 1 << RB;
     constexpr int SW = CT<R>::SWZ;
     constexpr int S = 1 + RB;
+    constexpr int SC = (int)cta_slots(RB, TB);
     extern __shared__ __align__(16) unsigned char smraw[];
     R *sre = (R *)smraw;
     R *sim = sre + (1 << C);
@@ -408,7 +418,7 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
     const int nd = (int)ldw(prog + H_NDSEG);
     const int nhoist = (int)ldw(prog + H_NHOIST);
     W *cta_ph = (W *)(prog + ((ldw(prog + H_WORDS) + 3) & ~3u));
-    W *thr_ph = (W *)((unsigned char *)cta_ph + (((size_t)nd * S * sizeof(W) + 15) & ~(size_t)15));
+    W *thr_ph = (W *)((unsigned char *)cta_ph + (((size_t)nd * SC * sizeof(W) + 15) & ~(size_t)15));
     __shared__ uint64_t s_git[NR / 2];    // global offset of load iteration `it`
     __shared__ uint32_t s_sit[NR / 2];    // swizzled smem position of `it` on the store
     __shared__ uint64_t s_dep[768];       // chunk number byte k -> its free-qubit bits
@@ -512,7 +522,7 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
             sre[p ^ 1] = pf[2 * it + 1].x;
             sim[p ^ 1] = pf[2 * it + 1].y;
         }
-        cta_sums<R, T>(prog, cta_ph, nd * S, base, tid);
+        cta_sums<R, T>(prog, cta_ph, nd * SC, base, tid);
         __syncthreads();
         const int64_t nch = ch + gridDim.x;
         const uint64_t nbase = nch < nchunks ? chunk_base(nch) : 0;
@@ -598,6 +608,7 @@ __global__ void __launch_bounds__(128) k_diag(typename CT<R>::T2 *__restrict__ a
     constexpr int NR = 1 << RB;
     constexpr int C = 7 + RB;
     constexpr int S = 1 + RB;
+    constexpr int SC = (int)cta_slots(RB, 7);
     extern __shared__ __align__(16) unsigned char smraw[];
     uint32_t *prog = (uint32_t *)smraw;
     const int tid = threadIdx.x;
@@ -606,14 +617,14 @@ __global__ void __launch_bounds__(128) k_diag(typename CT<R>::T2 *__restrict__ a
     const int nd = (int)ldw(prog + H_NDSEG);
     const int nhoist = (int)ldw(prog + H_NHOIST);
     W *cta_ph = (W *)(prog + ((ldw(prog + H_WORDS) + 3) & ~3u));
-    W *thr_ph = (W *)((unsigned char *)cta_ph + (((size_t)nd * S * sizeof(W) + 15) & ~(size_t)15));
+    W *thr_ph = (W *)((unsigned char *)cta_ph + (((size_t)nd * SC * sizeof(W) + 15) & ~(size_t)15));
     const uint32_t *sp = prog + ldw(prog + H_STAGE_OFF);
     const uint32_t *op = sp + S_SIZE + O_BODY;
     thread_sums<R, 128>(prog, thr_ph, nhoist * S, tid);
     const int64_t ntiles = (int64_t)1 << (n - C);
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint64_t base = (uint64_t)tile << C;
-        cta_sums<R, 128>(prog, cta_ph, nd * S, base, tid);
+        cta_sums<R, 128>(prog, cta_ph, nd * SC, base, tid);
         __syncthreads();
         const uint64_t x0 = base | (uint64_t)tid;
         T2 v[NR];

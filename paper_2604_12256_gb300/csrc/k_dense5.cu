@@ -195,18 +195,24 @@ __global__ void __launch_bounds__(kTcCols) k_dense5_tc(float2 *__restrict__ a, i
     const int64_t ncol = (int64_t)1 << (n - 5);
     const int64_t ntiles = (ncol + kTcCols - 1) / kTcCols;
     uint32_t phase = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        // ---- A tile: this thread's column, split into TF32 hi + lo
-        const int64_t col = tile * kTcCols + tid;
-        const bool valid = col < ncol;
-        const uint64_t b = valid ? d5_base((uint64_t)col, g) : 0;
-        float xr[32], xi[32];
+    // this thread's column of a tile: its 32 amplitudes into registers
+    float xr[32], xi[32];
+    auto load_col = [&](int64_t t, uint64_t &base, bool &ok) {
+        const int64_t col = t * kTcCols + tid;
+        ok = t < ntiles && col < ncol;
+        base = ok ? d5_base((uint64_t)col, g) : 0;
 #pragma unroll
         for (int c = 0; c < 32; c++) {
-            float2 v = valid ? a[b | g.off[c]] : make_float2(0.f, 0.f);
+            float2 v = ok ? a[base | g.off[c]] : make_float2(0.f, 0.f);
             xr[c] = v.x;
             xi[c] = v.y;
         }
+    };
+    uint64_t b = 0;
+    bool valid = false;
+    load_col(blockIdx.x, b, valid);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        // ---- A tile: this thread's column, split into TF32 hi + lo
 #pragma unroll
         for (int k4 = 0; k4 < 16; k4++) {
             uint32_t h[4], l[4];
@@ -247,6 +253,11 @@ __global__ void __launch_bounds__(kTcCols) k_dense5_tc(float2 *__restrict__ a, i
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
                          : "memory");
         }
+        // ---- the next tile's loads go out now and stay in flight through the
+        // wait and the epilogue (its columns are disjoint from this tile's)
+        uint64_t b_next;
+        bool valid_next;
+        load_col(tile + gridDim.x, b_next, valid_next);
         // ---- wait for the products (bounded), then read this thread's row
         uint32_t it = 0;
         while (!mbar_try_wait(mbar, phase)) {
@@ -282,6 +293,8 @@ __global__ void __launch_bounds__(kTcCols) k_dense5_tc(float2 *__restrict__ a, i
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
+        b = b_next;
+        valid = valid_next;
     }
     if (sm.abort_ && tid == 0) {
         atomicExch(status, 1);

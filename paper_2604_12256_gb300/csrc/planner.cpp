@@ -272,8 +272,10 @@ struct DsegCtx {
 // Split a segment's terms: slot terms (no register bit: slot 0; one register
 // bit j: slot 1 + j) go to the CTA table when they only test chunk-selecting
 // qubits, to the thread table when they only test thread bits (and the
-// segment is hoisted), else stay in the body; register-only terms fold into
-// the 2^RB table; terms with several register bits stay in the body.
+// segment is hoisted), else stay in the body; a slot-0 term on
+// chunk-selecting qubits and one thread bit i goes to the CTA table as a
+// coefficient of bit i (slot 1 + RB + i); register-only terms fold into the
+// 2^RB table; terms with several register bits stay in the body.
 static void encode_dseg(ProgWriter &pw, const std::vector<Term> &terms, const DsegCtx &cx)
 {
     const int RB = cx.RB;
@@ -285,11 +287,20 @@ static void encode_dseg(ProgWriter &pw, const std::vector<Term> &terms, const Ds
     std::vector<std::vector<Term>> lin(RB);
     std::vector<std::pair<Term, uint32_t>> multi;
     std::vector<uint64_t> tab(1u << RB, 0);
-    const uint32_t S = 1 + RB;
+    const uint32_t S = 1 + RB, SC = prog::cta_slots(RB, cx.TB);
     auto to_tables = [&](uint32_t slot, uint64_t nonreg, uint64_t w) {
-        const uint64_t mt = nonreg & thrall, mc = nonreg & ~thrall;
+        uint64_t mt = nonreg & thrall;
+        const uint64_t mc = nonreg & ~thrall;
+        if (slot == 0 && mt != 0 && mc != 0 && popc(mt) == 1) {
+            int i = 0;
+            while (i < cx.TB && (1ull << cx.gthr[i]) != mt) i++;
+            if (i < cx.TB) {
+                slot = 1 + RB + i;
+                mt = 0;
+            }
+        }
         if (mt == 0) {
-            cx.cta->push_back(cx.d * S + slot);
+            cx.cta->push_back(cx.d * SC + slot);
             cx.cta->push_back(0);
             cx.cta->push_back((uint32_t)mc);
             cx.cta->push_back((uint32_t)(mc >> 32));
@@ -1229,14 +1240,15 @@ static bool validate_program(const std::vector<uint32_t> &w, int n, bool diag_sw
         sp |= 1u << b;
     }
     // launch-wide term tables
-    const uint32_t ND = w[prog::H_NDSEG], NH = w[prog::H_NHOIST], S = 1 + RB, TB = C - RB;
+    const uint32_t ND = w[prog::H_NDSEG], NH = w[prog::H_NHOIST], S = 1 + RB, TB = C - RB,
+                   SC = prog::cta_slots(RB, TB);
     if (ND > (uint32_t)prog::kMaxDseg || NH > ND) return bad("segment counts");
     if (prog::smem_bytes(w.data(), diag_sweep) > 200 * 1024) return bad("shared memory");
     {
         size_t co = w[prog::H_CTA_OFF], cn = w[prog::H_NCTA], to = w[prog::H_THR_OFF], tn = w[prog::H_NTHR];
         if (co + cn * prog::kCtaWords > W || to + tn * prog::kThrWords > W) return bad("term tables");
         for (size_t i = 0; i < cn; i++)
-            if (w[co + i * prog::kCtaWords] >= ND * S) return bad("CTA table slot");
+            if (w[co + i * prog::kCtaWords] >= ND * SC) return bad("CTA table slot");
         for (size_t i = 0; i < tn; i++) {
             if (w[to + i * prog::kThrWords] >= NH * S) return bad("thread table slot");
             if (w[to + i * prog::kThrWords + 1] >> TB) return bad("thread table mask");

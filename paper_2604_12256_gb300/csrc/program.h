@@ -17,6 +17,12 @@
 
 #include <cstdint>
 
+#if defined(__CUDACC__)
+#define PROG_HD __host__ __device__
+#else
+#define PROG_HD
+#endif
+
 namespace svs {
 namespace prog {
 
@@ -109,16 +115,23 @@ constexpr int kMultiWords = 6;
 
 // Dynamic shared memory of a launch of this program: the chunk's re/im planes
 // (chunk kernel only), the per-chunk CTA sums and the per-thread sums.
+// Shared phase sums of one segment.  CTA table (per chunk): slot 0 = the
+// segment's phase at register index 0, slot 1 + j = the coefficient of
+// register bit j, slot 1 + RB + i = the coefficient of thread bit i (terms on
+// chunk-selecting qubits and one thread bit).  Thread table (per launch): the
+// first 1 + RB of those slots for terms on thread bits only.
+PROG_HD inline constexpr uint32_t cta_slots(uint32_t RB, uint32_t TB) { return 1 + RB + TB; }
+
 inline size_t smem_bytes(const uint32_t *w, bool diag_sweep)
 {
     const size_t C = w[H_C], RB = w[H_RB], wb = w[H_WBYTES];
-    const size_t T = (size_t)1 << (C - RB), S = 1 + RB;
+    const size_t T = (size_t)1 << (C - RB), S = 1 + RB, SC = cta_slots(RB, C - RB);
     const size_t planes = diag_sweep ? 0 : 2 * ((size_t)1 << C) * wb;
     const size_t progw = ((size_t)w[H_WORDS] * 4 + 15) & ~(size_t)15;
     // per-thread stage layouts (chunk kernel): thread part of x0 and of the
     // swizzled register-block offset for every stage
     const size_t layouts = diag_sweep ? 0 : (size_t)w[H_NSTAGE] * T * 12;
-    return planes + progw + (((size_t)w[H_NDSEG] * S * wb + 15) & ~(size_t)15) +
+    return planes + progw + (((size_t)w[H_NDSEG] * SC * wb + 15) & ~(size_t)15) +
            (((size_t)w[H_NHOIST] * S * T * wb + 15) & ~(size_t)15) + layouts;
 }
 
