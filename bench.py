@@ -41,7 +41,7 @@ WORKLOAD = "28-qubit diagonal-heavy gate-level stream (500 gates, 80% RZ/CP/RZZ,
 TRAFFIC_PER_AMP = {
     # profiles/k_chunk_diagheavy_25q.md: 475.6 MB per 2^25-amplitude launch;
     # a sweep's traffic grows with the amplitudes it processes
-    ("k_chunk.cu", "31c90410b3be81eee0a16191da362476d0f0d9a3afe9db3a91fa0f1bb6b115b9", ""): 475.6e6 / 2 ** 25,
+    ("chunk", "31c90410b3be81eee0a16191da362476d0f0d9a3afe9db3a91fa0f1bb6b115b9", ""): 475.6e6 / 2 ** 25,
 }
 
 
@@ -115,7 +115,17 @@ def _workload_circuit(args, n):
     from paper_2604_12256_gb300 import circuits as C
     if args.workload == "layered-dense":
         return C.layered(n, 20, 0)
+    if args.workload == "rzz-full":
+        return C.rzz_full(n)
     return C.diag_heavy(n, N_GATES, SEED)
+
+
+# kernel of each profiled op kind on the state (the profile counts each
+# launch's algorithmic bytes: 2 x 2^n x bytes/amp for a read+write sweep,
+# 2^n x bytes/amp for a write-only one)
+KIND_KERNELS = {"chunk": "k_chunk (cache-blocked chunk sweep)", "diag": "k_diag (fused-diagonal sweep)",
+                "dense": "k_dense5 (dense 5-qubit block)", "tensor": "k_tensor (merge-booster product)",
+                "gate": "k_gate_dense (gate-by-gate)", "gate_diag": "k_gate_diag (gate-by-gate diagonal)"}
 
 
 def cpu_oracle_sample(args, budget_s: float = 15.0):
@@ -260,19 +270,21 @@ def run_gpu(args, rank, world, dist):
         unfused = {"ms_per_step": unf_ms, "value": G * amps / (unf_ms / 1e3), "speedup_fused_vs_unfused": unf_ms / ms}
 
     peak, peak_kind = _peaks()
-    kind = "dense" if dense else "chunk"
+    # the dominant kernel: the op kind with the most device time on the state
+    kind = max(KIND_KERNELS, key=lambda k: prof[k]["ms"] if isinstance(prof.get(k), dict) else -1)
     kp = prof[kind]
     nl = max(1, kp["launches"])
     avg_ms = kp["ms"] / nl
     bytes_per_launch = kp["bytes"] / nl
-    kname = "k_dense5_tc (dense 5-qubit block, tcgen05 split-TF32)" if dense and args.precision == "tf32x3" \
-        and dt == S.SIM_C64 else ("k_dense5_fma (dense 5-qubit block, CUDA cores)" if dense
-                                  else "k_chunk (cache-blocked chunk sweep)")
-    ksrc = "k_dense5.cu" if dense else "k_chunk.cu"
+    kname = KIND_KERNELS[kind]
+    if kind == "dense":
+        kname = "k_dense5_tc (dense 5-qubit block, tcgen05 split-TF32)" if args.precision == "tf32x3" \
+            and dt == S.SIM_C64 else "k_dense5_fma (dense 5-qubit block, CUDA cores)"
+    ksrc = {"chunk": "k_chunk.cu", "diag": "k_chunk.cu", "dense": "k_dense5.cu"}.get(kind, "k_basic.cu")
     src = open(os.path.join(ROOT, "paper_2604_12256_gb300", "csrc", ksrc), "rb").read()
-    tpa = TRAFFIC_PER_AMP.get((ksrc, hashlib.sha256(src).hexdigest(), args.precision if dense else ""))
+    tpa = TRAFFIC_PER_AMP.get((kind, hashlib.sha256(src).hexdigest(), args.precision if dense else ""))
     traffic = tpa * amps if tpa is not None else None
-    if dense and (args.precision != "tf32x3" or dt == S.SIM_C128):
+    if kind == "dense" and (args.precision != "tf32x3" or dt == S.SIM_C128):
         # 32 complex multiply-adds per amplitude: 256 real flops
         fp64 = args.precision == "fp64" or dt == S.SIM_C128
         pk = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
@@ -293,7 +305,7 @@ def run_gpu(args, rank, world, dist):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "gates": G,
-                       "seed": 0 if dense else SEED, "parallelism": f"replicas x{world}",
+                       "seed": 0 if dense else (5 if args.workload == "rzz-full" else SEED), "parallelism": f"replicas x{world}",
                        "l2": f"state ({amps * s_amp / 2 ** 30:g} GiB) larger than L2, no flush",
                        "sweeps": plan["sweeps"], "chunk_ops": plan["chunk_ops"], "dense_ops": plan["dense_ops"],
                        "diag_fused": plan["diag_fused"], "plan_ms": plan["plan_ms"]},
@@ -461,9 +473,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--register-bits", type=int, default=0,
                     help="chunk bits per thread in the cache-blocked kernel (0 = library default)")
-    ap.add_argument("--workload", default="diag-heavy", choices=["diag-heavy", "layered-dense"],
+    ap.add_argument("--workload", default="diag-heavy", choices=["diag-heavy", "layered-dense", "rzz-full"],
                     help="diag-heavy: the 28-qubit gate-level stream; layered-dense: depth-20 layered "
-                         "circuit in dense 5-qubit blocks (34 qubits complex64 / 33 complex128 by default)")
+                         "circuit in dense 5-qubit blocks; rzz-full: RZZ on every qubit pair from |+...+> "
+                         "(both: 34 qubits complex64 / 33 complex128 by default)")
     ap.add_argument("--precision", default="tf32x3", choices=sorted(PRECISIONS),
                     help="dense-block arithmetic for --workload layered-dense")
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
@@ -481,6 +494,11 @@ def main():
         WORKLOAD = (f"{n}-qubit random layered circuit, depth 20 (Haar U(2) on every qubit, CZ brickwork), "
                     f"fused into dense 5-qubit blocks ({args.precision if args.dtype == 'c64' else 'fp64'}), "
                     f"{'complex128' if args.dtype == 'c128' else 'complex64'}")
+        N_QUBITS = n
+    elif args.workload == "rzz-full":
+        n = args.qubits or (33 if args.dtype == "c128" else 34)
+        WORKLOAD = (f"{n}-qubit full-connectivity RZZ gate-level stream ({n * (n - 1) // 2} RZZ, angles uniform "
+                    f"in [0, 2pi), after H on every qubit), {'complex128' if args.dtype == 'c128' else 'complex64'}")
         N_QUBITS = n
     elif args.qubits and args.qubits != N_QUBITS:
         WORKLOAD = WORKLOAD.replace(f"{N_QUBITS}-qubit", f"{args.qubits}-qubit")

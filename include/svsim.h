@@ -113,6 +113,8 @@ typedef struct {
     uint64_t bytes;          /* algorithmic HBM bytes of the plan                  */
     double flops;            /* algorithmic floating-point operations              */
     double plan_ms;          /* host optimizer time                                */
+    uint64_t tensor_fused;   /* tensor products computed by the next sweep's loads
+                                (counted in tensor_ops, not launched)              */
 } sim_plan_stats;
 
 /* ------------------------------------------------------------ lifecycle */

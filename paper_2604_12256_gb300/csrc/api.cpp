@@ -414,8 +414,17 @@ static int execute(sim_t *s, const Plan &p)
     // 2. launches (Algorithm 5)
     for (size_t i = 0; i < p.ops.size(); i++) {
         const Op &o = p.ops[i];
+        if (o.fused) continue;   // a tensor product computed by the next sweep's loads
         void *a = buf_ptr(s, o.buf);
         const unsigned char *cst = s->d_const + off[i];
+        TensorSrc src;
+        const bool fed = i > 0 && p.ops[i - 1].fused;
+        if (fed) {
+            const Op &t = p.ops[i - 1];
+            src.hi = buf_ptr(s, t.buf_hi);
+            src.lo = buf_ptr(s, t.buf_lo);
+            src.n_lo = t.n_lo;
+        }
         cudaError_t e = cudaSuccess;
         long pe = prof_begin(s);
         switch (o.kind) {
@@ -429,7 +438,7 @@ static int execute(sim_t *s, const Plan &p)
                                  s->stream);
             break;
         case OPK_DIAG:
-            e = launch_diag_sweep(a, o.n, f64, (const uint32_t *)cst, prog::smem_bytes(o.words.data(), true),
+            e = launch_diag_sweep(a, o.n, f64, (const uint32_t *)cst, prog::smem_bytes(o.words.data(), true), src,
                                   s->stream);
             break;
         case OPK_PHASE_SMALL:
@@ -437,8 +446,7 @@ static int execute(sim_t *s, const Plan &p)
             break;
         case OPK_CHUNK:
             e = launch_chunk(a, o.n, f64, o.prog.C, o.prog.RB, (const uint32_t *)cst,
-                             prog::smem_bytes(o.words.data(), false),
-                             s->stream);
+                             prog::smem_bytes(o.words.data(), false), src, s->stream);
             break;
         case OPK_TENSOR:
             e = launch_tensor(a, buf_ptr(s, o.buf_hi), o.n_hi, buf_ptr(s, o.buf_lo), o.n_lo, f64, s->stream);
@@ -446,7 +454,7 @@ static int execute(sim_t *s, const Plan &p)
         }
         if (e != cudaSuccess) return cuda_fail(s, e, "kernel launch");
         double amps = (double)((uint64_t)1 << o.n), sz = f64 ? 16.0 : 8.0;
-        double by = (o.kind == OPK_TENSOR || o.kind == OPK_INIT_BASIS) ? amps * sz : 2.0 * amps * sz;
+        double by = (o.kind == OPK_TENSOR || o.kind == OPK_INIT_BASIS || fed) ? amps * sz : 2.0 * amps * sz;
         prof_end(s, pe, (int)o.kind + (o.buf ? 8 : 0), by);
     }
     if (s->prof_on) s->prof.h2d_bytes += bl.b.size();

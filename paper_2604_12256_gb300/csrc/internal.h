@@ -103,6 +103,7 @@ struct Op {
     std::vector<Term> terms;       // DIAG
     ChunkProg prog;                // CHUNK
     int buf_lo = 0, buf_hi = 0, n_lo = 0, n_hi = 0;   // TENSOR: buf <- hi (x) lo
+    bool fused = false;            // TENSOR: computed by the next op's loads, not launched
     std::vector<uint32_t> words;   // CHUNK / DIAG: encoded device program
     int precision = 0;             // DENSE_TC: SIM_DENSE_* arithmetic
 };

@@ -395,10 +395,29 @@ __device__ __forceinline__ void cta_sums(const uint32_t *prog, typename CT<R>::W
     }
 }
 
+// Sweep input from a fused merge-booster product (TensorSrc in kernels.h):
+// amplitude x = hi[x >> n_lo] * lo[x & (2^n_lo - 1)], with the arithmetic of
+// k_tensor.  hi == nullptr: the sweep reads the state itself.
+template <typename T2> struct TSrc {
+    const T2 *hi;
+    const T2 *lo;
+    int n_lo;
+};
+template <typename T2> __device__ __forceinline__ T2 tensor_amp(const TSrc<T2> &s, uint64_t x)
+{
+    const T2 h = __ldg(&s.hi[x >> s.n_lo]);
+    const T2 l = __ldg(&s.lo[x & ((1ull << s.n_lo) - 1)]);
+    T2 w;
+    w.x = h.x * l.x - h.y * l.y;
+    w.y = h.x * l.y + h.y * l.x;
+    return w;
+}
+
 // ------------------------------------------------------------ K4 chunk sweep
 template <typename R, int C, int RB>
 __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(typename CT<R>::T2 *__restrict__ a,
-                                                         const uint32_t *__restrict__ gprog, int n)
+                                                         const uint32_t *__restrict__ gprog, int n,
+                                                         TSrc<typename CT<R>::T2> src)
 {
     using T2 = typename CT<R>::T2;
     using W = typename CT<R>::W;
@@ -493,6 +512,15 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
     };
     // coalesced loads of one chunk's amplitude pairs into registers
     auto load_regs = [&](T2 (&dst)[NR], uint64_t b) {
+        if (src.hi) {
+#pragma unroll
+            for (int it = 0; it < NR / 2; it++) {
+                const uint64_t g = b | g_tid | s_git[it];
+                dst[2 * it] = tensor_amp(src, g);
+                dst[2 * it + 1] = tensor_amp(src, g + 1);
+            }
+            return;
+        }
 #pragma unroll
         for (int it = 0; it < NR / 2; it++) {
             const uint64_t g = b | g_tid | s_git[it];
@@ -601,7 +629,7 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
 // tile + t + m * 128 (register bits on top -> each warp load is contiguous)
 template <typename R, int RB>
 __global__ void __launch_bounds__(128) k_diag(typename CT<R>::T2 *__restrict__ a, const uint32_t *__restrict__ gprog,
-                                              int n)
+                                              int n, TSrc<typename CT<R>::T2> src)
 {
     using T2 = typename CT<R>::T2;
     using W = typename CT<R>::W;
@@ -629,7 +657,8 @@ __global__ void __launch_bounds__(128) k_diag(typename CT<R>::T2 *__restrict__ a
         const uint64_t x0 = base | (uint64_t)tid;
         T2 v[NR];
 #pragma unroll
-        for (int m = 0; m < NR; m++) v[m] = __ldcs(a + x0 + ((uint64_t)m << 7));
+        for (int m = 0; m < NR; m++)
+            v[m] = src.hi ? tensor_amp(src, x0 + ((uint64_t)m << 7)) : __ldcs(a + x0 + ((uint64_t)m << 7));
         dseg_apply<R, RB, 128>(v, x0, op, cta_ph, thr_ph, nhoist, tid);
 #pragma unroll
         for (int m = 0; m < NR; m++) __stcs(a + x0 + ((uint64_t)m << 7), v[m]);
@@ -659,49 +688,56 @@ static cudaError_t sized_grid(K kern, bool &attr, int threads, size_t smem, int6
 }
 
 template <typename R, int C, int RB>
-static cudaError_t chunk_t(void *a, int n, const uint32_t *prog, size_t smem, cudaStream_t st)
+static cudaError_t chunk_t(void *a, int n, const uint32_t *prog, size_t smem, TensorSrc src, cudaStream_t st)
 {
+    using T2 = typename CT<R>::T2;
     constexpr int T = 1 << (C - RB);
     static bool attr = false;
     int grid = 0;
     cudaError_t e = sized_grid(k_chunk<R, C, RB>, attr, T, smem, (int64_t)1 << (n - C), grid);
     if (e != cudaSuccess) return e;
-    k_chunk<R, C, RB><<<grid, T, smem, st>>>((typename CT<R>::T2 *)a, prog, n);
+    const TSrc<T2> ts{(const T2 *)src.hi, (const T2 *)src.lo, src.n_lo};
+    k_chunk<R, C, RB><<<grid, T, smem, st>>>((T2 *)a, prog, n, ts);
     return counted(cudaGetLastError(), 1);
 }
 
 cudaError_t launch_chunk(void *a, int n, bool f64, int C, int RB, const uint32_t *prog, size_t smem,
-                         cudaStream_t st)
+                         TensorSrc src, cudaStream_t st)
 {
     if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
+    if (src.hi && (src.n_lo < 0 || src.n_lo > n || !src.lo)) return cudaErrorInvalidValue;
     if (!f64) {
-        if (C == 12 && RB == 5 && n >= 12) return chunk_t<float, 12, 5>(a, n, prog, smem, st);
-        if (C == 12 && RB == 4 && n >= 12) return chunk_t<float, 12, 4>(a, n, prog, smem, st);
-        if (C == 10 && RB == 5 && n >= 10) return chunk_t<float, 10, 5>(a, n, prog, smem, st);
+        if (C == 12 && RB == 5 && n >= 12) return chunk_t<float, 12, 5>(a, n, prog, smem, src, st);
+        if (C == 12 && RB == 4 && n >= 12) return chunk_t<float, 12, 4>(a, n, prog, smem, src, st);
+        if (C == 10 && RB == 5 && n >= 10) return chunk_t<float, 10, 5>(a, n, prog, smem, src, st);
     } else {
-        if (C == 11 && RB == 4 && n >= 11) return chunk_t<double, 11, 4>(a, n, prog, smem, st);
-        if (C == 9 && RB == 4 && n >= 9) return chunk_t<double, 9, 4>(a, n, prog, smem, st);
+        if (C == 11 && RB == 4 && n >= 11) return chunk_t<double, 11, 4>(a, n, prog, smem, src, st);
+        if (C == 9 && RB == 4 && n >= 9) return chunk_t<double, 9, 4>(a, n, prog, smem, src, st);
     }
     return cudaErrorInvalidValue;
 }
 
 template <typename R, int RB>
-static cudaError_t diag_t(void *a, int n, const uint32_t *prog, size_t smem, cudaStream_t st)
+static cudaError_t diag_t(void *a, int n, const uint32_t *prog, size_t smem, TensorSrc src, cudaStream_t st)
 {
+    using T2 = typename CT<R>::T2;
     constexpr int C = 7 + RB;
     if (n < C) return cudaErrorInvalidValue;
     static bool attr = false;
     int grid = 0;
     cudaError_t e = sized_grid(k_diag<R, RB>, attr, 128, smem, (int64_t)1 << (n - C), grid);
     if (e != cudaSuccess) return e;
-    k_diag<R, RB><<<grid, 128, smem, st>>>((typename CT<R>::T2 *)a, prog, n);
+    const TSrc<T2> ts{(const T2 *)src.hi, (const T2 *)src.lo, src.n_lo};
+    k_diag<R, RB><<<grid, 128, smem, st>>>((T2 *)a, prog, n, ts);
     return counted(cudaGetLastError(), 1);
 }
 
-cudaError_t launch_diag_sweep(void *a, int n, bool f64, const uint32_t *prog, size_t smem, cudaStream_t st)
+cudaError_t launch_diag_sweep(void *a, int n, bool f64, const uint32_t *prog, size_t smem, TensorSrc src,
+                              cudaStream_t st)
 {
     if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
-    return f64 ? diag_t<double, 4>(a, n, prog, smem, st) : diag_t<float, 5>(a, n, prog, smem, st);
+    if (src.hi && (src.n_lo < 0 || src.n_lo > n || !src.lo)) return cudaErrorInvalidValue;
+    return f64 ? diag_t<double, 4>(a, n, prog, smem, src, st) : diag_t<float, 5>(a, n, prog, smem, src, st);
 }
 
 }  // namespace svs

@@ -53,12 +53,24 @@ cudaError_t launch_topk(const void *a, int n, bool is_f64, int k, void *scratch,
                         uint64_t *idx_dev, double *p_dev, cudaStream_t st);
 
 // ---- optimizer-driven sweeps ----
+// Optional input of a sweep: instead of reading the state, amplitude x is
+// hi[x >> n_lo] * lo[x & (2^n_lo - 1)], the merge-booster tensor product
+// (Algorithm 7) that feeds this sweep and is never written on its own.
+// hi == nullptr: the sweep reads the state.  hi, lo: device sub-states of the
+// state's precision, 2^(n - n_lo) and 2^n_lo amplitudes.
+struct TensorSrc {
+    const void *hi = nullptr;
+    const void *lo = nullptr;
+    int n_lo = 0;
+};
+
 // Fused diagonal phase sweep (K3) and cache-blocked chunk sweep (K4): `prog`
 // is a device program written by the encoder in program.h.
 // `smem` = prog::smem_bytes() of the program (dynamic shared memory).
-cudaError_t launch_diag_sweep(void *a, int n, bool is_f64, const uint32_t *prog, size_t smem, cudaStream_t st);
+cudaError_t launch_diag_sweep(void *a, int n, bool is_f64, const uint32_t *prog, size_t smem, TensorSrc src,
+                              cudaStream_t st);
 cudaError_t launch_chunk(void *a, int n, bool is_f64, int C, int RB, const uint32_t *prog, size_t smem,
-                         cudaStream_t st);
+                         TensorSrc src, cudaStream_t st);
 
 // Phase polynomial on small registers: one thread per amplitude sums the
 // nt terms (device array of {mask, w} pairs, uint64 turns).

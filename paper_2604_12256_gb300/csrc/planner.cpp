@@ -884,8 +884,19 @@ static void account(Plan &p)
 {
     sim_plan_stats &s = p.stats;
     int sz = p.dtype == SIM_C64 ? 8 : 16;
-    for (const Op &o : p.ops) {
+    for (size_t i = 0; i < p.ops.size(); i++) {
+        const Op &o = p.ops[i];
         double amps = std::ldexp(1.0, o.n);
+        // a sweep fed by a fused tensor product reads no state: write-only
+        const bool fed = i > 0 && p.ops[i - 1].fused;
+        if (fed) s.bytes -= (uint64_t)(amps * sz);
+        if (o.fused) {   // no launch of its own
+            s.tensor_ops++;
+            s.tensor_fused++;
+            s.state_updates += (uint64_t)amps;
+            s.flops += amps * 6.0;
+            continue;
+        }
         s.ops++;
         switch (o.kind) {
         case OPK_INIT_BASIS:
@@ -1413,6 +1424,15 @@ bool make_plan(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_
     }
     schedule(G, n, opt, dt, 0, plan);
     finalize_words(plan);
+    // a tensor product that only feeds the next sweep of the same buffer is
+    // computed by that sweep's loads: one write-only pass instead of a write
+    // and a read-write pass
+    for (size_t i = 0; i + 1 < plan.ops.size(); i++) {
+        Op &t = plan.ops[i];
+        const Op &x = plan.ops[i + 1];
+        if (t.kind == OPK_TENSOR && x.buf == t.buf && x.n == t.n && (x.kind == OPK_DIAG || x.kind == OPK_CHUNK))
+            t.fused = true;
+    }
     for (const Op &o : plan.ops) {
         if (o.kind == OPK_CHUNK || o.kind == OPK_DIAG)
             if (!validate_program(o.words, o.n, o.kind == OPK_DIAG, err)) return false;
@@ -1462,7 +1482,7 @@ std::string plan_json(const Plan &p)
     os << "{\"n\":" << p.n << ",\"dtype\":" << (int)p.dtype << ",\"wbits\":" << (p.dtype == SIM_C64 ? 32 : 64);
     os << ",\"stats\":{\"gates_in\":" << s.gates_in << ",\"ops\":" << s.ops << ",\"sweeps\":" << s.sweeps
        << ",\"chunk_ops\":" << s.chunk_ops << ",\"diag_ops\":" << s.diag_ops << ",\"gate_ops\":" << s.gate_ops
-       << ",\"tensor_ops\":" << s.tensor_ops << ",\"dense_ops\":" << s.dense_ops << ",\"diag_fused\":" << s.diag_fused
+       << ",\"tensor_ops\":" << s.tensor_ops << ",\"tensor_fused\":" << s.tensor_fused << ",\"dense_ops\":" << s.dense_ops << ",\"diag_fused\":" << s.diag_fused
        << ",\"boosted_gates\":" << s.boosted_gates << ",\"state_updates\":" << s.state_updates
        << ",\"bytes\":" << s.bytes << "}";
     os << ",\"buffers\":[";
@@ -1522,7 +1542,7 @@ std::string plan_json(const Plan &p)
         }
         case OPK_TENSOR:
             os << "\"op\":\"tensor\",\"lo\":" << o.buf_lo << ",\"hi\":" << o.buf_hi << ",\"n_lo\":" << o.n_lo
-               << ",\"n_hi\":" << o.n_hi;
+               << ",\"n_hi\":" << o.n_hi << ",\"fused\":" << (o.fused ? "true" : "false");
             break;
         case OPK_DENSE_TC:
             os << "\"op\":\"gate\",\"qubits\":[";

@@ -46,7 +46,7 @@ class sim_plan_stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in
                 ("gates_in", "ops", "sweeps", "chunk_ops", "diag_ops", "gate_ops", "dense_ops",
                  "tensor_ops", "permute_ops", "diag_fused", "boosted_gates", "state_updates", "bytes")] + \
-               [("flops", ctypes.c_double), ("plan_ms", ctypes.c_double)]
+               [("flops", ctypes.c_double), ("plan_ms", ctypes.c_double), ("tensor_fused", ctypes.c_uint64)]
 
     def asdict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
