@@ -15,7 +15,10 @@
 // Per thread it reduces to base + sum_j m_j lin_j + tab[m] (+ rare terms with
 // several register bits) over the register index m, evaluated with integer
 // adds; one sin/cos per amplitude turns it into a complex factor.
+#include <cmath>
 #include <cstdint>
+#include <mutex>
+#include <vector>
 
 #include "kernels.h"
 #include "program.h"
@@ -70,11 +73,27 @@ __device__ __forceinline__ float2 cis_turns(uint32_t w)
     const float f = fmaf(-0.5f, fmaf(c, c, s * s), 1.5f);
     return make_float2(c * f, s * f);
 }
+// complex128: cis(2 pi w / 2^64) = T0[w >> 56] T1[(w >> 48) & 255]
+// T2[(w >> 40) & 255] cis(e), e = 2 pi (w mod 2^40) / 2^64 < 2 pi 2^-24, with
+// cis(e) = (1 - e^2/2, e (1 - e^2/6)) (the next terms are below 1e-27).
+// Tk[b] = cis(2 pi b / 2^(8k + 8)), rounded from long-double values on the
+// host (set_cis64_tables); three table products replace a sincospi, whose
+// FP64 work dominates phase sweeps on a GPU with a low FP64 rate.
+__device__ double2 g_cis64[3 * 256];
+
+__device__ __forceinline__ double2 cmul_d(double2 a, double2 b)
+{
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
 __device__ __forceinline__ double2 cis_turns(uint64_t w)
 {
-    double s, c;
-    sincospi((double)(int64_t)w * 1.0842021724855044340e-19, &s, &c);   // 2^-63
-    return make_double2(c, s);
+    const double2 t0 = g_cis64[w >> 56];
+    const double2 t1 = g_cis64[256 + ((w >> 48) & 255)];
+    const double2 t2 = g_cis64[512 + ((w >> 40) & 255)];
+    const double e = (double)(w & ((1ull << 40) - 1)) * (6.283185307179586477 * 0x1p-64);
+    const double e2 = e * e;
+    const double2 te = make_double2(fma(-0.5, e2, 1.0), e * fma(-1.0 / 6.0, e2, 1.0));
+    return cmul_d(cmul_d(cmul_d(t0, t1), t2), te);
 }
 
 // packed f32x2 arithmetic (sm_100+): a 64-bit register pair holds (re, im)
@@ -322,6 +341,22 @@ __device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uin
     // cis(0) = 1 to the amplitudes it would skip is exact)
     const bool tabnz = (ldw(body + D_FLAGS) & 1) != 0;
     if (nm == 0 && !tabnz) {
+        if constexpr (sizeof(R) == 8) {
+            // complex128 (FP64 is scarce): the phase is base + sum_j m_j lin[j],
+            // so cis(base) on every amplitude and cis(lin[j]) on those with
+            // register bit j set: 1 + RB sin/cos per thread instead of 2^RB
+            const auto cb = cis_turns(base);
+#pragma unroll
+            for (int m = 0; m < NR; m++) v[m] = cmul(v[m], cb);
+#pragma unroll
+            for (int j = 0; j < RB; j++) {
+                const auto cj = cis_turns(lin[j]);
+#pragma unroll
+                for (int m = 0; m < NR; m++)
+                    if ((m >> j) & 1) v[m] = cmul(v[m], cj);
+            }
+            return;
+        }
         // the common case: walk the register index in Gray-code order, one
         // add per amplitude
         W ph = base;
@@ -701,9 +736,38 @@ static cudaError_t chunk_t(void *a, int n, const uint32_t *prog, size_t smem, Te
     return counted(cudaGetLastError(), 1);
 }
 
+// Fill g_cis64 on the current device once (before its first complex128
+// sweep).  cudaMemcpyToSymbol from pageable memory returns when the copy is
+// done, so kernels enqueued afterwards on any stream see the tables.
+static cudaError_t set_cis64_tables()
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return cudaSuccess;
+    std::vector<double2> t(3 * 256);
+    const long double two_pi = 6.283185307179586476925286766559L;
+    for (int k = 0; k < 3; k++)
+        for (int b = 0; b < 256; b++) {
+            const long double x = two_pi * (long double)b / (long double)(1ull << (8 * k + 8));
+            t[256 * k + b] = make_double2((double)cosl(x), (double)sinl(x));
+        }
+    e = cudaMemcpyToSymbol(g_cis64, t.data(), t.size() * sizeof(double2));
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
 cudaError_t launch_chunk(void *a, int n, bool f64, int C, int RB, const uint32_t *prog, size_t smem,
                          TensorSrc src, cudaStream_t st)
 {
+    if (f64) {
+        cudaError_t e = set_cis64_tables();
+        if (e != cudaSuccess) return e;
+    }
     if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
     if (src.hi && (src.n_lo < 0 || src.n_lo > n || !src.lo)) return cudaErrorInvalidValue;
     if (!f64) {
@@ -735,6 +799,10 @@ static cudaError_t diag_t(void *a, int n, const uint32_t *prog, size_t smem, Ten
 cudaError_t launch_diag_sweep(void *a, int n, bool f64, const uint32_t *prog, size_t smem, TensorSrc src,
                               cudaStream_t st)
 {
+    if (f64) {
+        cudaError_t e = set_cis64_tables();
+        if (e != cudaSuccess) return e;
+    }
     if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
     if (src.hi && (src.n_lo < 0 || src.n_lo > n || !src.lo)) return cudaErrorInvalidValue;
     return f64 ? diag_t<double, 4>(a, n, prog, smem, src, st) : diag_t<float, 5>(a, n, prog, smem, src, st);
