@@ -357,18 +357,32 @@ __device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uin
             }
             return;
         }
-        // the common case: walk the register index in Gray-code order, one
-        // add per amplitude
-        W ph = base;
+        // complex64: the phase of register index m is base + sum_j m_j lin[j],
+        // so its factor is f[low bits of m] * g[high bits of m], both built
+        // from the 1 + RB values cis(base), cis(lin[j]): 1 + RB sin/cos and
+        // about two complex products per amplitude
+        constexpr int LB = RB / 2, HB = RB - LB;
+        typename CT<R>::T2 f[1 << LB], g[1 << HB];
+        f[0] = cis_turns(base);
 #pragma unroll
-        for (int k = 0; k < NR; k++) {
-            const int m = k ^ (k >> 1);
-            if (k > 0) {
-                const int j = low_bit(k);   // the bit that flips from k-1 to k (k is a constant here)
-                if ((m >> j) & 1) ph += lin[j];
-                else ph -= lin[j];
-            }
-            v[m] = cmul(v[m], cis_turns(ph));
+        for (int j = 0; j < LB; j++) {
+            const auto cj = cis_turns(lin[j]);
+#pragma unroll
+            for (int m = 0; m < (1 << j); m++) f[m | (1 << j)] = cmul(f[m], cj);
+        }
+        g[0].x = R(1);
+        g[0].y = R(0);
+#pragma unroll
+        for (int j = 0; j < HB; j++) {
+            const auto cj = cis_turns(lin[LB + j]);
+            g[1 << j] = cj;
+#pragma unroll
+            for (int m = 1; m < (1 << j); m++) g[m | (1 << j)] = cmul(g[m], cj);
+        }
+#pragma unroll
+        for (int m = 0; m < NR; m++) {
+            const int lo = m & ((1 << LB) - 1), hi = m >> LB;
+            v[m] = cmul(v[m], hi == 0 ? f[lo] : cmul(f[lo], g[hi]));
         }
         return;
     }

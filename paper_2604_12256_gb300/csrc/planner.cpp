@@ -274,8 +274,10 @@ struct DsegCtx {
 // qubits, to the thread table when they only test thread bits (and the
 // segment is hoisted), else stay in the body; a slot-0 term on
 // chunk-selecting qubits and one thread bit i goes to the CTA table as a
-// coefficient of bit i (slot 1 + RB + i); register-only terms fold into the
-// 2^RB table; terms with several register bits stay in the body.
+// coefficient of bit i (slot 1 + RB + i); a term on one register bit alone
+// is a constant CTA-table entry of its slot; terms on several register bits
+// only fold into the 2^RB table; other terms with several register bits stay
+// in the body.
 static void encode_dseg(ProgWriter &pw, const std::vector<Term> &terms, const DsegCtx &cx)
 {
     const int RB = cx.RB;
@@ -329,6 +331,10 @@ static void encode_dseg(ProgWriter &pw, const std::vector<Term> &terms, const Ds
         uint64_t nonreg = t.mask & ~regall;
         if (rm == 0) {
             if (!to_tables(0, nonreg, t.w)) base.push_back({nonreg, t.w});
+        } else if (nonreg == 0 && popc(rm) == 1) {
+            // a phase on one register bit alone: a constant part of lin[j]
+            // (a CTA-table entry whose mask is always met)
+            to_tables(1 + __builtin_ctz(rm), 0, t.w);
         } else if (nonreg == 0) {
             for (uint32_t m = 0; m < (1u << RB); m++) if ((m & rm) == rm) tab[m] += t.w;
         } else if (popc(rm) == 1) {
