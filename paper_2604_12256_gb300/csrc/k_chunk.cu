@@ -336,11 +336,12 @@ __device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uin
         }
     }
     const uint32_t *tab = t;
-    const uint32_t *mt = t + 2 * NR;
+    const R *ctab = (const R *)(t + 2 * NR);   // cis of the register table
+    const uint32_t *mt = t + 2 * NR + ctab_words(RB, sizeof(R));
     // (the pivot bit of the segment header is not used here: applying
     // cis(0) = 1 to the amplitudes it would skip is exact)
     const bool tabnz = (ldw(body + D_FLAGS) & 1) != 0;
-    if (nm == 0 && !tabnz) {
+    if (nm == 0) {
         if constexpr (sizeof(R) == 8) {
             // complex128 (FP64 is scarce): the phase is base + sum_j m_j lin[j],
             // so cis(base) on every amplitude and cis(lin[j]) on those with
@@ -354,6 +355,10 @@ __device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uin
 #pragma unroll
                 for (int m = 0; m < NR; m++)
                     if ((m >> j) & 1) v[m] = cmul(v[m], cj);
+            }
+            if (tabnz) {
+#pragma unroll
+                for (int m = 0; m < NR; m++) v[m] = cmul(v[m], ldm(ctab, m));
             }
             return;
         }
@@ -378,6 +383,15 @@ __device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uin
             g[1 << j] = cj;
 #pragma unroll
             for (int m = 1; m < (1 << j); m++) g[m | (1 << j)] = cmul(g[m], cj);
+        }
+        if (tabnz) {
+#pragma unroll
+            for (int m = 0; m < NR; m++) {
+                const int lo = m & ((1 << LB) - 1), hi = m >> LB;
+                const auto fg = hi == 0 ? f[lo] : cmul(f[lo], g[hi]);
+                v[m] = cmul(v[m], cmul(fg, ldm(ctab, m)));
+            }
+            return;
         }
 #pragma unroll
         for (int m = 0; m < NR; m++) {

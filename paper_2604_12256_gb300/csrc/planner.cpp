@@ -366,6 +366,28 @@ static void encode_dseg(ProgWriter &pw, const std::vector<Term> &terms, const Ds
     for (int j = 0; j < RB; j++)
         for (const Term &t : lin[j]) put_term(t);
     for (uint32_t m = 0; m < (1u << RB); m++) pw.put64(qweight(tab[m], f64));
+    // the same phases as complex factors (the kernels multiply by them instead
+    // of evaluating a sin/cos per amplitude)
+    for (uint32_t m = 0; m < (1u << RB); m++) {
+        const uint64_t q = qweight(tab[m], f64);
+        const long double th = 6.283185307179586476925286766559L *
+                               (f64 ? (long double)q * 0x1p-64L : (long double)(uint32_t)q * 0x1p-32L);
+        if (f64) {
+            const double c = (double)cosl(th), sn = (double)sinl(th);
+            uint64_t a, b;
+            std::memcpy(&a, &c, 8);
+            std::memcpy(&b, &sn, 8);
+            pw.put64(a);
+            pw.put64(b);
+        } else {
+            const float c = (float)cosl(th), sn = (float)sinl(th);
+            uint32_t a, b;
+            std::memcpy(&a, &c, 4);
+            std::memcpy(&b, &sn, 4);
+            pw.put(a);
+            pw.put(b);
+        }
+    }
     for (auto &mt : multi) {
         pw.put64(mt.first.mask);
         pw.put(mt.second);
@@ -1323,7 +1345,7 @@ static bool validate_program(const std::vector<uint32_t> &w, int n, bool diag_sw
                     nterm += b[prog::D_NLIN + j];
                 }
                 size_t need = prog::O_BODY + prog::D_TERMS + nterm * prog::kTermWords + 2 * ((size_t)1 << RB) +
-                              (size_t)b[prog::D_NMULTI] * prog::kMultiWords;
+                              prog::ctab_words(RB, wb) + (size_t)b[prog::D_NMULTI] * prog::kMultiWords;
                 if (len < need) return bad("phase body");
             } else {
                 return bad("op type");

@@ -108,10 +108,14 @@ enum : int {
 enum : int { DS_GENERAL = 0, DS_REAL = 1, DS_RX = 2 };
 // term (4 words): mask_lo, mask_hi, w_lo, w_hi   (mask over physical qubits,
 //                 register bits removed; w: uint32 in w_lo or uint64)
-// then reg table: 2^RB entries x 2 words (phase of the register-only terms)
+// then reg table: 2^RB entries x 2 words (phase of the register-only terms),
+// then the same table as complex factors cis(2 pi w / 2^wbits): 2^RB entries
+// x (re, im) as float (2 words) or double (4 words),
 // multi term (6 words): mask_lo, mask_hi, regmask, 0, w_lo, w_hi
 constexpr int kTermWords = 4;
 constexpr int kMultiWords = 6;
+// words of the complex register table (wb = bytes per real: 4 or 8)
+PROG_HD inline constexpr uint32_t ctab_words(uint32_t RB, uint32_t wb) { return (1u << RB) * (wb == 8 ? 4 : 2); }
 
 // Dynamic shared memory of a launch of this program: the chunk's re/im planes
 // (chunk kernel only), the per-chunk CTA sums and the per-thread sums.
