@@ -36,12 +36,18 @@ N_GATES = 500
 SEED = 1
 WORKLOAD = "28-qubit diagonal-heavy gate-level stream (500 gates, 80% RZ/CP/RZZ, 20% H/RX, after H on every qubit), complex64"
 
-# ncu DRAM traffic per chunk-sweep launch (dram__bytes_read.sum + write.sum),
-# keyed by the sha256 of k_chunk.cu at capture time; null when the kernel changed.
+# ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
+# the dominant kernel, per amplitude, keyed by (workload, op kind, sha256 of
+# the kernel's source file at capture time): null once the kernel changed.
+# A sweep's traffic grows with the amplitudes it processes, so a capture on a
+# smaller state scales to the full one (profiles/ has the captures).
 TRAFFIC_PER_AMP = {
-    # profiles/k_chunk_diagheavy_25q.md: 475.6 MB per 2^25-amplitude launch;
-    # a sweep's traffic grows with the amplitudes it processes
-    ("chunk", "31c90410b3be81eee0a16191da362476d0f0d9a3afe9db3a91fa0f1bb6b115b9", ""): 475.6e6 / 2 ** 25,
+    # profiles/k_chunk_diagheavy_25q.md: 475.66 MB per 2^25-amplitude sweep
+    ("diag-heavy", "chunk", "dfd82a588588948db505873e8d23462a0d48f457ee669f4b6232a43ad600ce80"): 475.66e6 / 2 ** 25,
+    # profiles/k_dense5_tc_layered_26q.md: 1011.81 MB per 2^26-amplitude block sweep
+    ("layered-dense", "dense", "296ab931d6b96dd94924c8fd7c08023b75ce31b514128b5938cd71767b66554b"): 1011.81e6 / 2 ** 26,
+    # profiles/k_diag_rzzfull_26q.md: 476.22 MB per write-only 2^26-amplitude sweep
+    ("rzz-full", "diag", "dfd82a588588948db505873e8d23462a0d48f457ee669f4b6232a43ad600ce80"): 476.22e6 / 2 ** 26,
 }
 
 
@@ -282,7 +288,9 @@ def run_gpu(args, rank, world, dist):
             and dt == S.SIM_C64 else "k_dense5_fma (dense 5-qubit block, CUDA cores)"
     ksrc = {"chunk": "k_chunk.cu", "diag": "k_chunk.cu", "dense": "k_dense5.cu"}.get(kind, "k_basic.cu")
     src = open(os.path.join(ROOT, "paper_2604_12256_gb300", "csrc", ksrc), "rb").read()
-    tpa = TRAFFIC_PER_AMP.get((kind, hashlib.sha256(src).hexdigest(), args.precision if dense else ""))
+    tpa = TRAFFIC_PER_AMP.get((args.workload, kind, hashlib.sha256(src).hexdigest()))
+    if (dense and args.precision != "tf32x3") or args.dtype != "c64":
+        tpa = None   # captured on complex64 (and the tensor-core variant) only
     traffic = tpa * amps if tpa is not None else None
     if kind == "dense" and (args.precision != "tf32x3" or dt == S.SIM_C128):
         # 32 complex multiply-adds per amplitude: 256 real flops
