@@ -2,6 +2,7 @@
 // simulation of Algorithm 5): runs a plan's ops as kernel launches on the
 // handle's stream.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -182,6 +183,67 @@ int sim_default_options(sim_options *opt)
 const char *sim_global_error(void) { return g_err.c_str(); }
 
 uint64_t sim_kernel_launches(void) { return launches_total(); }
+
+int sim_selftest_wait_timeout(void)
+{
+    const int n = 10;
+    const size_t N = (size_t)1 << n;
+    std::vector<float2> h(N), back(N);
+    for (size_t i = 0; i < N; i++) h[i] = make_float2(0.001f * (float)i, -0.0005f * (float)i);
+    std::vector<double2> u(32 * 32);
+    for (int r = 0; r < 32; r++)
+        for (int c = 0; c < 32; c++) u[r * 32 + c] = make_double2(r == (c ^ 1) ? 1.0 : 0.0, 0.0);   // X on qubit 0
+    float2 *d_a = nullptr;
+    double2 *d_u = nullptr;
+    int *d_st = nullptr;
+    cudaStream_t st = nullptr;
+    std::string msg;
+    int rc = SIM_OK, flag = 0;
+    auto ck = [&](cudaError_t e, const char *where) {
+        if (e != cudaSuccess && rc == SIM_OK) { rc = cuda_fail(nullptr, e, where); }
+        return rc == SIM_OK;
+    };
+    const int q[5] = {0, 1, 2, 3, 4};
+    if (ck(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream") &&
+        ck(cudaMalloc((void **)&d_a, N * sizeof(float2)), "malloc") &&
+        ck(cudaMalloc((void **)&d_u, u.size() * sizeof(double2)), "malloc") &&
+        ck(cudaMalloc((void **)&d_st, sizeof(int)), "malloc") &&
+        ck(cudaMemcpy(d_a, h.data(), N * sizeof(float2), cudaMemcpyHostToDevice), "copy") &&
+        ck(cudaMemcpy(d_u, u.data(), u.size() * sizeof(double2), cudaMemcpyHostToDevice), "copy") &&
+        ck(cudaMemset(d_st, 0, sizeof(int)), "memset") &&
+        // 1. every wait runs out: the status word is set, the state untouched
+        ck(launch_dense5_wait_selftest(d_a, n, d_u, d_st, 1u << 12, st), "self-test launch") &&
+        ck(cudaStreamSynchronize(st), "self-test sync") &&
+        ck(cudaMemcpy(&flag, d_st, sizeof(int), cudaMemcpyDeviceToHost), "status read") &&
+        ck(cudaMemcpy(back.data(), d_a, N * sizeof(float2), cudaMemcpyDeviceToHost), "state read")) {
+        if (flag != 1) { rc = SIM_EINVAL; msg = "the timed-out wait did not set the status word"; }
+        for (size_t i = 0; rc == SIM_OK && i < N; i++)
+            if (back[i].x != h[i].x || back[i].y != h[i].y) { rc = SIM_EINVAL; msg = "the aborted kernel wrote the state"; }
+    }
+    // 2. the context is still usable: a normal split-TF32 block is exact up to the TF32 split
+    if (rc == SIM_OK && ck(cudaMemset(d_st, 0, sizeof(int)), "memset") &&
+        ck(launch_dense5(d_a, n, false, SIM_DENSE_SPLIT_TF32, q, d_u, d_st, st), "block launch") &&
+        ck(cudaStreamSynchronize(st), "block sync") &&
+        ck(cudaMemcpy(&flag, d_st, sizeof(int), cudaMemcpyDeviceToHost), "status read") &&
+        ck(cudaMemcpy(back.data(), d_a, N * sizeof(float2), cudaMemcpyDeviceToHost), "state read")) {
+        if (flag != 0) { rc = SIM_ETIMEOUT; msg = "a normal block launch timed out after the self-test"; }
+        for (size_t i = 0; rc == SIM_OK && i < N; i++) {
+            const float2 want = h[i ^ 1];
+            if (std::fabs(back[i].x - want.x) > 1e-6f * (1.f + std::fabs(want.x)) ||
+                std::fabs(back[i].y - want.y) > 1e-6f * (1.f + std::fabs(want.y))) {
+                rc = SIM_EINVAL;
+                msg = "the block product after the self-test is wrong";
+            }
+        }
+    }
+    if (st) cudaStreamSynchronize(st);
+    if (d_a) cudaFree(d_a);
+    if (d_u) cudaFree(d_u);
+    if (d_st) cudaFree(d_st);
+    if (st) cudaStreamDestroy(st);
+    if (!msg.empty()) return fail(nullptr, rc, msg);
+    return rc;
+}
 
 const char *sim_last_error(const sim_t *s) { return s ? s->err.c_str() : g_err.c_str(); }
 

@@ -145,8 +145,13 @@ struct TcSmem {
     int abort_;
 };
 
+// wait_limit: mbarrier polls before a wait gives up (kWaitLimit in normal
+// use).  skip_mma != 0 (self-test only): the elected thread issues no MMA and
+// no commit, so the first wait runs out and the abort path is taken with
+// nothing in flight.
 __global__ void __launch_bounds__(kTcCols) k_dense5_tc(float2 *__restrict__ a, int n, Dense5Args g,
-                                                        const double2 *__restrict__ U, int *status)
+                                                        const double2 *__restrict__ U, int *status,
+                                                        uint32_t wait_limit, int skip_mma)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     TcSmem &sm = *reinterpret_cast<TcSmem *>(smraw);
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(kTcCols) k_dense5_tc(float2 *__restrict__ a, i
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
-        if (tid == 0) {
+        if (tid == 0 && !skip_mma) {
             // big = Ahi Bhi^T (columns 0..63); small = Ahi Blo^T + Alo Bhi^T
             // (columns 64..127), kept apart so that the accumulator does not
             // drop the small terms; 8 K-steps of 8 each
@@ -261,10 +266,10 @@ __global__ void __launch_bounds__(kTcCols) k_dense5_tc(float2 *__restrict__ a, i
         // ---- wait for the products (bounded), then read this thread's row
         uint32_t it = 0;
         while (!mbar_try_wait(mbar, phase)) {
-            if (++it > kWaitLimit) break;
+            if (++it > wait_limit) break;
             __nanosleep(64);
         }
-        if (it > kWaitLimit) sm.abort_ = 1;
+        if (it > wait_limit) sm.abort_ = 1;
         phase ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;");
         __syncthreads();
@@ -299,7 +304,7 @@ __global__ void __launch_bounds__(kTcCols) k_dense5_tc(float2 *__restrict__ a, i
     if (sm.abort_ && tid == 0) {
         atomicExch(status, 1);
         // give the products in flight one more bounded wait before freeing TMEM
-        for (uint32_t it = 0; it < kWaitLimit && !mbar_try_wait(mbar, phase ^ 1); it++) __nanosleep(64);
+        for (uint32_t it = 0; it < wait_limit && !mbar_try_wait(mbar, phase ^ 1); it++) __nanosleep(64);
     }
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemAlloc));
@@ -344,11 +349,31 @@ cudaError_t launch_dense5(void *a, int n, bool f64, int precision, const int *q,
         const int64_t tiles = (ncol + kTcCols - 1) / kTcCols;
         // two CTAs per SM: 2 x 64 TMEM columns, 2 x ~97 KB shared memory
         int grid = (int)std::min<int64_t>(tiles, (int64_t)device_sm_count() * 2);
-        k_dense5_tc<<<grid, kTcCols, smem, st>>>((float2 *)a, n, g, (const double2 *)U64, status);
+        k_dense5_tc<<<grid, kTcCols, smem, st>>>((float2 *)a, n, g, (const double2 *)U64, status, kWaitLimit, 0);
         return counted(cudaGetLastError(), 1);
     }
     int grid = (int)std::min<int64_t>((ncol + 127) / 128, (int64_t)device_sm_count() * 8);
     k_dense5_fma<float><<<grid, 128, 0, st>>>((float2 *)a, n, g, (const double2 *)U64);
+    return counted(cudaGetLastError(), 1);
+}
+
+// Self-test of the bounded wait: the tensor-core kernel on qubits 0..4 of a
+// complex64 state with its MMA issue suppressed and wait_limit polls per
+// wait, so every wait runs out; *status becomes 1 and the state is untouched.
+cudaError_t launch_dense5_wait_selftest(void *a, int n, const void *U64, int *status, uint32_t wait_limit,
+                                        cudaStream_t st)
+{
+    if (n < 5) return cudaErrorInvalidValue;
+    const int q[5] = {0, 1, 2, 3, 4};
+    const Dense5Args g = d5_args(q);
+    static bool attr = false;
+    const size_t smem = sizeof(TcSmem);
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_dense5_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_dense5_tc<<<1, kTcCols, smem, st>>>((float2 *)a, n, g, (const double2 *)U64, status, wait_limit, 1);
     return counted(cudaGetLastError(), 1);
 }
 

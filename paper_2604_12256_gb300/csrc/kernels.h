@@ -83,6 +83,10 @@ cudaError_t launch_phase_small(void *a, int n, bool is_f64, const uint64_t *term
 // of the tensor-core kernel gave up.
 cudaError_t launch_dense5(void *a, int n, bool is_f64, int precision, const int *q, const void *U64, int *status,
                           cudaStream_t st);
+// Self-test only: the tensor-core block kernel with its MMA issue suppressed,
+// so that its bounded waits (wait_limit polls each) run out; *status -> 1.
+cudaError_t launch_dense5_wait_selftest(void *a, int n, const void *U64, int *status, uint32_t wait_limit,
+                                        cudaStream_t st);
 
 int device_sm_count();
 

@@ -97,6 +97,7 @@ _SIGS = [
     ("sim_profile_enable", ctypes.c_int, [_P, ctypes.c_int]),
     ("sim_profile_read", ctypes.c_int, [_P, ctypes.POINTER(sim_profile)]),
     ("sim_kernel_launches", ctypes.c_uint64, []),
+    ("sim_selftest_wait_timeout", ctypes.c_int, []),
     ("sim_expectation_noalloc", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t, _P, _P]),
     ("srv_create", ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_P)]),
     ("srv_submit", ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),

@@ -73,3 +73,21 @@ def test_split_tf32_keeps_fp32_grade_accuracy():
     e_32 = np.max(np.abs(run_tc(c, S.SIM_C64, S.SIM_DENSE_FP32)[0] - exp))
     assert e_tc <= 16 * e_32 + 1e-9, (e_tc, e_32)
     assert e_tc <= 1e-6
+
+
+def test_bounded_wait_times_out_and_recovers():
+    """The tensor-core kernel's mbarrier waits are bounded: with its MMA issue
+    suppressed (self-test entry point) every wait gives up, the kernel sets its
+    status word, leaves the state alone and frees its tensor memory, and a
+    normal block launch afterwards is still exact; then the regular path
+    reports no timeout."""
+    lib = S.load()
+    assert lib.sim_selftest_wait_timeout() == S.SIM_OK, (lib.sim_global_error() or b"").decode()
+    c = C.layered(12, 2, 3)
+    opt = S.default_options(flags=S.SIM_F_TC, dense_precision=S.SIM_DENSE_SPLIT_TF32)
+    with S.Sim(12, S.SIM_C64) as s:
+        s.reset(0)
+        s.apply(c.gates, opt)
+        got = s.get_state()
+    exp = oracle.run(c)
+    assert np.abs(got - exp).max() < 1e-5
