@@ -333,6 +333,62 @@ def run_gpu(args, rank, world, dist):
     sim.close()
 
 
+def run_families(args, rank, world, dist):
+    """Per-gate time of the circuit families of Table 2 (BV, HS, QV, SC, VC)
+    at one qubit count: gate by gate (no optimizer), optimized without the
+    merge booster, and with it.  CUDA events on the handle's stream, median
+    of --steps runs after --warmup."""
+    import torch
+    from paper_2604_12256_gb300 import build as B
+    from paper_2604_12256_gb300 import circuits as C
+    from paper_2604_12256_gb300 import svsim as S
+
+    B.build()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    n = args.qubits or 28
+    buf = torch.empty(2 << n, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    sim = S.Sim(n, S.SIM_C64, dev_buf=buf.data_ptr(), nbytes=buf.numel() * 4, stream=stream.cuda_stream)
+    configs = {"naive": S.default_options(flags=0),
+               "ours": S.default_options(flags=S.SIM_F_DIAG | S.SIM_F_BLOCK | S.SIM_F_FUSE),
+               "ours_b": S.default_options()}
+    clocks = Clocks(dev)
+    clocks.start()
+    out = {}
+    for fam, gen in sorted(C.FAMILIES.items()):
+        c = gen(n if fam != "hs" or n % 2 == 0 else n - 1)
+        ga = S.GateArray(c.gates)
+        row = {"gates": len(c.gates)}
+        for key, opt in configs.items():
+            def step():
+                sim.reset(c.basis)
+                sim.apply(ga, opt)
+            for _ in range(args.warmup):
+                step()
+            times = []
+            for _ in range(args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            ms = statistics.median(times)
+            st = sim.stats()
+            row[key] = {"ms": ms, "ms_per_gate": ms / len(c.gates), "sweeps": st["sweeps"], "ops": st["ops"]}
+        row["speedup_ours_vs_naive"] = row["naive"]["ms"] / row["ours"]["ms"]
+        row["speedup_booster"] = row["ours"]["ms"] / row["ours_b"]["ms"]
+        out[fam] = row
+    clk = clocks.stop()
+    sim.close()
+    if rank == 0:
+        line = {"metric": "per-gate time of the circuit families (Table 2)", "unit": "ms/gate", "n_qubits": n,
+                "dtype": "c64", "data": "synthetic", "steps": args.steps, "warmup": args.warmup,
+                "higher_is_better": False, "families": out, "clocks": clk}
+        print(json.dumps(line), flush=True)
+
+
 def _pct(xs, q):
     xs = sorted(xs)
     return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))] if xs else None
@@ -489,6 +545,9 @@ def main():
                     help="dense-block arithmetic for --workload layered-dense")
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--no-unfused", action="store_true", help="skip the gate-by-gate comparison run")
+    ap.add_argument("--families", action="store_true",
+                    help="per-gate time of the BV / HS / QV / SC / VC families: gate by gate, optimized, "
+                         "optimized with the merge booster")
     ap.add_argument("--serve", action="store_true",
                     help="time the serving loop on a Poisson request stream instead")
     ap.add_argument("--requests", type=int, default=1000)
@@ -524,7 +583,7 @@ def main():
         dist_.init_process_group("nccl")
         dist = dist_
     try:
-        (run_serve if args.serve else run_gpu)(args, rank, world, dist)
+        (run_serve if args.serve else run_families if args.families else run_gpu)(args, rank, world, dist)
     finally:
         if dist is not None:
             dist.destroy_process_group()

@@ -209,6 +209,103 @@ def rzz_full(n: int, seed: int = 5) -> Circuit:
     return Circuit(n, gates, 0, f"rzzfull{n}")
 
 
+# ---------------------------------------------------------------- circuit
+# families of the per-gate comparison (Table 2): written from each family's
+# textbook definition, seeded, any qubit count.
+
+def bernstein_vazirani(n: int, seed: int = 6) -> Circuit:
+    """Bernstein-Vazirani on n - 1 data qubits (0..n-2) and an ancilla (n-1):
+    X and H on the ancilla, H on the data, CX(i -> ancilla) for each bit i
+    of a random secret s, H on the data.  The data register ends in |s>, the
+    ancilla in |->.  ``Circuit.name`` carries the secret."""
+    rng = np.random.default_rng(seed)
+    secret = [int(b) for b in rng.integers(0, 2, n - 1)]
+    anc = n - 1
+    g = [Gate("x", (anc,)), Gate("h", (anc,))] + [Gate("h", (q,)) for q in range(n - 1)]
+    g += [Gate("cx", (q, anc)) for q in range(n - 1) if secret[q]]
+    g += [Gate("h", (q,)) for q in range(n - 1)]
+    s = sum(b << q for q, b in enumerate(secret))
+    return Circuit(n, g, 0, f"bv{n}:secret={s}")
+
+
+def hidden_shift(n: int, seed: int = 7) -> Circuit:
+    """Hidden shift for the bent function f(x, y) = x . y on n = 2m qubits
+    (x = qubits 0..m-1, y = m..2m-1), whose dual is itself: H on all, X on
+    the shift bits, the f phase (CZ(i, m + i)), X on the shift bits, H on
+    all, the dual's phase (CZ(i, m + i)), H on all.  Ends in |s>.
+    ``Circuit.name`` carries the shift s."""
+    if n % 2:
+        raise ValueError("hidden shift needs an even qubit count")
+    m = n // 2
+    rng = np.random.default_rng(seed)
+    shift = [int(b) for b in rng.integers(0, 2, n)]
+    xs = [Gate("x", (q,)) for q in range(n) if shift[q]]
+    phase = [Gate("cz", (i, m + i)) for i in range(m)]
+    hs = [Gate("h", (q,)) for q in range(n)]
+    g = hs + xs + phase + xs + hs + phase + hs
+    s = sum(b << q for q, b in enumerate(shift))
+    return Circuit(n, g, 0, f"hs{n}:shift={s}")
+
+
+def quantum_volume(n: int, depth: int = 0, seed: int = 8) -> Circuit:
+    """Quantum-volume model circuit: ``depth`` (default n) layers, each a
+    random permutation of the qubits followed by a Haar-random SU(4)-class
+    unitary (U(4), Mezzadri's method) on each consecutive pair."""
+    rng = np.random.default_rng(seed)
+    g: List[Gate] = []
+    for _ in range(depth or n):
+        perm = rng.permutation(n)
+        for i in range(0, n - 1, 2):
+            g.append(Gate("unitary", (int(perm[i]), int(perm[i + 1])), matrix=haar_unitary(rng, 4)))
+    return Circuit(n, g, 0, f"qv{n}x{depth or n}")
+
+
+_SQRT_X = np.array([[1 + 1j, 1 - 1j], [1 - 1j, 1 + 1j]]) / 2.0
+_SQRT_Y = np.array([[1 + 1j, -1 - 1j], [1 + 1j, 1 + 1j]]) / 2.0
+_W = (np.array([[0, 1], [1, 0]]) + np.array([[0, -1j], [1j, 0]])) / math.sqrt(2.0)
+_SQRT_W = (np.eye(2) - 1j * _W) / math.sqrt(2.0) * np.exp(1j * math.pi / 4)   # (W ** 0.5: eigenvalues 1, i)
+
+
+def supremacy(n: int, cycles: int = 20, seed: int = 9) -> Circuit:
+    """Random-circuit-sampling style circuit on a line: H on every qubit, then
+    ``cycles`` cycles of a random gate from {sqrt(X), sqrt(Y), sqrt(W)} on
+    every qubit (never the same twice in a row on a qubit) followed by CZ on
+    (0,1),(2,3),... in even cycles and (1,2),(3,4),... in odd ones."""
+    rng = np.random.default_rng(seed)
+    mats = [_SQRT_X, _SQRT_Y, _SQRT_W]
+    last = [-1] * n
+    g = [Gate("h", (q,)) for q in range(n)]
+    for c in range(cycles):
+        for q in range(n):
+            k = int(rng.integers(3))
+            while k == last[q]:
+                k = int(rng.integers(3))
+            last[q] = k
+            g.append(Gate("u1q", (q,), matrix=mats[k]))
+        for q in range(c % 2, n - 1, 2):
+            g.append(Gate("cz", (q, q + 1)))
+    return Circuit(n, g, 0, f"sc{n}x{cycles}")
+
+
+def variational(n: int, layers: int = 10, seed: int = 10) -> Circuit:
+    """Hardware-efficient variational ansatz: ``layers`` layers of RY(a) and
+    RZ(b) on every qubit (angles uniform in [0, 2pi)) followed by a CZ chain
+    (0,1),(1,2),...,(n-2,n-1)."""
+    rng = np.random.default_rng(seed)
+    g: List[Gate] = []
+    for _ in range(layers):
+        for q in range(n):
+            g.append(Gate("ry", (q,), (float(rng.uniform(0, 2 * math.pi)),)))
+            g.append(Gate("rz", (q,), (float(rng.uniform(0, 2 * math.pi)),)))
+        for q in range(n - 1):
+            g.append(Gate("cz", (q, q + 1)))
+    return Circuit(n, g, 0, f"vc{n}x{layers}")
+
+
+FAMILIES = {"bv": bernstein_vazirani, "hs": hidden_shift, "qv": quantum_volume, "sc": supremacy,
+            "vc": variational}
+
+
 def random_mixed(n: int, n_gates: int, seed: int, max_k: int = 3) -> Circuit:
     """Random test circuit over the whole gate set (named gates, u1q, small
     dense unitaries and diagonals) for parity tests."""
