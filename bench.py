@@ -119,7 +119,7 @@ FP64_PEAK_TFLOPS = 1.25                                # GB300 nominal FP64 (non
 
 def _workload_circuit(args, n):
     from paper_2604_12256_gb300 import circuits as C
-    if args.workload == "layered-dense":
+    if args.workload in ("layered-dense", "layered"):
         return C.layered(n, 20, 0)
     if args.workload == "rzz-full":
         return C.rzz_full(n)
@@ -313,7 +313,8 @@ def run_gpu(args, rank, world, dist):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "gates": G,
-                       "seed": 0 if dense else (5 if args.workload == "rzz-full" else SEED), "parallelism": f"replicas x{world}",
+                       "seed": {"layered-dense": 0, "layered": 0, "rzz-full": 5}.get(args.workload, SEED),
+                       "parallelism": f"replicas x{world}",
                        "l2": f"state ({amps * s_amp / 2 ** 30:g} GiB) larger than L2, no flush",
                        "sweeps": plan["sweeps"], "chunk_ops": plan["chunk_ops"], "dense_ops": plan["dense_ops"],
                        "diag_fused": plan["diag_fused"], "plan_ms": plan["plan_ms"]},
@@ -537,10 +538,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--register-bits", type=int, default=0,
                     help="chunk bits per thread in the cache-blocked kernel (0 = library default)")
-    ap.add_argument("--workload", default="diag-heavy", choices=["diag-heavy", "layered-dense", "rzz-full"],
+    ap.add_argument("--workload", default="diag-heavy",
+                    choices=["diag-heavy", "layered-dense", "layered", "rzz-full"],
                     help="diag-heavy: the 28-qubit gate-level stream; layered-dense: depth-20 layered "
-                         "circuit in dense 5-qubit blocks; rzz-full: RZZ on every qubit pair from |+...+> "
-                         "(both: 34 qubits complex64 / 33 complex128 by default)")
+                         "circuit in dense 5-qubit blocks; layered: the same circuit on the default "
+                         "cache-blocked path; rzz-full: RZZ on every qubit pair from |+...+> "
+                         "(the last three: 34 qubits complex64 / 33 complex128 by default)")
     ap.add_argument("--precision", default="tf32x3", choices=sorted(PRECISIONS),
                     help="dense-block arithmetic for --workload layered-dense")
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
@@ -556,7 +559,12 @@ def main():
     ap.add_argument("--qubits", type=int, default=0,
                     help="qubits of the workload (0: its default; smaller for ncu captures)")
     args = ap.parse_args()
-    if args.workload == "layered-dense":
+    if args.workload == "layered":
+        n = args.qubits or (33 if args.dtype == "c128" else 34)
+        WORKLOAD = (f"{n}-qubit random layered circuit, depth 20 (Haar U(2) on every qubit, CZ brickwork), "
+                    f"cache-blocked path, {'complex128' if args.dtype == 'c128' else 'complex64'}")
+        N_QUBITS = n
+    elif args.workload == "layered-dense":
         n = args.qubits or (33 if args.dtype == "c128" else 34)
         WORKLOAD = (f"{n}-qubit random layered circuit, depth 20 (Haar U(2) on every qubit, CZ brickwork), "
                     f"fused into dense 5-qubit blocks ({args.precision if args.dtype == 'c64' else 'fp64'}), "
