@@ -206,3 +206,20 @@ def test_full_size_config1_properties(dtype):
     assert abs(nrm - 1) < tol * 10
     assert idx[0] == 0 and abs(p[0] - 1) < (1e-11 if dtype == S.SIM_C128 else 1e-4)
     assert p[1] < 1e-10
+
+
+def test_qubit_reversal_by_swaps():
+    """A full qubit reversal as SWAP gates on a random state: the relabelling
+    chunk stores give the permuted state exactly (a permutation moves
+    amplitudes without arithmetic)."""
+    n = 20
+    rng = np.random.default_rng(11)
+    a = (rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)).astype(np.complex64)
+    c = C.Circuit(n, [C.Gate("swap", (i, n - 1 - i)) for i in range(n // 2)])
+    exp = oracle.run(c, state=a.astype(np.complex128))
+    with S.Sim(n, S.SIM_C64) as s:
+        s.set_state(a)
+        s.apply(c.gates)
+        got = s.get_state()
+        assert s.stats()["sweeps"] <= 3
+    assert np.array_equal(got, exp.astype(np.complex64))

@@ -137,3 +137,19 @@ def test_dense_block_plans_are_exact(maker):
     assert all(op["op"] in ("gate", "phase") for op in p["ops"])
     assert all(len(op["qubits"]) == 5 for op in p["ops"] if op["op"] == "gate")
     np.testing.assert_allclose(interpret(p, basis=c.basis), oracle.run(c), atol=1e-12)
+
+
+def test_swap_network_is_a_relabelling():
+    """A qubit permutation given as SWAP gates (Eq. 4) costs no extra sweep
+    per SWAP: the chunk stores apply it as a relabelling, a few sweeps for a
+    full reversal, and the plan is exact."""
+    for n in (14, 28):
+        gates = [C.Gate("swap", (i, n - 1 - i)) for i in range(n // 2)]
+        plan = S.plan_json(n, gates, S.SIM_C128, None)
+        assert plan["stats"]["sweeps"] <= -(-n // 8) and plan["stats"]["gate_ops"] == 0
+        if n == 14:
+            rng = np.random.default_rng(3)
+            a = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+            a /= np.linalg.norm(a)
+            exp = oracle.run(C.Circuit(n, gates), state=a)
+            np.testing.assert_allclose(interpret(plan, init_state=a), exp, atol=1e-12, rtol=0)
