@@ -51,6 +51,24 @@ TRAFFIC_PER_AMP = {
 }
 
 
+def max_over_ranks(x: float, dist=None) -> float:
+    """The largest x over all ranks (the slowest rank's time); x itself
+    without a process group.  NCCL reduces a device tensor, gloo a host one."""
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job throughput of N independent replicas (weak scaling): the
+    units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -238,10 +256,7 @@ def run_gpu(args, rank, world, dist):
     prof = sim.profile_read()
     sim.profile_enable(False)
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
 
     # end-to-end through the C ABI: host gate list in, host results out
     pairs = [(i, (i * 7 + 3) % N_QUBITS) for i in range(16)]
@@ -306,7 +321,7 @@ def run_gpu(args, rank, world, dist):
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic, "peak_source": peak_kind}
     roof.update({"launches": kp["launches"], "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": bytes_per_launch})
     total_bytes = sum(v["bytes"] for k, v in prof.items() if isinstance(v, dict)) / args.steps
-    value = world * G * amps / (ms / 1e3)
+    value = whole_job_rate(G * amps, world, ms / 1e3)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -491,11 +506,7 @@ def run_serve(args, rank, world, dist):
         d["load"] = f
         pois.append(d)
     clk = clocks.stop()
-    value = sat["circuits_per_s"]
-    if dist is not None:
-        t = torch.tensor([R / value], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        value = world * R / float(t.item())
+    value = whole_job_rate(R, world, max_over_ranks(R / sat["circuits_per_s"], dist))
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "circuits/s", "n_gpus": world, "steps": R,
