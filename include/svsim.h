@@ -82,7 +82,14 @@ enum {
     SIM_F_BLOCK = 1u << 2,  /* cache blocking (gate-block search, Algorithm 2) */
     SIM_F_FUSE = 1u << 3,   /* cost-based gate fusion inside blocks           */
     SIM_F_TC = 1u << 4,     /* dense fused blocks on the tensor cores          */
-    SIM_F_ALL = 0x1f
+    SIM_F_REMAP = 1u << 5,  /* qubit reordering (Section 2.3) by block stores:
+                               the qubits of a block needed soonest by later
+                               gates move into the low positions, which the
+                               next block holds anyway; no extra sweep (one
+                               restoring sweep at most).  Opt-in: fewer sweeps
+                               on nearest-neighbour layered circuits, heavier
+                               sweeps on random ones                          */
+    SIM_F_ALL = 0x3f
 };
 
 /* Precision of dense fused blocks on the tensor-core path. */
@@ -90,7 +97,7 @@ enum { SIM_DENSE_SPLIT_TF32 = 0, SIM_DENSE_FP32 = 1, SIM_DENSE_FP64 = 2 };
 
 /* The environment of Section 4.1 (N comes from the handle, R is 0: one GPU). */
 typedef struct {
-    int max_fuse_qubits;   /* F: largest fused dense block (default 3)            */
+    int max_fuse_qubits;   /* F: largest fused dense block (default 2)            */
     int max_diag_qubits;   /* D: largest fused diagonal, 0 = unbounded (default 0) */
     int chunk_qubits;      /* C: qubits per cached chunk (0 = default: 12 c64, 11 c128) */
     int booster_div;       /* B: Divider uses divSize = (n+B-1)/B; 0 = divSize C   */

@@ -567,6 +567,7 @@ struct Cfg {
     int C, RB, L, F, Smax;
     bool fuse;
     bool f64;
+    bool remap = true;   // qubit reordering through the block stores
 };
 
 struct PendingDiag {
@@ -589,16 +590,22 @@ struct Scheduler {
     int buf;
     std::vector<char> done;
     std::vector<PendingDiag> pending;
-    int lam[64], laminv[64];
+    // Qubit frame (Section 2.3): laminv[q] = position holding logical qubit q,
+    // at[p] = logical qubit held by position p.  It persists across blocks:
+    // a block's store may move the qubits the next block needs first into the
+    // low positions (choose_frame).  lam[p] = where the block's store writes
+    // the data it loaded from position p (identity off the block).
+    int lam[64], laminv[64], at[64];
     int last_chunk_op = -1;
     std::vector<SStage> last_stages;
     uint64_t last_Q = 0;
-    int last_lam[64];
+    int last_lam[64], last_at[64];
+    int blk_pos[64];   // laminv when the current block began
 
     Scheduler(const std::vector<PGate> &g, int n_, Cfg c, Plan &p, int b) : G(g), n(n_), cfg(c), plan(p), buf(b)
     {
         done.assign(G.size(), 0);
-        for (int i = 0; i < 64; i++) lam[i] = laminv[i] = i;
+        for (int i = 0; i < 64; i++) lam[i] = laminv[i] = at[i] = i;
     }
 
     uint64_t phys(uint64_t lm) const
@@ -703,6 +710,165 @@ struct Scheduler {
         plan.ops.push_back(std::move(o));
     }
 
+    // Store of a block (positions Q, register stages) that leaves logical
+    // qubit q at position npos[q]; commits that frame.
+    void emit_block(uint64_t Q, const std::vector<SStage> &stages, const int *npos)
+    {
+        for (int p = 0; p < 64; p++) lam[p] = (p < n && ((Q >> p) & 1)) ? npos[at[p]] : p;
+        Op o;
+        o.kind = OPK_CHUNK;
+        o.buf = buf;
+        o.n = n;
+        finalize_chunk(o, Q, stages);
+        last_chunk_op = (int)plan.ops.size();
+        last_stages = stages;
+        last_Q = Q;
+        std::memcpy(last_lam, lam, sizeof(lam));
+        std::memcpy(last_at, at, sizeof(at));
+        plan.ops.push_back(std::move(o));
+        // the pending phases follow their qubits: position p -> lam[p]
+        for (PendingDiag &d : pending) {
+            d.mask = remap(d.mask);
+            for (Term &t : d.terms) t.mask = remap(t.mask);
+        }
+        for (int q = 0; q < n; q++) laminv[q] = npos[q];
+        for (int q = 0; q < n; q++) at[npos[q]] = q;
+        for (int p = 0; p < 64; p++) lam[p] = p;
+    }
+
+    // The frame after a block (qubit reordering of Section 2.3, applied by
+    // the block's own store, so it costs no sweep).  The frame is always a
+    // set of swaps between a low position l < L and the home position of the
+    // qubit it holds, so at most 2L positions are ever displaced.  The
+    // earliest-needed qubits of the dense gates still to come move into the
+    // low positions, which every block holds anyway, leaving the block's
+    // C - L other positions for further qubits.  Only qubits whose positions
+    // are (or can be added to) this block's Q move.  SWAP relabellings inside
+    // the block are undone by the same store.
+    void choose_frame(size_t first, uint64_t &Q, int *npos)
+    {
+        const int L = cfg.L;
+        // the block-start frame (the SWAP relabellings inside the block are
+        // undone by its store)
+        int fpos[64], fat[64];
+        std::memcpy(fpos, blk_pos, sizeof(int) * n);
+        for (int q = 0; q < n; q++) fat[fpos[q]] = q;
+        for (int q = 0; q < n; q++) npos[q] = fpos[q];
+        if (!cfg.remap || L == 0) return;
+        // wanted: the qubits of this block needed soonest by the dense gates
+        // still to come (their positions are in Q, so the store can move them;
+        // the next block then holds them in its low positions for free)
+        int want[8], nw = 0;
+        for (size_t i = first; i < G.size() && nw < L; i++) {
+            if (done[i] || G[i].diag || G[i].swap) continue;
+            for (int j = 0; j < G[i].k && nw < L; j++) {
+                const int q = G[i].q[j];
+                if (!((Q >> fpos[q]) & 1)) continue;
+                bool dup = false;
+                for (int k = 0; k < nw; k++) dup |= want[k] == q;
+                if (!dup) want[nw++] = q;
+            }
+        }
+        auto wanted = [&](int q) {
+            for (int k = 0; k < nw; k++) if (want[k] == q) return true;
+            return false;
+        };
+        auto room = [&](uint64_t add) { return popc(Q | add) <= cfg.C; };
+        int used[8] = {0};
+        for (int l = 0; l < L; l++) {
+            const int r = fat[l];                  // resident of low position l
+            if (wanted(r)) continue;
+            if (r != l && wanted(l)) {
+                // the position's own qubit is wanted: send r home, bring l back
+                const uint64_t need = (1ull << r);
+                if (room(need)) {
+                    Q |= need;
+                    npos[r] = r;
+                    npos[l] = l;
+                }
+                continue;
+            }
+            // a wanted qubit at its high home position w takes position l
+            int pick = -1;
+            for (int k = 0; k < nw && pick < 0; k++) {
+                const int w = want[k];
+                if (used[k] || w < L || fpos[w] != w) continue;
+                uint64_t need = 1ull << w;
+                if (r != l) need |= 1ull << r;
+                if (room(need)) pick = k;
+            }
+            if (pick < 0) continue;
+            const int w = want[pick];
+            used[pick] = 1;
+            Q |= 1ull << w;
+            if (r != l) {
+                Q |= 1ull << r;
+                npos[r] = r;                       // the old resident goes home
+            }
+            npos[w] = l;
+            npos[l] = w;                           // qubit l waits at w's home
+        }
+        // a valid permutation that moves only positions of Q; else no change
+        int seen[64] = {0};
+        bool ok = true;
+        for (int q = 0; q < n && ok; q++) {
+            const int p = npos[q];
+            ok = p >= 0 && p < n && !seen[p];
+            if (ok) seen[p] = 1;
+            if (ok && p != fpos[q]) ok = ((Q >> p) & 1) && ((Q >> fpos[q]) & 1);
+        }
+        if (!ok)
+            for (int q = 0; q < n; q++) npos[q] = fpos[q];
+    }
+
+    // After the last block: every qubit back to its own position, folded into
+    // the last block's store when it holds all displaced positions, else one
+    // permutation-only pass.  The pending phases follow.
+    void restore_identity_frame()
+    {
+        uint64_t D = 0;
+        for (int q = 0; q < n; q++) if (laminv[q] != q) D |= (1ull << laminv[q]) | (1ull << q);
+        if (!D) return;
+        int fat[64];
+        for (int p = 0; p < n; p++) fat[p] = at[p];
+        if (last_chunk_op >= 0 && last_chunk_op == (int)plan.ops.size() - 1 && (D & ~last_Q) == 0) {
+            // re-store the last block straight into the identity frame
+            std::memcpy(at, last_at, sizeof(at));
+            for (int p = 0; p < 64; p++) lam[p] = (p < n && ((last_Q >> p) & 1)) ? at[p] : p;
+            finalize_chunk(plan.ops[last_chunk_op], last_Q, last_stages);
+            std::memcpy(last_lam, lam, sizeof(lam));
+        } else {
+            uint64_t Q = ((1ull << cfg.L) - 1) | D;
+            for (int p = 0; p < n && popc(Q) < cfg.C; p++) Q |= 1ull << p;
+            for (int p = 0; p < 64; p++) lam[p] = (p < n && ((Q >> p) & 1)) ? fat[p] : p;
+            std::vector<SStage> one(1);
+            Op o;
+            o.kind = OPK_CHUNK;
+            o.buf = buf;
+            o.n = n;
+            finalize_chunk(o, Q, one);
+            last_chunk_op = (int)plan.ops.size();
+            last_stages = one;
+            last_Q = Q;
+            std::memcpy(last_lam, lam, sizeof(lam));
+            for (int p = 0; p < n; p++) last_at[p] = fat[p];
+            plan.ops.push_back(std::move(o));
+        }
+        // pending phases: position p held logical fat[p], now at its home
+        for (PendingDiag &d : pending) {
+            uint64_t m = 0, x = d.mask;
+            while (x) { int p = __builtin_ctzll(x); x &= x - 1; m |= 1ull << fat[p]; }
+            d.mask = m;
+            for (Term &t : d.terms) {
+                uint64_t tm = 0, y = t.mask;
+                while (y) { int p = __builtin_ctzll(y); y &= y - 1; tm |= 1ull << fat[p]; }
+                t.mask = tm;
+            }
+        }
+        for (int q = 0; q < n; q++) laminv[q] = at[q] = q;
+        for (int p = 0; p < 64; p++) lam[p] = p;
+    }
+
     void run()
     {
         const uint64_t lowL = (1ull << cfg.L) - 1;
@@ -717,6 +883,7 @@ struct Scheduler {
                     if (!done[i]) { make_pending(G[i]); done[i] = 1; }
                 break;
             }
+            std::memcpy(blk_pos, laminv, sizeof(blk_pos));
             std::vector<SStage> stages;
             uint64_t Q = lowL;
             for (int s = 0; s < cfg.Smax; s++) {
@@ -739,10 +906,10 @@ struct Scheduler {
                             // frame, so they commute with it
                             if (popc((Q | P) & ~lowL) <= cfg.C - cfg.L) {
                                 Q |= P;
-                                int pa = laminv[g.q[0]], pb = laminv[g.q[1]];
-                                std::swap(lam[pa], lam[pb]);
-                                laminv[lam[pa]] = pa;
-                                laminv[lam[pb]] = pb;
+                                const int pa = laminv[g.q[0]], pb = laminv[g.q[1]];
+                                std::swap(at[pa], at[pb]);
+                                laminv[at[pa]] = pa;
+                                laminv[at[pb]] = pb;
                                 done[i] = 1;
                                 placed = true;
                             } else {
@@ -809,25 +976,14 @@ struct Scheduler {
                 done[i] = 1;
                 continue;
             }
-            // pad the chunk to exactly C positions with the lowest free qubits
+            // the frame after this block, then pad the chunk to exactly C
+            // positions with the lowest free qubits
+            int npos[64];
+            choose_frame(first, Q, npos);
             for (int p = 0; p < n && popc(Q) < cfg.C; p++) Q |= 1ull << p;
-            Op o;
-            o.kind = OPK_CHUNK;
-            o.buf = buf;
-            o.n = n;
-            finalize_chunk(o, Q, stages);
-            last_chunk_op = (int)plan.ops.size();
-            last_stages = stages;
-            last_Q = Q;
-            std::memcpy(last_lam, lam, sizeof(lam));
-            plan.ops.push_back(std::move(o));
-            // next frame: position p's content moves to position lam[p]
-            for (PendingDiag &d : pending) {
-                d.mask = remap(d.mask);
-                for (Term &t : d.terms) t.mask = remap(t.mask);
-            }
-            for (int i = 0; i < 64; i++) lam[i] = laminv[i] = i;
+            emit_block(Q, stages, npos);
         }
+        restore_identity_frame();
         // the diagonals left at the end of the circuit
         if (!pending.empty()) {
             std::vector<Term> all;
@@ -1123,6 +1279,7 @@ static void schedule(const std::vector<PGate> &G, int n, const sim_options &opt,
     cfg.F = opt.max_fuse_qubits;
     cfg.Smax = opt.max_stages;
     cfg.fuse = (opt.flags & SIM_F_FUSE) != 0;
+    cfg.remap = (opt.flags & SIM_F_REMAP) != 0;
     cfg.f64 = dt == SIM_C128;
     Scheduler s(G, n, cfg, plan, buf);
     s.run();

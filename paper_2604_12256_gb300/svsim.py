@@ -20,8 +20,8 @@ LIB_PATH = os.path.join(_PKG, "libsvsim.so")
 
 SIM_C64, SIM_C128 = 0, 1
 SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_ETIMEOUT, SIM_EBUSY, SIM_EUNSUPPORTED = range(7)
-SIM_F_DIAG, SIM_F_BOOST, SIM_F_BLOCK, SIM_F_FUSE, SIM_F_TC = 1, 2, 4, 8, 16
-SIM_F_ALL = 0x1F
+SIM_F_DIAG, SIM_F_BOOST, SIM_F_BLOCK, SIM_F_FUSE, SIM_F_TC, SIM_F_REMAP = 1, 2, 4, 8, 16, 32
+SIM_F_ALL = 0x3F
 SIM_DENSE_SPLIT_TF32, SIM_DENSE_FP32, SIM_DENSE_FP64 = 0, 1, 2
 
 KIND = {"h": 0, "x": 1, "y": 2, "z": 3, "s": 4, "t": 5, "rx": 6, "ry": 7, "rz": 8, "p": 9,

@@ -223,3 +223,17 @@ def test_qubit_reversal_by_swaps():
         got = s.get_state()
         assert s.stats()["sweeps"] <= 3
     assert np.array_equal(got, exp.astype(np.complex64))
+
+
+@pytest.mark.parametrize("dtype,tol", [(S.SIM_C128, 1e-12), (S.SIM_C64, 1e-5)])
+def test_remap_frames_on_gpu(dtype, tol):
+    """Qubit reordering through the block stores (SIM_F_REMAP): the blocks
+    run in moving frames and the state comes back in the identity frame."""
+    c = C.layered(20, 12, 4)
+    flags = S.SIM_F_DIAG | S.SIM_F_BOOST | S.SIM_F_BLOCK | S.SIM_F_FUSE | S.SIM_F_REMAP
+    exp = oracle.run(c)
+    with S.Sim(c.n, dtype) as s:
+        s.reset(c.basis)
+        s.apply(c.gates, S.default_options(flags=flags))
+        got = s.get_state().astype(np.complex128)
+    assert np.abs(got - exp).max() < tol

@@ -153,3 +153,22 @@ def test_swap_network_is_a_relabelling():
             a /= np.linalg.norm(a)
             exp = oracle.run(C.Circuit(n, gates), state=a)
             np.testing.assert_allclose(interpret(plan, init_state=a), exp, atol=1e-12, rtol=0)
+
+
+@pytest.mark.parametrize("name", ["layered", "qft", "mixed"])
+def test_remap_plans_are_exact(name):
+    """With qubit reordering through the block stores (SIM_F_REMAP) the
+    frame changes between blocks and is restored at the end: still exact."""
+    c = CIRCUITS[name](14)
+    flags = S.SIM_F_DIAG | S.SIM_F_BOOST | S.SIM_F_BLOCK | S.SIM_F_FUSE | S.SIM_F_REMAP
+    plan = S.plan_json(c.n, c.gates, S.SIM_C128, c.basis, S.default_options(flags=flags))
+    np.testing.assert_allclose(interpret(plan, basis=c.basis), oracle.run(c), atol=1e-12, rtol=0)
+
+
+def test_remap_cuts_sweeps_on_layered_circuits():
+    c = C.layered(28, 20, 0)
+    base = S.default_options()
+    rm = S.default_options(flags=base.flags | S.SIM_F_REMAP)
+    s0 = S.plan_json(c.n, c.gates, S.SIM_C64, 0, base)["stats"]["sweeps"]
+    s1 = S.plan_json(c.n, c.gates, S.SIM_C64, 0, rm)["stats"]["sweeps"]
+    assert s1 < s0
