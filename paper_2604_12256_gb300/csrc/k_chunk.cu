@@ -720,8 +720,19 @@ __global__ void __launch_bounds__(128) k_diag(typename CT<R>::T2 *__restrict__ a
         const uint64_t x0 = base | (uint64_t)tid;
         T2 v[NR];
 #pragma unroll
-        for (int m = 0; m < NR; m++)
-            v[m] = src.hi ? tensor_amp(src, x0 + ((uint64_t)m << 7)) : __ldcs(a + x0 + ((uint64_t)m << 7));
+        for (int m = 0; m < NR; m++) {
+            if (!src.hi) {
+                v[m] = __ldcs(a + x0 + ((uint64_t)m << 7));
+            } else if (src.n_lo >= C) {
+                // the tile's 2^C amplitudes share one hi factor
+                const T2 h = __ldg(&src.hi[base >> src.n_lo]);
+                const T2 l = __ldg(&src.lo[(x0 + ((uint64_t)m << 7)) & ((1ull << src.n_lo) - 1)]);
+                v[m].x = h.x * l.x - h.y * l.y;
+                v[m].y = h.x * l.y + h.y * l.x;
+            } else {
+                v[m] = tensor_amp(src, x0 + ((uint64_t)m << 7));
+            }
+        }
         dseg_apply<R, RB, 128>(v, x0, op, cta_ph, thr_ph, nhoist, tid);
 #pragma unroll
         for (int m = 0; m < NR; m++) __stcs(a + x0 + ((uint64_t)m << 7), v[m]);
@@ -833,7 +844,7 @@ cudaError_t launch_diag_sweep(void *a, int n, bool f64, const uint32_t *prog, si
     }
     if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
     if (src.hi && (src.n_lo < 0 || src.n_lo > n || !src.lo)) return cudaErrorInvalidValue;
-    return f64 ? diag_t<double, 4>(a, n, prog, smem, src, st) : diag_t<float, 5>(a, n, prog, smem, src, st);
+    return f64 ? diag_t<double, 4>(a, n, prog, smem, src, st) : diag_t<float, 4>(a, n, prog, smem, src, st);
 }
 
 }  // namespace svs

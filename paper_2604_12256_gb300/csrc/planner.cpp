@@ -1168,7 +1168,7 @@ static void emit_unfused(const std::vector<PGate> &G, int n, int buf, Plan &plan
 // consecutive amplitudes, register bits on top).
 static std::vector<uint32_t> encode_diag_sweep(int n, const std::vector<Term> &terms, bool f64, int &C, int &RB)
 {
-    RB = f64 ? 4 : 5;
+    RB = 4;   // 16 amplitudes per thread: more resident warps than 32 (measured faster)
     C = 7 + RB;
     SStage st;
     SOp ph;
@@ -1370,7 +1370,7 @@ static void finalize_words(Plan &plan)
     for (Op &o : plan.ops) {
         if (o.kind == OPK_DIAG) {
             int C, RB;
-            if (o.n >= (f64 ? 11 : 12)) {
+            if (o.n >= 11) {
                 o.words = encode_diag_sweep(o.n, o.terms, f64, C, RB);
             } else {
                 // too small for the diagonal sweep's tile: run it as a one-stage chunk pass

@@ -237,3 +237,19 @@ def test_remap_frames_on_gpu(dtype, tol):
         s.apply(c.gates, S.default_options(flags=flags))
         got = s.get_state().astype(np.complex128)
     assert np.abs(got - exp).max() < tol
+
+
+@pytest.mark.parametrize("dtype,tol", [(S.SIM_C128, 1e-12), (S.SIM_C64, 1e-5)])
+def test_rzz_full_fed_phase_sweep(dtype, tol):
+    """Full-connectivity RZZ at 24 qubits: the merge booster's last product
+    (two 12-qubit halves) is computed by the loads of the single fused phase
+    sweep, whose tiles share one hi factor."""
+    c = C.rzz_full(24)
+    exp = oracle.run(c)
+    with S.Sim(c.n, dtype) as s:
+        s.reset(c.basis)
+        s.apply(c.gates)
+        st = s.stats()
+        got = s.get_state().astype(np.complex128)
+    assert st["tensor_fused"] == 1 and st["sweeps"] == 1
+    assert np.abs(got - exp).max() < tol
