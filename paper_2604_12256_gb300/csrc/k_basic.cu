@@ -343,19 +343,50 @@ __global__ void __launch_bounds__(kRedThreads) k_expect_part(const typename Cx<R
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if constexpr (sizeof(R) == 4) {
         // complex64: FP32 sums over batches of 32 amplitudes, FP64 across
-        // batches (the FP64 rate of this part is far below its FP32 rate)
-        int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-        while (i < N) {
-            float acc32[NT];
+        // batches (the FP64 rate of this part is far below its FP32 rate).
+        // The grid's stride S is a power of two, so a thread's index bits
+        // below log2 S are fixed: it visits i = tid + g(k) S for k = 0, 1, ...
+        // with g(k) = k ^ (k >> 1) (Gray code), and the parities
+        // popc(i & m_t) & 1 of all masks, as the bits of P, change by
+        // P ^= flip[ctz(k)] from one amplitude to the next.
+        __shared__ uint32_t flip[64];
+        const int sb = 63 - __clzll((unsigned long long)stride);     // log2 S
+        if (threadIdx.x < 64) {
+            uint32_t f = 0;
+            for (int t = 0; t < NT; t++)
+                if (threadIdx.x + sb < 64 && ((m[t] >> (threadIdx.x + sb)) & 1)) f |= 1u << t;
+            flip[threadIdx.x] = f;
+        }
+        __syncthreads();
+        const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const int64_t K = N >> sb;                                     // amplitudes per thread
+        uint32_t P = 0;
 #pragma unroll
-            for (int t = 0; t < NT; t++) acc32[t] = 0.f;
-            for (int b = 0; b < 32 && i < N; b++, i += stride) {
-                const float p = probf(a[i]);
+        for (int t = 0; t < NT; t++) P |= (uint32_t)(__popcll((uint64_t)tid & m[t]) & 1) << t;
+        if (K == 0) {   // fewer amplitudes than threads: one each, or none
+            if (tid < N) {
+                const float p = probf(a[tid]);
 #pragma unroll
-                for (int t = 0; t < NT; t++) acc32[t] += (__popcll((uint64_t)i & m[t]) & 1) ? -p : p;
+                for (int t = 0; t < NT; t++) acc[t] += ((P >> t) & 1) ? -(double)p : (double)p;
             }
+        } else {
+            for (int64_t k0 = 0; k0 < K; k0 += 32) {
+                float acc32[NT];
 #pragma unroll
-            for (int t = 0; t < NT; t++) acc[t] += (double)acc32[t];
+                for (int t = 0; t < NT; t++) acc32[t] = 0.f;
+                const int kn = (int)(K - k0 < 32 ? K - k0 : 32);
+#pragma unroll 4
+                for (int b = 0; b < kn; b++) {
+                    const int64_t k = k0 + b;
+                    if (k > 0) P ^= flip[__ffsll((long long)k) - 1];
+                    const float p = probf(a[tid + ((k ^ (k >> 1)) << sb)]);
+                    const uint32_t pb = __float_as_uint(p);
+#pragma unroll
+                    for (int t = 0; t < NT; t++) acc32[t] += __uint_as_float(pb ^ (((P >> t) & 1u) << 31));
+                }
+#pragma unroll
+                for (int t = 0; t < NT; t++) acc[t] += (double)acc32[t];
+            }
         }
     } else {
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
@@ -412,13 +443,19 @@ struct KI {
 constexpr int kTopThreads = 256;
 constexpr int kTopTile = kTopThreads * 4;
 constexpr int kTopCap = 2048;   // >= 1024 kept + one tile
+constexpr int kTopBlocksPerSM = 2;   // blocks per SM (more lists make the single-block merge slower)
 static int topk_blocks(int64_t N)
 {
     int64_t g = (N + kTopTile - 1) / kTopTile;
-    int64_t cap = 2 * (int64_t)device_sm_count();
+    int64_t cap = kTopBlocksPerSM * (int64_t)device_sm_count();
     return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
 }
-size_t topk_scratch_bytes(int k) { return (size_t)2 * kNumSMs * 2 * (size_t)k * sizeof(KI) + 4096; }
+// per-block lists (at most kTopBlocksPerSM x SMs of k entries) + the final k
+size_t topk_scratch_bytes(int k)
+{
+    const int sms = device_sm_count() > kNumSMs ? device_sm_count() : kNumSMs;
+    return ((size_t)kTopBlocksPerSM * sms + 1) * (size_t)k * sizeof(KI) + 4096;
+}
 
 __device__ __forceinline__ bool better(const KI &a, const KI &b) { return a.p > b.p || (a.p == b.p && a.i < b.i); }
 
@@ -452,7 +489,25 @@ __global__ void __launch_bounds__(kTopThreads) k_topk(const typename Cx<R>::T *_
     __syncthreads();
     int64_t per = (N + gridDim.x - 1) / gridDim.x;
     int64_t lo = (int64_t)blockIdx.x * per, hi = lo + per < N ? lo + per : N;
+    // the next tile's amplitudes are loaded while this tile is filtered and
+    // (now and then) sorted
+    using T2 = typename Cx<R>::T;
+    T2 nz[4];
+    auto load_tile = [&](int64_t t0) {
+        if constexpr (FROM_STATE) {
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int64_t i = t0 + e * kTopThreads + threadIdx.x;
+                if (i < hi) nz[e] = a[i];
+            }
+        }
+    };
+    if (lo < hi) load_tile(lo);
     for (int64_t t0 = lo; t0 < hi; t0 += kTopTile) {
+        T2 cz[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) cz[e] = nz[e];
+        if (t0 + kTopTile < hi) load_tile(t0 + kTopTile);
         KI th = thr;
         // complex64: a float pre-filter (rounded down by a margin far above
         // its rounding error) skips the FP64 probability of clear losers
@@ -463,7 +518,7 @@ __global__ void __launch_bounds__(kTopThreads) k_topk(const typename Cx<R>::T *_
             if (i < hi) {
                 KI v;
                 if constexpr (FROM_STATE) {
-                    const auto z = a[i];
+                    const auto z = cz[e];
                     if constexpr (sizeof(R) == 4) {
                         if (fmaf(z.x, z.x, z.y * z.y) < thf) continue;
                     }
