@@ -253,3 +253,22 @@ def test_rzz_full_fed_phase_sweep(dtype, tol):
         got = s.get_state().astype(np.complex128)
     assert st["tensor_fused"] == 1 and st["sweeps"] == 1
     assert np.abs(got - exp).max() < tol
+
+
+@pytest.mark.parametrize("n", [22, 24])
+def test_expectation_on_larger_states(n):
+    """<Z-string> at sizes where every thread of the reduction grid walks
+    several amplitudes (Gray-code parity updates across the grid stride),
+    with masks on bits below and above the stride; the reference is the same
+    sum in FP64 over the GPU's own state."""
+    rng = np.random.default_rng(n)
+    a = (rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)).astype(np.complex64)
+    a /= np.linalg.norm(a)
+    masks = [1, (1 << 17) | (1 << 18), (1 << (n - 1)) | 1, (1 << 19) | (1 << 5) | (1 << 21), (1 << n) - 1, 0,
+             (1 << 20) | (1 << 3)]
+    with S.Sim(n, S.SIM_C64) as s:
+        s.set_state(a)
+        got = s.expectation(masks)
+        back = s.get_state()
+    exp = oracle.expectation_z(back.astype(np.complex128), masks)
+    np.testing.assert_allclose(got, exp, atol=2e-6, rtol=0)
