@@ -42,12 +42,12 @@ WORKLOAD = "28-qubit diagonal-heavy gate-level stream (500 gates, 80% RZ/CP/RZZ,
 # A sweep's traffic grows with the amplitudes it processes, so a capture on a
 # smaller state scales to the full one (profiles/ has the captures).
 TRAFFIC_PER_AMP = {
-    # profiles/k_chunk_diagheavy_25q.md: 475.66 MB per 2^25-amplitude sweep
-    ("diag-heavy", "chunk", "dfd82a588588948db505873e8d23462a0d48f457ee669f4b6232a43ad600ce80"): 475.66e6 / 2 ** 25,
-    # profiles/k_dense5_tc_layered_26q.md: 1011.81 MB per 2^26-amplitude block sweep
-    ("layered-dense", "dense", "296ab931d6b96dd94924c8fd7c08023b75ce31b514128b5938cd71767b66554b"): 1011.81e6 / 2 ** 26,
-    # profiles/k_diag_rzzfull_26q.md: 476.22 MB per write-only 2^26-amplitude sweep
-    ("rzz-full", "diag", "dfd82a588588948db505873e8d23462a0d48f457ee669f4b6232a43ad600ce80"): 476.22e6 / 2 ** 26,
+    # profiles/k_chunk_diagheavy_25q.md: 475.49 MB per 2^25-amplitude sweep
+    ("diag-heavy", "chunk", "b6a05b0ee442df3fd6dace7605a89ae1b03495a192f463ce41a8c2aa8b45acda"): 475.49e6 / 2 ** 25,
+    # profiles/k_dense5_tc_layered_26q.md: 1011.93 MB per 2^26-amplitude block sweep
+    ("layered-dense", "dense", "d3c99ef16642f42a869fc41881935a038fdffd47e6556e1ae147d96b86411999"): 1011.93e6 / 2 ** 26,
+    # profiles/k_diag_rzzfull_26q.md: 475.27 MB per write-only 2^26-amplitude sweep
+    ("rzz-full", "diag", "b6a05b0ee442df3fd6dace7605a89ae1b03495a192f463ce41a8c2aa8b45acda"): 475.27e6 / 2 ** 26,
 }
 
 
