@@ -5,7 +5,7 @@
 // K4: each CTA takes chunks of 2^C amplitudes (C = 12 complex64, 11
 // complex128): the low chunk bits are contiguous qubits (coalesced 128-bit
 // loads), the others strided high qubits (direct indexing, no permutation
-// pass).  The chunk is staged through shared memory (planar re/im planes,
+// pass).  The chunk is staged through shared memory (interleaved complex,
 // XOR-swizzled) and processed in register stages: in each stage every thread
 // holds 2^RB amplitudes whose index bits are the stage's register bits; gates
 // on those bits are register arithmetic, diagonal phases may use any bit.
@@ -31,12 +31,12 @@ template <typename R> struct CT;
 template <> struct CT<float> {
     using T2 = float2;
     using W = uint32_t;
-    static constexpr int SWZ = 5;
+    static constexpr int SWZ = swizzle_bits(4);
 };
 template <> struct CT<double> {
     using T2 = double2;
     using W = uint64_t;
-    static constexpr int SWZ = 4;
+    static constexpr int SWZ = swizzle_bits(8);
 };
 
 // Program words are read from the CTA's shared-memory copy of the program.
@@ -491,9 +491,8 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
     constexpr int S = 1 + RB;
     constexpr int SC = (int)cta_slots(RB, TB);
     extern __shared__ __align__(16) unsigned char smraw[];
-    R *sre = (R *)smraw;
-    R *sim = sre + (1 << C);
-    uint32_t *prog = (uint32_t *)(sim + (1 << C));
+    T2 *sv = (T2 *)smraw;   // the chunk: interleaved (re, im), swizzled
+    uint32_t *prog = (uint32_t *)(sv + (1 << C));
     const int tid = threadIdx.x;
     stage_program<T>(gprog, prog, tid);
     __syncthreads();
@@ -608,10 +607,8 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
 #pragma unroll
         for (int it = 0; it < NR / 2; it++) {
             const uint32_t p = pld_tid ^ swz<SW, C>((uint32_t)it << (TB + 1));
-            sre[p] = pf[2 * it].x;
-            sim[p] = pf[2 * it].y;
-            sre[p ^ 1] = pf[2 * it + 1].x;
-            sim[p ^ 1] = pf[2 * it + 1].y;
+            sv[p] = pf[2 * it];
+            sv[p ^ 1] = pf[2 * it + 1];
         }
         cta_sums<R, T>(prog, cta_ph, nd * SC, base, tid);
         __syncthreads();
@@ -632,8 +629,7 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
 #pragma unroll
                 for (int j = 0; j < RB; j++)
                     if ((m >> j) & 1) pm ^= pv[j];
-                v[m].x = sre[pm];
-                v[m].y = sim[pm];
+                v[m] = sv[pm];
             }
             const int nops = (int)ldw(sp + S_NOPS);
             const uint32_t *op = sp + S_SIZE;
@@ -663,8 +659,7 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
 #pragma unroll
                 for (int j = 0; j < RB; j++)
                     if ((m >> j) & 1) pm ^= pv[j];
-                sre[pm] = v[m].x;
-                sim[pm] = v[m].y;
+                sv[pm] = v[m];
             }
             __syncthreads();
         }
@@ -675,11 +670,12 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
             const uint32_t p0 = pst_tid ^ s_sit[it];
             const uint32_t p1 = p0 ^ pst_one;
             if constexpr (sizeof(R) == 4) {
-                float4 q = make_float4(sre[p0], sim[p0], sre[p1], sim[p1]);
+                const T2 u0 = sv[p0], u1 = sv[p1];
+                float4 q = make_float4(u0.x, u0.y, u1.x, u1.y);
                 __stcs((float4 *)(a + g), q);
             } else {
-                __stcs(a + g, make_double2(sre[p0], sim[p0]));
-                __stcs(a + g + 1, make_double2(sre[p1], sim[p1]));
+                __stcs(a + g, sv[p0]);
+                __stcs(a + g + 1, sv[p1]);
             }
         }
         __syncthreads();

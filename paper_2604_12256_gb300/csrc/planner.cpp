@@ -490,7 +490,7 @@ static std::vector<uint32_t> encode_program(int n, int C, int RB, bool f64, uint
         for (int i = 0; i < C; i++) if (lam_end[qin[i]] == qin[i2]) src = i;
         pw.w[prog::H_SPERM + i2] = (uint32_t)src;
     }
-    int swz = f64 ? 4 : 5;
+    const int swz = prog::swizzle_bits(f64 ? 8 : 4);
     // phase segments whose thread-only terms are summed once per launch:
     // as many as fit the shared-memory budget of the thread table
     int nseg = 0;
@@ -1465,7 +1465,7 @@ static bool validate_program(const std::vector<uint32_t> &w, int n, bool diag_sw
             if ((int)b >= C || ((seen >> b) & 1)) return bad("thread bits");
             if (w[so + prog::S_GTHR + i] != w[prog::H_QIN + b]) return bad("thread bit positions");
             if (i < RB && w[so + prog::S_PV + i] !=
-                              prog::swizzle(1u << w[so + prog::S_REG + i], C, w[prog::H_WBYTES] == 8 ? 4 : 5))
+                              prog::swizzle(1u << w[so + prog::S_REG + i], C, prog::swizzle_bits(w[prog::H_WBYTES])))
                 return bad("register offsets");
             seen |= 1u << b;
         }

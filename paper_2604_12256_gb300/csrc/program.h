@@ -76,10 +76,14 @@ enum : int {
     S_SIZE = S_PV + kMaxRB     // even
 };
 
-// Shared-memory swizzle of the chunk planes: element y lives at
-// y ^ fold(y >> sw), folding sw-bit groups into the low bits (sw = 5 for
-// float planes, 4 for double).  Linear over GF(2), so offsets of disjoint bit
-// sets combine by XOR.
+// Shared-memory swizzle of the chunk (interleaved complex amplitudes):
+// element y lives at y ^ fold(y >> sw), folding sw-bit groups into the low
+// bits.  Linear over GF(2), so offsets of disjoint bit sets combine by XOR.
+// sw = log2 of the amplitudes in one 128-byte bank row: a warp's 8-byte
+// (complex64) accesses are served by half-warps and 16-byte (complex128)
+// ones by quarter-warps, so lanes whose chunk bits have distinct residues
+// mod sw never share a bank.
+PROG_HD inline constexpr int swizzle_bits(uint32_t wbytes) { return wbytes == 8 ? 3 : 4; }
 inline uint32_t swizzle(uint32_t y, int C, int sw)
 {
     uint32_t r = y;
@@ -117,7 +121,7 @@ constexpr int kMultiWords = 6;
 // words of the complex register table (wb = bytes per real: 4 or 8)
 PROG_HD inline constexpr uint32_t ctab_words(uint32_t RB, uint32_t wb) { return (1u << RB) * (wb == 8 ? 4 : 2); }
 
-// Dynamic shared memory of a launch of this program: the chunk's re/im planes
+// Dynamic shared memory of a launch of this program: the chunk's amplitudes
 // (chunk kernel only), the per-chunk CTA sums and the per-thread sums.
 // Shared phase sums of one segment.  CTA table (per chunk): slot 0 = the
 // segment's phase at register index 0, slot 1 + j = the coefficient of
