@@ -27,17 +27,103 @@ namespace svs {
 
 using namespace prog;
 
+// complex128 in registers and shared memory: each real as a double-float
+// pair (hi + lo, |lo| <= ulp(hi) / 2), about 48 significant bits.  The FP64
+// rate of this GPU is 1/64 of its FP32 rate, so gates and phases on
+// complex128 states run in FP32 error-free arithmetic (Knuth's two-sum and
+// the FMA two-product); HBM and the C ABI keep complex128, converted once
+// per chunk load and store.
+struct __align__(16) dfc {
+    float rh, rl, ih, il;
+};
+
 template <typename R> struct CT;
 template <> struct CT<float> {
-    using T2 = float2;
+    using T2 = float2;    // registers / shared memory
+    using G2 = float2;    // HBM
     using W = uint32_t;
     static constexpr int SWZ = swizzle_bits(4);
 };
 template <> struct CT<double> {
-    using T2 = double2;
+    using T2 = dfc;
+    using G2 = double2;
     using W = uint64_t;
     static constexpr int SWZ = swizzle_bits(8);
 };
+
+// ---- double-float arithmetic
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float v = s - a;
+    e = (a - (s - v)) + (b - v);
+}
+// s + e = a + b exactly when |a| >= |b| (or a == 0)
+__device__ __forceinline__ void quick_two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    e = b - (s - a);
+}
+// sum_k a_k b_k of double-float reals, accumulated in double-float: each
+// product p + its FMA error, the p's summed by two-sum, the low parts and
+// cross terms added to the error word
+template <int N>
+__device__ __forceinline__ void df_dot(const float (&ah)[N], const float (&al)[N], const float (&bh)[N],
+                                       const float (&bl)[N], float &rh, float &rl)
+{
+    float s = 0.f, e = 0.f;
+#pragma unroll
+    for (int k = 0; k < N; k++) {
+        const float p = ah[k] * bh[k];
+        float pe = fmaf(ah[k], bh[k], -p);
+        pe = fmaf(ah[k], bl[k], pe);
+        pe = fmaf(al[k], bh[k], pe);
+        float t;
+        two_sum(s, p, s, t);
+        e += t + pe;
+    }
+    quick_two_sum(s, e, rh, rl);
+}
+// a * b for double-float complex
+__device__ __forceinline__ dfc cmul(dfc a, dfc b)
+{
+    dfc r;
+    {
+        const float ah[2] = {a.rh, -a.ih}, al[2] = {a.rl, -a.il}, bh[2] = {b.rh, b.ih}, bl[2] = {b.rl, b.il};
+        df_dot<2>(ah, al, bh, bl, r.rh, r.rl);
+    }
+    {
+        const float ah[2] = {a.rh, a.ih}, al[2] = {a.rl, a.il}, bh[2] = {b.ih, b.rh}, bl[2] = {b.il, b.rl};
+        df_dot<2>(ah, al, bh, bl, r.ih, r.il);
+    }
+    return r;
+}
+// the complex number 1 in the type of x
+__device__ __forceinline__ float2 cone(float2) { return make_float2(1.f, 0.f); }
+__device__ __forceinline__ dfc cone(dfc)
+{
+    dfc r;
+    r.rh = 1.f;
+    r.rl = r.ih = r.il = 0.f;
+    return r;
+}
+// complex128 <-> double-float complex
+__device__ __forceinline__ dfc to_reg(double2 d)
+{
+    dfc r;
+    r.rh = __double2float_rn(d.x);
+    r.rl = __double2float_rn(d.x - (double)r.rh);
+    r.ih = __double2float_rn(d.y);
+    r.il = __double2float_rn(d.y - (double)r.ih);
+    return r;
+}
+__device__ __forceinline__ float2 to_reg(float2 v) { return v; }
+__device__ __forceinline__ double2 to_glob(dfc v)
+{
+    return make_double2((double)v.rh + (double)v.rl, (double)v.ih + (double)v.il);
+}
+__device__ __forceinline__ float2 to_glob(float2 v) { return v; }
 
 // Program words are read from the CTA's shared-memory copy of the program.
 __device__ __forceinline__ uint32_t ldw(const uint32_t *p) { return *p; }
@@ -49,9 +135,19 @@ template <typename R> __device__ __forceinline__ typename CT<R>::W ldwt(const ui
 template <> __device__ __forceinline__ uint32_t ldwt<float>(const uint32_t *p) { return *p; }
 template <> __device__ __forceinline__ uint64_t ldwt<double>(const uint32_t *p) { return ld64(p); }
 
-// complex matrix element i of a dense op body
+// complex element i of a dense op body or a complex table in the program:
+// complex64 as (re, im) floats, complex128 as double-float (rh, rl, ih, il)
 __device__ __forceinline__ float2 ldm(const float *b, int i) { return make_float2(b[2 * i], b[2 * i + 1]); }
-__device__ __forceinline__ double2 ldm(const double *b, int i) { return make_double2(b[2 * i], b[2 * i + 1]); }
+__device__ __forceinline__ dfc ldm(const double *b, int i)
+{
+    const float *f = (const float *)b + 4 * i;
+    dfc r;
+    r.rh = f[0];
+    r.rl = f[1];
+    r.ih = f[2];
+    r.il = f[3];
+    return r;
+}
 
 // stage the program (H_WORDS words, 16-byte aligned in both spaces) in shared memory
 template <int T>
@@ -76,24 +172,31 @@ __device__ __forceinline__ float2 cis_turns(uint32_t w)
 // complex128: cis(2 pi w / 2^64) = T0[w >> 56] T1[(w >> 48) & 255]
 // T2[(w >> 40) & 255] cis(e), e = 2 pi (w mod 2^40) / 2^64 < 2 pi 2^-24, with
 // cis(e) = (1 - e^2/2, e (1 - e^2/6)) (the next terms are below 1e-27).
-// Tk[b] = cis(2 pi b / 2^(8k + 8)), rounded from long-double values on the
-// host (set_cis64_tables); three table products replace a sincospi, whose
-// FP64 work dominates phase sweeps on a GPU with a low FP64 rate.
-__device__ double2 g_cis64[3 * 256];
+// Tk[b] = cis(2 pi b / 2^(8k + 8)) as double-float, split from long-double
+// values on the host (set_cis64_tables); the products run in double-float.
+__device__ dfc g_cis64[3 * 256];   // double-float (rh, rl, ih, il)
 
-__device__ __forceinline__ double2 cmul_d(double2 a, double2 b)
+__device__ __forceinline__ dfc cis_turns(uint64_t w)
 {
-    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 cis_turns(uint64_t w)
-{
-    const double2 t0 = g_cis64[w >> 56];
-    const double2 t1 = g_cis64[256 + ((w >> 48) & 255)];
-    const double2 t2 = g_cis64[512 + ((w >> 40) & 255)];
-    const double e = (double)(w & ((1ull << 40) - 1)) * (6.283185307179586477 * 0x1p-64);
-    const double e2 = e * e;
-    const double2 te = make_double2(fma(-0.5, e2, 1.0), e * fma(-1.0 / 6.0, e2, 1.0));
-    return cmul_d(cmul_d(cmul_d(t0, t1), t2), te);
+    const dfc t0 = g_cis64[w >> 56];
+    const dfc t1 = g_cis64[256 + ((w >> 48) & 255)];
+    const dfc t2 = g_cis64[512 + ((w >> 40) & 255)];
+    // e = 2 pi r / 2^64, r < 2^40 exact as a double-float (two 20-bit halves)
+    const uint64_t r = w & ((1ull << 40) - 1);
+    const float rh = (float)(uint32_t)(r >> 20) * 1048576.f, rl = (float)(uint32_t)(r & 0xFFFFF);
+    constexpr float kh = 0x1.921fb6p-62f;    // 2 pi 2^-64 = kh + kl to 1e-15
+    constexpr float kl = -0x1.777a5cp-87f;
+    float eh, el;
+    {
+        const float ah[2] = {rh, rl}, al[2] = {0.f, 0.f}, bh[2] = {kh, kh}, bl[2] = {kl, kl};
+        df_dot<2>(ah, al, bh, bl, eh, el);
+    }
+    const float e2 = eh * eh;   // < 1.4e-13: its float rounding is far below 1e-16 of 1
+    dfc te;
+    two_sum(1.f, -0.5f * e2, te.rh, te.rl);
+    te.ih = eh;
+    te.il = fmaf(-eh * (1.f / 6.f), e2, el);
+    return cmul(cmul(cmul(t0, t1), t2), te);
 }
 
 // packed f32x2 arithmetic (sm_100+): a 64-bit register pair holds (re, im)
@@ -149,7 +252,40 @@ __device__ __forceinline__ void dense_apply(typename CT<R>::T2 (&v)[NR], const u
     constexpr int D = 1 << K;
     constexpr int gm = (1 << P0) | (K > 1 ? (1 << P1) : 0);
     const R *mb = (const R *)body;
-    if constexpr (sizeof(R) == 4 && K == 1) {
+    if constexpr (sizeof(R) == 8) {
+        // complex128 in double-float: each output component is one
+        // double-float dot product over the 2D real products
+#pragma unroll
+        for (int g = 0; g < NR; g++) {
+            if (g & gm) continue;
+            dfc in[D];
+#pragma unroll
+            for (int c = 0; c < D; c++) {
+                const int off = ((c & 1) << P0) | (K > 1 ? (((c >> 1) & 1) << P1) : 0);
+                in[c] = v[g | off];
+            }
+#pragma unroll
+            for (int r = 0; r < D; r++) {
+                float ah[2 * D], al[2 * D], bh[2 * D], bl[2 * D];
+                float ch[2 * D], cl[2 * D], dh[2 * D], dl[2 * D];
+#pragma unroll
+                for (int c = 0; c < D; c++) {
+                    const dfc m = ldm(mb, r * D + c);
+                    // re: mr xr - mi xi      im: mr xi + mi xr
+                    ah[2 * c] = m.rh, al[2 * c] = m.rl, bh[2 * c] = in[c].rh, bl[2 * c] = in[c].rl;
+                    ah[2 * c + 1] = -m.ih, al[2 * c + 1] = -m.il, bh[2 * c + 1] = in[c].ih, bl[2 * c + 1] = in[c].il;
+                    ch[2 * c] = m.rh, cl[2 * c] = m.rl, dh[2 * c] = in[c].ih, dl[2 * c] = in[c].il;
+                    ch[2 * c + 1] = m.ih, cl[2 * c + 1] = m.il, dh[2 * c + 1] = in[c].rh, dl[2 * c + 1] = in[c].rl;
+                }
+                dfc o;
+                df_dot<2 * D>(ah, al, bh, bl, o.rh, o.rl);
+                df_dot<2 * D>(ch, cl, dh, dl, o.ih, o.il);
+                const int off = ((r & 1) << P0) | (K > 1 ? (((r >> 1) & 1) << P1) : 0);
+                v[g | off] = o;
+            }
+        }
+        return;
+    } else if constexpr (K == 1) {
         // complex64 2x2: m x = (mr, mr) * x + (-mi, mi) * (x.im, x.re), packed
         u64 Mr[4], Mi[4];
 #pragma unroll
@@ -166,41 +302,42 @@ __device__ __forceinline__ void dense_apply(typename CT<R>::T2 (&v)[NR], const u
             v[g | (1 << P0)] = upk(ffma2(s0, Mi[2], ffma2(x0, Mr[2], ffma2(s1, Mi[3], fmul2(x1, Mr[3])))));
         }
         return;
-    }
-    // K = 1: the matrix stays in registers; K = 2: its 16 entries are re-read
-    // (L1 broadcast) for every group to keep register pressure down
-    T2 M1[K == 1 ? 4 : 1];
-    if constexpr (K == 1) {
+    } else {
+        // complex64, K = 2: the 16 entries are re-read from shared memory for
+        // every group to keep register pressure down
+        T2 M1[K == 1 ? 4 : 1];
+        if constexpr (K == 1) {
 #pragma unroll
-        for (int i = 0; i < 4; i++) M1[i] = ldm(mb, i);
-    }
-    auto M = [&](int i) -> T2 {
-        if constexpr (K == 1) return M1[i];
-        else return ldm(mb, i);
-    };
-#pragma unroll
-    for (int g = 0; g < NR; g++) {
-        if (g & gm) continue;
-        T2 in[D];
-#pragma unroll
-        for (int c = 0; c < D; c++) {
-            int off = ((c & 1) << P0) | (K > 1 ? (((c >> 1) & 1) << P1) : 0);
-            in[c] = v[g | off];
+            for (int i = 0; i < 4; i++) M1[i] = ldm(mb, i);
         }
+        auto M = [&](int i) -> T2 {
+            if constexpr (K == 1) return M1[i];
+            else return ldm(mb, i);
+        };
 #pragma unroll
-        for (int r = 0; r < D; r++) {
-            R re = 0, im = 0;
+        for (int g = 0; g < NR; g++) {
+            if (g & gm) continue;
+            T2 in[D];
 #pragma unroll
             for (int c = 0; c < D; c++) {
-                const T2 mrc = M(r * D + c);
-                re = fma(mrc.x, in[c].x, re);
-                re = fma(-mrc.y, in[c].y, re);
-                im = fma(mrc.x, in[c].y, im);
-                im = fma(mrc.y, in[c].x, im);
+                int off = ((c & 1) << P0) | (K > 1 ? (((c >> 1) & 1) << P1) : 0);
+                in[c] = v[g | off];
             }
-            int off = ((r & 1) << P0) | (K > 1 ? (((r >> 1) & 1) << P1) : 0);
-            v[g | off].x = re;
-            v[g | off].y = im;
+#pragma unroll
+            for (int r = 0; r < D; r++) {
+                R re = 0, im = 0;
+#pragma unroll
+                for (int c = 0; c < D; c++) {
+                    const T2 mrc = M(r * D + c);
+                    re = fma(mrc.x, in[c].x, re);
+                    re = fma(-mrc.y, in[c].y, re);
+                    im = fma(mrc.x, in[c].y, im);
+                    im = fma(mrc.y, in[c].x, im);
+                }
+                int off = ((r & 1) << P0) | (K > 1 ? (((r >> 1) & 1) << P1) : 0);
+                v[g | off].x = re;
+                v[g | off].y = im;
+            }
         }
     }
 }
@@ -210,15 +347,47 @@ __device__ __forceinline__ void dense_apply(typename CT<R>::T2 (&v)[NR], const u
 template <typename R, int NR, int P, int SUB>
 __device__ __forceinline__ void dense1_special(typename CT<R>::T2 (&v)[NR], const uint32_t *body)
 {
-    const R *mb = (const R *)body;
-    // entry i of the row-major 2x2 matrix is (mb[2i], mb[2i+1])
-    // (the op body is in the shared-memory copy of the program: plain loads)
-    const R a = mb[0];
-    const R b = mb[SUB == DS_REAL ? 2 : 3];
-    const R c = mb[SUB == DS_REAL ? 4 : 5];
-    const R d = mb[6];
-    if constexpr (sizeof(R) == 4) {
-        // complex64: one packed f32x2 op updates (re, im) together
+    if constexpr (sizeof(R) == 8) {
+        // complex128 in double-float; a, b, c, d are the real numbers of the
+        // special form (entry i of the body: floats 4i .. 4i + 3 = rh rl ih il)
+        const float *f = (const float *)body;
+        const float ah = f[0], al = f[1], dh = f[12], dl = f[13];
+        const float bh = f[SUB == DS_REAL ? 4 : 6], bl = f[SUB == DS_REAL ? 5 : 7];
+        const float ch = f[SUB == DS_REAL ? 8 : 10], cl = f[SUB == DS_REAL ? 9 : 11];
+#pragma unroll
+        for (int g = 0; g < NR; g++) {
+            if (g & (1 << P)) continue;
+            const dfc x0 = v[g], x1 = v[g | (1 << P)];
+            dfc y0, y1;
+            if constexpr (SUB == DS_REAL) {   // [[a, b], [c, d]] real
+                const float p[2] = {ah, bh}, pl[2] = {al, bl}, q[2] = {ch, dh}, ql[2] = {cl, dl};
+                { const float xh[2] = {x0.rh, x1.rh}, xl[2] = {x0.rl, x1.rl}; df_dot<2>(p, pl, xh, xl, y0.rh, y0.rl);
+                  df_dot<2>(q, ql, xh, xl, y1.rh, y1.rl); }
+                { const float xh[2] = {x0.ih, x1.ih}, xl[2] = {x0.il, x1.il}; df_dot<2>(p, pl, xh, xl, y0.ih, y0.il);
+                  df_dot<2>(q, ql, xh, xl, y1.ih, y1.il); }
+            } else {   // [[a, i b], [i c, d]]: a x0 + i b x1, i c x0 + d x1
+                { const float p[2] = {ah, -bh}, pl[2] = {al, -bl}, xh[2] = {x0.rh, x1.ih}, xl[2] = {x0.rl, x1.il};
+                  df_dot<2>(p, pl, xh, xl, y0.rh, y0.rl); }
+                { const float p[2] = {ah, bh}, pl[2] = {al, bl}, xh[2] = {x0.ih, x1.rh}, xl[2] = {x0.il, x1.rl};
+                  df_dot<2>(p, pl, xh, xl, y0.ih, y0.il); }
+                { const float p[2] = {-ch, dh}, pl[2] = {-cl, dl}, xh[2] = {x0.ih, x1.rh}, xl[2] = {x0.il, x1.rl};
+                  df_dot<2>(p, pl, xh, xl, y1.rh, y1.rl); }
+                { const float p[2] = {ch, dh}, pl[2] = {cl, dl}, xh[2] = {x0.rh, x1.ih}, xl[2] = {x0.rl, x1.il};
+                  df_dot<2>(p, pl, xh, xl, y1.ih, y1.il); }
+            }
+            v[g] = y0;
+            v[g | (1 << P)] = y1;
+        }
+        return;
+    } else {
+        // complex64: one packed f32x2 op updates (re, im) together; entry i of
+        // the row-major 2x2 matrix is (mb[2i], mb[2i+1]) (the op body is in the
+        // shared-memory copy of the program: plain loads)
+        const R *mb = (const R *)body;
+        const R a = mb[0];
+        const R b = mb[SUB == DS_REAL ? 2 : 3];
+        const R c = mb[SUB == DS_REAL ? 4 : 5];
+        const R d = mb[6];
         if constexpr (SUB == DS_REAL) {
             const u64 A = pk2(a, a), B = pk2(b, b), Cc = pk2(c, c), D = pk2(d, d);
 #pragma unroll
@@ -239,23 +408,6 @@ __device__ __forceinline__ void dense1_special(typename CT<R>::T2 (&v)[NR], cons
                 v[g] = upk(ffma2(x0, A, fmul2(s1, B)));
                 v[g | (1 << P)] = upk(ffma2(x1, D, fmul2(s0, Cc)));
             }
-        }
-        return;
-    }
-#pragma unroll
-    for (int g = 0; g < NR; g++) {
-        if (g & (1 << P)) continue;
-        const auto x0 = v[g], x1 = v[g | (1 << P)];
-        if constexpr (SUB == DS_REAL) {
-            v[g].x = fma(a, x0.x, b * x1.x);
-            v[g].y = fma(a, x0.y, b * x1.y);
-            v[g | (1 << P)].x = fma(c, x0.x, d * x1.x);
-            v[g | (1 << P)].y = fma(c, x0.y, d * x1.y);
-        } else {   // [[a, i b], [i c, d]]
-            v[g].x = fma(a, x0.x, -b * x1.y);
-            v[g].y = fma(a, x0.y, b * x1.x);
-            v[g | (1 << P)].x = fma(-c, x0.y, d * x1.x);
-            v[g | (1 << P)].y = fma(c, x0.x, d * x1.y);
         }
     }
 }
@@ -342,30 +494,10 @@ __device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uin
     // cis(0) = 1 to the amplitudes it would skip is exact)
     const bool tabnz = (ldw(body + D_FLAGS) & 1) != 0;
     if (nm == 0) {
-        if constexpr (sizeof(R) == 8) {
-            // complex128 (FP64 is scarce): the phase is base + sum_j m_j lin[j],
-            // so cis(base) on every amplitude and cis(lin[j]) on those with
-            // register bit j set: 1 + RB sin/cos per thread instead of 2^RB
-            const auto cb = cis_turns(base);
-#pragma unroll
-            for (int m = 0; m < NR; m++) v[m] = cmul(v[m], cb);
-#pragma unroll
-            for (int j = 0; j < RB; j++) {
-                const auto cj = cis_turns(lin[j]);
-#pragma unroll
-                for (int m = 0; m < NR; m++)
-                    if ((m >> j) & 1) v[m] = cmul(v[m], cj);
-            }
-            if (tabnz) {
-#pragma unroll
-                for (int m = 0; m < NR; m++) v[m] = cmul(v[m], ldm(ctab, m));
-            }
-            return;
-        }
-        // complex64: the phase of register index m is base + sum_j m_j lin[j],
-        // so its factor is f[low bits of m] * g[high bits of m], both built
-        // from the 1 + RB values cis(base), cis(lin[j]): 1 + RB sin/cos and
-        // about two complex products per amplitude
+        // the phase of register index m is base + sum_j m_j lin[j], so its
+        // factor is f[low bits of m] * g[high bits of m], both built from the
+        // 1 + RB values cis(base), cis(lin[j]): 1 + RB sin/cos and about two
+        // complex products per amplitude
         constexpr int LB = RB / 2, HB = RB - LB;
         typename CT<R>::T2 f[1 << LB], g[1 << HB];
         f[0] = cis_turns(base);
@@ -375,8 +507,7 @@ __device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uin
 #pragma unroll
             for (int m = 0; m < (1 << j); m++) f[m | (1 << j)] = cmul(f[m], cj);
         }
-        g[0].x = R(1);
-        g[0].y = R(0);
+        g[0] = cone(f[0]);
 #pragma unroll
         for (int j = 0; j < HB; j++) {
             const auto cj = cis_turns(lin[LB + j]);
@@ -478,11 +609,12 @@ template <typename T2> __device__ __forceinline__ T2 tensor_amp(const TSrc<T2> &
 
 // ------------------------------------------------------------ K4 chunk sweep
 template <typename R, int C, int RB>
-__global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(typename CT<R>::T2 *__restrict__ a,
+__global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(typename CT<R>::G2 *__restrict__ a,
                                                          const uint32_t *__restrict__ gprog, int n,
-                                                         TSrc<typename CT<R>::T2> src)
+                                                         TSrc<typename CT<R>::G2> src)
 {
     using T2 = typename CT<R>::T2;
+    using G2 = typename CT<R>::G2;
     using W = typename CT<R>::W;
     constexpr int TB = C - RB;
     constexpr int T = 1 << TB;
@@ -578,8 +710,8 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
 #pragma unroll
             for (int it = 0; it < NR / 2; it++) {
                 const uint64_t g = b | g_tid | s_git[it];
-                dst[2 * it] = tensor_amp(src, g);
-                dst[2 * it + 1] = tensor_amp(src, g + 1);
+                dst[2 * it] = to_reg(tensor_amp(src, g));
+                dst[2 * it + 1] = to_reg(tensor_amp(src, g + 1));
             }
             return;
         }
@@ -591,8 +723,8 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
                 dst[2 * it] = make_float2(q.x, q.y);
                 dst[2 * it + 1] = make_float2(q.z, q.w);
             } else {
-                dst[2 * it] = __ldcs(a + g);
-                dst[2 * it + 1] = __ldcs(a + g + 1);
+                dst[2 * it] = to_reg(__ldcs(a + g));
+                dst[2 * it + 1] = to_reg(__ldcs(a + g + 1));
             }
         }
     };
@@ -674,8 +806,8 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
                 float4 q = make_float4(u0.x, u0.y, u1.x, u1.y);
                 __stcs((float4 *)(a + g), q);
             } else {
-                __stcs(a + g, sv[p0]);
-                __stcs(a + g + 1, sv[p1]);
+                __stcs(a + g, to_glob(sv[p0]));
+                __stcs(a + g + 1, to_glob(sv[p1]));
             }
         }
         __syncthreads();
@@ -687,10 +819,11 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
 // tile of 2^C consecutive amplitudes, C = 7 + RB: thread t holds amplitudes
 // tile + t + m * 128 (register bits on top -> each warp load is contiguous)
 template <typename R, int RB>
-__global__ void __launch_bounds__(128) k_diag(typename CT<R>::T2 *__restrict__ a, const uint32_t *__restrict__ gprog,
-                                              int n, TSrc<typename CT<R>::T2> src)
+__global__ void __launch_bounds__(128) k_diag(typename CT<R>::G2 *__restrict__ a, const uint32_t *__restrict__ gprog,
+                                              int n, TSrc<typename CT<R>::G2> src)
 {
     using T2 = typename CT<R>::T2;
+    using G2 = typename CT<R>::G2;
     using W = typename CT<R>::W;
     constexpr int NR = 1 << RB;
     constexpr int C = 7 + RB;
@@ -718,20 +851,22 @@ __global__ void __launch_bounds__(128) k_diag(typename CT<R>::T2 *__restrict__ a
 #pragma unroll
         for (int m = 0; m < NR; m++) {
             if (!src.hi) {
-                v[m] = __ldcs(a + x0 + ((uint64_t)m << 7));
+                v[m] = to_reg(__ldcs(a + x0 + ((uint64_t)m << 7)));
             } else if (src.n_lo >= C) {
                 // the tile's 2^C amplitudes share one hi factor
-                const T2 h = __ldg(&src.hi[base >> src.n_lo]);
-                const T2 l = __ldg(&src.lo[(x0 + ((uint64_t)m << 7)) & ((1ull << src.n_lo) - 1)]);
-                v[m].x = h.x * l.x - h.y * l.y;
-                v[m].y = h.x * l.y + h.y * l.x;
+                const G2 h = __ldg(&src.hi[base >> src.n_lo]);
+                const G2 l = __ldg(&src.lo[(x0 + ((uint64_t)m << 7)) & ((1ull << src.n_lo) - 1)]);
+                G2 w;
+                w.x = h.x * l.x - h.y * l.y;
+                w.y = h.x * l.y + h.y * l.x;
+                v[m] = to_reg(w);
             } else {
-                v[m] = tensor_amp(src, x0 + ((uint64_t)m << 7));
+                v[m] = to_reg(tensor_amp(src, x0 + ((uint64_t)m << 7)));
             }
         }
         dseg_apply<R, RB, 128>(v, x0, op, cta_ph, thr_ph, nhoist, tid);
 #pragma unroll
-        for (int m = 0; m < NR; m++) __stcs(a + x0 + ((uint64_t)m << 7), v[m]);
+        for (int m = 0; m < NR; m++) __stcs(a + x0 + ((uint64_t)m << 7), to_glob(v[m]));
         __syncthreads();
     }
 }
@@ -760,14 +895,14 @@ static cudaError_t sized_grid(K kern, bool &attr, int threads, size_t smem, int6
 template <typename R, int C, int RB>
 static cudaError_t chunk_t(void *a, int n, const uint32_t *prog, size_t smem, TensorSrc src, cudaStream_t st)
 {
-    using T2 = typename CT<R>::T2;
+    using G2 = typename CT<R>::G2;
     constexpr int T = 1 << (C - RB);
     static bool attr = false;
     int grid = 0;
     cudaError_t e = sized_grid(k_chunk<R, C, RB>, attr, T, smem, (int64_t)1 << (n - C), grid);
     if (e != cudaSuccess) return e;
-    const TSrc<T2> ts{(const T2 *)src.hi, (const T2 *)src.lo, src.n_lo};
-    k_chunk<R, C, RB><<<grid, T, smem, st>>>((T2 *)a, prog, n, ts);
+    const TSrc<G2> ts{(const G2 *)src.hi, (const G2 *)src.lo, src.n_lo};
+    k_chunk<R, C, RB><<<grid, T, smem, st>>>((G2 *)a, prog, n, ts);
     return counted(cudaGetLastError(), 1);
 }
 
@@ -784,14 +919,20 @@ static cudaError_t set_cis64_tables()
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(mu);
     if (done[dev]) return cudaSuccess;
-    std::vector<double2> t(3 * 256);
+    std::vector<dfc> t(3 * 256);
     const long double two_pi = 6.283185307179586476925286766559L;
+    auto split = [](long double v, float &h, float &l) {
+        h = (float)v;
+        l = (float)(v - (long double)h);
+    };
     for (int k = 0; k < 3; k++)
         for (int b = 0; b < 256; b++) {
             const long double x = two_pi * (long double)b / (long double)(1ull << (8 * k + 8));
-            t[256 * k + b] = make_double2((double)cosl(x), (double)sinl(x));
+            dfc &c = t[256 * k + b];
+            split(cosl(x), c.rh, c.rl);
+            split(sinl(x), c.ih, c.il);
         }
-    e = cudaMemcpyToSymbol(g_cis64, t.data(), t.size() * sizeof(double2));
+    e = cudaMemcpyToSymbol(g_cis64, t.data(), t.size() * sizeof(dfc));
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
@@ -819,15 +960,15 @@ cudaError_t launch_chunk(void *a, int n, bool f64, int C, int RB, const uint32_t
 template <typename R, int RB>
 static cudaError_t diag_t(void *a, int n, const uint32_t *prog, size_t smem, TensorSrc src, cudaStream_t st)
 {
-    using T2 = typename CT<R>::T2;
+    using G2 = typename CT<R>::G2;
     constexpr int C = 7 + RB;
     if (n < C) return cudaErrorInvalidValue;
     static bool attr = false;
     int grid = 0;
     cudaError_t e = sized_grid(k_diag<R, RB>, attr, 128, smem, (int64_t)1 << (n - C), grid);
     if (e != cudaSuccess) return e;
-    const TSrc<T2> ts{(const T2 *)src.hi, (const T2 *)src.lo, src.n_lo};
-    k_diag<R, RB><<<grid, 128, smem, st>>>((T2 *)a, prog, n, ts);
+    const TSrc<G2> ts{(const G2 *)src.hi, (const G2 *)src.lo, src.n_lo};
+    k_diag<R, RB><<<grid, 128, smem, st>>>((G2 *)a, prog, n, ts);
     return counted(cudaGetLastError(), 1);
 }
 

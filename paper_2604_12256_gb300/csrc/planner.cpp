@@ -269,6 +269,19 @@ struct DsegCtx {
     std::vector<uint32_t> *cta = nullptr, *thr = nullptr;
 };
 
+// A real as a double-float pair (hi = nearest float, lo = nearest float of
+// the rest): complex128 constants of chunk programs, as the kernels use them.
+static void put_df(ProgWriter &pw, long double v)
+{
+    const float h = (float)v;
+    const float l = (float)(v - (long double)h);
+    uint32_t a, b;
+    std::memcpy(&a, &h, 4);
+    std::memcpy(&b, &l, 4);
+    pw.put(a);
+    pw.put(b);
+}
+
 // Split a segment's terms: slot terms (no register bit: slot 0; one register
 // bit j: slot 1 + j) go to the CTA table when they only test chunk-selecting
 // qubits, to the thread table when they only test thread bits (and the
@@ -373,12 +386,8 @@ static void encode_dseg(ProgWriter &pw, const std::vector<Term> &terms, const Ds
         const long double th = 6.283185307179586476925286766559L *
                                (f64 ? (long double)q * 0x1p-64L : (long double)(uint32_t)q * 0x1p-32L);
         if (f64) {
-            const double c = (double)cosl(th), sn = (double)sinl(th);
-            uint64_t a, b;
-            std::memcpy(&a, &c, 8);
-            std::memcpy(&b, &sn, 8);
-            pw.put64(a);
-            pw.put64(b);
+            put_df(pw, cosl(th));
+            put_df(pw, sinl(th));
         } else {
             const float c = (float)cosl(th), sn = (float)sinl(th);
             uint32_t a, b;
@@ -440,12 +449,8 @@ static void encode_dense(ProgWriter &pw, const SOp &op, const int *reg, const in
     pw.put(0);
     for (const cd &z : M2) {
         if (f64) {
-            double re = z.real(), im = z.imag();
-            uint64_t a, b;
-            std::memcpy(&a, &re, 8);
-            std::memcpy(&b, &im, 8);
-            pw.put64(a);
-            pw.put64(b);
+            put_df(pw, z.real());   // the chunk kernel computes complex128 in double-float
+            put_df(pw, z.imag());
         } else {
             float re = (float)z.real(), im = (float)z.imag();
             uint32_t a, b;
