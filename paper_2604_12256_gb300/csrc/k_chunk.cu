@@ -108,20 +108,42 @@ __device__ __forceinline__ dfc cone(dfc)
     r.rl = r.ih = r.il = 0.f;
     return r;
 }
-// complex128 <-> double-float complex
+// complex128 <-> double-float complex, in bit operations plus one FP64 add
+// per real (the conversions would otherwise take the FP64 pipe too).  A
+// double is truncated to float's 24-bit significand; magnitudes below 2^-126
+// become 0 (amplitudes that small are far below every tolerance).
+__device__ __forceinline__ float trunc_to_float(double d)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(d);
+    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e < 1023 - 126) return __uint_as_float(sign);
+    return __uint_as_float(sign | ((uint32_t)(e - 1023 + 127) << 23) | (uint32_t)((b >> 29) & 0x7FFFFF));
+}
+__device__ __forceinline__ double widen(float f)   // exact; float subnormals become 0
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+    const uint32_t e = (u >> 23) & 0xFF;
+    if (e == 0) return __longlong_as_double((long long)sign);
+    return __longlong_as_double((long long)(sign | ((uint64_t)(e - 127 + 1023) << 52) | ((uint64_t)(u & 0x7FFFFF) << 29)));
+}
+__device__ __forceinline__ void split_df(double d, float &h, float &l)
+{
+    h = trunc_to_float(d);
+    l = trunc_to_float(d - widen(h));   // d - h is exact
+}
 __device__ __forceinline__ dfc to_reg(double2 d)
 {
     dfc r;
-    r.rh = __double2float_rn(d.x);
-    r.rl = __double2float_rn(d.x - (double)r.rh);
-    r.ih = __double2float_rn(d.y);
-    r.il = __double2float_rn(d.y - (double)r.ih);
+    split_df(d.x, r.rh, r.rl);
+    split_df(d.y, r.ih, r.il);
     return r;
 }
 __device__ __forceinline__ float2 to_reg(float2 v) { return v; }
 __device__ __forceinline__ double2 to_glob(dfc v)
 {
-    return make_double2((double)v.rh + (double)v.rl, (double)v.ih + (double)v.il);
+    return make_double2(widen(v.rh) + widen(v.rl), widen(v.ih) + widen(v.il));
 }
 __device__ __forceinline__ float2 to_glob(float2 v) { return v; }
 
@@ -848,18 +870,17 @@ __global__ void __launch_bounds__(128) k_diag(typename CT<R>::G2 *__restrict__ a
         __syncthreads();
         const uint64_t x0 = base | (uint64_t)tid;
         T2 v[NR];
+        // the tile's 2^C amplitudes share one hi factor when n_lo >= C:
+        // converted once, multiplied in the register precision
+        const bool shared_hi = src.hi && src.n_lo >= C;
+        const T2 h = shared_hi ? to_reg(__ldg(&src.hi[base >> src.n_lo])) : T2{};
 #pragma unroll
         for (int m = 0; m < NR; m++) {
             if (!src.hi) {
                 v[m] = to_reg(__ldcs(a + x0 + ((uint64_t)m << 7)));
-            } else if (src.n_lo >= C) {
-                // the tile's 2^C amplitudes share one hi factor
-                const G2 h = __ldg(&src.hi[base >> src.n_lo]);
+            } else if (shared_hi) {
                 const G2 l = __ldg(&src.lo[(x0 + ((uint64_t)m << 7)) & ((1ull << src.n_lo) - 1)]);
-                G2 w;
-                w.x = h.x * l.x - h.y * l.y;
-                w.y = h.x * l.y + h.y * l.x;
-                v[m] = to_reg(w);
+                v[m] = cmul(h, to_reg(l));
             } else {
                 v[m] = to_reg(tensor_amp(src, x0 + ((uint64_t)m << 7)));
             }
