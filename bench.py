@@ -132,7 +132,7 @@ class Clocks:
 
 PRECISIONS = {"tf32x3": 0, "fp32": 1, "fp64": 2}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # SMs x FP32 lanes x FMA x max SM clock
-FP64_PEAK_TFLOPS = 1.25                                # GB300 nominal FP64 (non-tensor) rate
+DF_FLOPS_PER_AMP = 2 * 64 * 15 + 2 * 3                 # double-float complex128 dense block
 
 
 def _workload_circuit(args, n):
@@ -307,14 +307,21 @@ def run_gpu(args, rank, world, dist):
     if (dense and args.precision != "tf32x3") or args.dtype != "c64":
         tpa = None   # captured on complex64 (and the tensor-core variant) only
     traffic = tpa * amps if tpa is not None else None
-    if kind == "dense" and (args.precision != "tf32x3" or dt == S.SIM_C128):
+    if kind == "dense" and dt == S.SIM_C128:
+        # double-float on the FP32 pipe: per amplitude 2 components x 64 real
+        # multiply-adds of 15 FP32 flops (a product, three FMAs, a two-sum and
+        # two adds), plus the final quick two-sums
+        kname = "k_dense5_df (dense 5-qubit block, double-float on the FP32 pipe)"
+        achieved = DF_FLOPS_PER_AMP * amps / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    elif kind == "dense" and args.precision != "tf32x3":
         # 32 complex multiply-adds per amplitude: 256 real flops
-        fp64 = args.precision == "fp64" or dt == S.SIM_C128
-        pk = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
         achieved = 256.0 * amps / (avg_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                "frac": achieved / pk, "traffic": traffic,
-                "peak_source": "FP64 nominal rate" if fp64 else "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
     else:
         achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9 if kp["ms"] > 0 else None
         roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -578,7 +585,7 @@ def main():
     elif args.workload == "layered-dense":
         n = args.qubits or (33 if args.dtype == "c128" else 34)
         WORKLOAD = (f"{n}-qubit random layered circuit, depth 20 (Haar U(2) on every qubit, CZ brickwork), "
-                    f"fused into dense 5-qubit blocks ({args.precision if args.dtype == 'c64' else 'fp64'}), "
+                    f"fused into dense 5-qubit blocks ({args.precision if args.dtype == 'c64' else 'double-float'}), "
                     f"{'complex128' if args.dtype == 'c128' else 'complex64'}")
         N_QUBITS = n
     elif args.workload == "rzz-full":

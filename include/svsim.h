@@ -92,7 +92,9 @@ enum {
     SIM_F_ALL = 0x3f
 };
 
-/* Precision of dense fused blocks on the tensor-core path. */
+/* Precision of dense fused blocks on complex64 states (complex128 states
+ * compute their blocks in double-float, pairs of FP32 numbers with about 48
+ * significant bits, whatever this field says). */
 enum { SIM_DENSE_SPLIT_TF32 = 0, SIM_DENSE_FP32 = 1, SIM_DENSE_FP64 = 2 };
 
 /* The environment of Section 4.1 (N comes from the handle, R is 0: one GPU). */

@@ -20,22 +20,13 @@
 #include <mutex>
 #include <vector>
 
+#include "dfloat.h"
 #include "kernels.h"
 #include "program.h"
 
 namespace svs {
 
 using namespace prog;
-
-// complex128 in registers and shared memory: each real as a double-float
-// pair (hi + lo, |lo| <= ulp(hi) / 2), about 48 significant bits.  The FP64
-// rate of this GPU is 1/64 of its FP32 rate, so gates and phases on
-// complex128 states run in FP32 error-free arithmetic (Knuth's two-sum and
-// the FMA two-product); HBM and the C ABI keep complex128, converted once
-// per chunk load and store.
-struct __align__(16) dfc {
-    float rh, rl, ih, il;
-};
 
 template <typename R> struct CT;
 template <> struct CT<float> {
@@ -51,100 +42,7 @@ template <> struct CT<double> {
     static constexpr int SWZ = swizzle_bits(8);
 };
 
-// ---- double-float arithmetic
-// s + e = a + b exactly (Knuth)
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = a + b;
-    const float v = s - a;
-    e = (a - (s - v)) + (b - v);
-}
-// s + e = a + b exactly when |a| >= |b| (or a == 0)
-__device__ __forceinline__ void quick_two_sum(float a, float b, float &s, float &e)
-{
-    s = a + b;
-    e = b - (s - a);
-}
-// sum_k a_k b_k of double-float reals, accumulated in double-float: each
-// product p + its FMA error, the p's summed by two-sum, the low parts and
-// cross terms added to the error word
-template <int N>
-__device__ __forceinline__ void df_dot(const float (&ah)[N], const float (&al)[N], const float (&bh)[N],
-                                       const float (&bl)[N], float &rh, float &rl)
-{
-    float s = 0.f, e = 0.f;
-#pragma unroll
-    for (int k = 0; k < N; k++) {
-        const float p = ah[k] * bh[k];
-        float pe = fmaf(ah[k], bh[k], -p);
-        pe = fmaf(ah[k], bl[k], pe);
-        pe = fmaf(al[k], bh[k], pe);
-        float t;
-        two_sum(s, p, s, t);
-        e += t + pe;
-    }
-    quick_two_sum(s, e, rh, rl);
-}
-// a * b for double-float complex
-__device__ __forceinline__ dfc cmul(dfc a, dfc b)
-{
-    dfc r;
-    {
-        const float ah[2] = {a.rh, -a.ih}, al[2] = {a.rl, -a.il}, bh[2] = {b.rh, b.ih}, bl[2] = {b.rl, b.il};
-        df_dot<2>(ah, al, bh, bl, r.rh, r.rl);
-    }
-    {
-        const float ah[2] = {a.rh, a.ih}, al[2] = {a.rl, a.il}, bh[2] = {b.ih, b.rh}, bl[2] = {b.il, b.rl};
-        df_dot<2>(ah, al, bh, bl, r.ih, r.il);
-    }
-    return r;
-}
-// the complex number 1 in the type of x
-__device__ __forceinline__ float2 cone(float2) { return make_float2(1.f, 0.f); }
-__device__ __forceinline__ dfc cone(dfc)
-{
-    dfc r;
-    r.rh = 1.f;
-    r.rl = r.ih = r.il = 0.f;
-    return r;
-}
-// complex128 <-> double-float complex, in bit operations plus one FP64 add
-// per real (the conversions would otherwise take the FP64 pipe too).  A
-// double is truncated to float's 24-bit significand; magnitudes below 2^-126
-// become 0 (amplitudes that small are far below every tolerance).
-__device__ __forceinline__ float trunc_to_float(double d)
-{
-    const uint64_t b = (uint64_t)__double_as_longlong(d);
-    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
-    const int e = (int)((b >> 52) & 0x7FF);
-    if (e < 1023 - 126) return __uint_as_float(sign);
-    return __uint_as_float(sign | ((uint32_t)(e - 1023 + 127) << 23) | (uint32_t)((b >> 29) & 0x7FFFFF));
-}
-__device__ __forceinline__ double widen(float f)   // exact; float subnormals become 0
-{
-    const uint32_t u = __float_as_uint(f);
-    const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
-    const uint32_t e = (u >> 23) & 0xFF;
-    if (e == 0) return __longlong_as_double((long long)sign);
-    return __longlong_as_double((long long)(sign | ((uint64_t)(e - 127 + 1023) << 52) | ((uint64_t)(u & 0x7FFFFF) << 29)));
-}
-__device__ __forceinline__ void split_df(double d, float &h, float &l)
-{
-    h = trunc_to_float(d);
-    l = trunc_to_float(d - widen(h));   // d - h is exact
-}
-__device__ __forceinline__ dfc to_reg(double2 d)
-{
-    dfc r;
-    split_df(d.x, r.rh, r.rl);
-    split_df(d.y, r.ih, r.il);
-    return r;
-}
 __device__ __forceinline__ float2 to_reg(float2 v) { return v; }
-__device__ __forceinline__ double2 to_glob(dfc v)
-{
-    return make_double2(widen(v.rh) + widen(v.rl), widen(v.ih) + widen(v.il));
-}
 __device__ __forceinline__ float2 to_glob(float2 v) { return v; }
 
 // Program words are read from the CTA's shared-memory copy of the program.

@@ -11,9 +11,10 @@
 //     as D(128 x 64) = A(128 x 64) B(64 x 64)^T with A = X^T of a 128-column
 //     tile (one CTA thread per column) and B = the 64 x 64 embedding.
 //   * k_dense5_fma<float>: FP32 CUDA cores (complex64 states).
-//   * k_dense5_fma<double>: FP64 (complex128 states).
+//   * k_dense5_df: double-float on the FP32 pipe (complex128 states).
 #include <cstdint>
 
+#include "dfloat.h"
 #include "kernels.h"
 
 namespace svs {
@@ -38,6 +39,49 @@ __device__ __forceinline__ uint64_t d5_base(uint64_t col, const Dense5Args &g)
 template <typename R> struct D5T;
 template <> struct D5T<float> { using T2 = float2; };
 template <> struct D5T<double> { using T2 = double2; };
+
+// complex128 states: the block in double-float on the FP32 pipe (the FP64
+// rate of this GPU is 1/64 of FP32's).  Each output component is a
+// double-float dot product of 64 real products; the matrix is split into
+// double-float pairs in shared memory, the column is converted once.
+__global__ void __launch_bounds__(128) k_dense5_df(double2 *__restrict__ a, int n, Dense5Args g,
+                                                   const double2 *__restrict__ U)
+{
+    __shared__ dfc su[32 * 32];
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+        const double2 u = U[i];
+        dfc m;
+        m.rh = __double2float_rn(u.x);
+        m.rl = __double2float_rn(u.x - (double)m.rh);
+        m.ih = __double2float_rn(u.y);
+        m.il = __double2float_rn(u.y - (double)m.ih);
+        su[i] = m;
+    }
+    __syncthreads();
+    const int64_t ncol = (int64_t)1 << (n - 5);
+    for (int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; col < ncol;
+         col += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t b = d5_base((uint64_t)col, g);
+        dfc x[32];
+#pragma unroll
+        for (int c = 0; c < 32; c++) x[c] = to_reg(a[b | g.off[c]]);
+        for (int r = 0; r < 32; r++) {
+            float rs = 0.f, re = 0.f, is = 0.f, ie = 0.f;
+#pragma unroll
+            for (int c = 0; c < 32; c++) {
+                const dfc u = su[r * 32 + c];
+                df_fma_acc(u.rh, u.rl, x[c].rh, x[c].rl, rs, re);
+                df_fma_acc(-u.ih, -u.il, x[c].ih, x[c].il, rs, re);
+                df_fma_acc(u.rh, u.rl, x[c].ih, x[c].il, is, ie);
+                df_fma_acc(u.ih, u.il, x[c].rh, x[c].rl, is, ie);
+            }
+            dfc y;
+            quick_two_sum(rs, re, y.rh, y.rl);
+            quick_two_sum(is, ie, y.ih, y.il);
+            a[b | g.off[r]] = to_glob(y);
+        }
+    }
+}
 
 template <typename R>
 __global__ void __launch_bounds__(128) k_dense5_fma(typename D5T<R>::T2 *__restrict__ a, int n, Dense5Args g,
@@ -335,7 +379,7 @@ cudaError_t launch_dense5(void *a, int n, bool f64, int precision, const int *q,
     const int64_t ncol = (int64_t)1 << (n - 5);
     if (f64) {
         int grid = (int)std::min<int64_t>((ncol + 127) / 128, (int64_t)device_sm_count() * 8);
-        k_dense5_fma<double><<<grid, 128, 0, st>>>((double2 *)a, n, g, (const double2 *)U64);
+        k_dense5_df<<<grid, 128, 0, st>>>((double2 *)a, n, g, (const double2 *)U64);
         return counted(cudaGetLastError(), 1);
     }
     if (precision == 0) {   // split-TF32 on the tensor cores
