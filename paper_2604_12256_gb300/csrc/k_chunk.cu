@@ -48,6 +48,8 @@ __device__ __forceinline__ float2 to_glob(float2 v) { return v; }
 // Program words are read from the CTA's shared-memory copy of the program.
 __device__ __forceinline__ uint32_t ldw(const uint32_t *p) { return *p; }
 __device__ __forceinline__ uint64_t ld64(const uint32_t *p) { return (uint64_t)p[0] | ((uint64_t)p[1] << 32); }
+// 128-bit read of 4 program words (the encoder aligns what is read this way)
+__device__ __forceinline__ uint4 ld4(const uint32_t *p) { return *(const uint4 *)p; }
 
 using namespace prog;
 
@@ -60,14 +62,22 @@ template <> __device__ __forceinline__ uint64_t ldwt<double>(const uint32_t *p) 
 __device__ __forceinline__ float2 ldm(const float *b, int i) { return make_float2(b[2 * i], b[2 * i + 1]); }
 __device__ __forceinline__ dfc ldm(const double *b, int i)
 {
-    const float *f = (const float *)b + 4 * i;
+    const float4 q = ((const float4 *)b)[i];
     dfc r;
-    r.rh = f[0];
-    r.rl = f[1];
-    r.ih = f[2];
-    r.il = f[3];
+    r.rh = q.x;
+    r.rl = q.y;
+    r.ih = q.z;
+    r.il = q.w;
     return r;
 }
+// element i of a 16-byte-aligned complex table: complex64 entries are read
+// two per 128-bit load (the loads of i and i ^ 1 are the same word)
+__device__ __forceinline__ float2 ldm_a(const float *b, int i)
+{
+    const float4 q = ((const float4 *)b)[i >> 1];
+    return (i & 1) ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
+}
+__device__ __forceinline__ dfc ldm_a(const double *b, int i) { return ldm(b, i); }
 
 // stage the program (H_WORDS words, 16-byte aligned in both spaces) in shared memory
 template <int T>
@@ -210,8 +220,9 @@ __device__ __forceinline__ void dense_apply(typename CT<R>::T2 (&v)[NR], const u
         u64 Mr[4], Mi[4];
 #pragma unroll
         for (int i = 0; i < 4; i++) {
-            Mr[i] = pk2(mb[2 * i], mb[2 * i]);
-            Mi[i] = pk2(-mb[2 * i + 1], mb[2 * i + 1]);
+            const float2 e = ldm_a(mb, i);
+            Mr[i] = pk2(e.x, e.x);
+            Mi[i] = pk2(-e.y, e.y);
         }
 #pragma unroll
         for (int g = 0; g < NR; g++) {
@@ -270,10 +281,11 @@ __device__ __forceinline__ void dense1_special(typename CT<R>::T2 (&v)[NR], cons
     if constexpr (sizeof(R) == 8) {
         // complex128 in double-float; a, b, c, d are the real numbers of the
         // special form (entry i of the body: floats 4i .. 4i + 3 = rh rl ih il)
-        const float *f = (const float *)body;
-        const float ah = f[0], al = f[1], dh = f[12], dl = f[13];
-        const float bh = f[SUB == DS_REAL ? 4 : 6], bl = f[SUB == DS_REAL ? 5 : 7];
-        const float ch = f[SUB == DS_REAL ? 8 : 10], cl = f[SUB == DS_REAL ? 9 : 11];
+        const float4 *f4 = (const float4 *)body;
+        const float4 qa = f4[0], qb = f4[1], qc = f4[2], qd = f4[3];
+        const float ah = qa.x, al = qa.y, dh = qd.x, dl = qd.y;
+        const float bh = SUB == DS_REAL ? qb.x : qb.z, bl = SUB == DS_REAL ? qb.y : qb.w;
+        const float ch = SUB == DS_REAL ? qc.x : qc.z, cl = SUB == DS_REAL ? qc.y : qc.w;
 #pragma unroll
         for (int g = 0; g < NR; g++) {
             if (g & (1 << P)) continue;
@@ -303,11 +315,11 @@ __device__ __forceinline__ void dense1_special(typename CT<R>::T2 (&v)[NR], cons
         // complex64: one packed f32x2 op updates (re, im) together; entry i of
         // the row-major 2x2 matrix is (mb[2i], mb[2i+1]) (the op body is in the
         // shared-memory copy of the program: plain loads)
-        const R *mb = (const R *)body;
-        const R a = mb[0];
-        const R b = mb[SUB == DS_REAL ? 2 : 3];
-        const R c = mb[SUB == DS_REAL ? 4 : 5];
-        const R d = mb[6];
+        const float4 m0 = ((const float4 *)body)[0], m1 = ((const float4 *)body)[1];
+        const R a = m0.x;
+        const R b = SUB == DS_REAL ? m0.z : m0.w;
+        const R c = SUB == DS_REAL ? m1.x : m1.y;
+        const R d = m1.z;
         if constexpr (SUB == DS_REAL) {
             const u64 A = pk2(a, a), B = pk2(b, b), Cc = pk2(c, c), D = pk2(d, d);
 #pragma unroll
@@ -369,9 +381,10 @@ __host__ __device__ __forceinline__ constexpr int low_bit(int k)
 __host__ __device__ __forceinline__ constexpr int log2_of(int x) { return low_bit(x); }
 
 // ------------------------------------------------------------ phase segment
-// Shared sums of a launch: cta_ph[d * SC + s] (per chunk; SC = 1 + RB + TB,
-// slots 1 + RB + i are coefficients of thread bit i) and
-// thr_ph[(d * S + s) * T + tid] (per thread, segments d < nhoist), S = 1 + RB.
+// Shared sums of a launch: cta_ph[d * SCP + s] (per chunk; SCP = 1 + RB + TB
+// slots padded to 16 bytes; slots 1 + RB + i are coefficients of thread bit
+// i) and thr_ph[(d * S + s) * T + tid] (per thread, segments d < nhoist),
+// S = 1 + RB.
 template <typename R, int RB, int T>
 __device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uint64_t x0, const uint32_t *body,
                                            const typename CT<R>::W *cta_ph, const typename CT<R>::W *thr_ph,
@@ -381,16 +394,34 @@ __device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uin
     constexpr int NR = 1 << RB;
     constexpr int S = 1 + RB;
     constexpr int TB = log2_of(T);
-    constexpr int SC = (int)cta_slots(RB, TB);
-    const int d = (int)ldw(body + D_INDEX);
+    constexpr int SCP = (int)cta_stride(RB, TB, sizeof(W));
+    const uint4 hd = ld4(body);   // D_INDEX, D_FLAGS, D_NBASE, D_NMULTI
+    const int d = (int)hd.x;
     const bool hoisted = d < nhoist;
-    const int nb = (int)ldw(body + D_NBASE);
-    const int nm = (int)ldw(body + D_NMULTI);
+    const int nb = (int)hd.z;
+    const int nm = (int)hd.w;
+    uint32_t nlin[(RB + 3) & ~3];
+#pragma unroll
+    for (int k = 0; k < (RB + 3) / 4; k++) {
+        const uint4 q = ld4(body + D_NLIN + 4 * k);
+        nlin[4 * k] = q.x, nlin[4 * k + 1] = q.y, nlin[4 * k + 2] = q.z, nlin[4 * k + 3] = q.w;
+    }
     const uint32_t *t = body + D_TERMS;
-    W base = cta_ph[d * SC];
+    // this chunk's sums of the segment: 128-bit loads of its padded slots
+    W cv[SCP];
+#pragma unroll
+    for (int k = 0; k < SCP * (int)sizeof(W) / 16; k++) {
+        const uint4 q = ((const uint4 *)(cta_ph + d * SCP))[k];
+        if constexpr (sizeof(W) == 4) {
+            cv[4 * k] = q.x, cv[4 * k + 1] = q.y, cv[4 * k + 2] = q.z, cv[4 * k + 3] = q.w;
+        } else {
+            cv[2 * k] = (W)q.x | ((W)q.y << 32), cv[2 * k + 1] = (W)q.z | ((W)q.w << 32);
+        }
+    }
+    W base = cv[0];
 #pragma unroll
     for (int i = 0; i < TB; i++)
-        if ((tid >> i) & 1) base += cta_ph[d * SC + 1 + RB + i];
+        if ((tid >> i) & 1) base += cv[1 + RB + i];
     if (hoisted) base += thr_ph[(d * S) * T + tid];
     for (int i = 0; i < nb; i++, t += kTermWords) {
         uint64_t m = ld64(t);
@@ -399,9 +430,9 @@ __device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uin
     W lin[RB];
 #pragma unroll
     for (int j = 0; j < RB; j++) {
-        lin[j] = cta_ph[d * SC + 1 + j];
+        lin[j] = cv[1 + j];
         if (hoisted) lin[j] += thr_ph[(d * S + 1 + j) * T + tid];
-        const int cnt = (int)ldw(body + D_NLIN + j);
+        const int cnt = (int)nlin[j];
         for (int i = 0; i < cnt; i++, t += kTermWords) {
             uint64_t m = ld64(t);
             if ((x0 & m) == m) lin[j] += ldwt<R>(t + 2);
@@ -412,7 +443,7 @@ __device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uin
     const uint32_t *mt = t + 2 * NR + ctab_words(RB, sizeof(R));
     // (the pivot bit of the segment header is not used here: applying
     // cis(0) = 1 to the amplitudes it would skip is exact)
-    const bool tabnz = (ldw(body + D_FLAGS) & 1) != 0;
+    const bool tabnz = (hd.y & 1) != 0;
     if (nm == 0) {
         // the phase of register index m is base + sum_j m_j lin[j], so its
         // factor is f[low bits of m] * g[high bits of m], both built from the
@@ -440,7 +471,7 @@ __device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uin
             for (int m = 0; m < NR; m++) {
                 const int lo = m & ((1 << LB) - 1), hi = m >> LB;
                 const auto fg = hi == 0 ? f[lo] : cmul(f[lo], g[hi]);
-                v[m] = cmul(v[m], cmul(fg, ldm(ctab, m)));
+                v[m] = cmul(v[m], cmul(fg, ldm_a(ctab, m)));
             }
             return;
         }
@@ -492,14 +523,19 @@ __device__ __forceinline__ void add_atomic(uint64_t *p, uint64_t v)
     atomicAdd((unsigned long long *)p, (unsigned long long)v);
 }
 
-// Per-chunk sums of the CTA table for chunk base `base` (block-wide; integer
-// adds are exact, so the atomics' order does not matter).
+// Per-chunk sums of the CTA table, in one of kCtaBuffers buffers of
+// `nslots` slots: cta_zero clears a buffer, cta_accum adds the entries whose
+// mask chunk base `base` meets (block-wide; integer adds are exact, so the
+// atomics' order does not matter).  The caller puts a barrier between the
+// two and another before the sums are read.
 template <typename R, int T>
-__device__ __forceinline__ void cta_sums(const uint32_t *prog, typename CT<R>::W *cta_ph, int nslots, uint64_t base,
-                                         int tid)
+__device__ __forceinline__ void cta_zero(typename CT<R>::W *buf, int nslots, int tid)
 {
-    for (int i = tid; i < nslots; i += T) cta_ph[i] = 0;
-    __syncthreads();
+    for (int i = tid; i < nslots; i += T) buf[i] = 0;
+}
+template <typename R, int T>
+__device__ __forceinline__ void cta_accum(const uint32_t *prog, typename CT<R>::W *cta_ph, uint64_t base, int tid)
+{
     const uint32_t *ct = prog + ldw(prog + H_CTA_OFF);
     const int nc = (int)ldw(prog + H_NCTA);
     for (int i = tid; i < nc; i += T) {
@@ -541,7 +577,7 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
     constexpr int NR = 1 << RB;
     constexpr int SW = CT<R>::SWZ;
     constexpr int S = 1 + RB;
-    constexpr int SC = (int)cta_slots(RB, TB);
+    constexpr int SCP = (int)cta_stride(RB, TB, sizeof(typename CT<R>::W));
     extern __shared__ __align__(16) unsigned char smraw[];
     T2 *sv = (T2 *)smraw;   // the chunk: interleaved (re, im), swizzled
     uint32_t *prog = (uint32_t *)(sv + (1 << C));
@@ -550,8 +586,9 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
     __syncthreads();
     const int nd = (int)ldw(prog + H_NDSEG);
     const int nhoist = (int)ldw(prog + H_NHOIST);
-    W *cta_ph = (W *)(prog + ((ldw(prog + H_WORDS) + 3) & ~3u));
-    W *thr_ph = (W *)((unsigned char *)cta_ph + (((size_t)nd * SC * sizeof(W) + 15) & ~(size_t)15));
+    W *cta_buf = (W *)(prog + ((ldw(prog + H_WORDS) + 3) & ~3u));
+    const int cbw = (int)(cta_buffer_bytes(nd, RB, TB, sizeof(W)) / sizeof(W));   // words of one buffer
+    W *thr_ph = cta_buf + kCtaBuffers * cbw;
     __shared__ uint64_t s_git[NR / 2];    // global offset of load iteration `it`
     __shared__ uint32_t s_sit[NR / 2];    // swizzled smem position of `it` on the store
     __shared__ uint64_t s_dep[768];       // chunk number byte k -> its free-qubit bits
@@ -612,6 +649,7 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
         s_x0[s * T + tid] = x0t;
         s_pb[s * T + tid] = swz<SW, C>(ybase);
     }
+    cta_zero<R, T>(cta_buf, 2 * cbw, tid);
     __syncthreads();
     const uint32_t pst_tid = swz<SW, C>(st_tid);
     const uint32_t pst_one = swz<SW, C>(st_one);
@@ -624,6 +662,8 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
         const uint64_t c = (uint64_t)chn;
         return s_dep[c & 255] | s_dep[256 + ((c >> 8) & 255)] | s_dep[512 + ((c >> 16) & 255)];
     };
+    if (blockIdx.x < nchunks) cta_accum<R, T>(prog, cta_buf, chunk_base(blockIdx.x), tid);
+    __syncthreads();
     // coalesced loads of one chunk's amplitude pairs into registers
     auto load_regs = [&](T2 (&dst)[NR], uint64_t b) {
         if (src.hi) {
@@ -652,7 +692,10 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
     // and three CTAs per SM, whose loads overlap each other's stages
     int64_t ch = blockIdx.x;
     uint64_t base = chunk_base(ch);
+    int cb = 0;   // CTA-table buffer of this chunk
     for (; ch < nchunks; ch += gridDim.x) {
+        const W *cta_ph = cta_buf + cb * cbw;
+        W *cta_next = cta_buf + (cb == 2 ? 0 : cb + 1) * cbw;
         T2 pf[NR];
         load_regs(pf, base);
         // ---- the chunk -> shared
@@ -662,16 +705,22 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
             sv[p] = pf[2 * it];
             sv[p ^ 1] = pf[2 * it + 1];
         }
-        cta_sums<R, T>(prog, cta_ph, nd * SC, base, tid);
+        // buffer (cb + 2) mod 3: last read by the previous chunk
+        cta_zero<R, T>(cta_buf + (cb == 0 ? 2 : cb - 1) * cbw, nd * SCP, tid);
         __syncthreads();
         const int64_t nch = ch + gridDim.x;
         const uint64_t nbase = nch < nchunks ? chunk_base(nch) : 0;
+        // the next chunk's sums (its buffer was cleared during the previous chunk)
+        if (nch < nchunks) cta_accum<R, T>(prog, cta_next, nbase, tid);
         // ---- register stages
         for (int s = 0; s < nst; s++) {
             const uint32_t *sp = prog + ldw(prog + H_STAGE_OFF + s);
-            uint32_t pv[RB];
+            uint32_t pv[(RB + 3) & ~3];
 #pragma unroll
-            for (int j = 0; j < RB; j++) pv[j] = ldw(sp + S_PV + j);
+            for (int k = 0; k < (RB + 3) / 4; k++) {
+                const uint4 q = ld4(sp + S_PV + 4 * k);
+                pv[4 * k] = q.x, pv[4 * k + 1] = q.y, pv[4 * k + 2] = q.z, pv[4 * k + 3] = q.w;
+            }
             const uint64_t x0 = base | s_x0[s * T + tid];
             const uint32_t pb = s_pb[s * T + tid];
             T2 v[NR];
@@ -732,6 +781,7 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
         }
         __syncthreads();
         base = nbase;
+        cb = cb == 2 ? 0 : cb + 1;
     }
 }
 
@@ -748,7 +798,7 @@ __global__ void __launch_bounds__(128) k_diag(typename CT<R>::G2 *__restrict__ a
     constexpr int NR = 1 << RB;
     constexpr int C = 7 + RB;
     constexpr int S = 1 + RB;
-    constexpr int SC = (int)cta_slots(RB, 7);
+    constexpr int SCP = (int)cta_stride(RB, 7, sizeof(typename CT<R>::W));
     extern __shared__ __align__(16) unsigned char smraw[];
     uint32_t *prog = (uint32_t *)smraw;
     const int tid = threadIdx.x;
@@ -756,16 +806,27 @@ __global__ void __launch_bounds__(128) k_diag(typename CT<R>::G2 *__restrict__ a
     __syncthreads();
     const int nd = (int)ldw(prog + H_NDSEG);
     const int nhoist = (int)ldw(prog + H_NHOIST);
-    W *cta_ph = (W *)(prog + ((ldw(prog + H_WORDS) + 3) & ~3u));
-    W *thr_ph = (W *)((unsigned char *)cta_ph + (((size_t)nd * SC * sizeof(W) + 15) & ~(size_t)15));
+    W *cta_buf = (W *)(prog + ((ldw(prog + H_WORDS) + 3) & ~3u));
+    const int cbw = (int)(cta_buffer_bytes(nd, RB, 7, sizeof(W)) / sizeof(W));   // words of one buffer
+    W *thr_ph = cta_buf + kCtaBuffers * cbw;
     const uint32_t *sp = prog + ldw(prog + H_STAGE_OFF);
     const uint32_t *op = sp + S_SIZE + O_BODY;
     thread_sums<R, 128>(prog, thr_ph, nhoist * S, tid);
     const int64_t ntiles = (int64_t)1 << (n - C);
+    cta_zero<R, 128>(cta_buf, 2 * cbw, tid);
+    __syncthreads();
+    if (blockIdx.x < ntiles) cta_accum<R, 128>(prog, cta_buf, (uint64_t)blockIdx.x << C, tid);
+    __syncthreads();
+    // one barrier per tile: tile i reads CTA buffer i mod 3 while the next
+    // tile's sums go to (i + 1) mod 3 (cleared during tile i - 1) and buffer
+    // (i + 2) mod 3, last read by tile i - 1, is cleared
+    int cb = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint64_t base = (uint64_t)tile << C;
-        cta_sums<R, 128>(prog, cta_ph, nd * SC, base, tid);
-        __syncthreads();
+        const W *cta_ph = cta_buf + cb * cbw;
+        cta_zero<R, 128>(cta_buf + (cb == 0 ? 2 : cb - 1) * cbw, nd * SCP, tid);
+        if (tile + gridDim.x < ntiles)
+            cta_accum<R, 128>(prog, cta_buf + (cb == 2 ? 0 : cb + 1) * cbw, (uint64_t)(tile + gridDim.x) << C, tid);
         const uint64_t x0 = base | (uint64_t)tid;
         T2 v[NR];
         // the tile's 2^C amplitudes share one hi factor when n_lo >= C:
@@ -787,6 +848,7 @@ __global__ void __launch_bounds__(128) k_diag(typename CT<R>::G2 *__restrict__ a
 #pragma unroll
         for (int m = 0; m < NR; m++) __stcs(a + x0 + ((uint64_t)m << 7), to_glob(v[m]));
         __syncthreads();
+        cb = cb == 2 ? 0 : cb + 1;
     }
 }
 

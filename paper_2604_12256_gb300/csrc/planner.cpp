@@ -208,6 +208,14 @@ struct ProgWriter {
     void put(uint32_t v) { w.push_back(v); }
     void put64(uint64_t v) { w.push_back((uint32_t)v); w.push_back((uint32_t)(v >> 32)); }
     void align2() { if (w.size() & 1) w.push_back(0); }
+    void align4() { while (w.size() & 3) w.push_back(0); }
+    // pad the op that starts at `start` to a multiple of 4 words and record
+    // its length (ops start 2 words before a 16-byte boundary)
+    void end_op(size_t start)
+    {
+        while ((w.size() - start) & 3) w.push_back(0);
+        w[start + prog::O_WORDS] = (uint32_t)(w.size() - start);
+    }
 };
 
 static inline uint64_t qweight(uint64_t w, bool f64)
@@ -302,7 +310,7 @@ static void encode_dseg(ProgWriter &pw, const std::vector<Term> &terms, const Ds
     std::vector<std::vector<Term>> lin(RB);
     std::vector<std::pair<Term, uint32_t>> multi;
     std::vector<uint64_t> tab(1u << RB, 0);
-    const uint32_t S = 1 + RB, SC = prog::cta_slots(RB, cx.TB);
+    const uint32_t S = 1 + RB, SCP = prog::cta_stride(RB, cx.TB, f64 ? 8 : 4);
     auto to_tables = [&](uint32_t slot, uint64_t nonreg, uint64_t w) {
         uint64_t mt = nonreg & thrall;
         const uint64_t mc = nonreg & ~thrall;
@@ -315,7 +323,7 @@ static void encode_dseg(ProgWriter &pw, const std::vector<Term> &terms, const Ds
             }
         }
         if (mt == 0) {
-            cx.cta->push_back(cx.d * SC + slot);
+            cx.cta->push_back(cx.d * SCP + slot);
             cx.cta->push_back(0);
             cx.cta->push_back((uint32_t)mc);
             cx.cta->push_back((uint32_t)(mc >> 32));
@@ -364,12 +372,14 @@ static void encode_dseg(ProgWriter &pw, const std::vector<Term> &terms, const Ds
     size_t start = pw.w.size();
     pw.put(prog::OP_DSEG);
     pw.put(0);   // words, patched below
+    pw.put((uint32_t)cx.d);
+    pw.put(tabnz ? 1u : 0u);
     pw.put((uint32_t)base.size());
     pw.put((uint32_t)multi.size());
     for (int j = 0; j < prog::kMaxRB; j++) pw.put(j < RB ? (uint32_t)lin[j].size() : 0);
     pw.put((uint32_t)pivot);
-    pw.put(tabnz ? 1u : 0u);
-    pw.put((uint32_t)cx.d);
+    pw.put(0);
+    pw.put(0);
     pw.put(0);
     auto put_term = [&](const Term &t) {
         pw.put64(t.mask);
@@ -403,8 +413,7 @@ static void encode_dseg(ProgWriter &pw, const std::vector<Term> &terms, const Ds
         pw.put(0);
         pw.put64(qweight(mt.first.w, f64));
     }
-    pw.align2();
-    pw.w[start + prog::O_WORDS] = (uint32_t)(pw.w.size() - start);
+    pw.end_op(start);
 }
 
 static void encode_dense(ProgWriter &pw, const SOp &op, const int *reg, const int *qin, int RB, bool f64)
@@ -460,8 +469,7 @@ static void encode_dense(ProgWriter &pw, const SOp &op, const int *reg, const in
             pw.put(b);
         }
     }
-    pw.align2();
-    pw.w[start + prog::O_WORDS] = (uint32_t)(pw.w.size() - start);
+    pw.end_op(start);
 }
 
 // shared-memory budget of the per-thread term table of one launch
@@ -507,7 +515,7 @@ static std::vector<uint32_t> encode_program(int n, int C, int RB, bool f64, uint
     std::vector<uint32_t> cta, thr_t;
     for (size_t s = 0; s < stages.size(); s++) {
         const SStage &st = stages[s];
-        pw.align2();
+        pw.align4();
         size_t sstart = pw.w.size();
         pw.w[prog::H_STAGE_OFF + s] = (uint32_t)sstart;
         int reg[prog::kMaxRB] = {0}, thr[prog::kMaxC] = {0};
@@ -1442,14 +1450,15 @@ static bool validate_program(const std::vector<uint32_t> &w, int n, bool diag_sw
     }
     // launch-wide term tables
     const uint32_t ND = w[prog::H_NDSEG], NH = w[prog::H_NHOIST], S = 1 + RB, TB = C - RB,
-                   SC = prog::cta_slots(RB, TB);
+                   SC = prog::cta_slots(RB, TB), SCP = prog::cta_stride(RB, TB, (uint32_t)wb);
     if (ND > (uint32_t)prog::kMaxDseg || NH > ND) return bad("segment counts");
     if (prog::smem_bytes(w.data(), diag_sweep) > 200 * 1024) return bad("shared memory");
     {
         size_t co = w[prog::H_CTA_OFF], cn = w[prog::H_NCTA], to = w[prog::H_THR_OFF], tn = w[prog::H_NTHR];
         if (co + cn * prog::kCtaWords > W || to + tn * prog::kThrWords > W) return bad("term tables");
         for (size_t i = 0; i < cn; i++)
-            if (w[co + i * prog::kCtaWords] >= ND * SC) return bad("CTA table slot");
+            if (w[co + i * prog::kCtaWords] >= ND * SCP || w[co + i * prog::kCtaWords] % SCP >= SC)
+                return bad("CTA table slot");
         for (size_t i = 0; i < tn; i++) {
             if (w[to + i * prog::kThrWords] >= NH * S) return bad("thread table slot");
             if (w[to + i * prog::kThrWords + 1] >> TB) return bad("thread table mask");
@@ -1458,7 +1467,7 @@ static bool validate_program(const std::vector<uint32_t> &w, int n, bool diag_sw
     uint32_t nseg_seen = 0;
     for (int s = 0; s < ns; s++) {
         size_t so = w[prog::H_STAGE_OFF + s];
-        if ((so & 1) || so + prog::S_SIZE > W) return bad("stage offset");
+        if ((so & 3) || so + prog::S_SIZE > W) return bad("stage offset");
         uint32_t seen = 0;
         for (int j = 0; j < RB; j++) {
             uint32_t b = w[so + prog::S_REG + j];
@@ -1477,9 +1486,10 @@ static bool validate_program(const std::vector<uint32_t> &w, int n, bool diag_sw
         const uint32_t nops = w[so + prog::S_NOPS];
         size_t op = so + prog::S_SIZE;
         for (uint32_t k = 0; k < nops; k++) {
-            if (op + 2 > W || (op & 1)) return bad("op offset");
+            // bodies are 16-byte aligned: ops start at 2 (mod 4) words
+            if (op + 2 > W || (op & 3) != 2) return bad("op offset");
             const uint32_t hdr = w[op], len = w[op + prog::O_WORDS];
-            if (len < 2 || op + len > W) return bad("op length");
+            if (len < 4 || (len & 3) || op + len > W) return bad("op length");
             const int type = hdr & 0xff;
             if (type == prog::OP_DENSE) {
                 if (diag_sweep) return bad("dense op in a diagonal sweep");

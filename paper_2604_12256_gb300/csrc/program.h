@@ -58,23 +58,28 @@ enum : int {
     H_PAD,
     H_SIZE
 };
-// CTA-table entry: slot (= d * (1 + RB) + s, s = 0 base / 1 + j linear in
-// register bit j), 0, mask_lo, mask_hi, w_lo, w_hi
+// CTA-table entry: slot (= d * cta_stride + s: s = 0 base, 1 + j linear in
+// register bit j, 1 + RB + i linear in thread bit i), 0, mask_lo, mask_hi,
+// w_lo, w_hi
 constexpr int kCtaWords = 6;
 // thread-table entry: slot, mask over the thread-index bits, w_lo, w_hi
 constexpr int kThrWords = 4;
 constexpr int kMaxDseg = 64;
 
-// stage
+// stage.  Stages start on 4-word (16-byte) boundaries; S_SIZE = 2 (mod 4)
+// and every op is padded to a multiple of 4 words, so each op starts 2 words
+// before a 16-byte boundary and its body (O_BODY = 2) is 16-byte aligned: the
+// kernels read stage headers, op bodies and tables with 128-bit loads.
 enum : int {
     S_NOPS = 0,
     S_WORDS = 1,
-    S_REG = 2,                 // kMaxRB words
+    S_PV = 4,                  // kMaxRB words: swizzled shared-memory offset of register bit j
+    S_REG = S_PV + kMaxRB,     // kMaxRB words
     S_THR = S_REG + kMaxRB,    // kMaxC words
     S_GTHR = S_THR + kMaxC,    // kMaxC words: physical qubit of thread bit i (= qin[thr[i]])
-    S_PV = S_GTHR + kMaxC,     // kMaxRB words: swizzled shared-memory offset of register bit j
-    S_SIZE = S_PV + kMaxRB     // even
+    S_SIZE = S_GTHR + kMaxC + 2
 };
+static_assert(S_PV % 4 == 0 && S_SIZE % 4 == 2, "stage header alignment");
 
 // Shared-memory swizzle of the chunk (interleaved complex amplitudes):
 // element y lives at y ^ fold(y >> sw), folding sw-bit groups into the low
@@ -96,50 +101,64 @@ enum : int { OP_DENSE = 1, OP_DSEG = 2 };
 enum : int { O_HDR = 0, O_WORDS = 1, O_BODY = 2 };
 // dense: hdr = OP_DENSE | k << 8 | code << 16 with code = p0 + 8 p1 + 64 p2
 //        (register positions, ascending); body = 2 * 4^k reals (float or double)
-// phase segment (DSEG) body:
+// phase segment (DSEG) body (16-byte aligned, read as 128-bit words):
 enum : int {
-    D_NBASE = 0,          // terms on thread/chunk bits only
-    D_NMULTI = 1,         // terms with >= 2 register bits and other bits
-    D_NLIN = 2,           // kMaxRB counts: terms with register bit j and other bits
+    D_INDEX = 0,          // segment number d
+    D_FLAGS = 1,          // bit 0: the register-only table is not all zero
+    D_NBASE = 2,          // terms on thread/chunk bits only
+    D_NMULTI = 3,         // terms with >= 2 register bits and other bits
+    D_NLIN = 4,           // kMaxRB counts: terms with register bit j and other bits
     D_PIVOT = D_NLIN + kMaxRB,   // register bit present in every term, or -1:
                                  // then only amplitudes with that bit set change
-    D_FLAGS = D_PIVOT + 1,       // bit 0: the register-only table is not all zero
-    D_INDEX = D_FLAGS + 1,       // segment number d
-    D_PAD = D_INDEX + 1,
-    D_TERMS = D_PAD + 1          // even
+    D_TERMS = D_PIVOT + 4        // 16-byte aligned (words D_PIVOT + 1 .. + 3 are 0)
 };
+static_assert(D_NLIN % 4 == 0 && D_TERMS % 4 == 0, "segment header alignment");
 // dense op subtypes (hdr bits 12..15), for k = 1
 enum : int { DS_GENERAL = 0, DS_REAL = 1, DS_RX = 2 };
 // term (4 words): mask_lo, mask_hi, w_lo, w_hi   (mask over physical qubits,
 //                 register bits removed; w: uint32 in w_lo or uint64)
 // then reg table: 2^RB entries x 2 words (phase of the register-only terms),
 // then the same table as complex factors cis(2 pi w / 2^wbits): 2^RB entries
-// x (re, im) as float (2 words) or double (4 words),
+// x (re, im) as float (2 words) or double-float (4 words), 16-byte aligned,
 // multi term (6 words): mask_lo, mask_hi, regmask, 0, w_lo, w_hi
 constexpr int kTermWords = 4;
 constexpr int kMultiWords = 6;
 // words of the complex register table (wb = bytes per real: 4 or 8)
 PROG_HD inline constexpr uint32_t ctab_words(uint32_t RB, uint32_t wb) { return (1u << RB) * (wb == 8 ? 4 : 2); }
 
-// Dynamic shared memory of a launch of this program: the chunk's amplitudes
-// (chunk kernel only), the per-chunk CTA sums and the per-thread sums.
 // Shared phase sums of one segment.  CTA table (per chunk): slot 0 = the
 // segment's phase at register index 0, slot 1 + j = the coefficient of
 // register bit j, slot 1 + RB + i = the coefficient of thread bit i (terms on
 // chunk-selecting qubits and one thread bit).  Thread table (per launch): the
 // first 1 + RB of those slots for terms on thread bits only.
 PROG_HD inline constexpr uint32_t cta_slots(uint32_t RB, uint32_t TB) { return 1 + RB + TB; }
+// a segment's CTA slots padded to 16 bytes (read with 128-bit loads)
+PROG_HD inline constexpr uint32_t cta_stride(uint32_t RB, uint32_t TB, uint32_t wb)
+{
+    return wb == 8 ? (cta_slots(RB, TB) + 1) & ~1u : (cta_slots(RB, TB) + 3) & ~3u;
+}
+// The CTA table is triple-buffered: while chunk i reads buffer i mod 3, the
+// sums of chunk i + 1 are accumulated into buffer (i + 1) mod 3 and buffer
+// (i + 2) mod 3 is cleared, all between barriers the chunk needs anyway.
+constexpr int kCtaBuffers = 3;
+PROG_HD inline constexpr size_t cta_buffer_bytes(uint32_t nd, uint32_t RB, uint32_t TB, uint32_t wb)
+{
+    return ((size_t)nd * cta_stride(RB, TB, wb) * wb + 15) & ~(size_t)15;
+}
 
+// Dynamic shared memory of a launch of this program: the chunk's amplitudes
+// (chunk kernel only), the program, the CTA-table buffers, the per-thread
+// sums and the per-thread stage layouts (chunk kernel only).
 inline size_t smem_bytes(const uint32_t *w, bool diag_sweep)
 {
     const size_t C = w[H_C], RB = w[H_RB], wb = w[H_WBYTES];
-    const size_t T = (size_t)1 << (C - RB), S = 1 + RB, SC = cta_slots(RB, C - RB);
+    const size_t T = (size_t)1 << (C - RB), S = 1 + RB;
     const size_t planes = diag_sweep ? 0 : 2 * ((size_t)1 << C) * wb;
     const size_t progw = ((size_t)w[H_WORDS] * 4 + 15) & ~(size_t)15;
     // per-thread stage layouts (chunk kernel): thread part of x0 and of the
     // swizzled register-block offset for every stage
     const size_t layouts = diag_sweep ? 0 : (size_t)w[H_NSTAGE] * T * 12;
-    return planes + progw + (((size_t)w[H_NDSEG] * SC * wb + 15) & ~(size_t)15) +
+    return planes + progw + kCtaBuffers * cta_buffer_bytes(w[H_NDSEG], (uint32_t)RB, (uint32_t)(C - RB), (uint32_t)wb) +
            (((size_t)w[H_NHOIST] * S * T * wb + 15) & ~(size_t)15) + layouts;
 }
 
