@@ -223,6 +223,10 @@ def run_gpu(args, rank, world, dist):
         opt.dense_precision = PRECISIONS[args.precision]
     if args.register_bits:
         opt.register_bits = args.register_bits
+    if args.jit and not dense:
+        # chunk sweeps run kernels specialised to their programs, compiled
+        # (NVRTC) during the first warm-up step and cached
+        opt.flags |= S.SIM_F_JIT
 
     def step():
         sim.reset(0)
@@ -257,6 +261,7 @@ def run_gpu(args, rank, world, dist):
     sim.profile_enable(False)
     clk = clocks.stop()
     ms = max_over_ranks(ms, dist)
+    jit = S.jit_info()
 
     # end-to-end through the C ABI: host gate list in, host results out
     pairs = [(i, (i * 7 + 3) % N_QUBITS) for i in range(16)]
@@ -301,7 +306,7 @@ def run_gpu(args, rank, world, dist):
     if kind == "dense":
         kname = "k_dense5_tc (dense 5-qubit block, tcgen05 split-TF32)" if args.precision == "tf32x3" \
             and dt == S.SIM_C64 else "k_dense5_fma (dense 5-qubit block, CUDA cores)"
-    ksrc = {"chunk": "k_chunk.cu", "diag": "k_chunk.cu", "dense": "k_dense5.cu"}.get(kind, "k_basic.cu")
+    ksrc = {"chunk": "chunk_dev.cuh", "diag": "chunk_dev.cuh", "dense": "k_dense5.cu"}.get(kind, "k_basic.cu")
     src = open(os.path.join(ROOT, "paper_2604_12256_gb300", "csrc", ksrc), "rb").read()
     tpa = TRAFFIC_PER_AMP.get((args.workload, kind, hashlib.sha256(src).hexdigest()))
     if (dense and args.precision != "tf32x3") or args.dtype != "c64":
@@ -339,7 +344,11 @@ def run_gpu(args, rank, world, dist):
                        "parallelism": f"replicas x{world}",
                        "l2": f"state ({amps * s_amp / 2 ** 30:g} GiB) larger than L2, no flush",
                        "sweeps": plan["sweeps"], "chunk_ops": plan["chunk_ops"], "dense_ops": plan["dense_ops"],
-                       "diag_fused": plan["diag_fused"], "plan_ms": plan["plan_ms"]},
+                       "diag_fused": plan["diag_fused"], "plan_ms": plan["plan_ms"],
+                       "chunk_kernels": ("specialised per program at run time (NVRTC), compiled in the first "
+                                         "warm-up step and cached: %d programs, %.0f ms of compile"
+                                         % (jit["programs"], jit["compile_ms"])) if opt.flags & S.SIM_F_JIT
+                       else "interpreter"},
             "hbm_gbs": total_bytes / (ms / 1e3) / 1e9,
             "hbm_frac_of_" + peak_kind: total_bytes / (ms / 1e3) / 1e9 / peak,
             "roofline": roof,
@@ -565,6 +574,9 @@ def main():
     ap.add_argument("--precision", default="tf32x3", choices=sorted(PRECISIONS),
                     help="dense-block arithmetic for --workload layered-dense")
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--no-jit", dest="jit", action="store_false",
+                    help="run the chunk sweeps on the interpreter kernel instead of kernels specialised to "
+                         "their programs")
     ap.add_argument("--no-unfused", action="store_true", help="skip the gate-by-gate comparison run")
     ap.add_argument("--families", action="store_true",
                     help="per-gate time of the BV / HS / QV / SC / VC families: gate by gate, optimized, "

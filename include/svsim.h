@@ -89,7 +89,15 @@ enum {
                                restoring sweep at most).  Opt-in: fewer sweeps
                                on nearest-neighbour layered circuits, heavier
                                sweeps on random ones                          */
-    SIM_F_ALL = 0x3f
+    SIM_F_JIT = 1u << 6,    /* complex64 cache-blocked sweeps run kernels
+                               specialised to their program: ops decoded once
+                               on the host and compiled (NVRTC, needs
+                               libnvrtc.so.13) into straight-line code, cached
+                               per program for the process; the first apply of
+                               a new program pays its compile (~0.3 s, in
+                               parallel over a plan's programs).  Results are
+                               bit-identical to the interpreter kernel's      */
+    SIM_F_ALL = 0x7f
 };
 
 /* Precision of dense fused blocks on complex64 states (complex128 states
@@ -258,6 +266,17 @@ const char *sim_global_error(void);
 int sim_plan_json(int n_qubits, sim_dtype dtype, uint64_t basis_index,
                   const sim_gate *gates, size_t n, const sim_options *opt,
                   char *buf, size_t buflen, size_t *needed);
+
+/* Plan the circuit as sim_plan_json does and generate and compile (NVRTC,
+ * no GPU needed) the specialised kernel of every chunk sweep that SIM_F_JIT
+ * would run; *n_programs receives their count.  SIM_EINVAL with the
+ * compiler's log in sim_global_error() when one does not compile. */
+int sim_jit_check(int n_qubits, sim_dtype dtype, uint64_t basis_index, const sim_gate *gates, size_t n,
+                  const sim_options *opt, int *n_programs);
+
+/* Specialised kernels compiled and cached by this process so far, and the
+ * wall time their compiles took (ms). */
+int sim_jit_info(uint64_t *programs, double *compile_ms);
 
 /* ------------------------------------------------------------ serving */
 /* A request loop with continuous batching (not in the paper; the serving

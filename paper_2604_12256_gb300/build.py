@@ -46,6 +46,31 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+# device headers compiled at run time into specialised sweep kernels (jit.cpp)
+JIT_HEADERS = ("chunk_dev.cuh", "program.h", "dfloat.h")
+
+
+def _write_jit_headers() -> str:
+    """C++ source holding the run-time compiler's headers as strings."""
+    out = os.path.join(BUILD, "jit_headers.cpp")
+    lines = ["// generated by build.py from csrc: headers of the specialised sweep kernels",
+             "namespace svs {", f"extern const int kJitHeaderCount = {len(JIT_HEADERS)};",
+             "extern const char *const kJitHeaderNames[] = {" +
+             ", ".join(f'"{h}"' for h in JIT_HEADERS) + "};",
+             "extern const char *const kJitHeaderSources[] = {"]
+    for h in JIT_HEADERS:
+        with open(os.path.join(CSRC, h)) as f:
+            text = f.read()
+        assert ")svsjit\"" not in text
+        lines.append('R"svsjit(' + text + ')svsjit",')
+    lines += ["};", "}  // namespace svs", ""]
+    data = "\n".join(lines)
+    if not os.path.exists(out) or open(out).read() != data:
+        with open(out, "w") as f:
+            f.write(data)
+    return out
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
@@ -53,6 +78,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = os.path.join(cuda, "bin", "nvcc")
     os.makedirs(BUILD, exist_ok=True)
     cu, cpp = _sources()
+    cpp.append(_write_jit_headers())
     common_inc = ["-I", INC, "-I", CSRC]
     jobs = []
     for src in cu:

@@ -404,7 +404,7 @@ static int ensure_sub(sim_t *s, int id, int nq)
 
 static void *buf_ptr(sim_t *s, int id) { return id == 0 ? s->state : s->sub[id]; }
 
-static int execute(sim_t *s, const Plan &p)
+static int execute(sim_t *s, const Plan &p, bool jit)
 {
     const bool f64 = s->dt == SIM_C128;
     if (s->reset_pending) {
@@ -473,6 +473,21 @@ static int execute(sim_t *s, const Plan &p)
         CK(s, cudaEventRecord(s->pin_ev, s->stream));
         s->pin_pending = true;
     }
+    // specialised chunk kernels: compile the programs not cached yet (all of
+    // them at once, in parallel) before the first launch
+    std::vector<char> use_jit(p.ops.size(), 0);
+    if (jit) {
+        std::vector<const std::vector<uint32_t> *> progs;
+        for (size_t i = 0; i < p.ops.size(); i++) {
+            const Op &o = p.ops[i];
+            if (o.kind == OPK_CHUNK && jit_supported(f64, o.prog.C, o.prog.RB)) {
+                use_jit[i] = 1;
+                progs.push_back(&o.words);
+            }
+        }
+        std::string err;
+        if (!progs.empty() && !jit_prepare(progs, err)) return fail(s, SIM_ECUDA, err);
+    }
     // 2. launches (Algorithm 5)
     for (size_t i = 0; i < p.ops.size(); i++) {
         const Op &o = p.ops[i];
@@ -507,8 +522,12 @@ static int execute(sim_t *s, const Plan &p)
             e = launch_phase_small(a, o.n, f64, (const uint64_t *)cst, (int)o.terms.size(), s->stream);
             break;
         case OPK_CHUNK:
-            e = launch_chunk(a, o.n, f64, o.prog.C, o.prog.RB, (const uint32_t *)cst,
-                             prog::smem_bytes(o.words.data(), false), src, s->stream);
+            if (use_jit[i])
+                e = launch_chunk_jit(a, o.n, o.words, (const uint32_t *)cst, prog::smem_bytes(o.words.data(), false),
+                                     src, s->stream);
+            else
+                e = launch_chunk(a, o.n, f64, o.prog.C, o.prog.RB, (const uint32_t *)cst,
+                                 prog::smem_bytes(o.words.data(), false), src, s->stream);
             break;
         case OPK_TENSOR:
             e = launch_tensor(a, buf_ptr(s, o.buf_hi), o.n_hi, buf_ptr(s, o.buf_lo), o.n_lo, f64, s->stream);
@@ -540,7 +559,7 @@ int sim_apply_circuit(sim_t *s, const sim_gate *gates, size_t n, const sim_optio
     } catch (const std::bad_alloc &) {
         return fail(s, SIM_ENOMEM, "host allocation failed while planning");
     }
-    int rc = execute(s, p);
+    int rc = execute(s, p, (o.flags & SIM_F_JIT) != 0);
     if (rc) return rc;
     s->stats = p.stats;
     if (n > 0) s->product = false;
@@ -681,6 +700,42 @@ int sim_plan_json(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, si
     if (needed) *needed = js.size() + 1;
     if (!buf || buflen < js.size() + 1) return fail(nullptr, SIM_ENOMEM, "buffer too small for the plan");
     std::memcpy(buf, js.c_str(), js.size() + 1);
+    return SIM_OK;
+}
+
+int sim_jit_info(uint64_t *programs, double *compile_ms)
+{
+    const size_t n = jit_cache_size(compile_ms);
+    if (programs) *programs = n;
+    return SIM_OK;
+}
+
+int sim_jit_check(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_t ng, const sim_options *opt,
+                  int *n_programs)
+{
+    int rc = check_n(n, dt);
+    if (rc) return rc;
+    if (ng > 0 && !gates) return fail(nullptr, SIM_EINVAL, "null gate array");
+    sim_options o;
+    if (opt) o = *opt;
+    else fill_default_options(o);
+    Plan p;
+    std::string err;
+    try {
+        if (!make_plan(n, dt, basis, gates, ng, o, p, err)) return fail(nullptr, SIM_EINVAL, err);
+        int np = 0;
+        for (const Op &op : p.ops) {
+            if (op.kind != OPK_CHUNK || !jit_supported(dt == SIM_C128, op.prog.C, op.prog.RB)) continue;
+            std::string src;
+            std::vector<char> cubin;
+            if (!jit_source(op.words, src, err) || !jit_compile(src, cubin, err) || cubin.empty())
+                return fail(nullptr, SIM_EINVAL, err.empty() ? "empty cubin" : err);
+            np++;
+        }
+        if (n_programs) *n_programs = np;
+    } catch (const std::bad_alloc &) {
+        return fail(nullptr, SIM_ENOMEM, "host allocation failed while planning");
+    }
     return SIM_OK;
 }
 

@@ -6,8 +6,10 @@
 // Knuth's two-sum and the FMA two-product.
 #pragma once
 
+#if !defined(__CUDACC_RTC__)
 #include <cstdint>
 #include <cuda_runtime.h>
+#endif
 
 namespace svs {
 

@@ -20,769 +20,19 @@
 #include <mutex>
 #include <vector>
 
-#include "dfloat.h"
+#include "chunk_dev.cuh"
 #include "kernels.h"
-#include "program.h"
 
 namespace svs {
-
 using namespace prog;
 
-template <typename R> struct CT;
-template <> struct CT<float> {
-    using T2 = float2;    // registers / shared memory
-    using G2 = float2;    // HBM
-    using W = uint32_t;
-    static constexpr int SWZ = swizzle_bits(4);
-};
-template <> struct CT<double> {
-    using T2 = dfc;
-    using G2 = double2;
-    using W = uint64_t;
-    static constexpr int SWZ = swizzle_bits(8);
-};
-
-__device__ __forceinline__ float2 to_reg(float2 v) { return v; }
-__device__ __forceinline__ float2 to_glob(float2 v) { return v; }
-
-// Program words are read from the CTA's shared-memory copy of the program.
-__device__ __forceinline__ uint32_t ldw(const uint32_t *p) { return *p; }
-__device__ __forceinline__ uint64_t ld64(const uint32_t *p) { return (uint64_t)p[0] | ((uint64_t)p[1] << 32); }
-// 128-bit read of 4 program words (the encoder aligns what is read this way)
-__device__ __forceinline__ uint4 ld4(const uint32_t *p) { return *(const uint4 *)p; }
-
-using namespace prog;
-
-template <typename R> __device__ __forceinline__ typename CT<R>::W ldwt(const uint32_t *p);
-template <> __device__ __forceinline__ uint32_t ldwt<float>(const uint32_t *p) { return *p; }
-template <> __device__ __forceinline__ uint64_t ldwt<double>(const uint32_t *p) { return ld64(p); }
-
-// complex element i of a dense op body or a complex table in the program:
-// complex64 as (re, im) floats, complex128 as double-float (rh, rl, ih, il)
-__device__ __forceinline__ float2 ldm(const float *b, int i) { return make_float2(b[2 * i], b[2 * i + 1]); }
-__device__ __forceinline__ dfc ldm(const double *b, int i)
-{
-    const float4 q = ((const float4 *)b)[i];
-    dfc r;
-    r.rh = q.x;
-    r.rl = q.y;
-    r.ih = q.z;
-    r.il = q.w;
-    return r;
-}
-// element i of a 16-byte-aligned complex table: complex64 entries are read
-// two per 128-bit load (the loads of i and i ^ 1 are the same word)
-__device__ __forceinline__ float2 ldm_a(const float *b, int i)
-{
-    const float4 q = ((const float4 *)b)[i >> 1];
-    return (i & 1) ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
-}
-__device__ __forceinline__ dfc ldm_a(const double *b, int i) { return ldm(b, i); }
-
-// stage the program (H_WORDS words, 16-byte aligned in both spaces) in shared memory
-template <int T>
-__device__ __forceinline__ void stage_program(const uint32_t *__restrict__ g, uint32_t *s, int tid)
-{
-    const int nw = (int)__ldg(g + H_WORDS);
-    const uint4 *g4 = (const uint4 *)g;
-    uint4 *s4 = (uint4 *)s;
-    for (int i = tid; i < (nw >> 2); i += T) s4[i] = __ldg(g4 + i);
-    for (int i = (nw & ~3) + tid; i < nw; i += T) s[i] = __ldg(g + i);
-}
-
-// exp(2 pi i w / 2^bits) for the weight type
-__device__ __forceinline__ float2 cis_turns(uint32_t w)
-{
-    float s, c;
-    __sincosf((float)(int32_t)w * 1.46291807926715968e-09f, &s, &c);   // 2 pi / 2^32
-    // one Newton step towards |c + i s| = 1 so that phases do not bias the norm
-    const float f = fmaf(-0.5f, fmaf(c, c, s * s), 1.5f);
-    return make_float2(c * f, s * f);
-}
-// complex128: cis(2 pi w / 2^64) = T0[w >> 56] T1[(w >> 48) & 255]
-// T2[(w >> 40) & 255] cis(e), e = 2 pi (w mod 2^40) / 2^64 < 2 pi 2^-24, with
-// cis(e) = (1 - e^2/2, e (1 - e^2/6)) (the next terms are below 1e-27).
-// Tk[b] = cis(2 pi b / 2^(8k + 8)) as double-float, split from long-double
-// values on the host (set_cis64_tables); the products run in double-float.
-__device__ dfc g_cis64[3 * 256];   // double-float (rh, rl, ih, il)
-
-__device__ __forceinline__ dfc cis_turns(uint64_t w)
-{
-    const dfc t0 = g_cis64[w >> 56];
-    const dfc t1 = g_cis64[256 + ((w >> 48) & 255)];
-    const dfc t2 = g_cis64[512 + ((w >> 40) & 255)];
-    // e = 2 pi r / 2^64, r < 2^40 exact as a double-float (two 20-bit halves)
-    const uint64_t r = w & ((1ull << 40) - 1);
-    const float rh = (float)(uint32_t)(r >> 20) * 1048576.f, rl = (float)(uint32_t)(r & 0xFFFFF);
-    constexpr float kh = 0x1.921fb6p-62f;    // 2 pi 2^-64 = kh + kl to 1e-15
-    constexpr float kl = -0x1.777a5cp-87f;
-    float eh, el;
-    {
-        const float ah[2] = {rh, rl}, al[2] = {0.f, 0.f}, bh[2] = {kh, kh}, bl[2] = {kl, kl};
-        df_dot<2>(ah, al, bh, bl, eh, el);
-    }
-    const float e2 = eh * eh;   // < 1.4e-13: its float rounding is far below 1e-16 of 1
-    dfc te;
-    two_sum(1.f, -0.5f * e2, te.rh, te.rl);
-    te.ih = eh;
-    te.il = fmaf(-eh * (1.f / 6.f), e2, el);
-    return cmul(cmul(cmul(t0, t1), t2), te);
-}
-
-// packed f32x2 arithmetic (sm_100+): a 64-bit register pair holds (re, im)
-using u64 = unsigned long long;
-__device__ __forceinline__ u64 pk2(float lo, float hi)
-{
-    u64 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ u64 pk(float2 v) { return pk2(v.x, v.y); }
-__device__ __forceinline__ float2 upk(u64 r)
-{
-    float2 v;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
-    return v;
-}
-__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c)
-{
-    u64 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ u64 fmul2(u64 a, u64 b)
-{
-    u64 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-
-template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b)
-{
-    T2 r;
-    r.x = a.x * b.x - a.y * b.y;
-    r.y = a.x * b.y + a.y * b.x;
-    return r;
-}
-
-// shared-memory swizzle: phys(y) = y ^ fold_SWZ(y >> SWZ); linear over GF(2)
-template <int SWZ, int C> __device__ __forceinline__ uint32_t swz(uint32_t y)
-{
-    uint32_t r = y;
-#pragma unroll
-    for (int s = SWZ; s < C; s += SWZ) r ^= (y >> s) & ((1u << SWZ) - 1);
-    return r;
-}
-
-// ------------------------------------------------------------ dense ops
-template <typename R, int NR, int K, int P0, int P1>
-__device__ __forceinline__ void dense_apply(typename CT<R>::T2 (&v)[NR], const uint32_t *body)
-{
-    using T2 = typename CT<R>::T2;
-    constexpr int D = 1 << K;
-    constexpr int gm = (1 << P0) | (K > 1 ? (1 << P1) : 0);
-    const R *mb = (const R *)body;
-    if constexpr (sizeof(R) == 8) {
-        // complex128 in double-float: each output component is one
-        // double-float dot product over the 2D real products
-#pragma unroll
-        for (int g = 0; g < NR; g++) {
-            if (g & gm) continue;
-            dfc in[D];
-#pragma unroll
-            for (int c = 0; c < D; c++) {
-                const int off = ((c & 1) << P0) | (K > 1 ? (((c >> 1) & 1) << P1) : 0);
-                in[c] = v[g | off];
-            }
-#pragma unroll
-            for (int r = 0; r < D; r++) {
-                float ah[2 * D], al[2 * D], bh[2 * D], bl[2 * D];
-                float ch[2 * D], cl[2 * D], dh[2 * D], dl[2 * D];
-#pragma unroll
-                for (int c = 0; c < D; c++) {
-                    const dfc m = ldm(mb, r * D + c);
-                    // re: mr xr - mi xi      im: mr xi + mi xr
-                    ah[2 * c] = m.rh, al[2 * c] = m.rl, bh[2 * c] = in[c].rh, bl[2 * c] = in[c].rl;
-                    ah[2 * c + 1] = -m.ih, al[2 * c + 1] = -m.il, bh[2 * c + 1] = in[c].ih, bl[2 * c + 1] = in[c].il;
-                    ch[2 * c] = m.rh, cl[2 * c] = m.rl, dh[2 * c] = in[c].ih, dl[2 * c] = in[c].il;
-                    ch[2 * c + 1] = m.ih, cl[2 * c + 1] = m.il, dh[2 * c + 1] = in[c].rh, dl[2 * c + 1] = in[c].rl;
-                }
-                dfc o;
-                df_dot<2 * D>(ah, al, bh, bl, o.rh, o.rl);
-                df_dot<2 * D>(ch, cl, dh, dl, o.ih, o.il);
-                const int off = ((r & 1) << P0) | (K > 1 ? (((r >> 1) & 1) << P1) : 0);
-                v[g | off] = o;
-            }
-        }
-        return;
-    } else if constexpr (K == 1) {
-        // complex64 2x2: m x = (mr, mr) * x + (-mi, mi) * (x.im, x.re), packed
-        u64 Mr[4], Mi[4];
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const float2 e = ldm_a(mb, i);
-            Mr[i] = pk2(e.x, e.x);
-            Mi[i] = pk2(-e.y, e.y);
-        }
-#pragma unroll
-        for (int g = 0; g < NR; g++) {
-            if (g & gm) continue;
-            const float2 y0 = v[g], y1 = v[g | (1 << P0)];
-            const u64 x0 = pk(y0), x1 = pk(y1), s0 = pk2(y0.y, y0.x), s1 = pk2(y1.y, y1.x);
-            v[g] = upk(ffma2(s0, Mi[0], ffma2(x0, Mr[0], ffma2(s1, Mi[1], fmul2(x1, Mr[1])))));
-            v[g | (1 << P0)] = upk(ffma2(s0, Mi[2], ffma2(x0, Mr[2], ffma2(s1, Mi[3], fmul2(x1, Mr[3])))));
-        }
-        return;
-    } else {
-        // complex64, K = 2: the 16 entries are re-read from shared memory for
-        // every group to keep register pressure down
-        T2 M1[K == 1 ? 4 : 1];
-        if constexpr (K == 1) {
-#pragma unroll
-            for (int i = 0; i < 4; i++) M1[i] = ldm(mb, i);
-        }
-        auto M = [&](int i) -> T2 {
-            if constexpr (K == 1) return M1[i];
-            else return ldm(mb, i);
-        };
-#pragma unroll
-        for (int g = 0; g < NR; g++) {
-            if (g & gm) continue;
-            T2 in[D];
-#pragma unroll
-            for (int c = 0; c < D; c++) {
-                int off = ((c & 1) << P0) | (K > 1 ? (((c >> 1) & 1) << P1) : 0);
-                in[c] = v[g | off];
-            }
-#pragma unroll
-            for (int r = 0; r < D; r++) {
-                R re = 0, im = 0;
-#pragma unroll
-                for (int c = 0; c < D; c++) {
-                    const T2 mrc = M(r * D + c);
-                    re = fma(mrc.x, in[c].x, re);
-                    re = fma(-mrc.y, in[c].y, re);
-                    im = fma(mrc.x, in[c].y, im);
-                    im = fma(mrc.y, in[c].x, im);
-                }
-                int off = ((r & 1) << P0) | (K > 1 ? (((r >> 1) & 1) << P1) : 0);
-                v[g | off].x = re;
-                v[g | off].y = im;
-            }
-        }
-    }
-}
-
-// 2x2 matrices with all-real entries (H, RY): 4 flops per amplitude;
-// real diagonal and imaginary off-diagonal (RX): likewise
-template <typename R, int NR, int P, int SUB>
-__device__ __forceinline__ void dense1_special(typename CT<R>::T2 (&v)[NR], const uint32_t *body)
-{
-    if constexpr (sizeof(R) == 8) {
-        // complex128 in double-float; a, b, c, d are the real numbers of the
-        // special form (entry i of the body: floats 4i .. 4i + 3 = rh rl ih il)
-        const float4 *f4 = (const float4 *)body;
-        const float4 qa = f4[0], qb = f4[1], qc = f4[2], qd = f4[3];
-        const float ah = qa.x, al = qa.y, dh = qd.x, dl = qd.y;
-        const float bh = SUB == DS_REAL ? qb.x : qb.z, bl = SUB == DS_REAL ? qb.y : qb.w;
-        const float ch = SUB == DS_REAL ? qc.x : qc.z, cl = SUB == DS_REAL ? qc.y : qc.w;
-#pragma unroll
-        for (int g = 0; g < NR; g++) {
-            if (g & (1 << P)) continue;
-            const dfc x0 = v[g], x1 = v[g | (1 << P)];
-            dfc y0, y1;
-            if constexpr (SUB == DS_REAL) {   // [[a, b], [c, d]] real
-                const float p[2] = {ah, bh}, pl[2] = {al, bl}, q[2] = {ch, dh}, ql[2] = {cl, dl};
-                { const float xh[2] = {x0.rh, x1.rh}, xl[2] = {x0.rl, x1.rl}; df_dot<2>(p, pl, xh, xl, y0.rh, y0.rl);
-                  df_dot<2>(q, ql, xh, xl, y1.rh, y1.rl); }
-                { const float xh[2] = {x0.ih, x1.ih}, xl[2] = {x0.il, x1.il}; df_dot<2>(p, pl, xh, xl, y0.ih, y0.il);
-                  df_dot<2>(q, ql, xh, xl, y1.ih, y1.il); }
-            } else {   // [[a, i b], [i c, d]]: a x0 + i b x1, i c x0 + d x1
-                { const float p[2] = {ah, -bh}, pl[2] = {al, -bl}, xh[2] = {x0.rh, x1.ih}, xl[2] = {x0.rl, x1.il};
-                  df_dot<2>(p, pl, xh, xl, y0.rh, y0.rl); }
-                { const float p[2] = {ah, bh}, pl[2] = {al, bl}, xh[2] = {x0.ih, x1.rh}, xl[2] = {x0.il, x1.rl};
-                  df_dot<2>(p, pl, xh, xl, y0.ih, y0.il); }
-                { const float p[2] = {-ch, dh}, pl[2] = {-cl, dl}, xh[2] = {x0.ih, x1.rh}, xl[2] = {x0.il, x1.rl};
-                  df_dot<2>(p, pl, xh, xl, y1.rh, y1.rl); }
-                { const float p[2] = {ch, dh}, pl[2] = {cl, dl}, xh[2] = {x0.rh, x1.ih}, xl[2] = {x0.rl, x1.il};
-                  df_dot<2>(p, pl, xh, xl, y1.ih, y1.il); }
-            }
-            v[g] = y0;
-            v[g | (1 << P)] = y1;
-        }
-        return;
-    } else {
-        // complex64: one packed f32x2 op updates (re, im) together; entry i of
-        // the row-major 2x2 matrix is (mb[2i], mb[2i+1]) (the op body is in the
-        // shared-memory copy of the program: plain loads)
-        const float4 m0 = ((const float4 *)body)[0], m1 = ((const float4 *)body)[1];
-        const R a = m0.x;
-        const R b = SUB == DS_REAL ? m0.z : m0.w;
-        const R c = SUB == DS_REAL ? m1.x : m1.y;
-        const R d = m1.z;
-        if constexpr (SUB == DS_REAL) {
-            const u64 A = pk2(a, a), B = pk2(b, b), Cc = pk2(c, c), D = pk2(d, d);
-#pragma unroll
-            for (int g = 0; g < NR; g++) {
-                if (g & (1 << P)) continue;
-                const u64 x0 = pk(v[g]), x1 = pk(v[g | (1 << P)]);
-                v[g] = upk(ffma2(x0, A, fmul2(x1, B)));
-                v[g | (1 << P)] = upk(ffma2(x0, Cc, fmul2(x1, D)));
-            }
-        } else {   // [[a, i b], [i c, d]]: a x0 + i b x1, i c x0 + d x1
-            const u64 A = pk2(a, a), D = pk2(d, d), B = pk2(-b, b), Cc = pk2(-c, c);
-#pragma unroll
-            for (int g = 0; g < NR; g++) {
-                if (g & (1 << P)) continue;
-                const float2 y0 = v[g], y1 = v[g | (1 << P)];
-                const u64 x0 = pk(y0), x1 = pk(y1);
-                const u64 s0 = pk2(y0.y, y0.x), s1 = pk2(y1.y, y1.x);   // i x = (-im, re) via the signs
-                v[g] = upk(ffma2(x0, A, fmul2(s1, B)));
-                v[g | (1 << P)] = upk(ffma2(x1, D, fmul2(s0, Cc)));
-            }
-        }
-    }
-}
-
-// walk the (P0 < P1 < RB) combinations at compile time
-template <typename R, int NR, int RB, int K, int P0, int P1>
-struct DenseDispatch {
-    static __device__ __forceinline__ void run(int code, int sub, typename CT<R>::T2 (&v)[NR], const uint32_t *body)
-    {
-        constexpr int mycode = K == 1 ? P0 : (P0 | (P1 << 3));
-        if (code == mycode) {
-            if constexpr (K == 1) {
-                if (sub == DS_REAL) dense1_special<R, NR, P0, DS_REAL>(v, body);
-                else if (sub == DS_RX) dense1_special<R, NR, P0, DS_RX>(v, body);
-                else dense_apply<R, NR, K, P0, P1>(v, body);
-            } else {
-                dense_apply<R, NR, K, P0, P1>(v, body);
-            }
-            return;
-        }
-        if constexpr (K == 1) {
-            if constexpr (P0 + 1 < RB) DenseDispatch<R, NR, RB, K, P0 + 1, 0>::run(code, sub, v, body);
-        } else {
-            if constexpr (P1 + 1 < RB) DenseDispatch<R, NR, RB, K, P0, P1 + 1>::run(code, sub, v, body);
-            else if constexpr (P0 + 2 < RB) DenseDispatch<R, NR, RB, K, P0 + 1, P0 + 2>::run(code, sub, v, body);
-        }
-    }
-};
-
-// index of the lowest set bit; folds to a constant for unrolled loop indices
-__host__ __device__ __forceinline__ constexpr int low_bit(int k)
-{
-    int j = 0;
-    while (j < 31 && !((k >> j) & 1)) j++;
-    return j;
-}
-
-// log2 of a power of two
-__host__ __device__ __forceinline__ constexpr int log2_of(int x) { return low_bit(x); }
-
-// ------------------------------------------------------------ phase segment
-// Shared sums of a launch: cta_ph[d * SCP + s] (per chunk; SCP = 1 + RB + TB
-// slots padded to 16 bytes; slots 1 + RB + i are coefficients of thread bit
-// i) and thr_ph[(d * S + s) * T + tid] (per thread, segments d < nhoist),
-// S = 1 + RB.
-template <typename R, int RB, int T>
-__device__ __forceinline__ void dseg_apply(typename CT<R>::T2 (&v)[1 << RB], uint64_t x0, const uint32_t *body,
-                                           const typename CT<R>::W *cta_ph, const typename CT<R>::W *thr_ph,
-                                           int nhoist, int tid)
-{
-    using W = typename CT<R>::W;
-    constexpr int NR = 1 << RB;
-    constexpr int S = 1 + RB;
-    constexpr int TB = log2_of(T);
-    constexpr int SCP = (int)cta_stride(RB, TB, sizeof(W));
-    const uint4 hd = ld4(body);   // D_INDEX, D_FLAGS, D_NBASE, D_NMULTI
-    const int d = (int)hd.x;
-    const bool hoisted = d < nhoist;
-    const int nb = (int)hd.z;
-    const int nm = (int)hd.w;
-    uint32_t nlin[(RB + 3) & ~3];
-#pragma unroll
-    for (int k = 0; k < (RB + 3) / 4; k++) {
-        const uint4 q = ld4(body + D_NLIN + 4 * k);
-        nlin[4 * k] = q.x, nlin[4 * k + 1] = q.y, nlin[4 * k + 2] = q.z, nlin[4 * k + 3] = q.w;
-    }
-    const uint32_t *t = body + D_TERMS;
-    // this chunk's sums of the segment: 128-bit loads of its padded slots
-    W cv[SCP];
-#pragma unroll
-    for (int k = 0; k < SCP * (int)sizeof(W) / 16; k++) {
-        const uint4 q = ((const uint4 *)(cta_ph + d * SCP))[k];
-        if constexpr (sizeof(W) == 4) {
-            cv[4 * k] = q.x, cv[4 * k + 1] = q.y, cv[4 * k + 2] = q.z, cv[4 * k + 3] = q.w;
-        } else {
-            cv[2 * k] = (W)q.x | ((W)q.y << 32), cv[2 * k + 1] = (W)q.z | ((W)q.w << 32);
-        }
-    }
-    W base = cv[0];
-#pragma unroll
-    for (int i = 0; i < TB; i++)
-        if ((tid >> i) & 1) base += cv[1 + RB + i];
-    if (hoisted) base += thr_ph[(d * S) * T + tid];
-    for (int i = 0; i < nb; i++, t += kTermWords) {
-        uint64_t m = ld64(t);
-        if ((x0 & m) == m) base += ldwt<R>(t + 2);
-    }
-    W lin[RB];
-#pragma unroll
-    for (int j = 0; j < RB; j++) {
-        lin[j] = cv[1 + j];
-        if (hoisted) lin[j] += thr_ph[(d * S + 1 + j) * T + tid];
-        const int cnt = (int)nlin[j];
-        for (int i = 0; i < cnt; i++, t += kTermWords) {
-            uint64_t m = ld64(t);
-            if ((x0 & m) == m) lin[j] += ldwt<R>(t + 2);
-        }
-    }
-    const uint32_t *tab = t;
-    const R *ctab = (const R *)(t + 2 * NR);   // cis of the register table
-    const uint32_t *mt = t + 2 * NR + ctab_words(RB, sizeof(R));
-    // (the pivot bit of the segment header is not used here: applying
-    // cis(0) = 1 to the amplitudes it would skip is exact)
-    const bool tabnz = (hd.y & 1) != 0;
-    if (nm == 0) {
-        // the phase of register index m is base + sum_j m_j lin[j], so its
-        // factor is f[low bits of m] * g[high bits of m], both built from the
-        // 1 + RB values cis(base), cis(lin[j]): 1 + RB sin/cos and about two
-        // complex products per amplitude
-        constexpr int LB = RB / 2, HB = RB - LB;
-        typename CT<R>::T2 f[1 << LB], g[1 << HB];
-        f[0] = cis_turns(base);
-#pragma unroll
-        for (int j = 0; j < LB; j++) {
-            const auto cj = cis_turns(lin[j]);
-#pragma unroll
-            for (int m = 0; m < (1 << j); m++) f[m | (1 << j)] = cmul(f[m], cj);
-        }
-        g[0] = cone(f[0]);
-#pragma unroll
-        for (int j = 0; j < HB; j++) {
-            const auto cj = cis_turns(lin[LB + j]);
-            g[1 << j] = cj;
-#pragma unroll
-            for (int m = 1; m < (1 << j); m++) g[m | (1 << j)] = cmul(g[m], cj);
-        }
-        if (tabnz) {
-#pragma unroll
-            for (int m = 0; m < NR; m++) {
-                const int lo = m & ((1 << LB) - 1), hi = m >> LB;
-                const auto fg = hi == 0 ? f[lo] : cmul(f[lo], g[hi]);
-                v[m] = cmul(v[m], cmul(fg, ldm_a(ctab, m)));
-            }
-            return;
-        }
-#pragma unroll
-        for (int m = 0; m < NR; m++) {
-            const int lo = m & ((1 << LB) - 1), hi = m >> LB;
-            v[m] = cmul(v[m], hi == 0 ? f[lo] : cmul(f[lo], g[hi]));
-        }
-        return;
-    }
-    W ph = base;
-#pragma unroll
-    for (int k = 0; k < NR; k++) {
-        const int m = k ^ (k >> 1);
-        if (k > 0) {
-            const int j = low_bit(k);
-            if ((m >> j) & 1) ph += lin[j];
-            else ph -= lin[j];
-        }
-        W p = ph + ldwt<R>(tab + 2 * m);
-        for (int i = 0; i < nm; i++) {
-            const uint32_t *q = mt + i * kMultiWords;
-            uint64_t mm = ld64(q);
-            uint32_t rm = ldw(q + 2);
-            if ((x0 & mm) == mm && ((uint32_t)m & rm) == rm) p += ldwt<R>(q + 4);
-        }
-        v[m] = cmul(v[m], cis_turns(p));
-    }
-}
-
-// Per-thread sums of the thread table (once per launch; each thread owns its
-// column, so no synchronisation is needed before its own use).
-template <typename R, int T>
-__device__ __forceinline__ void thread_sums(const uint32_t *prog, typename CT<R>::W *thr_ph, int nslots, int tid)
-{
-    using W = typename CT<R>::W;
-    for (int i = 0; i < nslots; i++) thr_ph[i * T + tid] = 0;
-    const uint32_t *tt = prog + ldw(prog + H_THR_OFF);
-    const int nt = (int)ldw(prog + H_NTHR);
-    for (int i = 0; i < nt; i++, tt += kThrWords) {
-        const uint32_t tm = ldw(tt + 1);
-        if (((uint32_t)tid & tm) == tm) thr_ph[ldw(tt) * T + tid] += ldwt<R>(tt + 2);
-    }
-}
-
-__device__ __forceinline__ void add_atomic(uint32_t *p, uint32_t v) { atomicAdd((unsigned int *)p, (unsigned int)v); }
-__device__ __forceinline__ void add_atomic(uint64_t *p, uint64_t v)
-{
-    atomicAdd((unsigned long long *)p, (unsigned long long)v);
-}
-
-// Per-chunk sums of the CTA table, in one of kCtaBuffers buffers of
-// `nslots` slots: cta_zero clears a buffer, cta_accum adds the entries whose
-// mask chunk base `base` meets (block-wide; integer adds are exact, so the
-// atomics' order does not matter).  The caller puts a barrier between the
-// two and another before the sums are read.
-template <typename R, int T>
-__device__ __forceinline__ void cta_zero(typename CT<R>::W *buf, int nslots, int tid)
-{
-    for (int i = tid; i < nslots; i += T) buf[i] = 0;
-}
-template <typename R, int T>
-__device__ __forceinline__ void cta_accum(const uint32_t *prog, typename CT<R>::W *cta_ph, uint64_t base, int tid)
-{
-    const uint32_t *ct = prog + ldw(prog + H_CTA_OFF);
-    const int nc = (int)ldw(prog + H_NCTA);
-    for (int i = tid; i < nc; i += T) {
-        const uint32_t *e = ct + i * kCtaWords;
-        const uint64_t m = ld64(e + 2);
-        if ((base & m) == m) add_atomic(&cta_ph[ldw(e)], ldwt<R>(e + 4));
-    }
-}
-
-// Sweep input from a fused merge-booster product (TensorSrc in kernels.h):
-// amplitude x = hi[x >> n_lo] * lo[x & (2^n_lo - 1)], with the arithmetic of
-// k_tensor.  hi == nullptr: the sweep reads the state itself.
-template <typename T2> struct TSrc {
-    const T2 *hi;
-    const T2 *lo;
-    int n_lo;
-};
-template <typename T2> __device__ __forceinline__ T2 tensor_amp(const TSrc<T2> &s, uint64_t x)
-{
-    const T2 h = __ldg(&s.hi[x >> s.n_lo]);
-    const T2 l = __ldg(&s.lo[x & ((1ull << s.n_lo) - 1)]);
-    T2 w;
-    w.x = h.x * l.x - h.y * l.y;
-    w.y = h.x * l.y + h.y * l.x;
-    return w;
-}
-
-// ------------------------------------------------------------ K4 chunk sweep
+// ------------------------------------------------------------ K4 chunk sweep (interpreter)
 template <typename R, int C, int RB>
 __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(typename CT<R>::G2 *__restrict__ a,
                                                          const uint32_t *__restrict__ gprog, int n,
                                                          TSrc<typename CT<R>::G2> src)
 {
-    using T2 = typename CT<R>::T2;
-    using G2 = typename CT<R>::G2;
-    using W = typename CT<R>::W;
-    constexpr int TB = C - RB;
-    constexpr int T = 1 << TB;
-    constexpr int NR = 1 << RB;
-    constexpr int SW = CT<R>::SWZ;
-    constexpr int S = 1 + RB;
-    constexpr int SCP = (int)cta_stride(RB, TB, sizeof(typename CT<R>::W));
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T2 *sv = (T2 *)smraw;   // the chunk: interleaved (re, im), swizzled
-    uint32_t *prog = (uint32_t *)(sv + (1 << C));
-    const int tid = threadIdx.x;
-    stage_program<T>(gprog, prog, tid);
-    __syncthreads();
-    const int nd = (int)ldw(prog + H_NDSEG);
-    const int nhoist = (int)ldw(prog + H_NHOIST);
-    W *cta_buf = (W *)(prog + ((ldw(prog + H_WORDS) + 3) & ~3u));
-    const int cbw = (int)(cta_buffer_bytes(nd, RB, TB, sizeof(W)) / sizeof(W));   // words of one buffer
-    W *thr_ph = cta_buf + kCtaBuffers * cbw;
-    __shared__ uint64_t s_git[NR / 2];    // global offset of load iteration `it`
-    __shared__ uint32_t s_sit[NR / 2];    // swizzled smem position of `it` on the store
-    __shared__ uint64_t s_dep[768];       // chunk number byte k -> its free-qubit bits
-
-    int qin[C];
-#pragma unroll
-    for (int i = 0; i < C; i++) qin[i] = (int)ldw(prog + H_QIN + i);
-    int sperm[C];
-#pragma unroll
-    for (int i = 0; i < C; i++) sperm[i] = (int)ldw(prog + H_SPERM + i);
-    const uint64_t freem = ld64(prog + H_FREE_LO);
-    const int nst = (int)ldw(prog + H_NSTAGE);
-
-    // element pair e = it * T + tid covers chunk indices y = 2e, 2e + 1:
-    // y bit 0 = pair member, bits 1..TB = tid, bits TB+1.. = it
-    uint64_t g_tid = 0;
-    uint32_t st_tid = 0;   // store: chunk position of output index 2*tid
-#pragma unroll
-    for (int i = 0; i < TB; i++)
-        if ((tid >> i) & 1) { g_tid |= 1ull << qin[i + 1]; st_tid |= 1u << sperm[i + 1]; }
-    const uint32_t st_one = 1u << sperm[0];
-    if (tid < NR / 2) {
-        uint64_t g = 0;
-        uint32_t sp = 0;
-#pragma unroll
-        for (int b = 0; b < RB - 1; b++)
-            if ((tid >> b) & 1) { g |= 1ull << qin[TB + 1 + b]; sp |= 1u << sperm[TB + 1 + b]; }
-        s_git[tid] = g;
-        s_sit[tid] = swz<SW, C>(sp);
-    }
-    thread_sums<R, T>(prog, thr_ph, nhoist * S, tid);
-    // deposit tables: entry 256 k + i = the chunk-number bits i << 8k spread
-    // over the free qubits (n - C <= 22 < 24 bits)
-    for (int e = tid; e < 768; e += T) {
-        const int k = e >> 8;
-        uint64_t b = 0, fm = freem, cv = (uint64_t)(e & 255) << (8 * k);
-        while (fm) {
-            uint64_t low = fm & (~fm + 1);
-            if (cv & 1) b |= low;
-            cv >>= 1;
-            fm ^= low;
-        }
-        s_dep[e] = b;
-    }
-    // this thread's part of every stage's layout (the same for all chunks)
-    uint64_t *s_x0 = (uint64_t *)((unsigned char *)thr_ph + (((size_t)nhoist * S * T * sizeof(W) + 15) & ~(size_t)15));
-    uint32_t *s_pb = (uint32_t *)(s_x0 + (size_t)nst * T);
-    for (int s = 0; s < nst; s++) {
-        const uint32_t *sp = prog + ldw(prog + H_STAGE_OFF + s);
-        uint32_t ybase = 0;
-        uint64_t x0t = 0;
-        for (int i = 0; i < TB; i++) {
-            if ((tid >> i) & 1) {
-                ybase |= 1u << ldw(sp + S_THR + i);
-                x0t |= 1ull << ldw(sp + S_GTHR + i);
-            }
-        }
-        s_x0[s * T + tid] = x0t;
-        s_pb[s * T + tid] = swz<SW, C>(ybase);
-    }
-    cta_zero<R, T>(cta_buf, 2 * cbw, tid);
-    __syncthreads();
-    const uint32_t pst_tid = swz<SW, C>(st_tid);
-    const uint32_t pst_one = swz<SW, C>(st_one);
-    const uint32_t pld_tid = swz<SW, C>((uint32_t)tid << 1);
-
-    const int64_t nchunks = (int64_t)1 << (n - C);
-    // chunk base: spread the chunk number over the free (non-chunk) qubits
-    // (deposit is linear over disjoint input bytes: three 256-entry tables)
-    auto chunk_base = [&](int64_t chn) {
-        const uint64_t c = (uint64_t)chn;
-        return s_dep[c & 255] | s_dep[256 + ((c >> 8) & 255)] | s_dep[512 + ((c >> 16) & 255)];
-    };
-    if (blockIdx.x < nchunks) cta_accum<R, T>(prog, cta_buf, chunk_base(blockIdx.x), tid);
-    __syncthreads();
-    // coalesced loads of one chunk's amplitude pairs into registers
-    auto load_regs = [&](T2 (&dst)[NR], uint64_t b) {
-        if (src.hi) {
-#pragma unroll
-            for (int it = 0; it < NR / 2; it++) {
-                const uint64_t g = b | g_tid | s_git[it];
-                dst[2 * it] = to_reg(tensor_amp(src, g));
-                dst[2 * it + 1] = to_reg(tensor_amp(src, g + 1));
-            }
-            return;
-        }
-#pragma unroll
-        for (int it = 0; it < NR / 2; it++) {
-            const uint64_t g = b | g_tid | s_git[it];
-            if constexpr (sizeof(R) == 4) {
-                float4 q = __ldcs((const float4 *)(a + g));
-                dst[2 * it] = make_float2(q.x, q.y);
-                dst[2 * it + 1] = make_float2(q.z, q.w);
-            } else {
-                dst[2 * it] = to_reg(__ldcs(a + g));
-                dst[2 * it + 1] = to_reg(__ldcs(a + g + 1));
-            }
-        }
-    };
-    // no register double buffer: without one the kernel fits in 80 registers
-    // and three CTAs per SM, whose loads overlap each other's stages
-    int64_t ch = blockIdx.x;
-    uint64_t base = chunk_base(ch);
-    int cb = 0;   // CTA-table buffer of this chunk
-    for (; ch < nchunks; ch += gridDim.x) {
-        const W *cta_ph = cta_buf + cb * cbw;
-        W *cta_next = cta_buf + (cb == 2 ? 0 : cb + 1) * cbw;
-        T2 pf[NR];
-        load_regs(pf, base);
-        // ---- the chunk -> shared
-#pragma unroll
-        for (int it = 0; it < NR / 2; it++) {
-            const uint32_t p = pld_tid ^ swz<SW, C>((uint32_t)it << (TB + 1));
-            sv[p] = pf[2 * it];
-            sv[p ^ 1] = pf[2 * it + 1];
-        }
-        // buffer (cb + 2) mod 3: last read by the previous chunk
-        cta_zero<R, T>(cta_buf + (cb == 0 ? 2 : cb - 1) * cbw, nd * SCP, tid);
-        __syncthreads();
-        const int64_t nch = ch + gridDim.x;
-        const uint64_t nbase = nch < nchunks ? chunk_base(nch) : 0;
-        // the next chunk's sums (its buffer was cleared during the previous chunk)
-        if (nch < nchunks) cta_accum<R, T>(prog, cta_next, nbase, tid);
-        // ---- register stages
-        for (int s = 0; s < nst; s++) {
-            const uint32_t *sp = prog + ldw(prog + H_STAGE_OFF + s);
-            uint32_t pv[(RB + 3) & ~3];
-#pragma unroll
-            for (int k = 0; k < (RB + 3) / 4; k++) {
-                const uint4 q = ld4(sp + S_PV + 4 * k);
-                pv[4 * k] = q.x, pv[4 * k + 1] = q.y, pv[4 * k + 2] = q.z, pv[4 * k + 3] = q.w;
-            }
-            const uint64_t x0 = base | s_x0[s * T + tid];
-            const uint32_t pb = s_pb[s * T + tid];
-            T2 v[NR];
-#pragma unroll
-            for (int m = 0; m < NR; m++) {
-                uint32_t pm = pb;
-#pragma unroll
-                for (int j = 0; j < RB; j++)
-                    if ((m >> j) & 1) pm ^= pv[j];
-                v[m] = sv[pm];
-            }
-            const int nops = (int)ldw(sp + S_NOPS);
-            const uint32_t *op = sp + S_SIZE;
-            for (int k = 0; k < nops; k++) {
-                const uint32_t hdr = ldw(op + O_HDR);
-                const int type = hdr & 0xff;
-                if (type == OP_DENSE) {
-                    const int kq = (hdr >> 8) & 0xf;
-                    const int sub = (hdr >> 12) & 0xf;
-                    const int code = (int)(hdr >> 16);
-                    if (kq == 1) DenseDispatch<R, NR, RB, 1, 0, 0>::run(code, sub, v, op + O_BODY);
-                    else DenseDispatch<R, NR, RB, 2, 0, 1>::run(code, sub, v, op + O_BODY);
-                } else {
-                    dseg_apply<R, RB, T>(v, x0, op + O_BODY, cta_ph, thr_ph, nhoist, tid);
-                }
-                op += ldw(op + O_WORDS);
-            }
-            // make the compiler rebuild the 2^RB addresses here instead of
-            // keeping them live across the ops (register pressure)
-            uint32_t pbw = pb;
-            asm volatile("" : "+r"(pbw));
-#pragma unroll
-            for (int j = 0; j < RB; j++) asm volatile("" : "+r"(pv[j]));
-#pragma unroll
-            for (int m = 0; m < NR; m++) {
-                uint32_t pm = pbw;
-#pragma unroll
-                for (int j = 0; j < RB; j++)
-                    if ((m >> j) & 1) pm ^= pv[j];
-                sv[pm] = v[m];
-            }
-            __syncthreads();
-        }
-        // ---- store: shared -> HBM, output bit i' takes chunk bit sperm[i']
-#pragma unroll
-        for (int it = 0; it < NR / 2; it++) {
-            const uint64_t g = base | g_tid | s_git[it];
-            const uint32_t p0 = pst_tid ^ s_sit[it];
-            const uint32_t p1 = p0 ^ pst_one;
-            if constexpr (sizeof(R) == 4) {
-                const T2 u0 = sv[p0], u1 = sv[p1];
-                float4 q = make_float4(u0.x, u0.y, u1.x, u1.y);
-                __stcs((float4 *)(a + g), q);
-            } else {
-                __stcs(a + g, to_glob(sv[p0]));
-                __stcs(a + g + 1, to_glob(sv[p1]));
-            }
-        }
-        __syncthreads();
-        base = nbase;
-        cb = cb == 2 ? 0 : cb + 1;
-    }
+    chunk_sweep<R, C, RB, InterpOps>(a, gprog, n, src);
 }
 
 // ------------------------------------------------------------ K3 diagonal sweep

@@ -5,6 +5,9 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 namespace svs {
@@ -71,6 +74,20 @@ cudaError_t launch_diag_sweep(void *a, int n, bool is_f64, const uint32_t *prog,
                               cudaStream_t st);
 cudaError_t launch_chunk(void *a, int n, bool is_f64, int C, int RB, const uint32_t *prog, size_t smem,
                          TensorSrc src, cudaStream_t st);
+
+// Chunk sweeps specialised to one program (jit.cpp; complex64, C = 12,
+// RB = 4): jit_prepare compiles (NVRTC) and loads the kernels of the given
+// host programs that are not cached yet, in parallel; launch_chunk_jit runs
+// the cached kernel of host program `w` (device copy `prog`), with the same
+// arguments and results as launch_chunk.
+bool jit_supported(bool is_f64, int C, int RB);
+bool jit_prepare(const std::vector<const std::vector<uint32_t> *> &progs, std::string &err);
+cudaError_t launch_chunk_jit(void *a, int n, const std::vector<uint32_t> &w, const uint32_t *prog, size_t smem,
+                             TensorSrc src, cudaStream_t st);
+size_t jit_cache_size(double *compile_ms);   // kernels cached, total compile wall time
+// the generated source and its NVRTC compile (no device needed)
+bool jit_source(const std::vector<uint32_t> &w, std::string &src, std::string &err);
+bool jit_compile(const std::string &src, std::vector<char> &cubin, std::string &err);
 
 // Phase polynomial on small registers: one thread per amplitude sums the
 // nt terms (device array of {mask, w} pairs, uint64 turns).

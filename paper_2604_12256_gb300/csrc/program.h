@@ -15,7 +15,17 @@
 // the SWAP relabelling of Section 2.3 for free.
 #pragma once
 
+#if defined(__CUDACC_RTC__)
+// run-time compilation of specialised sweep kernels: no host headers
+typedef int int32_t;
+typedef unsigned int uint32_t;
+typedef unsigned long long uint64_t;
+typedef long long int64_t;
+typedef decltype(sizeof(0)) size_t;
+#else
+#include <cstddef>
 #include <cstdint>
+#endif
 
 #if defined(__CUDACC__)
 #define PROG_HD __host__ __device__

@@ -20,8 +20,8 @@ LIB_PATH = os.path.join(_PKG, "libsvsim.so")
 
 SIM_C64, SIM_C128 = 0, 1
 SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_ETIMEOUT, SIM_EBUSY, SIM_EUNSUPPORTED = range(7)
-SIM_F_DIAG, SIM_F_BOOST, SIM_F_BLOCK, SIM_F_FUSE, SIM_F_TC, SIM_F_REMAP = 1, 2, 4, 8, 16, 32
-SIM_F_ALL = 0x3F
+SIM_F_DIAG, SIM_F_BOOST, SIM_F_BLOCK, SIM_F_FUSE, SIM_F_TC, SIM_F_REMAP, SIM_F_JIT = 1, 2, 4, 8, 16, 32, 64
+SIM_F_ALL = 0x7F
 SIM_DENSE_SPLIT_TF32, SIM_DENSE_FP32, SIM_DENSE_FP64 = 0, 1, 2
 
 KIND = {"h": 0, "x": 1, "y": 2, "z": 3, "s": 4, "t": 5, "rx": 6, "ry": 7, "rz": 8, "p": 9,
@@ -110,6 +110,9 @@ _SIGS = [
     ("sim_plan_json", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _P, ctypes.c_size_t,
                                      ctypes.POINTER(sim_options), ctypes.c_char_p, ctypes.c_size_t,
                                      ctypes.POINTER(ctypes.c_size_t)]),
+    ("sim_jit_info", ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]),
+    ("sim_jit_check", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _P, ctypes.c_size_t,
+                                     ctypes.POINTER(sim_options), ctypes.POINTER(ctypes.c_int)]),
 ]
 
 
@@ -185,6 +188,27 @@ def plan_json(n: int, gates, dtype: int = SIM_C64, basis: Optional[int] = 0,
     buf = ctypes.create_string_buffer(need.value)
     _check(lib.sim_plan_json(n, dtype, b, ga.ptr, ga.n, optp, buf, need.value, ctypes.byref(need)))
     return json.loads(buf.value.decode())
+
+
+def jit_check(n: int, gates, dtype: int = SIM_C64, basis: Optional[int] = 0,
+              opt: Optional[sim_options] = None) -> int:
+    """Generate and compile (no GPU needed) the specialised kernels that
+    SIM_F_JIT would run for this circuit; returns how many there are."""
+    lib = load()
+    ga = gates if isinstance(gates, GateArray) else GateArray(gates)
+    b = (1 << 64) - 1 if basis is None else basis
+    cnt = ctypes.c_int(0)
+    optp = ctypes.byref(opt) if opt is not None else None
+    _check(lib.sim_jit_check(n, dtype, b, ga.ptr, ga.n, optp, ctypes.byref(cnt)))
+    return cnt.value
+
+
+def jit_info() -> dict:
+    """Specialised kernels cached in this process and their total compile time."""
+    lib = load()
+    n, ms = ctypes.c_uint64(0), ctypes.c_double(0)
+    _check(lib.sim_jit_info(ctypes.byref(n), ctypes.byref(ms)))
+    return {"programs": n.value, "compile_ms": ms.value}
 
 
 class Sim:
