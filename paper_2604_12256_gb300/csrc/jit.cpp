@@ -21,6 +21,7 @@
 
 #include <chrono>
 #include <cinttypes>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -96,6 +97,179 @@ std::string flit(uint32_t bits)
 
 constexpr const char *kKernelName = "svs_chunk_jit";
 
+// ---- phase segments
+// Where each sum of a segment comes from, read off the program's tables: a
+// slot is "dynamic" when an entry depends on the chunk (a CTA entry with a
+// mask), on the thread (a thread-table entry) or on the amplitude block (a
+// term in the body); otherwise it is the constant sum of its always-met CTA
+// entries, zero when there are none.
+struct SlotSrc {
+    bool cta_dyn = false;   // CTA entries with a mask: read the per-chunk sum
+    uint32_t cst = 0;       // sum of the always-met CTA entries
+    bool thr = false;       // thread-table entries (hoisted segment)
+    bool dynamic() const { return cta_dyn || thr; }
+};
+
+// A complex factor while the code is generated: exactly one, a constant
+// (folded on the host in long double) or a run-time value in a variable.
+struct Fac {
+    enum Kind { ONE, CONST, VAR } kind = ONE;
+    long double re = 1, im = 0;
+    std::string var;
+};
+
+std::string flit_f(long double v)
+{
+    const float f = (float)v;
+    uint32_t b;
+    std::memcpy(&b, &f, 4);
+    return flit(b);
+}
+
+std::string fac_expr(const Fac &f)
+{
+    if (f.kind == Fac::VAR) return f.var;
+    return "make_float2(" + flit_f(f.re) + ", " + flit_f(f.im) + ")";
+}
+
+Fac cis_const(uint32_t w)
+{
+    const long double th = 6.283185307179586476925286766559L * (long double)w * 0x1p-32L;
+    Fac f;
+    f.kind = w == 0 ? Fac::ONE : Fac::CONST;
+    f.re = cosl(th);
+    f.im = sinl(th);
+    return f;
+}
+
+// a * b, emitting a run-time product into `o` (variable `name`) when needed
+Fac fac_mul(std::ostringstream &o, const Fac &a, const Fac &b, const std::string &name)
+{
+    if (a.kind == Fac::ONE) return b;
+    if (b.kind == Fac::ONE) return a;
+    Fac r;
+    if (a.kind == Fac::CONST && b.kind == Fac::CONST) {
+        r.kind = Fac::CONST;
+        r.re = a.re * b.re - a.im * b.im;
+        r.im = a.re * b.im + a.im * b.re;
+        return r;
+    }
+    r.kind = Fac::VAR;
+    r.var = name;
+    o << "                const float2 " << name << " = cmul(" << fac_expr(a) << ", " << fac_expr(b) << ");\n";
+    return r;
+}
+
+// Straight-line code of one factored phase segment (no terms on several
+// register bits and other bits) of a complex64, RB = 4, T = 256 program:
+// the sums it needs, one sin/cos per run-time factor, the product table over
+// the register bits that carry a phase, and one complex product per
+// amplitude whose factor is not exactly one.
+void gen_segment(std::ostringstream &o, const std::vector<uint32_t> &w, size_t body, const std::vector<SlotSrc> &slots,
+                 int RB, int TB, int T, int SCP)
+{
+    using namespace prog;
+    const uint32_t *b = &w[body];
+    const int d = (int)b[D_INDEX], nb = (int)b[D_NBASE];
+    const int NR = 1 << RB, S = 1 + RB;
+    const bool tabnz = (b[D_FLAGS] & 1) != 0;
+    o << "            {   // phase segment " << d << "\n";
+    // which 128-bit words of the segment's CTA slots are read
+    std::vector<char> need_q((size_t)SCP / 4, 0);
+    auto slot_dyn = [&](int k) { return slots[(size_t)d * SCP + k].cta_dyn; };
+    for (int k = 0; k < 1 + RB + TB; k++)
+        if (slot_dyn(k)) need_q[k / 4] = 1;
+    for (int q = 0; q < SCP / 4; q++)
+        if (need_q[q])
+            o << "                const uint4 cq" << q << " = ((const uint4 *)(cta_ph + " << d * SCP << "))[" << q
+              << "];\n";
+    const char *comp = "xyzw";
+    auto cta_val = [&](int k) { return "cq" + std::to_string(k / 4) + "." + comp[k % 4]; };
+    const uint32_t *t = b + D_TERMS;
+    // sum of slot s (0 = base, 1 + j = register bit j): body terms follow
+    // the interpreter's order (base terms, then each register bit's)
+    auto emit_sum = [&](int s, int nterm, const std::string &name) -> bool {
+        const SlotSrc &ss = slots[(size_t)d * SCP + s];
+        const bool thr = s < S && ss.thr;
+        if (!ss.cta_dyn && !thr && nterm == 0) return false;   // constant or zero: folded
+        o << "                uint32_t " << name << " = " << (ss.cta_dyn ? cta_val(s) : std::to_string(ss.cst) + "u")
+          << ";\n";
+        if (s == 0)
+            for (int i = 0; i < TB; i++)
+                if (slot_dyn(1 + RB + i))
+                    o << "                if (tid & " << (1 << i) << ") " << name << " += " << cta_val(1 + RB + i) << ";\n";
+        if (thr) o << "                " << name << " += thr_ph[" << (d * S + s) * T << " + tid];\n";
+        for (int i = 0; i < nterm; i++, t += kTermWords) {
+            const uint64_t m = (uint64_t)t[0] | ((uint64_t)t[1] << 32);
+            o << "                if ((x0 & 0x" << std::hex << m << "ull) == 0x" << m << std::dec << "ull) " << name
+              << " += " << t[2] << "u;\n";
+        }
+        return true;
+    };
+    Fac fb;
+    // the base: CTA thread-bit coefficients make it run-time too
+    {
+        bool coef = false;
+        for (int i = 0; i < TB; i++) coef = coef || slot_dyn(1 + RB + i);
+        const SlotSrc &s0 = slots[(size_t)d * SCP];
+        if (emit_sum(0, nb, "pb") || coef) {
+            if (!(s0.cta_dyn || s0.thr || nb)) {
+                // only thread-bit coefficients: start from the constant
+                o << "                uint32_t pb = " << s0.cst << "u;\n";
+                for (int i = 0; i < TB; i++)
+                    if (slot_dyn(1 + RB + i))
+                        o << "                if (tid & " << (1 << i) << ") pb += " << cta_val(1 + RB + i) << ";\n";
+            }
+            o << "                const float2 e0 = cis_turns(pb);\n";
+            fb.kind = Fac::VAR;
+            fb.var = "e0";
+        } else {
+            fb = cis_const(s0.cst);
+        }
+    }
+    std::vector<Fac> fl(RB);
+    for (int j = 0; j < RB; j++) {
+        const std::string nm = "pl" + std::to_string(j);
+        if (emit_sum(1 + j, (int)b[D_NLIN + j], nm)) {
+            o << "                const float2 e" << 1 + j << " = cis_turns(" << nm << ");\n";
+            fl[j].kind = Fac::VAR;
+            fl[j].var = "e" + std::to_string(1 + j);
+        } else {
+            fl[j] = cis_const(slots[(size_t)d * SCP + 1 + j].cst);
+        }
+    }
+    // product table over the register bits with a phase: tb[idx], idx the
+    // bits of m at those positions
+    std::vector<int> K;
+    for (int j = 0; j < RB; j++)
+        if (fl[j].kind != Fac::ONE) K.push_back(j);
+    std::vector<Fac> tb(1);
+    tb[0] = fb;
+    for (size_t k = 0; k < K.size(); k++) {
+        const size_t h = tb.size();
+        tb.resize(2 * h);
+        for (size_t i = 0; i < h; i++)
+            tb[h + i] = fac_mul(o, tb[i], fl[K[k]], "f" + std::to_string(h + i));
+    }
+    const uint32_t *tab = t;   // register-only phases, then their complex factors
+    const float *ctab = (const float *)(t + 2 * NR);
+    for (int m = 0; m < NR; m++) {
+        size_t idx = 0;
+        for (size_t k = 0; k < K.size(); k++)
+            if ((m >> K[k]) & 1) idx |= (size_t)1 << k;
+        Fac f = tb[idx];
+        if (tabnz && tab[2 * m] != 0) {
+            Fac c;
+            c.kind = Fac::CONST;
+            c.re = ctab[2 * m];   // the program's float factor, as the interpreter multiplies
+            c.im = ctab[2 * m + 1];
+            f = fac_mul(o, f, c, "g" + std::to_string(m));
+        }
+        if (f.kind != Fac::ONE) o << "                v[" << m << "] = cmul(v[" << m << "], " << fac_expr(f) << ");\n";
+    }
+    o << "            }\n";
+}
+
 }  // namespace
 
 bool jit_supported(bool f64, int C, int RB) { return !f64 && C == 12 && RB == 4; }
@@ -110,7 +284,21 @@ bool jit_source(const std::vector<uint32_t> &w, std::string &src, std::string &e
         err = "specialised kernels: complex64 chunk programs with C = 12, RB = 4 only";
         return false;
     }
-    const int T = 1 << (C - RB), NR = 1 << RB;
+    const int T = 1 << (C - RB), NR = 1 << RB, TB = C - RB, S = 1 + RB;
+    const int SCP = (int)cta_stride(RB, TB, 4);
+    // where every phase sum comes from (per segment and slot)
+    const int nd = (int)w[H_NDSEG];
+    std::vector<SlotSrc> slots((size_t)nd * SCP);
+    for (uint32_t i = 0; i < w[H_NCTA]; i++) {
+        const uint32_t *e = &w[w[H_CTA_OFF] + (size_t)i * kCtaWords];
+        SlotSrc &ss = slots[e[0]];
+        if (e[2] | e[3]) ss.cta_dyn = true;
+        else ss.cst += e[4];
+    }
+    for (uint32_t i = 0; i < w[H_NTHR]; i++) {
+        const uint32_t *e = &w[w[H_THR_OFF] + (size_t)i * kThrWords];
+        slots[(size_t)(e[0] / S) * SCP + e[0] % S].thr = true;
+    }
     std::ostringstream o;
     o << "#include \"chunk_dev.cuh\"\nnamespace svs {\nstruct JOps {\n";
     o << "    static constexpr int kStages = " << ns << ";\n";
@@ -139,7 +327,10 @@ bool jit_source(const std::vector<uint32_t> &w, std::string &src, std::string &e
             const size_t body = op + O_BODY;
             if ((hdr & 0xff) == OP_DENSE) {
                 const int kq = (hdr >> 8) & 0xf, sub = (hdr >> 12) & 0xf, code = (int)(hdr >> 16);
-                if (kq == 1 && sub != DS_GENERAL) {
+                if (kq == 1 && sub == DS_REAL && w[body] == 0x3f800000u && w[body + 2] == 0 && w[body + 4] == 0 &&
+                    w[body + 6] == 0x3f800000u) {
+                    // exactly the identity in complex64 (e.g. H H): nothing to do
+                } else if (kq == 1 && sub != DS_GENERAL) {
                     const bool re = sub == DS_REAL;
                     o << "            dense1_special_f<" << NR << ", " << code << ", " << sub << ">(v, " << flit(w[body])
                       << ", " << flit(w[body + (re ? 2 : 3)]) << ", " << flit(w[body + (re ? 4 : 5)]) << ", "
@@ -152,13 +343,11 @@ bool jit_source(const std::vector<uint32_t> &w, std::string &src, std::string &e
                     o << "            dense_apply<R, " << NR << ", 2, " << (code & 7) << ", " << ((code >> 3) & 7)
                       << ">(v, prog + " << body << ");\n";
                 }
+            } else if (w[body + D_NMULTI]) {
+                // terms on several register bits and other bits: the general path
+                o << "            dseg_apply<R, RB, T, 3>(v, x0, prog + " << body << ", cta_ph, thr_ph, nhoist, tid);\n";
             } else {
-                // the segment's path: factored (without / with the register
-                // table) or with terms on several register bits
-                const uint32_t *b = &w[body];
-                const int mode = b[D_NMULTI] ? 3 : (b[D_FLAGS] & 1) ? 2 : 1;
-                o << "            dseg_apply<R, RB, T, " << mode << ">(v, x0, prog + " << body
-                  << ", cta_ph, thr_ph, nhoist, tid);\n";
+                gen_segment(o, w, body, slots, RB, TB, T, SCP);
             }
             op += len;
         }
