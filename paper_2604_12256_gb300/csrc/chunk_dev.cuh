@@ -706,6 +706,46 @@ __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, 
             }
         }
     };
+    // a direct stage (program.h: specialised kernels only) moves its own
+    // amplitudes between HBM and registers: register index m of the thread
+    // whose stage-s thread bits are at xb is amplitude xb | Ops::roff(s, m)
+    auto load_direct = [&](T2 (&dst)[NR], uint64_t xb, int s) {
+#pragma unroll
+        for (int m = 0; m < NR; m++) {
+            const uint64_t g = xb | Ops::roff(s, m);
+            if (src.hi) {
+                dst[m] = to_reg(tensor_amp(src, g));
+            } else if constexpr (sizeof(R) == 4) {
+                if (Ops::paired(s)) {   // m, m + 1 adjacent: one 16-byte load
+                    if (m & 1) continue;
+                    const float4 q = __ldcs((const float4 *)(a + g));
+                    dst[m] = make_float2(q.x, q.y);
+                    dst[m + 1] = make_float2(q.z, q.w);
+                } else {
+                    dst[m] = __ldcs(a + g);
+                }
+            } else {
+                dst[m] = to_reg(__ldcs(a + g));
+            }
+        }
+    };
+    auto store_direct = [&](const T2 (&val)[NR], uint64_t xb, int s) {
+#pragma unroll
+        for (int m = 0; m < NR; m++) {
+            const uint64_t g = xb | Ops::roff(s, m);
+            if constexpr (sizeof(R) == 4) {
+                if (Ops::paired(s)) {
+                    if (m & 1) continue;
+                    __stcs((float4 *)(a + g), make_float4(val[m].x, val[m].y, val[m + 1].x, val[m + 1].y));
+                } else {
+                    __stcs(a + g, val[m]);
+                }
+            } else {
+                __stcs(a + g, to_glob(val[m]));
+            }
+        }
+    };
+    constexpr bool kDF = Ops::kDirectFirst, kDL = Ops::kDirectLast;
     // no register double buffer: without one the kernel fits in 80 registers
     // and three CTAs per SM, whose loads overlap each other's stages
     int64_t ch = blockIdx.x;
@@ -714,18 +754,26 @@ __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, 
     for (; ch < nchunks; ch += gridDim.x) {
         const W *cta_ph = cta_buf + cb * cbw;
         W *cta_next = cta_buf + (cb == 2 ? 0 : cb + 1) * cbw;
-        T2 pf[NR];
-        load_regs(pf, base);
-        // ---- the chunk -> shared
+        T2 v0[NR];   // stage 0's amplitudes when it loads them itself
+        if constexpr (kDF) {
+            load_direct(v0, base | s_x0[tid], 0);
+        } else {
+            T2 pf[NR];
+            load_regs(pf, base);
+            // ---- the chunk -> shared
 #pragma unroll
-        for (int it = 0; it < NR / 2; it++) {
-            const uint32_t p = pld_tid ^ swz<SW, C>((uint32_t)it << (TB + 1));
-            sv[p] = pf[2 * it];
-            sv[p ^ 1] = pf[2 * it + 1];
+            for (int it = 0; it < NR / 2; it++) {
+                const uint32_t p = pld_tid ^ swz<SW, C>((uint32_t)it << (TB + 1));
+                sv[p] = pf[2 * it];
+                sv[p ^ 1] = pf[2 * it + 1];
+            }
         }
         // buffer (cb + 2) mod 3: last read by the previous chunk
         cta_zero<R, T>(cta_buf + (cb == 0 ? 2 : cb - 1) * cbw, nd * SCP, tid);
-        __syncthreads();
+        // (the chunk in shared memory; with a direct first stage nothing
+        // before the first stage's own store needs a barrier: the CTA
+        // buffers it reads were completed before the last chunk's barriers)
+        if constexpr (!kDF) __syncthreads();
         const int64_t nch = ch + gridDim.x;
         const uint64_t nbase = nch < nchunks ? chunk_base(nch) : 0;
         // the next chunk's sums (its buffer was cleared during the previous chunk)
@@ -738,15 +786,24 @@ __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, 
             const uint64_t x0 = base | s_x0[s * T + tid];
             const uint32_t pb = s_pb[s * T + tid];
             T2 v[NR];
+            if (kDF && s == 0) {
 #pragma unroll
-            for (int m = 0; m < NR; m++) {
-                uint32_t pm = pb;
+                for (int m = 0; m < NR; m++) v[m] = v0[m];
+            } else {
 #pragma unroll
-                for (int j = 0; j < RB; j++)
-                    if ((m >> j) & 1) pm ^= pv[j];
-                v[m] = sv[pm];
+                for (int m = 0; m < NR; m++) {
+                    uint32_t pm = pb;
+#pragma unroll
+                    for (int j = 0; j < RB; j++)
+                        if ((m >> j) & 1) pm ^= pv[j];
+                    v[m] = sv[pm];
+                }
             }
             Ops::template run<R, RB, T>(s, v, x0, prog, sp, cta_ph, thr_ph, nhoist, tid);
+            if (kDL && s == Ops::kStages - 1) {
+                store_direct(v, x0, s);
+                return;
+            }
             // make the compiler rebuild the 2^RB addresses here instead of
             // keeping them live across the ops (register pressure); the
             // specialised kernels' offsets are constants
@@ -774,7 +831,7 @@ __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, 
         }
         // ---- store: shared -> HBM, output bit i' takes chunk bit sperm[i']
 #pragma unroll
-        for (int it = 0; it < NR / 2; it++) {
+        for (int it = 0; it < (kDL ? 0 : NR / 2); it++) {
             const uint64_t g = base | g_tid | s_git[it];
             const uint32_t p0 = pst_tid ^ s_sit[it];
             const uint32_t p1 = p0 ^ pst_one;
@@ -797,6 +854,9 @@ __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, 
 // The interpreter: the ops of stage s, as the program in shared memory lists them.
 struct InterpOps {
     static constexpr int kStages = 0;
+    static constexpr bool kDirectFirst = false, kDirectLast = false;
+    static __device__ __forceinline__ uint64_t roff(int, int) { return 0; }
+    static __device__ __forceinline__ bool paired(int) { return false; }
     static __device__ __forceinline__ uint32_t stage_off(const uint32_t *prog, int s)
     {
         return ldw(prog + H_STAGE_OFF + s);

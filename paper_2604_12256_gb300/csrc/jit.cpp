@@ -302,6 +302,26 @@ bool jit_source(const std::vector<uint32_t> &w, std::string &src, std::string &e
     std::ostringstream o;
     o << "#include \"chunk_dev.cuh\"\nnamespace svs {\nstruct JOps {\n";
     o << "    static constexpr int kStages = " << ns << ";\n";
+    // direct boundary stages: their register offsets in HBM
+    const uint32_t direct = w[H_DIRECT];
+    o << "    static constexpr bool kDirectFirst = " << ((direct & DIRECT_FIRST) ? "true" : "false")
+      << ", kDirectLast = " << ((direct & DIRECT_LAST) ? "true" : "false") << ";\n";
+    o << "    static __device__ __forceinline__ bool paired(int s)\n    {\n";
+    for (int s = 0; s < ns; s++)
+        o << "        if (s == " << s << ") return " << (w[w[H_STAGE_OFF + s] + S_REG] == 0 ? "true" : "false") << ";\n";
+    o << "        return false;\n    }\n";
+    o << "    static __device__ __forceinline__ uint64_t roff(int s, int m)\n    {\n";
+    for (int s = 0; s < ns; s++) {
+        if (!((s == 0 && (direct & DIRECT_FIRST)) || (s == ns - 1 && (direct & DIRECT_LAST)))) continue;
+        const size_t so = w[H_STAGE_OFF + s];
+        for (int m = 0; m < NR; m++) {
+            uint64_t off = 0;
+            for (int j = 0; j < RB; j++)
+                if ((m >> j) & 1) off |= 1ull << w[H_QIN + w[so + S_REG + j]];
+            o << "        if (s == " << s << " && m == " << m << ") return " << off << "ull;\n";
+        }
+    }
+    o << "        return 0;\n    }\n";
     o << "    static __device__ __forceinline__ uint32_t stage_off(const uint32_t *, int s)\n    {\n";
     for (int s = 0; s < ns; s++) o << "        if (s == " << s << ") return " << w[H_STAGE_OFF + s] << "u;\n";
     o << "        return 0u;\n    }\n";

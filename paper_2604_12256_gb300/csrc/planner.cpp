@@ -264,6 +264,57 @@ static void stage_layout(int C, int RB, int swz, const std::vector<int> &need_re
         if (!used[b]) { thr[nt++] = b; used[b] = 1; }
 }
 
+// A direct layout (program.h) for a stage that needs register bits
+// `need_reg`, if there is one.  Paired (a 16-byte access per two
+// amplitudes) when qubit 0 is needed or a register bit is left for it:
+// register bit 0 = chunk bit 0, lanes 0..2 = chunk bits 1..3, lane 3 a bit
+// of the remaining swizzle residue (no shared-memory bank conflicts).
+// Otherwise unpaired (8-byte accesses): lanes 0..3 = chunk bits 0..3.  The
+// other register bits are the needed ones, then the highest free bits; the
+// other thread bits the free ones in ascending order.
+static bool direct_layout(int C, int RB, int swz, const std::vector<int> &need_reg, int *reg, int *thr)
+{
+    if (C - RB < 5 || RB < 2) return false;
+    int nhigh = 0;
+    bool has0 = false;
+    for (int b : need_reg) {
+        if (b >= 1 && b <= 3) return false;   // qubits 1..3 are lanes
+        if (b == 0) has0 = true;
+        else nhigh++;
+    }
+    const bool paired = has0 || nhigh <= RB - 1;
+    if (has0 && nhigh > RB - 1) return false;
+    std::vector<char> used(C, 0);
+    int nr = 0;
+    if (paired) {
+        reg[nr++] = 0;
+        used[0] = 1;
+    }
+    for (int b : need_reg)
+        if (b != 0) {
+            reg[nr++] = b;
+            used[b] = 1;
+        }
+    std::vector<int> lanes;
+    for (int b = paired ? 1 : 0; b <= 3; b++) {
+        lanes.push_back(b);
+        used[b] = 1;
+    }
+    for (int b = 4; b < C && lanes.size() < 4; b++)
+        if (!used[b] && b % swz == 0) { lanes.push_back(b); used[b] = 1; }
+    for (int b = C - 1; b >= 4 && nr < RB; b--)
+        if (!used[b]) { reg[nr++] = b; used[b] = 1; }
+    if (nr < RB) return false;
+    const int nl = std::min(5, C - RB);
+    for (int b = 0; b < C && (int)lanes.size() < nl; b++)
+        if (!used[b]) { lanes.push_back(b); used[b] = 1; }
+    int nt = 0;
+    for (int b : lanes) thr[nt++] = b;
+    for (int b = 0; b < C; b++)
+        if (!used[b]) { thr[nt++] = b; used[b] = 1; }
+    return nt == C - RB;
+}
+
 // Context of one phase segment: where the register and thread bits sit in
 // this stage, the segment's number and the launch-wide term tables.
 struct DsegCtx {
@@ -504,6 +555,12 @@ static std::vector<uint32_t> encode_program(int n, int C, int RB, bool f64, uint
         pw.w[prog::H_SPERM + i2] = (uint32_t)src;
     }
     const int swz = prog::swizzle_bits(f64 ? 8 : 4);
+    // direct boundary stages (complex64, the lowest 4 qubits in the chunk)
+    bool low4 = !f64 && C >= 4;
+    for (int i = 0; i < 4 && low4; i++) low4 = qin[i] == i;
+    bool sperm_id = true;
+    for (int i = 0; i < C; i++) sperm_id = sperm_id && pw.w[prog::H_SPERM + i] == (uint32_t)i;
+    uint32_t direct = 0;
     // phase segments whose thread-only terms are summed once per launch:
     // as many as fit the shared-memory budget of the thread table
     int nseg = 0;
@@ -525,7 +582,13 @@ static std::vector<uint32_t> encode_program(int n, int C, int RB, bool f64, uint
         } else {
             std::vector<int> need;
             for (int i = 0; i < C; i++) if ((st.R >> qin[i]) & 1) need.push_back(i);
-            stage_layout(C, RB, swz, need, reg, thr);
+            const bool first = s == 0, last = s + 1 == stages.size() && sperm_id;
+            if ((first || last) && low4 && direct_layout(C, RB, swz, need, reg, thr)) {
+                if (first) direct |= prog::DIRECT_FIRST;
+                if (last) direct |= prog::DIRECT_LAST;
+            } else {
+                stage_layout(C, RB, swz, need, reg, thr);
+            }
         }
         pw.w.resize(sstart + prog::S_SIZE, 0);
         pw.w[sstart + prog::S_NOPS] = (uint32_t)st.ops.size();
@@ -564,6 +627,7 @@ static std::vector<uint32_t> encode_program(int n, int C, int RB, bool f64, uint
     pw.align2();
     pw.w[prog::H_NDSEG] = (uint32_t)nd;
     pw.w[prog::H_NHOIST] = (uint32_t)nhoist;
+    pw.w[prog::H_DIRECT] = direct;
     pw.w[prog::H_CTA_OFF] = (uint32_t)pw.w.size();
     pw.w[prog::H_NCTA] = (uint32_t)(cta.size() / prog::kCtaWords);
     pw.w.insert(pw.w.end(), cta.begin(), cta.end());
@@ -1464,6 +1528,22 @@ static bool validate_program(const std::vector<uint32_t> &w, int n, bool diag_sw
             if (w[to + i * prog::kThrWords + 1] >> TB) return bad("thread table mask");
         }
     }
+    const uint32_t direct = w[prog::H_DIRECT];
+    if (direct & ~3u) return bad("direct flags");
+    auto direct_ok = [&](size_t so) {
+        const bool paired = w[so + prog::S_REG] == 0;
+        bool ok = wb == 4 && C - RB >= 5;
+        for (int i = 0; i < (paired ? 3 : 4) && ok; i++)
+            ok = w[so + prog::S_THR + i] == (uint32_t)(i + (paired ? 1 : 0));
+        for (int i = 0; i < 4 && ok; i++) ok = w[prog::H_QIN + i] == (uint32_t)i;
+        return ok;
+    };
+    if ((direct & prog::DIRECT_FIRST) && (ns < 1 || !direct_ok(w[prog::H_STAGE_OFF]))) return bad("direct first stage");
+    if (direct & prog::DIRECT_LAST) {
+        bool ok = ns >= 1 && direct_ok(w[prog::H_STAGE_OFF + ns - 1]);
+        for (int i = 0; i < C && ok; i++) ok = w[prog::H_SPERM + i] == (uint32_t)i;
+        if (!ok) return bad("direct last stage");
+    }
     uint32_t nseg_seen = 0;
     for (int s = 0; s < ns; s++) {
         size_t so = w[prog::H_STAGE_OFF + s];
@@ -1716,7 +1796,7 @@ std::string plan_json(const Plan &p)
             for (int i = 0; i < cp.C; i++) os << (i ? "," : "") << cp.qin[i];
             os << "],\"qout\":[";
             for (int i = 0; i < cp.C; i++) os << (i ? "," : "") << cp.qout[i];
-            os << "],\"words\":" << o.words.size() << ",\"stages\":[";
+            os << "],\"words\":" << o.words.size() << ",\"direct\":" << o.words[prog::H_DIRECT] << ",\"stages\":[";
             for (size_t si = 0; si < cp.stages.size(); si++) {
                 os << (si ? "," : "") << "[";
                 const Stage &st = cp.stages[si];

@@ -65,7 +65,8 @@ enum : int {
     H_THR_OFF,           // thread table: word offset, count (kThrWords each)
     H_NTHR,
     H_WORDS,             // total words of the program (it is staged in shared memory)
-    H_PAD,
+    H_DIRECT,            // bit 0: stage 0's layout is a direct layout, bit 1: the last
+                         // stage's is and the store permutation is the identity
     H_SIZE
 };
 // CTA-table entry: slot (= d * cta_stride + s: s = 0 base, 1 + j linear in
@@ -90,6 +91,16 @@ enum : int {
     S_SIZE = S_GTHR + kMaxC + 2
 };
 static_assert(S_PV % 4 == 0 && S_SIZE % 4 == 2, "stage header alignment");
+
+// Direct layout of a stage: paired, register bit 0 is chunk bit 0 (qubit 0,
+// so a thread's amplitudes m and m + 1 are adjacent in HBM: one 16-byte
+// complex64 access) and thread bits 0..2 are chunk bits 1..3 (qubits 1..3:
+// eight lanes cover 128 contiguous bytes); or unpaired, thread bits 0..3 are
+// chunk bits 0..3 (16 lanes, 128 bytes).  A stage with such a layout can take its
+// amplitudes straight from HBM (the first stage) or write them straight back
+// (the last), without a pass through shared memory; kernels specialised to
+// the program do so, the interpreter ignores the flags.
+enum : uint32_t { DIRECT_FIRST = 1, DIRECT_LAST = 2 };
 
 // Shared-memory swizzle of the chunk (interleaved complex amplitudes):
 // element y lives at y ^ fold(y >> sw), folding sw-bit groups into the low
