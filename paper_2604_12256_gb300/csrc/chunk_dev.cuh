@@ -215,6 +215,67 @@ __device__ __forceinline__ void dense1_special_f(float2 (&v)[NR], float a, float
     }
 }
 
+// Scaled one-qubit forms (specialised kernels): the op is s * N with N
+// below and the sweep's product of the scalars s applied once elsewhere, so
+// each output amplitude costs one packed f32x2 instruction.
+__device__ __forceinline__ u64 fadd2(u64 a, u64 b)
+{
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 fsub2(u64 a, u64 b)
+{
+    u64 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// N = [[1, +-1], [+-1, +-1]] (H-like): row r is x0 + x1 (0), x0 - x1 (1) or x1 - x0 (2)
+template <int NR, int P, int R0, int R1>
+__device__ __forceinline__ void dense1_pm(float2 (&v)[NR])
+{
+#pragma unroll
+    for (int g = 0; g < NR; g++) {
+        if (g & (1 << P)) continue;
+        const u64 x0 = pk(v[g]), x1 = pk(v[g | (1 << P)]);
+        v[g] = upk(R0 == 0 ? fadd2(x0, x1) : R0 == 1 ? fsub2(x0, x1) : fsub2(x1, x0));
+        v[g | (1 << P)] = upk(R1 == 0 ? fadd2(x0, x1) : R1 == 1 ? fsub2(x0, x1) : fsub2(x1, x0));
+    }
+}
+// N = [[1, t0], [t1, 1]] real (RY-like)
+template <int NR, int P>
+__device__ __forceinline__ void dense1_rot(float2 (&v)[NR], float t0, float t1)
+{
+    const u64 A = pk2(t0, t0), B = pk2(t1, t1);
+#pragma unroll
+    for (int g = 0; g < NR; g++) {
+        if (g & (1 << P)) continue;
+        const u64 x0 = pk(v[g]), x1 = pk(v[g | (1 << P)]);
+        v[g] = upk(ffma2(x1, A, x0));
+        v[g | (1 << P)] = upk(ffma2(x0, B, x1));
+    }
+}
+// N = [[1, i u0], [i u1, 1]] (RX-like): x0 + i u0 x1 = x0 + (-u0, u0) * (x1.im, x1.re)
+template <int NR, int P>
+__device__ __forceinline__ void dense1_rxn(float2 (&v)[NR], float u0, float u1)
+{
+    const u64 A = pk2(-u0, u0), B = pk2(-u1, u1);
+#pragma unroll
+    for (int g = 0; g < NR; g++) {
+        if (g & (1 << P)) continue;
+        const float2 y0 = v[g], y1 = v[g | (1 << P)];
+        v[g] = upk(ffma2(pk2(y1.y, y1.x), A, pk(y0)));
+        v[g | (1 << P)] = upk(ffma2(pk2(y0.y, y0.x), B, pk(y1)));
+    }
+}
+template <int NR>
+__device__ __forceinline__ void scale_all(float2 (&v)[NR], float s)
+{
+    const u64 S = pk2(s, s);
+#pragma unroll
+    for (int m = 0; m < NR; m++) v[m] = upk(fmul2(pk(v[m]), S));
+}
+
 template <typename R, int NR, int K, int P0, int P1>
 __device__ __forceinline__ void dense_apply(typename CT<R>::T2 (&v)[NR], const uint32_t *body)
 {

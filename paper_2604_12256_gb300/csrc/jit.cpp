@@ -166,7 +166,7 @@ Fac fac_mul(std::ostringstream &o, const Fac &a, const Fac &b, const std::string
 // the register bits that carry a phase, and one complex product per
 // amplitude whose factor is not exactly one.
 void gen_segment(std::ostringstream &o, const std::vector<uint32_t> &w, size_t body, const std::vector<SlotSrc> &slots,
-                 int RB, int TB, int T, int SCP)
+                 int RB, int TB, int T, int SCP, long double scale)
 {
     using namespace prog;
     const uint32_t *b = &w[body];
@@ -243,6 +243,13 @@ void gen_segment(std::ostringstream &o, const std::vector<uint32_t> &w, size_t b
     std::vector<int> K;
     for (int j = 0; j < RB; j++)
         if (fl[j].kind != Fac::ONE) K.push_back(j);
+    if (scale != 1.0L) {   // the sweep's deferred scale of its scaled one-qubit ops
+        Fac sc;
+        sc.kind = Fac::CONST;
+        sc.re = scale;
+        sc.im = 0;
+        fb = fac_mul(o, fb, sc, "e0s");
+    }
     std::vector<Fac> tb(1);
     tb[0] = fb;
     for (size_t k = 0; k < K.size(); k++) {
@@ -268,6 +275,55 @@ void gen_segment(std::ostringstream &o, const std::vector<uint32_t> &w, size_t b
         if (f.kind != Fac::ONE) o << "                v[" << m << "] = cmul(v[" << m << "], " << fac_expr(f) << ");\n";
     }
     o << "            }\n";
+}
+
+// A one-qubit op as s * N with one packed instruction per output amplitude
+// (dense1_pm / dense1_rot / dense1_rxn), or none of those forms.
+struct Scaled {
+    int form = 0;            // 0 none, 1 +-1 entries, 2 real [[1, t0], [t1, 1]], 3 [[1, i u0], [i u1, 1]]
+    long double s = 1;       // the scalar
+    float t0 = 0, t1 = 0;    // form 2, 3
+    int r0 = 0, r1 = 0;      // form 1: rows (0 x0 + x1, 1 x0 - x1, 2 x1 - x0)
+};
+
+Scaled scaled_form(const uint32_t *b, int sub)
+{
+    using namespace prog;
+    auto f = [&](int i) {
+        float x;
+        std::memcpy(&x, &b[i], 4);
+        return (long double)x;
+    };
+    Scaled r;
+    const long double a = f(0), d = f(6);
+    if (a == 0 || fabsl(a) < 0.125L) return r;   // keep magnitudes bounded
+    if (sub == DS_REAL) {
+        const long double bb = f(2), cc = f(4);
+        if (fabsl(bb) == fabsl(a) && fabsl(cc) == fabsl(a) && fabsl(d) == fabsl(a)) {
+            // rows (1, b/a), (c/a, d/a) of +-1: x0 + x1, x0 - x1, x1 - x0
+            const int sb = bb / a > 0 ? 1 : -1, sc = cc / a > 0 ? 1 : -1, sd = d / a > 0 ? 1 : -1;
+            if (sc < 0 && sd < 0) return r;
+            r.form = 1;
+            r.s = a;
+            r.r0 = sb > 0 ? 0 : 1;
+            r.r1 = sc > 0 ? (sd > 0 ? 0 : 1) : 2;
+            return r;
+        }
+        if (d == a) {
+            r.form = 2;
+            r.s = a;
+            r.t0 = (float)(bb / a);
+            r.t1 = (float)(cc / a);
+        }
+        return r;
+    }
+    if (sub == DS_RX && d == a) {
+        r.form = 3;
+        r.s = a;
+        r.t0 = (float)(f(3) / a);
+        r.t1 = (float)(f(5) / a);
+    }
+    return r;
 }
 
 }  // namespace
@@ -338,6 +394,31 @@ bool jit_source(const std::vector<uint32_t> &w, std::string &src, std::string &e
          "    static __device__ __forceinline__ void run(int s, typename CT<R>::T2 (&v)[1 << RB], uint64_t x0,\n"
          "        const uint32_t *prog, const uint32_t *, const typename CT<R>::W *cta_ph,\n"
          "        const typename CT<R>::W *thr_ph, int nhoist, int tid)\n    {\n";
+    // pass 1: the scaled forms of one-qubit ops and the sweep's product of
+    // their scalars (kept above 2^-40 so that no amplitude underflows)
+    std::map<size_t, Scaled> scaled;
+    long double scale = 1;
+    bool has_seg = false;
+    for (int s = 0; s < ns; s++) {
+        size_t op = w[H_STAGE_OFF + s] + S_SIZE;
+        for (uint32_t k = 0; k < w[w[H_STAGE_OFF + s] + S_NOPS]; k++) {
+            const uint32_t hdr = w[op];
+            const size_t body = op + O_BODY;
+            if ((hdr & 0xff) == OP_DENSE && ((hdr >> 8) & 0xf) == 1) {
+                const Scaled sf = scaled_form(&w[body], (hdr >> 12) & 0xf);
+                if (sf.form && fabsl(scale * sf.s) >= 0x1p-40L) {
+                    scaled[body] = sf;
+                    scale *= sf.s;
+                }
+            } else if ((hdr & 0xff) == OP_DSEG && !w[body + D_NMULTI]) {
+                has_seg = true;
+            }
+            op += w[op + O_WORDS];
+        }
+    }
+    // the scale goes into the first factored phase segment's base factor, or
+    // multiplies the amplitudes at the end of the last stage
+    bool scale_done = scale == 1.0L;
     for (int s = 0; s < ns; s++) {
         const size_t so = w[H_STAGE_OFF + s];
         o << "        if (s == " << s << ") {\n";
@@ -347,9 +428,17 @@ bool jit_source(const std::vector<uint32_t> &w, std::string &src, std::string &e
             const size_t body = op + O_BODY;
             if ((hdr & 0xff) == OP_DENSE) {
                 const int kq = (hdr >> 8) & 0xf, sub = (hdr >> 12) & 0xf, code = (int)(hdr >> 16);
+                const auto sc = scaled.find(body);
                 if (kq == 1 && sub == DS_REAL && w[body] == 0x3f800000u && w[body + 2] == 0 && w[body + 4] == 0 &&
                     w[body + 6] == 0x3f800000u) {
                     // exactly the identity in complex64 (e.g. H H): nothing to do
+                } else if (sc != scaled.end()) {
+                    const Scaled &f = sc->second;
+                    if (f.form == 1)
+                        o << "            dense1_pm<" << NR << ", " << code << ", " << f.r0 << ", " << f.r1 << ">(v);\n";
+                    else
+                        o << "            dense1_" << (f.form == 2 ? "rot<" : "rxn<") << NR << ", " << code << ">(v, "
+                          << flit_f(f.t0) << ", " << flit_f(f.t1) << ");\n";
                 } else if (kq == 1 && sub != DS_GENERAL) {
                     const bool re = sub == DS_REAL;
                     o << "            dense1_special_f<" << NR << ", " << code << ", " << sub << ">(v, " << flit(w[body])
@@ -367,12 +456,15 @@ bool jit_source(const std::vector<uint32_t> &w, std::string &src, std::string &e
                 // terms on several register bits and other bits: the general path
                 o << "            dseg_apply<R, RB, T, 3>(v, x0, prog + " << body << ", cta_ph, thr_ph, nhoist, tid);\n";
             } else {
-                gen_segment(o, w, body, slots, RB, TB, T, SCP);
+                gen_segment(o, w, body, slots, RB, TB, T, SCP, scale_done ? 1.0L : scale);
+                scale_done = true;
             }
             op += len;
         }
+        if (s == ns - 1 && !scale_done) o << "            scale_all<" << NR << ">(v, " << flit_f(scale) << ");\n";
         o << "        }\n";
     }
+    (void)has_seg;
     o << "    }\n};\n}  // namespace svs\n";
     o << "extern \"C\" __global__ void __launch_bounds__(" << T << ", 3) " << kKernelName
       << "(svs::CT<float>::G2 *__restrict__ a, const uint32_t *__restrict__ gprog, int n, "

@@ -282,7 +282,15 @@ static bool direct_layout(int C, int RB, int swz, const std::vector<int> &need_r
         if (b == 0) has0 = true;
         else nhigh++;
     }
-    const bool paired = has0 || nhigh <= RB - 1;
+    // paired needs a free bit of residue 0 for lane 3 (bits 1..3 have
+    // residues 1..3); without one the unpaired form is conflict-free
+    bool free0 = false;
+    for (int b = swz; b < C; b += swz) {
+        bool taken = false;
+        for (int x : need_reg) taken = taken || x == b;
+        free0 = free0 || !taken;
+    }
+    const bool paired = has0 || (nhigh <= RB - 1 && free0);
     if (has0 && nhigh > RB - 1) return false;
     std::vector<char> used(C, 0);
     int nr = 0;
@@ -1796,7 +1804,18 @@ std::string plan_json(const Plan &p)
             for (int i = 0; i < cp.C; i++) os << (i ? "," : "") << cp.qin[i];
             os << "],\"qout\":[";
             for (int i = 0; i < cp.C; i++) os << (i ? "," : "") << cp.qout[i];
-            os << "],\"words\":" << o.words.size() << ",\"direct\":" << o.words[prog::H_DIRECT] << ",\"stages\":[";
+            os << "],\"words\":" << o.words.size() << ",\"direct\":" << o.words[prog::H_DIRECT] << ",\"layouts\":[";
+            // each stage's register and thread bits (chunk bit numbers)
+            for (uint32_t si = 0; si < o.words[prog::H_NSTAGE]; si++) {
+                const size_t so = o.words[prog::H_STAGE_OFF + si];
+                const int RBw = (int)o.words[prog::H_RB], TBw = (int)o.words[prog::H_C] - RBw;
+                os << (si ? "," : "") << "{\"reg\":[";
+                for (int j = 0; j < RBw; j++) os << (j ? "," : "") << o.words[so + prog::S_REG + j];
+                os << "],\"thr\":[";
+                for (int i = 0; i < TBw; i++) os << (i ? "," : "") << o.words[so + prog::S_THR + i];
+                os << "]}";
+            }
+            os << "],\"stages\":[";
             for (size_t si = 0; si < cp.stages.size(); si++) {
                 os << (si ? "," : "") << "[";
                 const Stage &st = cp.stages[si];
