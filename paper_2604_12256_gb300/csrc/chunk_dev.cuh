@@ -268,6 +268,35 @@ __device__ __forceinline__ void dense1_rxn(float2 (&v)[NR], float u0, float u1)
         v[g | (1 << P)] = upk(ffma2(pk2(y0.y, y0.x), B, pk(y1)));
     }
 }
+// complex64 4x4 on register bits P0 < P1 from its entries (re, im) m[0..31],
+// row major (specialised kernels: compile-time entries become immediate
+// operands; the same multiply-add order as dense_apply's)
+template <int NR, int P0, int P1>
+__device__ __forceinline__ void dense2_f(float2 (&v)[NR], const float (&m)[32])
+{
+    constexpr int gm = (1 << P0) | (1 << P1);
+#pragma unroll
+    for (int g = 0; g < NR; g++) {
+        if (g & gm) continue;
+        float2 in[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) in[c] = v[g | ((c & 1) << P0) | (((c >> 1) & 1) << P1)];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            float re = 0, im = 0;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const float mr = m[8 * r + 2 * c], mi = m[8 * r + 2 * c + 1];
+                re = fmaf(mr, in[c].x, re);
+                re = fmaf(-mi, in[c].y, re);
+                im = fmaf(mr, in[c].y, im);
+                im = fmaf(mi, in[c].x, im);
+            }
+            v[g | ((r & 1) << P0) | (((r >> 1) & 1) << P1)] = make_float2(re, im);
+        }
+    }
+}
+
 template <int NR>
 __device__ __forceinline__ void scale_all(float2 (&v)[NR], float s)
 {

@@ -449,8 +449,9 @@ bool jit_source(const std::vector<uint32_t> &w, std::string &src, std::string &e
                     for (int i = 0; i < 8; i++) o << (i ? ", " : "") << flit(w[body + i]);
                     o << "}; dense1_general_f<" << NR << ", " << code << ">(v, m); }\n";
                 } else {
-                    o << "            dense_apply<R, " << NR << ", 2, " << (code & 7) << ", " << ((code >> 3) & 7)
-                      << ">(v, prog + " << body << ");\n";
+                    o << "            { const float m[32] = {";
+                    for (int i = 0; i < 32; i++) o << (i ? ", " : "") << flit(w[body + i]);
+                    o << "}; dense2_f<" << NR << ", " << (code & 7) << ", " << ((code >> 3) & 7) << ">(v, m); }\n";
                 }
             } else if (w[body + D_NMULTI]) {
                 // terms on several register bits and other bits: the general path
