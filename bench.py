@@ -42,12 +42,15 @@ WORKLOAD = "28-qubit diagonal-heavy gate-level stream (500 gates, 80% RZ/CP/RZZ,
 # A sweep's traffic grows with the amplitudes it processes, so a capture on a
 # smaller state scales to the full one (profiles/ has the captures).
 TRAFFIC_PER_AMP = {
-    # profiles/k_chunk_diagheavy_25q.md: 475.49 MB per 2^25-amplitude sweep
-    ("diag-heavy", "chunk", "b6a05b0ee442df3fd6dace7605a89ae1b03495a192f463ce41a8c2aa8b45acda"): 475.49e6 / 2 ** 25,
-    # profiles/k_dense5_tc_layered_26q.md: 1011.93 MB per 2^26-amplitude block sweep
-    ("layered-dense", "dense", "d3c99ef16642f42a869fc41881935a038fdffd47e6556e1ae147d96b86411999"): 1011.93e6 / 2 ** 26,
-    # profiles/k_diag_rzzfull_26q.md: 475.27 MB per write-only 2^26-amplitude sweep
-    ("rzz-full", "diag", "b6a05b0ee442df3fd6dace7605a89ae1b03495a192f463ce41a8c2aa8b45acda"): 475.27e6 / 2 ** 26,
+    # profiles/svs_chunk_jit_diagheavy_25q.md: 475.56 MB per 2^25-amplitude sweep
+    # (the specialised kernel: keyed by its device templates and generator)
+    ("diag-heavy", "chunk-jit", "05a395a413e139e56f70ea9ee876126797f552a34eb308619cea7d31c0b15d2b"): 475.56e6 / 2 ** 25,
+    # profiles/k_chunk_diagheavy_25q.md: 476.05 MB per 2^25-amplitude sweep (interpreter)
+    ("diag-heavy", "chunk", "007d53d58b2799ad1780931734828151bc5c81d48642592966dbe94944b0f552"): 476.05e6 / 2 ** 25,
+    # profiles/k_dense5_tc_layered_26q.md: 1011.84 MB per 2^26-amplitude block sweep
+    ("layered-dense", "dense", "902dcf26ad8abd672acf4f9ec16df78b31986b3b9a62774a4456ee0248f2943f"): 1011.84e6 / 2 ** 26,
+    # profiles/k_diag_rzzfull_26q.md: 475.29 MB per write-only 2^26-amplitude sweep
+    ("rzz-full", "diag", "007d53d58b2799ad1780931734828151bc5c81d48642592966dbe94944b0f552"): 475.29e6 / 2 ** 26,
 }
 
 
@@ -306,9 +309,13 @@ def run_gpu(args, rank, world, dist):
     if kind == "dense":
         kname = "k_dense5_tc (dense 5-qubit block, tcgen05 split-TF32)" if args.precision == "tf32x3" \
             and dt == S.SIM_C64 else "k_dense5_fma (dense 5-qubit block, CUDA cores)"
-    ksrc = {"chunk": "chunk_dev.cuh", "diag": "chunk_dev.cuh", "dense": "k_dense5.cu"}.get(kind, "k_basic.cu")
-    src = open(os.path.join(ROOT, "paper_2604_12256_gb300", "csrc", ksrc), "rb").read()
-    tpa = TRAFFIC_PER_AMP.get((args.workload, kind, hashlib.sha256(src).hexdigest()))
+    jit_on = kind == "chunk" and bool(opt.flags & S.SIM_F_JIT)
+    ksrc = {"chunk": ("chunk_dev.cuh", "jit.cpp") if jit_on else ("chunk_dev.cuh",), "diag": ("chunk_dev.cuh",),
+            "dense": ("k_dense5.cu",)}.get(kind, ("k_basic.cu",))
+    src = b"".join(open(os.path.join(ROOT, "paper_2604_12256_gb300", "csrc", f), "rb").read() for f in ksrc)
+    tpa = TRAFFIC_PER_AMP.get((args.workload, "chunk-jit" if jit_on else kind, hashlib.sha256(src).hexdigest()))
+    if jit_on:
+        kname = "svs_chunk_jit (cache-blocked chunk sweep specialised to its program)"
     if (dense and args.precision != "tf32x3") or args.dtype != "c64":
         tpa = None   # captured on complex64 (and the tensor-core variant) only
     traffic = tpa * amps if tpa is not None else None
