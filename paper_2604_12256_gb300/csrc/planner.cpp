@@ -1682,6 +1682,99 @@ bool make_batch_ops(int n, sim_dtype dt, const sim_gate *gates, size_t ng, std::
     return true;
 }
 
+// ------------------------------------------------------------ Euler split
+// A one-qubit unitary U = e^{i phi} V, V = [[p, -conj(q)], [q, conj(p)]] in
+// SU(2), is exactly D1 R D2 with R = [[|p|, -|q|], [|q|, |p|]] real,
+// D2 = diag(1, e^{-i(a+b)}) and D1 = e^{i phi} diag(e^{ia}, e^{ib}), a =
+// arg p, b = arg q.  Where U's neighbours on its qubit are diagonal gates (or
+// the circuit's ends), D1 and D2 join those diagonals' phase polynomial and
+// the sweep applies only the real R, which costs a third of a complex 2x2.
+// D2 commutes back to the previous gate on the qubit (diagonal, or none) and
+// is emitted right after it, so that it joins the phases flushed before the
+// whole layer of R's rather than forcing one flush per R.  Real and RX-form
+// matrices (already cheap) are left alone.
+static std::vector<PGate> euler_split(const std::vector<PGate> &G, int n, uint64_t &split)
+{
+    split = 0;
+    // neighbours on the qubit: previous / next gate touching it
+    std::vector<int> prev(G.size(), -1), next(G.size(), -1), last(n, -1);
+    for (size_t i = 0; i < G.size(); i++)
+        for (int j = 0; j < G[i].k; j++) {
+            const int q = G[i].q[j];
+            if (last[q] >= 0 && G[i].k == 1) prev[i] = last[q];
+            if (last[q] >= 0 && G[last[q]].k == 1) next[last[q]] = (int)i;
+            last[q] = (int)i;
+        }
+    std::vector<PGate> front;                  // D2s of gates first on their qubit
+    std::vector<std::vector<PGate>> after(G.size());   // D2s emitted after gate i
+    std::vector<std::vector<PGate>> at(G.size());      // gate i's replacement (R, D1), if split
+    std::vector<char> done(G.size(), 0);
+    for (size_t i = 0; i < G.size(); i++) {
+        const PGate &g = G[i];
+        bool cand = g.k == 1 && !g.diag && !g.swap && g.M.size() == 4 && (prev[i] < 0 || G[prev[i]].diag) &&
+                    (next[i] < 0 || G[next[i]].diag);
+        if (cand) {
+            bool real = true, rx = true;
+            for (int e = 0; e < 4; e++) {
+                real = real && g.M[e].imag() == 0;
+                rx = rx && ((e == 0 || e == 3) ? g.M[e].imag() == 0 : g.M[e].real() == 0);
+            }
+            cand = !real && !rx;
+        }
+        cd p, q, det;
+        if (cand) {
+            det = g.M[0] * g.M[3] - g.M[1] * g.M[2];
+            cand = std::abs(std::abs(det) - 1.0) < 1e-12;
+        }
+        double phi = 0;
+        if (cand) {
+            phi = 0.5 * std::arg(det);
+            const cd e = std::polar(1.0, -phi);
+            p = g.M[0] * e;
+            q = g.M[2] * e;
+            // V must be [[p, -conj q], [q, conj p]] (det V = 1, up to the
+            // branch of the square root: then p, q change sign together)
+            const cd v01 = g.M[1] * e, v11 = g.M[3] * e;
+            cand = std::abs(v01 + std::conj(q)) < 1e-12 && std::abs(v11 - std::conj(p)) < 1e-12;
+        }
+        if (!cand) continue;
+        const double a = std::abs(p) > 0 ? std::arg(p) : 0.0, b = std::abs(q) > 0 ? std::arg(q) : 0.0;
+        const int qb = g.q[0];
+        auto diag_gate = [&](double th0, double th1) {
+            PGate d;
+            d.kind = kFusedDiag;
+            d.diag = true;
+            d.k = 1;
+            d.q[0] = qb;
+            d.qmask = 1ull << qb;
+            d.n_src = 0;
+            d.terms = {Term{0, turns_of(th0)}, Term{1ull << qb, turns_of(th1 - th0)}};
+            normalize_terms(d.terms);
+            return d;
+        };
+        (prev[i] >= 0 ? after[prev[i]] : front).push_back(diag_gate(0.0, -(a + b)));   // D2
+        PGate r;
+        r.kind = kFusedDense;
+        r.k = 1;
+        r.q[0] = qb;
+        r.qmask = 1ull << qb;
+        r.n_src = g.n_src;
+        r.M = {cd(std::abs(p), 0), cd(-std::abs(q), 0), cd(std::abs(q), 0), cd(std::abs(p), 0)};
+        at[i].push_back(std::move(r));
+        at[i].push_back(diag_gate(phi + a, phi + b));   // D1
+        done[i] = 1;
+        split++;
+    }
+    std::vector<PGate> out(front);
+    out.reserve(G.size() + 2 * split);
+    for (size_t i = 0; i < G.size(); i++) {
+        if (done[i]) out.insert(out.end(), at[i].begin(), at[i].end());
+        else out.push_back(G[i]);
+        out.insert(out.end(), after[i].begin(), after[i].end());
+    }
+    return out;
+}
+
 bool make_plan(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_t ng, const sim_options &opt_in,
                Plan &plan, std::string &err)
 {
@@ -1705,6 +1798,10 @@ bool make_plan(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_
     plan.stats.gates_in = ng;
     // Algorithm 4, machine level: booster, diagonal detector, blocking + fusion
     if ((opt.flags & SIM_F_BOOST) && basis != UINT64_MAX && ng > 0) run_booster(G, n, opt, dt, basis, plan);
+    if ((opt.flags & SIM_F_DIAG) && (opt.flags & SIM_F_BLOCK) && !(opt.flags & SIM_F_TC)) {
+        uint64_t nsplit = 0;
+        G = euler_split(G, n, nsplit);
+    }
     if (opt.flags & SIM_F_DIAG) {
         uint64_t absorbed = 0;
         G = diagonal_detector(G, opt.max_diag_qubits, absorbed);
