@@ -172,3 +172,19 @@ def test_remap_cuts_sweeps_on_layered_circuits():
     s0 = S.plan_json(c.n, c.gates, S.SIM_C64, 0, base)["stats"]["sweeps"]
     s1 = S.plan_json(c.n, c.gates, S.SIM_C64, 0, rm)["stats"]["sweeps"]
     assert s1 < s0
+
+
+def test_euler_split_real_rotations_and_exact():
+    """General one-qubit unitaries between diagonal gates are split into
+    diag . real rotation . diag: the chunk sweeps on the full state carry only
+    real 2x2 ops, the plan stays exact, and the phases do not add segments."""
+    c = C.layered(14, 8, 3)
+    plan = S.plan_json(c.n, c.gates, S.SIM_C128, c.basis, S.default_options())
+    ops = [x for o in plan["ops"] if o["op"] == "chunk" and o["n"] == c.n for st in o["stages"] for x in st]
+    dense = [x for x in ops if "dense" in x and len(x["dense"]) == 1]
+    assert dense and all(abs(e[1]) == 0 for x in dense for e in x["matrix"])
+    np.testing.assert_allclose(interpret(plan, basis=c.basis), oracle.run(c), atol=1e-12, rtol=0)
+    # the leading phase of each rotation joins its layer's segment: at most
+    # one phase segment per layer and register stage, not one per rotation
+    nseg = sum(1 for x in ops if "phase" in x)
+    assert nseg <= len(dense) // 4
