@@ -144,6 +144,10 @@ def _workload_circuit(args, n):
         return C.layered(n, 20, 0)
     if args.workload == "rzz-full":
         return C.rzz_full(n)
+    if args.workload == "qft":
+        return C.qft(n, 2)
+    if args.workload == "qaoa":
+        return C.qaoa(n, 4, 3)
     return C.diag_heavy(n, N_GATES, SEED)
 
 
@@ -232,7 +236,7 @@ def run_gpu(args, rank, world, dist):
         opt.flags |= S.SIM_F_JIT
 
     def step():
-        sim.reset(0)
+        sim.reset(circ.basis)
         sim.apply(ga, opt)
 
     for _ in range(args.warmup):
@@ -273,7 +277,7 @@ def run_gpu(args, rank, world, dist):
     te = []
     for _ in range(max(1, args.steps)):
         t0 = time.perf_counter()
-        sim.reset(0)
+        sim.reset(circ.basis)
         sim.apply(circ.gates, opt)      # marshal from the Python gate list each step
         idx, p = sim.top_k(64)
         ev = sim.expectation(masks)
@@ -286,12 +290,12 @@ def run_gpu(args, rank, world, dist):
     if not args.no_unfused:
         # the unfused gate-by-gate GPU path on the same circuit (one timed run)
         unf = S.default_options(flags=0)
-        sim.reset(0)
+        sim.reset(circ.basis)
         sim.apply(ga, unf)
         torch.cuda.synchronize()
         u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         u0.record(stream)
-        sim.reset(0)
+        sim.reset(circ.basis)
         sim.apply(ga, unf)
         u1.record(stream)
         torch.cuda.synchronize()
@@ -347,7 +351,7 @@ def run_gpu(args, rank, world, dist):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "gates": G,
-                       "seed": {"layered-dense": 0, "layered": 0, "rzz-full": 5}.get(args.workload, SEED),
+                       "seed": {"layered-dense": 0, "layered": 0, "rzz-full": 5, "qft": 2, "qaoa": 3}.get(args.workload, SEED),
                        "parallelism": f"replicas x{world}",
                        "l2": f"state ({amps * s_amp / 2 ** 30:g} GiB) larger than L2, no flush",
                        "sweeps": plan["sweeps"], "chunk_ops": plan["chunk_ops"], "dense_ops": plan["dense_ops"],
@@ -573,11 +577,13 @@ def main():
     ap.add_argument("--register-bits", type=int, default=0,
                     help="chunk bits per thread in the cache-blocked kernel (0 = library default)")
     ap.add_argument("--workload", default="diag-heavy",
-                    choices=["diag-heavy", "layered-dense", "layered", "rzz-full"],
+                    choices=["diag-heavy", "layered-dense", "layered", "rzz-full", "qft", "qaoa"],
                     help="diag-heavy: the 28-qubit gate-level stream; layered-dense: depth-20 layered "
                          "circuit in dense 5-qubit blocks; layered: the same circuit on the default "
                          "cache-blocked path; rzz-full: RZZ on every qubit pair from |+...+> "
-                         "(the last three: 34 qubits complex64 / 33 complex128 by default)")
+                         "(the last three: 34 qubits complex64 / 33 complex128 by default); qft, qaoa: "
+                         "the 30-qubit circuit-level pair (QFT with the reversal SWAPs on a random basis "
+                         "state; QAOA p = 4 on a random 3-regular graph)")
     ap.add_argument("--precision", default="tf32x3", choices=sorted(PRECISIONS),
                     help="dense-block arithmetic for --workload layered-dense")
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
@@ -611,6 +617,13 @@ def main():
         n = args.qubits or (33 if args.dtype == "c128" else 34)
         WORKLOAD = (f"{n}-qubit full-connectivity RZZ gate-level stream ({n * (n - 1) // 2} RZZ, angles uniform "
                     f"in [0, 2pi), after H on every qubit), {'complex128' if args.dtype == 'c128' else 'complex64'}")
+        N_QUBITS = n
+    elif args.workload in ("qft", "qaoa"):
+        n = args.qubits or 30
+        WORKLOAD = (f"{n}-qubit QFT (H + controlled-phase ladder + reversal SWAPs) on a random basis state"
+                    if args.workload == "qft" else
+                    f"{n}-qubit QAOA p = 4 on a random 3-regular graph (RZZ per edge, RX mixer)")
+        WORKLOAD += f", {'complex128' if args.dtype == 'c128' else 'complex64'}"
         N_QUBITS = n
     elif args.qubits and args.qubits != N_QUBITS:
         WORKLOAD = WORKLOAD.replace(f"{N_QUBITS}-qubit", f"{args.qubits}-qubit")

@@ -299,9 +299,21 @@ __global__ void __launch_bounds__(kRedThreads) k_norm_part(const typename Cx<R>:
     __shared__ double sh[32];
     double acc = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-        if constexpr (sizeof(R) == 4) acc += (double)probf(a[i]);
-        else acc += prob_of(a[i]);
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if constexpr (sizeof(R) == 4) {
+        // complex64: FP32 sums over runs of 32 amplitudes (four independent
+        // chains), FP64 across runs, as the <Z> partials
+        for (int64_t i = i0; i < N; i += 32 * stride) {
+            float f[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int b = 0; b < 32; b++) {
+                const int64_t j = i + b * stride;
+                if (j < N) f[b & 3] += probf(a[j]);
+            }
+            acc += (double)((f[0] + f[1]) + (f[2] + f[3]));
+        }
+    } else {
+        for (int64_t i = i0; i < N; i += stride) acc += prob_of(a[i]);
     }
     double s = block_sum(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
@@ -342,50 +354,59 @@ __global__ void __launch_bounds__(kRedThreads) k_expect_part(const typename Cx<R
     for (int t = 0; t < NT; t++) acc[t] = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if constexpr (sizeof(R) == 4) {
-        // complex64: FP32 sums over batches of 32 amplitudes, FP64 across
-        // batches (the FP64 rate of this part is far below its FP32 rate).
-        // The grid's stride S is a power of two, so a thread's index bits
-        // below log2 S are fixed: it visits i = tid + g(k) S for k = 0, 1, ...
-        // with g(k) = k ^ (k >> 1) (Gray code), and the parities
-        // popc(i & m_t) & 1 of all masks, as the bits of P, change by
-        // P ^= flip[ctz(k)] from one amplitude to the next.
-        __shared__ uint32_t flip[64];
+        // complex64: FP32 sums over runs of 32 amplitudes, FP64 across runs
+        // (the FP64 rate of this part is far below its FP32 rate).  The
+        // grid's stride S = 2^sb is a power of two, so a thread visits
+        // i = tid + k S, k = 0 .. K-1, and in a run k = k0 + b (b < 32, k0 a
+        // multiple of 32) the sign of mask m is (-1)^(P0 + popc(b & u)) with
+        // u = (m >> sb) & 31 and P0 the parity of the run's other bits.  So
+        // the run's signed sum for m is (-1)^P0 W[u], W the Walsh-Hadamard
+        // transform of its 32 probabilities: one 5-level butterfly per run
+        // gives every mask's sum (kept in this thread's shared-memory column
+        // and read back at the masks' u).
+        __shared__ float wsh[32 * kRedThreads];
         const int sb = 63 - __clzll((unsigned long long)stride);     // log2 S
-        if (threadIdx.x < 64) {
-            uint32_t f = 0;
-            for (int t = 0; t < NT; t++)
-                if (threadIdx.x + sb < 64 && ((m[t] >> (threadIdx.x + sb)) & 1)) f |= 1u << t;
-            flip[threadIdx.x] = f;
-        }
-        __syncthreads();
         const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
         const int64_t K = N >> sb;                                     // amplitudes per thread
-        uint32_t P = 0;
+        uint32_t u[NT];
+        uint32_t Pt = 0;   // parities of tid & m_t
 #pragma unroll
-        for (int t = 0; t < NT; t++) P |= (uint32_t)(__popcll((uint64_t)tid & m[t]) & 1) << t;
-        if (K == 0) {   // fewer amplitudes than threads: one each, or none
-            if (tid < N) {
-                const float p = probf(a[tid]);
+        for (int t = 0; t < NT; t++) {
+            u[t] = sb < 64 ? (uint32_t)((m[t] >> sb) & 31) : 0;
+            Pt |= (uint32_t)(__popcll((uint64_t)tid & m[t]) & 1) << t;
+        }
+        if (K < 32) {   // short rows (N < 32 S): amplitude by amplitude
+            const int64_t kn = K > 0 ? K : (tid < N ? 1 : 0);
+            for (int64_t k = 0; k < kn; k++) {
+                const int64_t i = tid + (k << sb);
+                const double p = (double)probf(a[i]);
 #pragma unroll
-                for (int t = 0; t < NT; t++) acc[t] += ((P >> t) & 1) ? -(double)p : (double)p;
+                for (int t = 0; t < NT; t++) acc[t] += (__popcll((uint64_t)i & m[t]) & 1) ? -p : p;
             }
         } else {
+            float *col = wsh + threadIdx.x;
             for (int64_t k0 = 0; k0 < K; k0 += 32) {
-                float acc32[NT];
+                float w[32];
 #pragma unroll
-                for (int t = 0; t < NT; t++) acc32[t] = 0.f;
-                const int kn = (int)(K - k0 < 32 ? K - k0 : 32);
-#pragma unroll 4
-                for (int b = 0; b < kn; b++) {
-                    const int64_t k = k0 + b;
-                    if (k > 0) P ^= flip[__ffsll((long long)k) - 1];
-                    const float p = probf(a[tid + ((k ^ (k >> 1)) << sb)]);
-                    const uint32_t pb = __float_as_uint(p);
+                for (int b = 0; b < 32; b++) w[b] = probf(a[tid + ((k0 + b) << sb)]);
 #pragma unroll
-                    for (int t = 0; t < NT; t++) acc32[t] += __uint_as_float(pb ^ (((P >> t) & 1u) << 31));
+                for (int h = 1; h < 32; h <<= 1)
+#pragma unroll
+                    for (int j = 0; j < 32; j++)
+                        if (!(j & h)) {
+                            const float x = w[j], y = w[j | h];
+                            w[j] = x + y;
+                            w[j | h] = x - y;
+                        }
+#pragma unroll
+                for (int b = 0; b < 32; b++) col[b * kRedThreads] = w[b];
+                const uint64_t hi = (uint64_t)k0 << sb;   // the run's index bits above sb + 4
+#pragma unroll
+                for (int t = 0; t < NT; t++) {
+                    const float c = col[u[t] * kRedThreads];
+                    const uint32_t neg = ((Pt >> t) ^ (uint32_t)__popcll(hi & m[t])) & 1u;
+                    acc[t] += (double)__uint_as_float(__float_as_uint(c) ^ (neg << 31));
                 }
-#pragma unroll
-                for (int t = 0; t < NT; t++) acc[t] += (double)acc32[t];
             }
         }
     } else {
@@ -489,25 +510,34 @@ __global__ void __launch_bounds__(kTopThreads) k_topk(const typename Cx<R>::T *_
     __syncthreads();
     int64_t per = (N + gridDim.x - 1) / gridDim.x;
     int64_t lo = (int64_t)blockIdx.x * per, hi = lo + per < N ? lo + per : N;
-    // the next tile's amplitudes are loaded while this tile is filtered and
-    // (now and then) sorted
+    // the next batch of NB tiles is loaded while this batch is filtered and
+    // (now and then) sorted: complex64 keeps 16 amplitudes per thread in
+    // flight (enough bytes per SM to cover the HBM latency)
     using T2 = typename Cx<R>::T;
-    T2 nz[4];
-    auto load_tile = [&](int64_t t0) {
+    constexpr int NB = (FROM_STATE && sizeof(R) == 4) ? 4 : 1;
+    T2 nz[4 * NB];
+    auto load_batch = [&](int64_t t0) {
         if constexpr (FROM_STATE) {
 #pragma unroll
-            for (int e = 0; e < 4; e++) {
+            for (int e = 0; e < 4 * NB; e++) {
                 const int64_t i = t0 + e * kTopThreads + threadIdx.x;
                 if (i < hi) nz[e] = a[i];
             }
         }
     };
-    if (lo < hi) load_tile(lo);
-    for (int64_t t0 = lo; t0 < hi; t0 += kTopTile) {
+    if (lo < hi) load_batch(lo);
+    for (int64_t t00 = lo; t00 < hi; t00 += (int64_t)kTopTile * NB) {
+        T2 cb[4 * NB];
+#pragma unroll
+        for (int e = 0; e < 4 * NB; e++) cb[e] = nz[e];
+        if (t00 + (int64_t)kTopTile * NB < hi) load_batch(t00 + (int64_t)kTopTile * NB);
+#pragma unroll
+        for (int sbt = 0; sbt < NB; sbt++) {
+        const int64_t t0 = t00 + (int64_t)sbt * kTopTile;
+        if (t0 >= hi) break;
         T2 cz[4];
 #pragma unroll
-        for (int e = 0; e < 4; e++) cz[e] = nz[e];
-        if (t0 + kTopTile < hi) load_tile(t0 + kTopTile);
+        for (int e = 0; e < 4; e++) cz[e] = cb[4 * sbt + e];
         KI th = thr;
         // complex64: a float pre-filter (rounded down by a margin far above
         // its rounding error) skips the FP64 probability of clear losers
@@ -538,6 +568,7 @@ __global__ void __launch_bounds__(kTopThreads) k_topk(const typename Cx<R>::T *_
             if (threadIdx.x == 0) { cnt = k; thr = buf[k - 1]; }
         }
         __syncthreads();
+        }
     }
     // final: sort what is kept and write exactly k entries (padded with worst)
     for (int j = cnt + threadIdx.x; j < kTopCap; j += blockDim.x) buf[j] = worst;
