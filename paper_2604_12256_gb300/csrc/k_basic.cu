@@ -354,8 +354,10 @@ __global__ void __launch_bounds__(kRedThreads) k_expect_part(const typename Cx<R
     for (int t = 0; t < NT; t++) acc[t] = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if constexpr (sizeof(R) == 4) {
-        // complex64: FP32 sums over runs of 32 amplitudes, FP64 across runs
-        // (the FP64 rate of this part is far below its FP32 rate).  The
+        // complex64: FP32 sums over groups of 8 runs of 32 amplitudes, FP64
+        // across groups (the FP64 rate of this part is 1/64 of its FP32
+        // rate: one conversion and add per term per run would cost as much
+        // as the HBM read).  The
         // grid's stride S = 2^sb is a power of two, so a thread visits
         // i = tid + k S, k = 0 .. K-1, and in a run k = k0 + b (b < 32, k0 a
         // multiple of 32) the sign of mask m is (-1)^(P0 + popc(b & u)) with
@@ -385,6 +387,9 @@ __global__ void __launch_bounds__(kRedThreads) k_expect_part(const typename Cx<R
             }
         } else {
             float *col = wsh + threadIdx.x;
+            float acc32[NT];
+#pragma unroll
+            for (int t = 0; t < NT; t++) acc32[t] = 0.f;
             for (int64_t k0 = 0; k0 < K; k0 += 32) {
                 float w[32];
 #pragma unroll
@@ -405,7 +410,14 @@ __global__ void __launch_bounds__(kRedThreads) k_expect_part(const typename Cx<R
                 for (int t = 0; t < NT; t++) {
                     const float c = col[u[t] * kRedThreads];
                     const uint32_t neg = ((Pt >> t) ^ (uint32_t)__popcll(hi & m[t])) & 1u;
-                    acc[t] += (double)__uint_as_float(__float_as_uint(c) ^ (neg << 31));
+                    acc32[t] += __uint_as_float(__float_as_uint(c) ^ (neg << 31));
+                }
+                if ((k0 & 255) == 224 || k0 + 32 >= K) {   // every 8th run, and the last
+#pragma unroll
+                    for (int t = 0; t < NT; t++) {
+                        acc[t] += (double)acc32[t];
+                        acc32[t] = 0.f;
+                    }
                 }
             }
         }
@@ -505,8 +517,12 @@ __global__ void __launch_bounds__(kTopThreads) k_topk(const typename Cx<R>::T *_
     __shared__ KI buf[kTopCap];
     __shared__ int cnt;
     __shared__ KI thr;
+    // complex64: a float pre-filter threshold (the FP64 k-th best rounded
+    // down by a margin far above the float rounding error), set with thr so
+    // that the hot loop does no FP64 work and reads one shared word per tile
+    __shared__ float thr_f;
     const KI worst = {-1.0, ~0ull};
-    if (threadIdx.x == 0) { cnt = 0; thr = worst; }
+    if (threadIdx.x == 0) { cnt = 0; thr = worst; thr_f = -1.0f; }
     __syncthreads();
     int64_t per = (N + gridDim.x - 1) / gridDim.x;
     int64_t lo = (int64_t)blockIdx.x * per, hi = lo + per < N ? lo + per : N;
@@ -538,10 +554,8 @@ __global__ void __launch_bounds__(kTopThreads) k_topk(const typename Cx<R>::T *_
         T2 cz[4];
 #pragma unroll
         for (int e = 0; e < 4; e++) cz[e] = cb[4 * sbt + e];
-        KI th = thr;
-        // complex64: a float pre-filter (rounded down by a margin far above
-        // its rounding error) skips the FP64 probability of clear losers
-        const float thf = th.p > 0 ? __double2float_rd(th.p * (1.0 - 1e-5)) : -1.0f;
+        const float thf = thr_f;
+        int ins = 0;   // candidates this thread appended
 #pragma unroll
         for (int e = 0; e < 4; e++) {
             int64_t i = t0 + e * kTopThreads + threadIdx.x;
@@ -557,17 +571,27 @@ __global__ void __launch_bounds__(kTopThreads) k_topk(const typename Cx<R>::T *_
                 } else {
                     v = cand[i];
                 }
-                if (better(v, th)) { int pos = atomicAdd(&cnt, 1); buf[pos] = v; }
+                if (better(v, thr)) { int pos = atomicAdd(&cnt, 1); buf[pos] = v; ins++; }
             }
         }
-        __syncthreads();
-        // sort and cut back to k only when another tile might not fit
-        if (cnt > kTopCap - kTopTile) {
-            for (int j = cnt + threadIdx.x; j < kTopCap; j += blockDim.x) buf[j] = worst;
-            bitonic_desc(buf, kTopCap);
-            if (threadIdx.x == 0) { cnt = k; thr = buf[k - 1]; }
+        // one barrier when no thread appended anything (the common case once
+        // the threshold has risen); otherwise every thread reads the count
+        // before a second barrier (so all take the same branch), and the
+        // buffer is sorted and cut back to k when another tile might not fit
+        if (__syncthreads_or(ins)) {
+            const int c = cnt;
+            __syncthreads();
+            if (c > kTopCap - kTopTile) {
+                for (int j = c + threadIdx.x; j < kTopCap; j += blockDim.x) buf[j] = worst;
+                bitonic_desc(buf, kTopCap);
+                if (threadIdx.x == 0) {
+                    cnt = k;
+                    thr = buf[k - 1];
+                    thr_f = thr.p > 0 ? __double2float_rd(thr.p * (1.0 - 1e-5)) : -1.0f;
+                }
+                __syncthreads();
+            }
         }
-        __syncthreads();
         }
     }
     // final: sort what is kept and write exactly k entries (padded with worst)

@@ -7,6 +7,7 @@ or was not built; there is no fallback.
 from __future__ import annotations
 
 import ctypes
+import itertools
 import json
 import os
 from typing import Iterable, Optional, Sequence
@@ -148,30 +149,40 @@ def default_options(**kw) -> sim_options:
     return o
 
 
+# sim_gate as a numpy record (same layout: 64 bytes)
+_GATE_DTYPE = np.dtype([("kind", "<u4"), ("nq", "<u4"), ("q", "<u4", (6,)), ("param", "<f8", (3,)),
+                        ("matrix", "<u8")])
+assert _GATE_DTYPE.itemsize == ctypes.sizeof(sim_gate)
+
+
 class GateArray:
     """A circuit marshalled into a contiguous sim_gate array (keeps the
-    matrix buffers alive)."""
+    matrix buffers alive).  Built column by column as a numpy record array:
+    no per-field ctypes writes."""
 
     def __init__(self, gates: Sequence[_circ.Gate]):
-        self.n = len(gates)
-        self.arr = (sim_gate * max(1, self.n))()
+        self.n = n = len(gates)
+        self.arr = np.zeros(max(1, n), dtype=_GATE_DTYPE)
         self._keep = []
+        if n == 0:
+            return
+        z6, z3 = (0,) * 6, (0.0,) * 3
+        chain = itertools.chain.from_iterable
+        self.arr["kind"][:n] = np.fromiter((KIND[g.kind] for g in gates), np.uint32, n)
+        self.arr["nq"][:n] = np.fromiter((len(g.qubits) for g in gates), np.uint32, n)
+        self.arr["q"][:n] = np.fromiter(chain((tuple(g.qubits) + z6)[:6] for g in gates), np.uint32,
+                                        6 * n).reshape(n, 6)
+        self.arr["param"][:n] = np.fromiter(chain((tuple(g.params) + z3)[:3] for g in gates), np.float64,
+                                            3 * n).reshape(n, 3)
         for i, g in enumerate(gates):
-            s = self.arr[i]
-            s.kind = KIND[g.kind]
-            s.nq = len(g.qubits)
-            for j, q in enumerate(g.qubits):
-                s.q[j] = q
-            for j, p in enumerate(g.params):
-                s.param[j] = p
             if g.matrix is not None:
                 buf = np.ascontiguousarray(g.matrix, np.complex128).reshape(-1).view(np.float64).copy()
                 self._keep.append(buf)
-                s.matrix = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                self.arr["matrix"][i] = buf.ctypes.data
 
     @property
     def ptr(self):
-        return ctypes.cast(self.arr, ctypes.c_void_p)
+        return ctypes.c_void_p(self.arr.ctypes.data)
 
 
 def plan_json(n: int, gates, dtype: int = SIM_C64, basis: Optional[int] = 0,
@@ -350,7 +361,7 @@ class Server:
                      dtype: int = SIM_C64) -> int:
         """Queue an already marshalled gate list (the server copies it)."""
         m = np.ascontiguousarray(np.array(list(masks), dtype=np.uint64)) if len(masks) else None
-        req = srv_request(n, dtype, ctypes.cast(ga.arr, ctypes.c_void_p), ga.n, basis, top_k,
+        req = srv_request(n, dtype, ga.ptr, ga.n, basis, top_k,
                           m.ctypes.data if m is not None else None, 0 if m is None else len(m))
         t = ctypes.c_uint64()
         _check(self.lib.srv_submit(self.h, ctypes.byref(req), ctypes.byref(t)))
