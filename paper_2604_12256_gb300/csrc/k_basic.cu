@@ -490,7 +490,14 @@ size_t topk_scratch_bytes(int k)
     return ((size_t)kTopBlocksPerSM * sms + 1) * (size_t)k * sizeof(KI) + 4096;
 }
 
-__device__ __forceinline__ bool better(const KI &a, const KI &b) { return a.p > b.p || (a.p == b.p && a.i < b.i); }
+// (p desc, index asc).  Probabilities are >= +0 and the empty entry has p =
+// -1, so the order of p is the order of its bits read as a signed 64-bit
+// integer: the comparison runs on the integer pipe, not the slow FP64 one.
+__device__ __forceinline__ bool better(const KI &a, const KI &b)
+{
+    const long long pa = __double_as_longlong(a.p), pb = __double_as_longlong(b.p);
+    return pa > pb || (pa == pb && a.i < b.i);
+}
 
 __device__ void bitonic_desc(KI *buf, int cap)
 {
@@ -600,6 +607,107 @@ __global__ void __launch_bounds__(kTopThreads) k_topk(const typename Cx<R>::T *_
     for (int j = threadIdx.x; j < k; j += blockDim.x) out[(size_t)blockIdx.x * k + j] = buf[j];
 }
 
+// ---- complex64, k <= 128: warps that never wait for each other.  Each warp
+// streams its own contiguous slice of the state (kTwStep amplitudes per
+// step, the next step's loads in flight) and keeps its candidates in its own
+// shared-memory buffer: lanes that beat the warp's threshold (a float
+// pre-filter, then the exact (p, index) order) are placed by ballot and
+// prefix count; when the buffer could overflow the warp sorts it (bitonic,
+// warp-synchronous) and cuts it to its best k.  The block then merges its
+// warps' lists, and the single-block pass merges the blocks'.
+constexpr int kTwWarps = 16;    // warps per block
+constexpr int kTwStep = 128;    // amplitudes per warp step (4 per lane; the next step's loads in flight)
+constexpr int kTwCap = 256;     // candidate buffer per warp (>= 128 kept + one step)
+constexpr int kTwBlocksPerSM = 2;   // 32 warps per SM: enough loads in flight to cover the HBM latency
+constexpr int kTwMaxK = 128;
+
+__device__ __forceinline__ void warp_bitonic_desc(KI *buf, int cap, int lane)
+{
+    for (int size = 2; size <= cap; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            __syncwarp();
+            for (int t = lane; t < cap / 2; t += 32) {
+                const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
+                const bool desc = (lo & size) == 0;
+                const KI x = buf[lo], y = buf[hi];
+                if (desc ? better(y, x) : better(x, y)) { buf[lo] = y; buf[hi] = x; }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(32 * kTwWarps, kTwBlocksPerSM) k_topk_warp(const float2 *__restrict__ a, int64_t N, int k,
+                                                                 KI *__restrict__ out)
+{
+    extern __shared__ __align__(16) unsigned char tw_raw[];
+    KI *wbuf = (KI *)tw_raw;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    KI *buf = wbuf + (size_t)wid * kTwCap;
+    const KI worst = {-1.0, ~0ull};
+    const int64_t W = (int64_t)gridDim.x * kTwWarps, gw = (int64_t)blockIdx.x * kTwWarps + wid;
+    const int64_t per = (((N + W - 1) / W) + kTwStep - 1) & ~(int64_t)(kTwStep - 1);   // whole steps
+    const int64_t lo = gw * per < N ? gw * per : N, hi = lo + per < N ? lo + per : N;
+    int cnt = 0;
+    KI thr = worst;
+    float thf = -1.0f;
+    float2 nz[kTwStep / 32];
+    auto load = [&](int64_t t0) {
+#pragma unroll
+        for (int e = 0; e < kTwStep / 32; e++) {
+            const int64_t i = t0 + e * 32 + lane;
+            if (i < hi) nz[e] = a[i];
+        }
+    };
+    if (lo < hi) load(lo);
+    for (int64_t t0 = lo; t0 < hi; t0 += kTwStep) {
+        float2 cz[kTwStep / 32];
+#pragma unroll
+        for (int e = 0; e < kTwStep / 32; e++) cz[e] = nz[e];
+        if (t0 + kTwStep < hi) load(t0 + kTwStep);
+#pragma unroll
+        for (int e = 0; e < kTwStep / 32; e++) {
+            const int64_t i = t0 + e * 32 + lane;
+            KI v;
+            bool c = false;
+            if (i < hi && fmaf(cz[e].x, cz[e].x, cz[e].y * cz[e].y) >= thf) {
+                v.p = prob_of(cz[e]);
+                v.i = (uint64_t)i;
+                c = better(v, thr);
+            }
+            const unsigned m = __ballot_sync(~0u, c);
+            if (c) buf[cnt + __popc(m & ((1u << lane) - 1))] = v;
+            cnt += __popc(m);
+        }
+        if (cnt > kTwCap - kTwStep) {   // sort and cut back to k
+            __syncwarp();
+            for (int j = cnt + lane; j < kTwCap; j += 32) buf[j] = worst;
+            warp_bitonic_desc(buf, kTwCap, lane);
+            cnt = k;
+            thr = buf[k - 1];
+            thf = thr.p > 0 ? __double2float_rd(thr.p * (1.0 - 1e-5)) : -1.0f;
+        }
+    }
+    __syncwarp();
+    for (int j = cnt + lane; j < kTwCap; j += 32) buf[j] = worst;
+    warp_bitonic_desc(buf, kTwCap, lane);
+    // block merge: the warps' best k, gathered (through registers: the
+    // regions overlap) into the first 16 k entries, sorted
+    __syncthreads();
+    const int M = kTwWarps * k;
+    int P = 1;
+    while (P < M) P <<= 1;
+    KI tmp[(kTwWarps * kTwMaxK) / (32 * kTwWarps)];   // <= 4 per thread
+    int nt = 0;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) tmp[nt++] = wbuf[(size_t)(j / k) * kTwCap + j % k];
+    __syncthreads();
+    nt = 0;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) wbuf[j] = tmp[nt++];
+    for (int j = M + threadIdx.x; j < P; j += blockDim.x) wbuf[j] = worst;
+    bitonic_desc(wbuf, P);
+    for (int j = threadIdx.x; j < k; j += blockDim.x) out[(size_t)blockIdx.x * k + j] = wbuf[j];
+}
+
 __global__ void k_topk_split(const KI *in, int k, uint64_t *idx, double *p)
 {
     for (int j = threadIdx.x; j < k; j += blockDim.x) { idx[j] = in[j].i; p[j] = in[j].p; }
@@ -612,9 +720,27 @@ cudaError_t launch_topk(const void *a, int n, bool f64, int k, void *scratch, ui
     int64_t N = (int64_t)1 << n;
     int G = topk_blocks(N);
     KI *lists = (KI *)scratch;
-    KI *final_ = lists + (size_t)G * k;
-    if (f64) k_topk<double, true><<<G, kTopThreads, 0, st>>>((const double2 *)a, nullptr, N, k, lists);
-    else k_topk<float, true><<<G, kTopThreads, 0, st>>>((const float2 *)a, nullptr, N, k, lists);
+    KI *final_;
+    if (!f64 && k <= kTwMaxK && N >= (int64_t)kTwStep * kTwWarps) {
+        // blocks of independent warps, kTwBlocksPerSM per SM
+        static bool attr = false;
+        const size_t smem = (size_t)kTwWarps * kTwCap * sizeof(KI);
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_topk_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        const int64_t steps = (N + kTwStep - 1) / kTwStep;   // at most one warp per step
+        const int64_t gmax = (steps + kTwWarps - 1) / kTwWarps;
+        G = (int)((int64_t)kTwBlocksPerSM * device_sm_count() < gmax ? (int64_t)kTwBlocksPerSM * device_sm_count()
+                                                                          : gmax);
+        final_ = lists + (size_t)G * k;
+        k_topk_warp<<<G, 32 * kTwWarps, smem, st>>>((const float2 *)a, N, k, lists);
+    } else {
+        final_ = lists + (size_t)G * k;
+        if (f64) k_topk<double, true><<<G, kTopThreads, 0, st>>>((const double2 *)a, nullptr, N, k, lists);
+        else k_topk<float, true><<<G, kTopThreads, 0, st>>>((const float2 *)a, nullptr, N, k, lists);
+    }
     k_topk<float, false><<<1, kTopThreads, 0, st>>>(nullptr, lists, (int64_t)G * k, k, final_);
     k_topk_split<<<1, 256, 0, st>>>(final_, k, idx, p);
     return counted(cudaGetLastError(), 3);
