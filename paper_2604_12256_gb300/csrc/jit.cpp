@@ -328,7 +328,7 @@ Scaled scaled_form(const uint32_t *b, int sub)
 
 }  // namespace
 
-bool jit_supported(bool f64, int C, int RB) { return !f64 && C == 12 && RB == 4; }
+bool jit_supported(bool f64, int C, int RB) { return !f64 && C == 12 && (RB == 4 || RB == 5); }
 
 // CUDA source of the kernel specialised to program `w` (complex64, C = 12,
 // RB = 4).  Ops are walked as the interpreter walks them.
@@ -337,7 +337,7 @@ bool jit_source(const std::vector<uint32_t> &w, std::string &src, std::string &e
     using namespace prog;
     const int C = (int)w[H_C], RB = (int)w[H_RB], ns = (int)w[H_NSTAGE];
     if (w[H_WBYTES] != 4 || !jit_supported(false, C, RB)) {
-        err = "specialised kernels: complex64 chunk programs with C = 12, RB = 4 only";
+        err = "specialised kernels: complex64 chunk programs with C = 12, RB = 4 or 5 only";
         return false;
     }
     const int T = 1 << (C - RB), NR = 1 << RB, TB = C - RB, S = 1 + RB;

@@ -1352,7 +1352,10 @@ static void schedule(const std::vector<PGate> &G, int n, const sim_options &opt,
         return;
     }
     int C = 0, RB = 0;
-    bool blocked = (opt.flags & SIM_F_BLOCK) && chunk_shape(n, dt, opt.chunk_qubits, opt.register_bits, C, RB);
+    // kernels specialised per program hold 32 amplitudes per thread (fewer
+    // register stages per sweep); the interpreter is faster at 16
+    const int want_rb = opt.register_bits ? opt.register_bits : ((opt.flags & SIM_F_JIT) && dt == SIM_C64 ? 5 : 0);
+    bool blocked = (opt.flags & SIM_F_BLOCK) && chunk_shape(n, dt, opt.chunk_qubits, want_rb, C, RB);
     if (!blocked) {
         emit_unfused(G, n, buf, plan);
         return;

@@ -42,21 +42,26 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("rb", [4, 5])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_jit_equals_interpreter(name):
+def test_jit_equals_interpreter(name, rb):
+    """Same plan (explicit register bits), both kernels."""
     c = CASES[name]()
-    ref, st_ref = run(c, BASE)
-    got, st = run(c, BASE | S.SIM_F_JIT)
+    ref, st_ref = run(c, BASE, register_bits=rb)
+    got, st = run(c, BASE | S.SIM_F_JIT, register_bits=rb)
     assert st["chunk_ops"] > 0
     st.pop("plan_ms"), st_ref.pop("plan_ms")
     assert st == st_ref   # same plan
     assert np.max(np.abs(got - ref)) <= 1e-6
 
 
-def test_jit_against_oracle():
+@pytest.mark.parametrize("rb", [0, 4])
+def test_jit_against_oracle(rb):
+    """The default shape of specialised kernels (32 amplitudes per thread)
+    and the 16-amplitude one."""
     c = C.random_mixed(15, 250, 21)
     exp = oracle.run(c)
-    got, _ = run(c, BASE | S.SIM_F_JIT)
+    got, _ = run(c, BASE | S.SIM_F_JIT, register_bits=rb)
     got = got.astype(np.complex128)
     assert np.max(np.abs(got - exp)) <= 1e-5
     assert abs(np.vdot(got, exp)) ** 2 / (np.vdot(got, got).real * np.vdot(exp, exp).real) >= 1 - 1e-6
@@ -70,7 +75,7 @@ def test_jit_cached_and_launch_count():
     k0 = S.kernel_launches()
     b, _ = run(c, BASE | S.SIM_F_JIT)
     k1 = S.kernel_launches()
-    d, _ = run(c, BASE)
+    d, _ = run(c, BASE, register_bits=5)
     k2 = S.kernel_launches()
     assert k1 - k0 == k2 - k1
     assert np.array_equal(a, b) and np.max(np.abs(a - d)) <= 1e-6
