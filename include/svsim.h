@@ -89,14 +89,15 @@ enum {
                                restoring sweep at most).  Opt-in: fewer sweeps
                                on nearest-neighbour layered circuits, heavier
                                sweeps on random ones                          */
-    SIM_F_JIT = 1u << 6,    /* complex64 cache-blocked sweeps run kernels
-                               specialised to their program: ops decoded once
-                               on the host and compiled (NVRTC, needs
-                               libnvrtc.so.13) into straight-line code, cached
-                               per program for the process; the first apply of
-                               a new program pays its compile (~0.3 s, in
-                               parallel over a plan's programs).  Results are
-                               bit-identical to the interpreter kernel's      */
+    SIM_F_JIT = 1u << 6,    /* complex64 cache-blocked and fused-diagonal
+                               sweeps run kernels specialised to their
+                               program: ops decoded once on the host and
+                               compiled (NVRTC, needs libnvrtc.so.13) into
+                               straight-line code, cached per program for the
+                               process; the first apply of a new program pays
+                               its compile (about 0.3-1 s, in parallel over a
+                               plan's programs).  Results equal the interpreter
+                               kernels' up to rounding order                  */
     SIM_F_ALL = 0x7f
 };
 

@@ -477,12 +477,15 @@ static int execute(sim_t *s, const Plan &p, bool jit)
     // them at once, in parallel) before the first launch
     std::vector<char> use_jit(p.ops.size(), 0);
     if (jit) {
-        std::vector<const std::vector<uint32_t> *> progs;
+        std::vector<JitProg> progs;
         for (size_t i = 0; i < p.ops.size(); i++) {
             const Op &o = p.ops[i];
             if (o.kind == OPK_CHUNK && jit_supported(f64, o.prog.C, o.prog.RB)) {
                 use_jit[i] = 1;
-                progs.push_back(&o.words);
+                progs.push_back({&o.words, JIT_CHUNK});
+            } else if (o.kind == OPK_DIAG && jit_supported_diag(f64, (int)o.words[prog::H_RB])) {
+                use_jit[i] = 1;
+                progs.push_back({&o.words, JIT_DIAG});
             }
         }
         std::string err;
@@ -515,8 +518,12 @@ static int execute(sim_t *s, const Plan &p, bool jit)
                                  s->stream);
             break;
         case OPK_DIAG:
-            e = launch_diag_sweep(a, o.n, f64, (const uint32_t *)cst, prog::smem_bytes(o.words.data(), true), src,
-                                  s->stream);
+            if (use_jit[i])
+                e = launch_diag_jit(a, o.n, o.words, (const uint32_t *)cst, prog::smem_bytes(o.words.data(), true),
+                                    src, s->stream);
+            else
+                e = launch_diag_sweep(a, o.n, f64, (const uint32_t *)cst, prog::smem_bytes(o.words.data(), true),
+                                      src, s->stream);
             break;
         case OPK_PHASE_SMALL:
             e = launch_phase_small(a, o.n, f64, (const uint64_t *)cst, (int)o.terms.size(), s->stream);
@@ -725,10 +732,13 @@ int sim_jit_check(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, si
         if (!make_plan(n, dt, basis, gates, ng, o, p, err)) return fail(nullptr, SIM_EINVAL, err);
         int np = 0;
         for (const Op &op : p.ops) {
-            if (op.kind != OPK_CHUNK || !jit_supported(dt == SIM_C128, op.prog.C, op.prog.RB)) continue;
+            int kind = -1;
+            if (op.kind == OPK_CHUNK && jit_supported(dt == SIM_C128, op.prog.C, op.prog.RB)) kind = JIT_CHUNK;
+            if (op.kind == OPK_DIAG && jit_supported_diag(dt == SIM_C128, (int)op.words[prog::H_RB])) kind = JIT_DIAG;
+            if (kind < 0) continue;
             std::string src;
             std::vector<char> cubin;
-            if (!jit_source(op.words, src, err) || !jit_compile(src, cubin, err) || cubin.empty())
+            if (!jit_source(op.words, kind, src, err) || !jit_compile(src, cubin, err) || cubin.empty())
                 return fail(nullptr, SIM_EINVAL, err.empty() ? "empty cubin" : err);
             np++;
         }

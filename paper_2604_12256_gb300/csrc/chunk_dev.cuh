@@ -985,4 +985,84 @@ struct InterpOps {
     }
 };
 
+// ------------------------------------------------------------ K3 diagonal sweep
+// tile of 2^C consecutive amplitudes, C = 7 + RB: thread t holds amplitudes
+// tile + t + m * 128 (register bits on top -> each warp load is contiguous)
+// `Ops::seg` applies the sweep's one phase segment to a thread's amplitudes:
+// DiagInterp decodes it from the program, a kernel specialised to the
+// program (jit.cpp) is generated from it.
+template <typename R, int RB, typename Ops>
+__device__ __forceinline__ void diag_sweep(typename CT<R>::G2 *__restrict__ a, const uint32_t *__restrict__ gprog,
+                                           int n, TSrc<typename CT<R>::G2> src)
+{
+    using T2 = typename CT<R>::T2;
+    using G2 = typename CT<R>::G2;
+    using W = typename CT<R>::W;
+    constexpr int NR = 1 << RB;
+    constexpr int C = 7 + RB;
+    constexpr int S = 1 + RB;
+    constexpr int SCP = (int)cta_stride(RB, 7, sizeof(typename CT<R>::W));
+    extern __shared__ __align__(16) unsigned char smraw[];
+    uint32_t *prog = (uint32_t *)smraw;
+    const int tid = threadIdx.x;
+    stage_program<128>(gprog, prog, tid);
+    __syncthreads();
+    const int nd = (int)ldw(prog + H_NDSEG);
+    const int nhoist = (int)ldw(prog + H_NHOIST);
+    W *cta_buf = (W *)(prog + ((ldw(prog + H_WORDS) + 3) & ~3u));
+    const int cbw = (int)(cta_buffer_bytes(nd, RB, 7, sizeof(W)) / sizeof(W));   // words of one buffer
+    W *thr_ph = cta_buf + kCtaBuffers * cbw;
+    const uint32_t *sp = prog + ldw(prog + H_STAGE_OFF);
+    const uint32_t *op = sp + S_SIZE + O_BODY;
+    thread_sums<R, 128>(prog, thr_ph, nhoist * S, tid);
+    const int64_t ntiles = (int64_t)1 << (n - C);
+    cta_zero<R, 128>(cta_buf, 2 * cbw, tid);
+    __syncthreads();
+    if (blockIdx.x < ntiles) cta_accum<R, 128>(prog, cta_buf, (uint64_t)blockIdx.x << C, tid);
+    __syncthreads();
+    // one barrier per tile: tile i reads CTA buffer i mod 3 while the next
+    // tile's sums go to (i + 1) mod 3 (cleared during tile i - 1) and buffer
+    // (i + 2) mod 3, last read by tile i - 1, is cleared
+    int cb = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint64_t base = (uint64_t)tile << C;
+        const W *cta_ph = cta_buf + cb * cbw;
+        cta_zero<R, 128>(cta_buf + (cb == 0 ? 2 : cb - 1) * cbw, nd * SCP, tid);
+        if (tile + gridDim.x < ntiles)
+            cta_accum<R, 128>(prog, cta_buf + (cb == 2 ? 0 : cb + 1) * cbw, (uint64_t)(tile + gridDim.x) << C, tid);
+        const uint64_t x0 = base | (uint64_t)tid;
+        T2 v[NR];
+        // the tile's 2^C amplitudes share one hi factor when n_lo >= C:
+        // converted once, multiplied in the register precision
+        const bool shared_hi = src.hi && src.n_lo >= C;
+        const T2 h = shared_hi ? to_reg(__ldg(&src.hi[base >> src.n_lo])) : T2{};
+#pragma unroll
+        for (int m = 0; m < NR; m++) {
+            if (!src.hi) {
+                v[m] = to_reg(__ldcs(a + x0 + ((uint64_t)m << 7)));
+            } else if (shared_hi) {
+                const G2 l = __ldg(&src.lo[(x0 + ((uint64_t)m << 7)) & ((1ull << src.n_lo) - 1)]);
+                v[m] = cmul(h, to_reg(l));
+            } else {
+                v[m] = to_reg(tensor_amp(src, x0 + ((uint64_t)m << 7)));
+            }
+        }
+        Ops::template seg<R, RB, 128>(v, x0, prog, op, cta_ph, thr_ph, nhoist, tid);
+#pragma unroll
+        for (int m = 0; m < NR; m++) __stcs(a + x0 + ((uint64_t)m << 7), to_glob(v[m]));
+        __syncthreads();
+        cb = cb == 2 ? 0 : cb + 1;
+    }
+}
+
+struct DiagInterp {
+    template <typename R, int RB, int T>
+    static __device__ __forceinline__ void seg(typename CT<R>::T2 (&v)[1 << RB], uint64_t x0, const uint32_t *,
+                                               const uint32_t *op, const typename CT<R>::W *cta_ph,
+                                               const typename CT<R>::W *thr_ph, int nhoist, int tid)
+    {
+        dseg_apply<R, RB, T>(v, x0, op, cta_ph, thr_ph, nhoist, tid);
+    }
+};
+
 }  // namespace svs

@@ -96,6 +96,7 @@ std::string flit(uint32_t bits)
 }
 
 constexpr const char *kKernelName = "svs_chunk_jit";
+constexpr const char *kDiagKernelName = "svs_diag_jit";
 
 // ---- phase segments
 // Where each sum of a segment comes from, read off the program's tables: a
@@ -329,12 +330,57 @@ Scaled scaled_form(const uint32_t *b, int sub)
 }  // namespace
 
 bool jit_supported(bool f64, int C, int RB) { return !f64 && C == 12 && (RB == 4 || RB == 5); }
+bool jit_supported_diag(bool f64, int RB) { return !f64 && RB == 4; }
+
+// CUDA source of the fused diagonal sweep (K3) specialised to program `w`:
+// its one phase segment as generated code, the sweep as in the interpreter.
+static bool jit_source_diag(const std::vector<uint32_t> &w, std::string &src, std::string &err)
+{
+    using namespace prog;
+    const int C = (int)w[H_C], RB = (int)w[H_RB];
+    if (w[H_WBYTES] != 4 || !jit_supported_diag(false, RB) || C != 7 + RB || w[H_NSTAGE] != 1) {
+        err = "specialised kernels: complex64 diagonal sweeps with RB = 4 only";
+        return false;
+    }
+    const int TB = 7, S = 1 + RB, SCP = (int)cta_stride(RB, TB, 4);
+    const int nd = (int)w[H_NDSEG];
+    std::vector<SlotSrc> slots((size_t)nd * SCP);
+    for (uint32_t i = 0; i < w[H_NCTA]; i++) {
+        const uint32_t *e = &w[w[H_CTA_OFF] + (size_t)i * kCtaWords];
+        SlotSrc &ss = slots[e[0]];
+        if (e[2] | e[3]) ss.cta_dyn = true;
+        else ss.cst += e[4];
+    }
+    for (uint32_t i = 0; i < w[H_NTHR]; i++) {
+        const uint32_t *e = &w[w[H_THR_OFF] + (size_t)i * kThrWords];
+        slots[(size_t)(e[0] / S) * SCP + e[0] % S].thr = true;
+    }
+    const size_t body = w[H_STAGE_OFF] + S_SIZE + O_BODY;
+    std::ostringstream o;
+    o << "#include \"chunk_dev.cuh\"\nnamespace svs {\nstruct JDiag {\n"
+         "    template <typename R, int RB, int T>\n"
+         "    static __device__ __forceinline__ void seg(typename CT<R>::T2 (&v)[1 << RB], uint64_t x0,\n"
+         "        const uint32_t *prog, const uint32_t *, const typename CT<R>::W *cta_ph,\n"
+         "        const typename CT<R>::W *thr_ph, int nhoist, int tid)\n    {\n";
+    if (w[body + D_NMULTI])
+        o << "            dseg_apply<R, RB, T, 3>(v, x0, prog + " << body << ", cta_ph, thr_ph, nhoist, tid);\n";
+    else
+        gen_segment(o, w, body, slots, RB, TB, 128, SCP, 1.0L);
+    o << "    }\n};\n}  // namespace svs\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(128) " << kDiagKernelName
+      << "(svs::CT<float>::G2 *__restrict__ a, const uint32_t *__restrict__ gprog, int n, "
+         "svs::TSrc<svs::CT<float>::G2> src)\n{\n    svs::diag_sweep<float, "
+      << RB << ", svs::JDiag>(a, gprog, n, src);\n}\n";
+    src = o.str();
+    return true;
+}
 
 // CUDA source of the kernel specialised to program `w` (complex64, C = 12,
 // RB = 4).  Ops are walked as the interpreter walks them.
-bool jit_source(const std::vector<uint32_t> &w, std::string &src, std::string &err)
+bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std::string &err)
 {
     using namespace prog;
+    if (kind == JIT_DIAG) return jit_source_diag(w, src, err);
     const int C = (int)w[H_C], RB = (int)w[H_RB], ns = (int)w[H_NSTAGE];
     if (w[H_WBYTES] != 4 || !jit_supported(false, C, RB)) {
         err = "specialised kernels: complex64 chunk programs with C = 12, RB = 4 or 5 only";
@@ -520,7 +566,10 @@ std::mutex g_mu;
 std::map<std::string, std::shared_ptr<JitKernel>> g_cache;
 double g_compile_ms = 0;   // wall time of jit_prepare's compiles
 
-std::string key_of(const std::vector<uint32_t> &w) { return std::string((const char *)w.data(), w.size() * 4); }
+std::string key_of(const std::vector<uint32_t> &w, int kind)
+{
+    return std::string(1, (char)('0' + kind)) + std::string((const char *)w.data(), w.size() * 4);
+}
 
 std::shared_ptr<JitKernel> lookup(const std::string &key)
 {
@@ -530,16 +579,16 @@ std::shared_ptr<JitKernel> lookup(const std::string &key)
 }
 
 // compile and load one program's kernel into the cache
-bool build_one(const std::vector<uint32_t> &w, std::string &err)
+bool build_one(const std::vector<uint32_t> &w, int kind, std::string &err)
 {
-    const std::string key = key_of(w);
+    const std::string key = key_of(w, kind);
     if (lookup(key)) return true;
     std::string src;
     std::vector<char> cubin;
-    if (!jit_source(w, src, err) || !jit_compile(src, cubin, err)) return false;
+    if (!jit_source(w, kind, src, err) || !jit_compile(src, cubin, err)) return false;
     auto k = std::make_shared<JitKernel>();
     cudaError_t e = cudaLibraryLoadData(&k->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
-    if (e == cudaSuccess) e = cudaLibraryGetKernel(&k->kern, k->lib, kKernelName);
+    if (e == cudaSuccess) e = cudaLibraryGetKernel(&k->kern, k->lib, kind == JIT_DIAG ? kDiagKernelName : kKernelName);
     if (e != cudaSuccess) {
         err = std::string("loading a specialised kernel: ") + cudaGetErrorString(e);
         return false;
@@ -551,14 +600,14 @@ bool build_one(const std::vector<uint32_t> &w, std::string &err)
 
 }  // namespace
 
-bool jit_prepare(const std::vector<const std::vector<uint32_t> *> &progs, std::string &err)
+bool jit_prepare(const std::vector<JitProg> &progs, std::string &err)
 {
-    std::vector<const std::vector<uint32_t> *> todo;
-    for (const auto *w : progs)
-        if (!lookup(key_of(*w))) {
+    std::vector<JitProg> todo;
+    for (const JitProg &p : progs)
+        if (!lookup(key_of(*p.w, p.kind))) {
             bool dup = false;
-            for (const auto *x : todo) dup = dup || *x == *w;
-            if (!dup) todo.push_back(w);
+            for (const JitProg &x : todo) dup = dup || (x.kind == p.kind && *x.w == *p.w);
+            if (!dup) todo.push_back(p);
         }
     if (todo.empty()) return true;
     const auto t0 = std::chrono::steady_clock::now();
@@ -568,7 +617,7 @@ bool jit_prepare(const std::vector<const std::vector<uint32_t> *> &progs, std::s
     std::vector<std::thread> th;
     for (size_t t = 0; t < nt; t++)
         th.emplace_back([&, t] {
-            for (size_t i = t; i < todo.size(); i += nt) build_one(*todo[i], errs[i]);
+            for (size_t i = t; i < todo.size(); i += nt) build_one(*todo[i].w, todo[i].kind, errs[i]);
         });
     for (auto &x : th) x.join();
     {
@@ -593,7 +642,7 @@ size_t jit_cache_size(double *compile_ms)
 cudaError_t launch_chunk_jit(void *a, int n, const std::vector<uint32_t> &w, const uint32_t *prog, size_t smem,
                              TensorSrc src, cudaStream_t st)
 {
-    std::shared_ptr<JitKernel> k = lookup(key_of(w));
+    std::shared_ptr<JitKernel> k = lookup(key_of(w, JIT_CHUNK));
     if (!k) return cudaErrorInvalidDeviceFunction;   // jit_prepare first
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -620,6 +669,42 @@ cudaError_t launch_chunk_jit(void *a, int n, const std::vector<uint32_t> &w, con
     } ts{src.hi, src.lo, src.n_lo};
     void *args[] = {&a, (void *)&prog, &n, &ts};
     e = cudaLaunchKernel((const void *)k->kern, dim3(grid), dim3(1 << (C - RB)), args, smem, st);
+    return counted(e, 1);
+}
+
+// The specialised fused diagonal sweep: tiles of 2^(7 + RB) amplitudes, 128
+// threads, grid = resident CTAs x SMs (as launch_diag_sweep).
+cudaError_t launch_diag_jit(void *a, int n, const std::vector<uint32_t> &w, const uint32_t *prog, size_t smem,
+                            TensorSrc src, cudaStream_t st)
+{
+    std::shared_ptr<JitKernel> k = lookup(key_of(w, JIT_DIAG));
+    if (!k) return cudaErrorInvalidDeviceFunction;   // jit_prepare first
+    if (src.hi && (src.n_lo < 0 || src.n_lo > n || !src.lo)) return cudaErrorInvalidValue;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!((k->dev_mask >> dev) & 1)) {
+            e = cudaKernelSetAttributeForDevice(k->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024, dev);
+            if (e != cudaSuccess) return e;
+            k->dev_mask |= 1u << dev;
+        }
+    }
+    const int C = (int)w[prog::H_C];
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)k->kern, 128, smem);
+    if (e != cudaSuccess) return e;
+    if (occ <= 0) return cudaErrorInvalidConfiguration;
+    const int64_t work = (int64_t)1 << (n - C);
+    const int64_t g = (int64_t)device_sm_count() * occ;
+    const int grid = (int)(g < work ? g : work);
+    struct {
+        const void *hi, *lo;
+        int n_lo;
+    } ts{src.hi, src.lo, src.n_lo};
+    void *args[] = {&a, (void *)&prog, &n, &ts};
+    e = cudaLaunchKernel((const void *)k->kern, dim3(grid), dim3(128), args, smem, st);
     return counted(e, 1);
 }
 

@@ -80,13 +80,23 @@ cudaError_t launch_chunk(void *a, int n, bool is_f64, int C, int RB, const uint3
 // host programs that are not cached yet, in parallel; launch_chunk_jit runs
 // the cached kernel of host program `w` (device copy `prog`), with the same
 // arguments and results as launch_chunk.
+// Fused diagonal sweeps (K3, complex64, RB = 4) likewise: launch_diag_jit
+// has launch_diag_sweep's arguments and results.
+enum { JIT_CHUNK = 0, JIT_DIAG = 1 };
+struct JitProg {
+    const std::vector<uint32_t> *w;   // host program words
+    int kind;                         // JIT_CHUNK or JIT_DIAG
+};
 bool jit_supported(bool is_f64, int C, int RB);
-bool jit_prepare(const std::vector<const std::vector<uint32_t> *> &progs, std::string &err);
+bool jit_supported_diag(bool is_f64, int RB);
+bool jit_prepare(const std::vector<JitProg> &progs, std::string &err);
 cudaError_t launch_chunk_jit(void *a, int n, const std::vector<uint32_t> &w, const uint32_t *prog, size_t smem,
                              TensorSrc src, cudaStream_t st);
+cudaError_t launch_diag_jit(void *a, int n, const std::vector<uint32_t> &w, const uint32_t *prog, size_t smem,
+                            TensorSrc src, cudaStream_t st);
 size_t jit_cache_size(double *compile_ms);   // kernels cached, total compile wall time
 // the generated source and its NVRTC compile (no device needed)
-bool jit_source(const std::vector<uint32_t> &w, std::string &src, std::string &err);
+bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std::string &err);
 bool jit_compile(const std::string &src, std::vector<char> &cubin, std::string &err);
 
 // Phase polynomial on small registers: one thread per amplitude sums the

@@ -39,6 +39,7 @@ CASES = {
     "mixed16": lambda: C.random_mixed(16, 300, 11),
     "mixed14": lambda: C.random_mixed(14, 400, 12),
     "supremacy16": lambda: C.supremacy(16, 8, 13),
+    "rzz_full16": lambda: C.rzz_full(16, 14),   # a fused diagonal sweep (K3) fed by the booster
 }
 
 
@@ -49,7 +50,7 @@ def test_jit_equals_interpreter(name, rb):
     c = CASES[name]()
     ref, st_ref = run(c, BASE, register_bits=rb)
     got, st = run(c, BASE | S.SIM_F_JIT, register_bits=rb)
-    assert st["chunk_ops"] > 0
+    assert st["chunk_ops"] + st["diag_ops"] > 0
     st.pop("plan_ms"), st_ref.pop("plan_ms")
     assert st == st_ref   # same plan
     assert np.max(np.abs(got - ref)) <= 1e-6
