@@ -313,13 +313,14 @@ def run_gpu(args, rank, world, dist):
     if kind == "dense":
         kname = "k_dense5_tc (dense 5-qubit block, tcgen05 split-TF32)" if args.precision == "tf32x3" \
             and dt == S.SIM_C64 else "k_dense5_fma (dense 5-qubit block, CUDA cores)"
-    jit_on = kind == "chunk" and bool(opt.flags & S.SIM_F_JIT)
-    ksrc = {"chunk": ("chunk_dev.cuh", "jit.cpp") if jit_on else ("chunk_dev.cuh",), "diag": ("chunk_dev.cuh",),
-            "dense": ("k_dense5.cu",)}.get(kind, ("k_basic.cu",))
+    jit_on = kind in ("chunk", "diag") and bool(opt.flags & S.SIM_F_JIT) and dt == S.SIM_C64
+    ksrc = {"chunk": ("chunk_dev.cuh",), "diag": ("chunk_dev.cuh",),
+            "dense": ("k_dense5.cu",)}.get(kind, ("k_basic.cu",)) + (("jit.cpp",) if jit_on else ())
     src = b"".join(open(os.path.join(ROOT, "paper_2604_12256_gb300", "csrc", f), "rb").read() for f in ksrc)
-    tpa = TRAFFIC_PER_AMP.get((args.workload, "chunk-jit" if jit_on else kind, hashlib.sha256(src).hexdigest()))
+    tpa = TRAFFIC_PER_AMP.get((args.workload, kind + ("-jit" if jit_on else ""), hashlib.sha256(src).hexdigest()))
     if jit_on:
-        kname = "svs_chunk_jit (cache-blocked chunk sweep specialised to its program)"
+        kname = ("svs_chunk_jit (cache-blocked chunk sweep specialised to its program)" if kind == "chunk" else
+                 "svs_diag_jit (fused-diagonal sweep specialised to its program)")
     if (dense and args.precision != "tf32x3") or args.dtype != "c64":
         tpa = None   # captured on complex64 (and the tensor-core variant) only
     traffic = tpa * amps if tpa is not None else None
