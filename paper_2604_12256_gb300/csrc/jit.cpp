@@ -1,20 +1,28 @@
-// jit.cpp -- chunk-sweep kernels specialised to one program at run time.
+// jit.cpp -- sweep kernels specialised to one program at run time.
 //
-// The interpreter kernel (k_chunk.cu) decodes every op of every stage from
+// The interpreter kernels (k_chunk.cu) decode every op of every stage from
 // the program in shared memory for every chunk: a branch tree over the op's
-// register positions and subtype, and loads of its header and matrix.  For a
-// program that is swept many times this work is the same each time, so the
-// specialised kernel does it once, on the host: its source lists the stage
-// layouts and the ops as straight-line calls of the same device templates
-// (chunk_dev.cuh), with compile-time register positions and the 2x2 matrices
-// of one-qubit ops as literals.  The phase tables, term lists and per-chunk
-// sums stay in the staged program, exactly as the interpreter reads them, so
-// both kernels compute the same arithmetic in the same order: their results
-// are bit-identical.
+// register positions and subtype, loads of its header and matrix, loops over
+// phase terms.  For a program that is swept many times this work is the same
+// each time, so the specialised kernel does it once, on the host.  Its source
+// instantiates the same sweep templates (chunk_dev.cuh: chunk_sweep,
+// diag_sweep) with:
+// - the stage layouts and the ops as straight-line calls, register positions
+//   compile-time, 2x2 and 4x4 matrices as literals, exact identity ops
+//   dropped;
+// - phase segments generated from the program's CTA and thread tables (zero
+//   and constant sums folded on the host, only the per-chunk sums needed
+//   read, a product table over the register bits that carry a phase);
+// - H-, RY- and RX-like one-qubit ops without their scalar (one packed f32x2
+//   instruction per output amplitude), the sweep's product of scalars
+//   applied once;
+// - direct first and last stages where the program's layouts allow them.
+// The arithmetic is the interpreter's up to the rounding order of those
+// rewrites; the results agree to a few float ulps.
 //
 // Compilation uses NVRTC (loaded with dlopen, so the library loads without
 // it) to a sm_103a cubin, loaded with cudaLibraryLoadData; kernels are cached
-// per program (its words) for the life of the process.
+// per program (its kind and words) for the life of the process.
 #include <cuda_runtime.h>
 #include <dlfcn.h>
 #include <nvrtc.h>
