@@ -44,13 +44,13 @@ WORKLOAD = "28-qubit diagonal-heavy gate-level stream (500 gates, 80% RZ/CP/RZZ,
 TRAFFIC_PER_AMP = {
     # profiles/svs_chunk_jit_diagheavy_25q.md: 475.97 MB per 2^25-amplitude sweep
     # (the specialised kernel: keyed by its device templates and generator)
-    ("diag-heavy", "chunk-jit", "5bdfa1e5944a54d3aecb7b79c9413ba5804d8b77fc59b3c59c46ec6ef9e47327"): 475.97e6 / 2 ** 25,
+    ("diag-heavy", "chunk-jit", "359062f70d7e6966f803d6dcbb4c08f0795e984a9309e29795f9a2ea43905579"): 475.97e6 / 2 ** 25,
     # profiles/k_chunk_diagheavy_25q.md: 476.05 MB per 2^25-amplitude sweep (interpreter)
     ("diag-heavy", "chunk", "8f96366b3d7184491700fbf33588aba4d28412cc874eee7e00ed69b7789963a2"): 476.05e6 / 2 ** 25,
     # profiles/k_dense5_tc_layered_26q.md: 1011.84 MB per 2^26-amplitude block sweep
     ("layered-dense", "dense", "902dcf26ad8abd672acf4f9ec16df78b31986b3b9a62774a4456ee0248f2943f"): 1011.84e6 / 2 ** 26,
     # profiles/svs_diag_jit_rzzfull_26q.md: 475.18 MB per write-only 2^26-amplitude sweep
-    ("rzz-full", "diag-jit", "5bdfa1e5944a54d3aecb7b79c9413ba5804d8b77fc59b3c59c46ec6ef9e47327"): 475.18e6 / 2 ** 26,
+    ("rzz-full", "diag-jit", "359062f70d7e6966f803d6dcbb4c08f0795e984a9309e29795f9a2ea43905579"): 475.18e6 / 2 ** 26,
     # profiles/k_diag_rzzfull_26q.md: 475.29 MB per write-only 2^26-amplitude sweep (interpreter)
     ("rzz-full", "diag", "8f96366b3d7184491700fbf33588aba4d28412cc874eee7e00ed69b7789963a2"): 475.29e6 / 2 ** 26,
 }
