@@ -608,18 +608,23 @@ __global__ void __launch_bounds__(kTopThreads) k_topk(const typename Cx<R>::T *_
 }
 
 // ---- complex64, k <= 128: warps that never wait for each other.  Each warp
-// streams its own contiguous slice of the state (kTwStep amplitudes per
-// step, the next step's loads in flight) and keeps its candidates in its own
-// shared-memory buffer: lanes that beat the warp's threshold (a float
-// pre-filter, then the exact (p, index) order) are placed by ballot and
-// prefix count; when the buffer could overflow the warp sorts it (bitonic,
+// streams its own contiguous slice of the state, kTwStep amplitudes per step
+// in 16-byte loads (two amplitudes per load, eight per lane), with the next
+// step's loads in flight.  A float pre-filter against the warp's threshold
+// marks the lanes' candidates; one vote skips the rest of the step when
+// there are none (the common case once the threshold has risen).  Otherwise
+// the candidates are tested in the exact (p, index) order and placed by
+// ballot and prefix count into the warp's shared-memory buffer, half a step
+// at a time; when the buffer could overflow the warp sorts it (bitonic,
 // warp-synchronous) and cuts it to its best k.  The block then merges its
 // warps' lists, and the single-block pass merges the blocks'.
 constexpr int kTwWarps = 16;    // warps per block
-constexpr int kTwStep = 128;    // amplitudes per warp step (4 per lane; the next step's loads in flight)
-constexpr int kTwCap = 256;     // candidate buffer per warp (>= 128 kept + one step)
-constexpr int kTwBlocksPerSM = 2;   // 32 warps per SM: enough loads in flight to cover the HBM latency
+constexpr int kTwStep = 256;    // amplitudes per warp step (8 per lane in 4 16-byte loads)
+constexpr int kTwHalf = kTwStep / 2;   // candidates placed between overflow checks
+constexpr int kTwCap = 256;     // candidate buffer per warp (>= 128 kept + half a step)
+constexpr int kTwBlocksPerSM = 2;   // 32 warps per SM, 2 KB of loads in flight each
 constexpr int kTwMaxK = 128;
+static_assert(kTwCap >= kTwMaxK + kTwHalf && kTwStep % 64 == 0, "a half step must fit above the kept k");
 
 __device__ __forceinline__ void warp_bitonic_desc(KI *buf, int cap, int lane)
 {
@@ -651,41 +656,54 @@ __global__ void __launch_bounds__(32 * kTwWarps, kTwBlocksPerSM) k_topk_warp(con
     int cnt = 0;
     KI thr = worst;
     float thf = -1.0f;
-    float2 nz[kTwStep / 32];
+    // lo, hi and every step start are multiples of kTwStep (N is a power of
+    // two >= kTwStep * kTwWarps), so a step never straddles hi and each
+    // 16-byte load holds amplitudes 2j, 2j + 1 of the slice
+    const float4 *a4 = (const float4 *)a;
+    constexpr int kL = kTwStep / 64;   // 16-byte loads per lane per step
+    float4 nz[kL];
     auto load = [&](int64_t t0) {
 #pragma unroll
-        for (int e = 0; e < kTwStep / 32; e++) {
-            const int64_t i = t0 + e * 32 + lane;
-            if (i < hi) nz[e] = a[i];
-        }
+        for (int e = 0; e < kL; e++) nz[e] = a4[(t0 >> 1) + e * 32 + lane];
     };
     if (lo < hi) load(lo);
     for (int64_t t0 = lo; t0 < hi; t0 += kTwStep) {
-        float2 cz[kTwStep / 32];
+        float2 cz[2 * kL];
 #pragma unroll
-        for (int e = 0; e < kTwStep / 32; e++) cz[e] = nz[e];
-        if (t0 + kTwStep < hi) load(t0 + kTwStep);
-#pragma unroll
-        for (int e = 0; e < kTwStep / 32; e++) {
-            const int64_t i = t0 + e * 32 + lane;
-            KI v;
-            bool c = false;
-            if (i < hi && fmaf(cz[e].x, cz[e].x, cz[e].y * cz[e].y) >= thf) {
-                v.p = prob_of(cz[e]);
-                v.i = (uint64_t)i;
-                c = better(v, thr);
-            }
-            const unsigned m = __ballot_sync(~0u, c);
-            if (c) buf[cnt + __popc(m & ((1u << lane) - 1))] = v;
-            cnt += __popc(m);
+        for (int e = 0; e < kL; e++) {
+            cz[2 * e] = make_float2(nz[e].x, nz[e].y);
+            cz[2 * e + 1] = make_float2(nz[e].z, nz[e].w);
         }
-        if (cnt > kTwCap - kTwStep) {   // sort and cut back to k
-            __syncwarp();
-            for (int j = cnt + lane; j < kTwCap; j += 32) buf[j] = worst;
-            warp_bitonic_desc(buf, kTwCap, lane);
-            cnt = k;
-            thr = buf[k - 1];
-            thf = thr.p > 0 ? __double2float_rd(thr.p * (1.0 - 1e-5)) : -1.0f;
+        if (t0 + kTwStep < hi) load(t0 + kTwStep);
+        // element f of this lane is amplitude t0 + 64 (f / 2) + 2 lane + (f & 1)
+        unsigned pass = 0;
+#pragma unroll
+        for (int f = 0; f < 2 * kL; f++)
+            if (fmaf(cz[f].x, cz[f].x, cz[f].y * cz[f].y) >= thf) pass |= 1u << f;
+        if (!__any_sync(~0u, pass != 0)) continue;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+#pragma unroll
+            for (int f = h * kL; f < (h + 1) * kL; f++) {
+                KI v;
+                bool c = false;
+                if ((pass >> f) & 1) {
+                    v.p = prob_of(cz[f]);
+                    v.i = (uint64_t)(t0 + 64 * (f >> 1) + 2 * lane + (f & 1));
+                    c = better(v, thr);
+                }
+                const unsigned m = __ballot_sync(~0u, c);
+                if (c) buf[cnt + __popc(m & ((1u << lane) - 1))] = v;
+                cnt += __popc(m);
+            }
+            if (cnt > kTwCap - kTwHalf) {   // sort and cut back to k
+                __syncwarp();
+                for (int j = cnt + lane; j < kTwCap; j += 32) buf[j] = worst;
+                warp_bitonic_desc(buf, kTwCap, lane);
+                cnt = k;
+                thr = buf[k - 1];
+                thf = thr.p > 0 ? __double2float_rd(thr.p * (1.0 - 1e-5)) : -1.0f;
+            }
         }
     }
     __syncwarp();
@@ -721,7 +739,7 @@ cudaError_t launch_topk(const void *a, int n, bool f64, int k, void *scratch, ui
     int G = topk_blocks(N);
     KI *lists = (KI *)scratch;
     KI *final_;
-    if (!f64 && k <= kTwMaxK && N >= (int64_t)kTwStep * kTwWarps) {
+    if (!f64 && k <= kTwMaxK && N >= (int64_t)kTwStep * kTwWarps && ((uintptr_t)a & 15) == 0) {
         // blocks of independent warps, kTwBlocksPerSM per SM
         static bool attr = false;
         const size_t smem = (size_t)kTwWarps * kTwCap * sizeof(KI);
