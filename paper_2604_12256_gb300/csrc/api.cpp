@@ -630,10 +630,18 @@ int sim_top_k(sim_t *s, int k, uint64_t *idx, double *prob)
     unsigned char *base = (unsigned char *)s->d_topk;
     uint64_t *di = (uint64_t *)(base + topk_scratch_bytes(1024));
     double *dp = (double *)(di + 1024);
-    CK(s, launch_topk(s->state, s->n, s->dt == SIM_C128, kk, base, di, dp, s->stream));
-    CK(s, cudaMemcpyAsync(idx, di, sizeof(uint64_t) * kk, cudaMemcpyDeviceToHost, s->stream));
-    CK(s, cudaMemcpyAsync(prob, dp, sizeof(double) * kk, cudaMemcpyDeviceToHost, s->stream));
-    CK(s, cudaStreamSynchronize(s->stream));
+    // first with warps that keep only their best kTopWarpKeep candidates;
+    // again with the exact kernel if a warp slice could have lost one
+    const int keep = kk > kTopWarpKeep ? kTopWarpKeep : 0;
+    int64_t slice = 0;
+    for (int pass = 0; pass < 2; pass++) {
+        CK(s, launch_topk(s->state, s->n, s->dt == SIM_C128, kk, base, di, dp, s->stream, pass ? 0 : keep,
+                          pass ? nullptr : &slice));
+        CK(s, cudaMemcpyAsync(idx, di, sizeof(uint64_t) * kk, cudaMemcpyDeviceToHost, s->stream));
+        CK(s, cudaMemcpyAsync(prob, dp, sizeof(double) * kk, cudaMemcpyDeviceToHost, s->stream));
+        CK(s, cudaStreamSynchronize(s->stream));
+        if (pass || !topk_warp_suspect(idx, kk, slice, keep)) break;
+    }
     for (int i = kk; i < k; i++) { idx[i] = UINT64_MAX; prob[i] = -1.0; }
     return SIM_OK;
 }

@@ -4,8 +4,10 @@
 // merge booster (Algorithm 7 / Algorithm 5 first branch) and the read-out
 // reductions (norm, <Z-string>, probabilities, top-k) in FP64 accumulation
 // with a fixed reduction order.
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
+#include <vector>
 
 #include "kernels.h"
 
@@ -614,21 +616,34 @@ __global__ void __launch_bounds__(kTopThreads) k_topk(const typename Cx<R>::T *_
 // marks the lanes' candidates; one vote skips the rest of the step when
 // there are none (the common case once the threshold has risen).  Otherwise
 // the candidates are tested in the exact (p, index) order and placed by
-// ballot and prefix count into the warp's shared-memory buffer, half a step
-// at a time; when the buffer could overflow the warp sorts it (bitonic,
-// warp-synchronous) and cuts it to its best k.  The block then merges its
-// warps' lists, and the single-block pass merges the blocks'.
+// ballot and prefix count into the warp's shared-memory buffer of CAP
+// entries, FPC x 32 at a time; when the buffer could overflow the warp sorts
+// it (bitonic, warp-synchronous) and cuts it to its best kw.  The block then
+// merges its warps' lists into its best k, and the single-block pass merges
+// the blocks'.
+//
+// A warp that keeps its best kw = k is exact.  Keeping fewer (kw = 16, a
+// 64-entry buffer) cuts the sorts, which bound this kernel, about tenfold: a
+// warp inserts about kw ln(slice / kw) candidates.  It is exact unless a
+// warp dropped an element of the true top k, and that needs all kw of the
+// warp's kept entries to be in the top k too (each beats the dropped one);
+// the caller checks that on the result and reruns with kw = k if so.
 constexpr int kTwWarps = 16;    // warps per block
 constexpr int kTwStep = 256;    // amplitudes per warp step (8 per lane in 4 16-byte loads)
-constexpr int kTwHalf = kTwStep / 2;   // candidates placed between overflow checks
-constexpr int kTwCap = 256;     // candidate buffer per warp (>= 128 kept + half a step)
 constexpr int kTwBlocksPerSM = 2;   // 32 warps per SM, 2 KB of loads in flight each
 constexpr int kTwMaxK = 128;
-static_assert(kTwCap >= kTwMaxK + kTwHalf && kTwStep % 64 == 0, "a half step must fit above the kept k");
+constexpr int kTwCap = 256;     // exact mode: >= 128 kept + 128 placed between checks (FPC = 4)
+constexpr int kTwCapKeep = 64;  // reduced mode: >= 32 kept + 32 placed between checks (FPC = 1)
+static_assert(kTwStep % 64 == 0 && kTwCap >= kTwMaxK + 4 * 32 && kTwCapKeep >= 32 + 32, "buffer sizes");
+static_assert(kTwWarps * kTopWarpKeep >= kTwMaxK && kTopWarpKeep <= 32, "a block's warps keep at least k");
 
+// (stage loops kept rolled: the sort is inlined at every overflow check of
+// the unrolled placement loop)
 __device__ __forceinline__ void warp_bitonic_desc(KI *buf, int cap, int lane)
 {
+#pragma unroll 1
     for (int size = 2; size <= cap; size <<= 1) {
+#pragma unroll 1
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
             __syncwarp();
             for (int t = lane; t < cap / 2; t += 32) {
@@ -642,13 +657,14 @@ __device__ __forceinline__ void warp_bitonic_desc(KI *buf, int cap, int lane)
     __syncwarp();
 }
 
+template <int CAP, int FPC>
 __global__ void __launch_bounds__(32 * kTwWarps, kTwBlocksPerSM) k_topk_warp(const float2 *__restrict__ a, int64_t N, int k,
-                                                                 KI *__restrict__ out)
+                                                                 int kw, KI *__restrict__ out)
 {
     extern __shared__ __align__(16) unsigned char tw_raw[];
     KI *wbuf = (KI *)tw_raw;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    KI *buf = wbuf + (size_t)wid * kTwCap;
+    KI *buf = wbuf + (size_t)wid * CAP;
     const KI worst = {-1.0, ~0ull};
     const int64_t W = (int64_t)gridDim.x * kTwWarps, gw = (int64_t)blockIdx.x * kTwWarps + wid;
     const int64_t per = (((N + W - 1) / W) + kTwStep - 1) & ~(int64_t)(kTwStep - 1);   // whole steps
@@ -682,42 +698,39 @@ __global__ void __launch_bounds__(32 * kTwWarps, kTwBlocksPerSM) k_topk_warp(con
             if (fmaf(cz[f].x, cz[f].x, cz[f].y * cz[f].y) >= thf) pass |= 1u << f;
         if (!__any_sync(~0u, pass != 0)) continue;
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-#pragma unroll
-            for (int f = h * kL; f < (h + 1) * kL; f++) {
-                KI v;
-                bool c = false;
-                if ((pass >> f) & 1) {
-                    v.p = prob_of(cz[f]);
-                    v.i = (uint64_t)(t0 + 64 * (f >> 1) + 2 * lane + (f & 1));
-                    c = better(v, thr);
-                }
-                const unsigned m = __ballot_sync(~0u, c);
-                if (c) buf[cnt + __popc(m & ((1u << lane) - 1))] = v;
-                cnt += __popc(m);
+        for (int f = 0; f < 2 * kL; f++) {
+            KI v;
+            bool c = false;
+            if ((pass >> f) & 1) {
+                v.p = prob_of(cz[f]);
+                v.i = (uint64_t)(t0 + 64 * (f >> 1) + 2 * lane + (f & 1));
+                c = better(v, thr);
             }
-            if (cnt > kTwCap - kTwHalf) {   // sort and cut back to k
+            const unsigned m = __ballot_sync(~0u, c);
+            if (c) buf[cnt + __popc(m & ((1u << lane) - 1))] = v;
+            cnt += __popc(m);
+            if ((f + 1) % FPC == 0 && cnt > CAP - 32 * FPC) {   // sort and cut back to kw
                 __syncwarp();
-                for (int j = cnt + lane; j < kTwCap; j += 32) buf[j] = worst;
-                warp_bitonic_desc(buf, kTwCap, lane);
-                cnt = k;
-                thr = buf[k - 1];
+                for (int j = cnt + lane; j < CAP; j += 32) buf[j] = worst;
+                warp_bitonic_desc(buf, CAP, lane);
+                cnt = kw;
+                thr = buf[kw - 1];
                 thf = thr.p > 0 ? __double2float_rd(thr.p * (1.0 - 1e-5)) : -1.0f;
             }
         }
     }
     __syncwarp();
-    for (int j = cnt + lane; j < kTwCap; j += 32) buf[j] = worst;
-    warp_bitonic_desc(buf, kTwCap, lane);
-    // block merge: the warps' best k, gathered (through registers: the
-    // regions overlap) into the first 16 k entries, sorted
+    for (int j = cnt + lane; j < CAP; j += 32) buf[j] = worst;
+    warp_bitonic_desc(buf, CAP, lane);
+    // block merge: the warps' best kw, gathered (through registers: the
+    // regions overlap) into the first 16 kw entries, sorted; the block's best k
     __syncthreads();
-    const int M = kTwWarps * k;
+    const int M = kTwWarps * kw;
     int P = 1;
     while (P < M) P <<= 1;
     KI tmp[(kTwWarps * kTwMaxK) / (32 * kTwWarps)];   // <= 4 per thread
     int nt = 0;
-    for (int j = threadIdx.x; j < M; j += blockDim.x) tmp[nt++] = wbuf[(size_t)(j / k) * kTwCap + j % k];
+    for (int j = threadIdx.x; j < M; j += blockDim.x) tmp[nt++] = wbuf[(size_t)(j / kw) * CAP + j % kw];
     __syncthreads();
     nt = 0;
     for (int j = threadIdx.x; j < M; j += blockDim.x) wbuf[j] = tmp[nt++];
@@ -726,34 +739,52 @@ __global__ void __launch_bounds__(32 * kTwWarps, kTwBlocksPerSM) k_topk_warp(con
     for (int j = threadIdx.x; j < k; j += blockDim.x) out[(size_t)blockIdx.x * k + j] = wbuf[j];
 }
 
+bool topk_warp_suspect(const uint64_t *idx, int k, int64_t slice, int keep)
+{
+    if (slice <= 0 || keep <= 0 || k < keep) return false;
+    std::vector<uint64_t> w(idx, idx + k);
+    for (uint64_t &x : w) x /= (uint64_t)slice;
+    std::sort(w.begin(), w.end());
+    for (int i = 0; i + keep <= k; i++)
+        if (w[i] == w[i + keep - 1]) return true;
+    return false;
+}
+
 __global__ void k_topk_split(const KI *in, int k, uint64_t *idx, double *p)
 {
     for (int j = threadIdx.x; j < k; j += blockDim.x) { idx[j] = in[j].i; p[j] = in[j].p; }
 }
 
 cudaError_t launch_topk(const void *a, int n, bool f64, int k, void *scratch, uint64_t *idx, double *p,
-                        cudaStream_t st)
+                        cudaStream_t st, int warp_keep, int64_t *warp_slice)
 {
     if (k < 1 || k > 1024) return cudaErrorInvalidValue;
+    if (warp_slice) *warp_slice = 0;
     int64_t N = (int64_t)1 << n;
     int G = topk_blocks(N);
     KI *lists = (KI *)scratch;
     KI *final_;
     if (!f64 && k <= kTwMaxK && N >= (int64_t)kTwStep * kTwWarps && ((uintptr_t)a & 15) == 0) {
         // blocks of independent warps, kTwBlocksPerSM per SM
-        static bool attr = false;
-        const size_t smem = (size_t)kTwWarps * kTwCap * sizeof(KI);
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(k_topk_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
         const int64_t steps = (N + kTwStep - 1) / kTwStep;   // at most one warp per step
         const int64_t gmax = (steps + kTwWarps - 1) / kTwWarps;
         G = (int)((int64_t)kTwBlocksPerSM * device_sm_count() < gmax ? (int64_t)kTwBlocksPerSM * device_sm_count()
                                                                           : gmax);
         final_ = lists + (size_t)G * k;
-        k_topk_warp<<<G, 32 * kTwWarps, smem, st>>>((const float2 *)a, N, k, lists);
+        const bool keep = warp_keep == kTopWarpKeep && warp_keep < k;
+        static bool attr[2] = {false, false};
+        const size_t smem = (size_t)kTwWarps * (keep ? kTwCapKeep : kTwCap) * sizeof(KI);
+        auto kern = keep ? k_topk_warp<kTwCapKeep, 1> : k_topk_warp<kTwCap, 4>;
+        if (!attr[keep]) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr[keep] = true;
+        }
+        kern<<<G, 32 * kTwWarps, smem, st>>>((const float2 *)a, N, k, keep ? warp_keep : k, lists);
+        if (keep && warp_slice) {   // the warps' slice length, as the kernel computes it
+            const int64_t W = (int64_t)G * kTwWarps;
+            *warp_slice = (((N + W - 1) / W) + kTwStep - 1) & ~(int64_t)(kTwStep - 1);
+        }
     } else {
         final_ = lists + (size_t)G * k;
         if (f64) k_topk<double, true><<<G, kTopThreads, 0, st>>>((const double2 *)a, nullptr, N, k, lists);

@@ -50,10 +50,20 @@ cudaError_t launch_expect_z(const void *a, int n, bool is_f64, const uint64_t *m
 // p_x for all x -> out_dev[2^n]
 cudaError_t launch_probs(const void *a, int n, bool is_f64, double *out_dev, cudaStream_t st);
 // top-k (k <= 1024): scratch must hold topk_scratch_bytes(k); results to
-// idx_dev[k], p_dev[k] (largest first, ties to the lower index)
+// idx_dev[k], p_dev[k] (largest first, ties to the lower index).
+// warp_keep = kTopWarpKeep (< k) lets the complex64 kernel's warps keep only
+// their best kTopWarpKeep candidates; *warp_slice then receives the
+// amplitudes per warp slice (else 0), and the result is exact unless
+// topk_warp_suspect() holds for it, when the call must be repeated with
+// warp_keep = 0.
+constexpr int kTopWarpKeep = 16;
 size_t topk_scratch_bytes(int k);
 cudaError_t launch_topk(const void *a, int n, bool is_f64, int k, void *scratch,
-                        uint64_t *idx_dev, double *p_dev, cudaStream_t st);
+                        uint64_t *idx_dev, double *p_dev, cudaStream_t st, int warp_keep = 0,
+                        int64_t *warp_slice = nullptr);
+// true when some warp slice holds >= keep of the k result indices (it may
+// have dropped an element of the true top k)
+bool topk_warp_suspect(const uint64_t *idx, int k, int64_t slice, int keep);
 
 // ---- optimizer-driven sweeps ----
 // Optional input of a sweep: instead of reading the state, amplitude x is

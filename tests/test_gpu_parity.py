@@ -165,6 +165,45 @@ def test_topk_large_random_state(dtype, k):
     np.testing.assert_array_equal(p, ep)
 
 
+def _topk_state(n, seed, peaks=()):
+    """a random complex64-representable state; `peaks` = (start, count):
+    that many large distinct amplitudes at consecutive indices"""
+    rng = np.random.default_rng(seed)
+    a = (rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)) * 1e-3
+    for start, count in peaks:
+        a[start:start + count] = np.linspace(1.0, 2.0, count) * np.exp(1j * rng.uniform(0, 6.28, count))
+    return a / np.linalg.norm(a)
+
+
+@pytest.mark.parametrize("k,peaks,launches", [
+    (64, (), 3),                        # spread: the warps' best 16 suffice, one pass
+    (128, (), 3),
+    (64, ((1024, 40),), 6),             # 40 of the top 64 in one warp's slice: exact rerun
+    (64, ((1024, 15), (8192, 15)), None),   # 15 per slice: below the rerun bound, still exact
+    (17, ((4096, 17),), 6),             # k just above the per-warp keep, all in one slice
+])
+def test_topk_warp_keep_and_rerun(k, peaks, launches):
+    """complex64 top-k with k <= 128 first lets each warp keep only its best
+    16 candidates; the result is exact unless some warp's whole kept list is
+    in it, and then the call reruns the kernel that keeps k per warp (3
+    kernel launches per pass).  Either way the result equals the oracle's."""
+    n = 20
+    a = _topk_state(n, k + len(peaks), peaks)
+    with S.Sim(n, S.SIM_C64) as s:
+        s.set_state(a)
+        ref = s.get_state().astype(np.complex128)
+        l0 = S.kernel_launches()
+        idx, p = s.top_k(k)
+        used = S.kernel_launches() - l0
+    eidx, ep = oracle.top_k(ref, k)
+    assert list(idx) == list(eidx)
+    np.testing.assert_array_equal(p, ep)
+    if launches is not None:
+        assert used == launches
+    else:
+        assert used in (3, 6)
+
+
 def test_topk_ties_uniform():
     with S.Sim(16, S.SIM_C64) as s:
         s.apply([C.Gate("h", (q,)) for q in range(16)])
