@@ -236,6 +236,8 @@ def run_gpu(args, rank, world, dist):
         # chunk sweeps run kernels specialised to their programs, compiled
         # (NVRTC) during the first warm-up step and cached
         opt.flags |= S.SIM_F_JIT
+    if args.remap:
+        opt.flags |= S.SIM_F_REMAP
 
     def step():
         sim.reset(circ.basis)
@@ -359,6 +361,7 @@ def run_gpu(args, rank, world, dist):
                        "l2": f"state ({amps * s_amp / 2 ** 30:g} GiB) larger than L2, no flush",
                        "sweeps": plan["sweeps"], "chunk_ops": plan["chunk_ops"], "dense_ops": plan["dense_ops"],
                        "diag_fused": plan["diag_fused"], "plan_ms": plan["plan_ms"],
+                       **({"remap": True} if args.remap else {}),
                        "chunk_kernels": ("specialised per program at run time (NVRTC), compiled in the first "
                                          "warm-up step and cached: %d programs, %.0f ms of compile"
                                          % (jit["programs"], jit["compile_ms"])) if opt.flags & S.SIM_F_JIT
@@ -594,6 +597,9 @@ def main():
                     help="run the chunk sweeps on the interpreter kernel instead of kernels specialised to "
                          "their programs")
     ap.add_argument("--no-unfused", action="store_true", help="skip the gate-by-gate comparison run")
+    ap.add_argument("--remap", action="store_true",
+                    help="persistent qubit frame: each block's store moves the qubits later blocks need into "
+                         "the low positions")
     ap.add_argument("--families", action="store_true",
                     help="per-gate time of the BV / HS / QV / SC / VC families: gate by gate, optimized, "
                          "optimized with the merge booster")
