@@ -438,6 +438,65 @@ def run_families(args, rank, world, dist):
         print(json.dumps(line), flush=True)
 
 
+def run_readouts(args, rank, world, dist):
+    """Time of the read-outs (K9) on the workload's final state: top-64, the
+    sixteen <Z_a Z_b> of the e2e leg, and the norm.  Each call returns its
+    result in host memory, so it ends with a synchronise and a small copy;
+    the CUDA-event time of a call (the handle's stream) counts its kernels
+    and that copy, the wall time the host side too.  Median of --steps calls
+    after --warmup.  Each read-out reads the state once: 2^n x 8 bytes."""
+    import torch
+    from paper_2604_12256_gb300 import build as B
+    from paper_2604_12256_gb300 import svsim as S
+
+    B.build()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    n = args.qubits or N_QUBITS
+    circ = _workload_circuit(args, n)
+    buf = torch.empty(2 << n, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    sim = S.Sim(n, S.SIM_C64, dev_buf=buf.data_ptr(), nbytes=buf.numel() * 4, stream=stream.cuda_stream)
+    opt = S.default_options()
+    if args.jit:
+        opt.flags |= S.SIM_F_JIT
+    sim.reset(circ.basis)
+    sim.apply(circ.gates, opt)
+    torch.cuda.synchronize()
+    masks = [(1 << a) | (1 << ((a * 7 + 3) % n)) for a in range(16)]
+    calls = {"top64": lambda: sim.top_k(64), "zz16": lambda: sim.expectation(masks), "norm": lambda: sim.norm()}
+    peak, peak_kind = _peaks()
+    state_bytes = (1 << n) * 8
+    clocks = Clocks(dev)
+    clocks.start()
+    out = {}
+    for name, call in calls.items():
+        for _ in range(args.warmup):
+            call()
+        ev, wall = [], []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            wall.append((time.perf_counter() - t0) * 1e3)
+            ev.append(e0.elapsed_time(e1))
+        ms = statistics.median(ev)
+        gbs = state_bytes / (ms / 1e3) / 1e9
+        out[name] = {"ms": ms, "wall_ms": statistics.median(wall), "hbm_gbs": gbs,
+                     "hbm_frac_of_" + peak_kind: gbs / peak}
+    clk = clocks.stop()
+    sim.close()
+    if rank == 0:
+        line = {"metric": "read-out time per call (top-64, 16 <ZZ>, norm)", "unit": "ms", "n_qubits": n,
+                "dtype": "c64", "data": "synthetic", "workload": args.workload, "steps": args.steps,
+                "warmup": args.warmup, "higher_is_better": False, "bytes_per_call": state_bytes,
+                "readouts": out, "clocks": clk}
+        print(json.dumps(line), flush=True)
+
+
 def _pct(xs, q):
     xs = sorted(xs)
     return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))] if xs else None
@@ -597,6 +656,8 @@ def main():
                     help="run the chunk sweeps on the interpreter kernel instead of kernels specialised to "
                          "their programs")
     ap.add_argument("--no-unfused", action="store_true", help="skip the gate-by-gate comparison run")
+    ap.add_argument("--readouts", action="store_true",
+                    help="time the read-outs (top-64, 16 <ZZ>, norm) on the workload's final state")
     ap.add_argument("--remap", action="store_true",
                     help="persistent qubit frame: each block's store moves the qubits later blocks need into "
                          "the low positions")
@@ -650,7 +711,8 @@ def main():
         dist_.init_process_group("nccl")
         dist = dist_
     try:
-        (run_serve if args.serve else run_families if args.families else run_gpu)(args, rank, world, dist)
+        (run_serve if args.serve else run_families if args.families else run_readouts if args.readouts
+         else run_gpu)(args, rank, world, dist)
     finally:
         if dist is not None:
             dist.destroy_process_group()
