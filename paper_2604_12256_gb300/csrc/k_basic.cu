@@ -271,7 +271,9 @@ cudaError_t launch_tensor(void *out, const void *hi, int n_hi, const void *lo, i
 // ------------------------------------------------------------ reductions
 // A fixed grid (kRedBlocks x kRedThreads) makes every sum's order independent
 // of the device, so results are bit-reproducible run to run.
-constexpr int kRedBlocks = 1024;
+constexpr int kRedBlocks = kReduceBlocks;   // norm
+constexpr int kExpBlocks = 512;              // <Z> strings
+static_assert(kExpBlocks <= kReduceBlocks, "partials buffer");
 constexpr int kRedThreads = 256;
 int reduce_partials() { return kRedBlocks; }
 
@@ -443,9 +445,9 @@ cudaError_t launch_expect_z(const void *a, int n, bool f64, const uint64_t *mask
 {
     if (nt < 1 || nt > 16) return cudaErrorInvalidValue;
     int64_t N = (int64_t)1 << n;
-    if (f64) k_expect_part<double, 16><<<kRedBlocks, kRedThreads, 0, st>>>((const double2 *)a, N, masks, nt, part);
-    else k_expect_part<float, 16><<<kRedBlocks, kRedThreads, 0, st>>>((const float2 *)a, N, masks, nt, part);
-    k_sum_parts<<<nt, 256, 0, st>>>(part, kRedBlocks, nt, out);
+    if (f64) k_expect_part<double, 16><<<kExpBlocks, kRedThreads, 0, st>>>((const double2 *)a, N, masks, nt, part);
+    else k_expect_part<float, 16><<<kExpBlocks, kRedThreads, 0, st>>>((const float2 *)a, N, masks, nt, part);
+    k_sum_parts<<<nt, 256, 0, st>>>(part, kExpBlocks, nt, out);
     return counted(cudaGetLastError(), 2);
 }
 

@@ -39,7 +39,13 @@ cudaError_t launch_tensor(void *out, const void *hi, int n_hi, const void *lo, i
                           bool is_f64, cudaStream_t st);
 
 // ---- read-out (FP64 accumulation, fixed reduction order) ----
-// Partials buffer `part` must hold reduce_partials() doubles per term.
+// Partials buffer `part` must hold reduce_partials() (= kReduceBlocks)
+// doubles per term.  The reductions' grids are fixed, so every sum's order
+// is independent of the device: the norm runs 1024 blocks of 256 threads,
+// the <Z> kernel 512 (a power-of-two stride either way; fewer blocks halve
+// the <Z> kernel's per-block setup and 16-term block reductions, while the
+// light norm kernel needs the blocks to keep enough loads in flight).
+constexpr int kReduceBlocks = 1024;
 int reduce_partials();
 // sum_x |a_x|^2 -> *out_dev (device double)
 cudaError_t launch_norm(const void *a, int n, bool is_f64, double *part, double *out_dev,

@@ -19,9 +19,9 @@
 
 namespace {
 
-// kRedBlocks partials for each of up to 16 Z strings (the kernels' fixed grid)
+// kReduceBlocks partials for each of up to 16 Z strings (the kernels' fixed grid)
 constexpr int kMaxTermsPerCall = 16;
-constexpr int kScratchDoubles = 1024 * kMaxTermsPerCall;   // 128 KiB
+constexpr int kScratchDoubles = svs::kReduceBlocks * kMaxTermsPerCall;   // 128 KiB
 
 // One copy per device that loads the library, kept until the process exits.
 // Every call on a device shares it; the kernels overwrite every partial they
