@@ -188,3 +188,21 @@ def test_euler_split_real_rotations_and_exact():
     # one phase segment per layer and register stage, not one per rotation
     nseg = sum(1 for x in ops if "phase" in x)
     assert nseg <= len(dense) // 4
+
+
+@pytest.mark.parametrize("name,make,max_sweeps", [
+    ("diag-heavy 28", lambda: C.diag_heavy(28, 500, 1), 8),
+    ("qaoa 30", lambda: C.qaoa(30, 4, 3), 13),
+    ("qft 30", lambda: C.qft(30, 2), 4),
+    ("layered 30", lambda: C.layered(30, 20, 0), 33),
+])
+def test_benchmark_workloads_sweep_budget(name, make, max_sweeps):
+    """The full-state passes of the benchmarked workloads, with the options
+    the bench uses (defaults + specialised kernels): each sweep reads and
+    writes the whole state, so a planner change that adds one shows up in
+    every step.  The bounds are the counts the planner reaches now."""
+    c = make()
+    opt = S.default_options(flags=S.default_options().flags | S.SIM_F_JIT)
+    st = S.plan_json(c.n, c.gates, S.SIM_C64, c.basis, opt)["stats"]
+    assert st["sweeps"] <= max_sweeps, (name, st)
+    assert st["chunk_ops"] + st["diag_ops"] >= 1
