@@ -255,7 +255,9 @@ def run_gpu(args, rank, world, dist):
     clocks = Clocks(dev)
     clocks.start()
     time.sleep(0.3)
-    sim.profile_enable(True)
+    # per-launch CUDA events around the launches on the state (the roofline's
+    # kernel durations); none around the booster's small sub-state launches
+    sim.profile_enable(True, state_only=True)
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

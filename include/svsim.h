@@ -237,7 +237,10 @@ typedef struct {
     uint64_t h2d_bytes;      /* plan constants copied host -> device          */
 } sim_profile;
 
-/* on != 0: clear the counters and start recording; 0: stop. */
+/* on != 0: clear the counters and start recording; 0: stop.  on = 2
+ * records only the launches on the handle's own state, not those on the
+ * merge booster's sub-states (two events fewer around each of those small
+ * launches); their counters stay zero. */
 int sim_profile_enable(sim_t *s, int on);
 /* Synchronise the handle's stream and return the accumulated counters. */
 int sim_profile_read(sim_t *s, sim_profile *out);

@@ -48,6 +48,7 @@ struct sim_t {
     sim_plan_stats stats{};
     // profiling: event pairs around launches, resolved at sim_profile_read
     bool prof_on = false;
+    bool prof_all = true;       // false: only ops on the handle's state (not the booster's sub-states)
     sim_profile prof{};
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
@@ -65,10 +66,11 @@ static cudaEvent_t prof_event(sim_t *s, size_t i)
     return s->ev_pool[i];
 }
 
-// record the start of a launch of kind `kind`; returns the pair index
-static long prof_begin(sim_t *s)
+// record the start of a launch on buffer `buf` (0: the handle's state);
+// returns the pair index, or -1 when it is not recorded
+static long prof_begin(sim_t *s, int buf = 0)
 {
-    if (!s->prof_on) return -1;
+    if (!s->prof_on || (buf != 0 && !s->prof_all)) return -1;
     size_t i = s->ev_used;
     cudaEvent_t a = prof_event(s, i), b = prof_event(s, i + 1);
     if (!a || !b) return -1;
@@ -506,7 +508,7 @@ static int execute(sim_t *s, const Plan &p, bool jit)
             src.n_lo = t.n_lo;
         }
         cudaError_t e = cudaSuccess;
-        long pe = prof_begin(s);
+        long pe = prof_begin(s, o.buf);
         switch (o.kind) {
         case OPK_INIT_BASIS: e = launch_init_basis(a, o.n, f64, o.basis, s->stream); break;
         case OPK_GATE: e = launch_gate_dense(a, o.n, f64, o.gate.k, o.gate.q, cst, s->stream); break;
@@ -675,6 +677,7 @@ int sim_profile_enable(sim_t *s, int on)
     s->ev_used = 0;
     if (on) s->prof = sim_profile{};
     s->prof_on = on != 0;
+    s->prof_all = on != 2;
     return SIM_OK;
 }
 

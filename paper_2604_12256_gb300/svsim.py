@@ -275,8 +275,10 @@ class Sim:
         _check(self.lib.sim_last_plan_stats(self.h, ctypes.byref(st)), self.h)
         return st.asdict()
 
-    def profile_enable(self, on: bool = True):
-        _check(self.lib.sim_profile_enable(self.h, 1 if on else 0), self.h)
+    def profile_enable(self, on: bool = True, state_only: bool = False):
+        """sim_profile_enable: state_only records only the launches on this
+        handle's state (not on the merge booster's sub-states)."""
+        _check(self.lib.sim_profile_enable(self.h, (2 if state_only else 1) if on else 0), self.h)
 
     def profile_read(self) -> dict:
         p = sim_profile()
