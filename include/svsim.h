@@ -173,7 +173,11 @@ int sim_sync(sim_t *s);
 int sim_probabilities(sim_t *s, double *out);
 
 /* The k (1..1024) largest probabilities, ties to the lower index, largest
- * first: idx[k], prob[k] host arrays. */
+ * first: idx[k], prob[k] host arrays (Section 2.1: p_x = |a_x|^2, in FP64).
+ * Exact.  For complex64 and 16 < k <= 128 the state is read once with
+ * warps that keep only their best 16 candidates, and a second time only
+ * when one warp's slice holds 16 of the result (a top k crowded into one
+ * region, e.g. a uniform state's ties).  Synchronises the handle's stream. */
 int sim_top_k(sim_t *s, int k, uint64_t *idx, double *prob);
 
 /* <Z-string m> = sum_x |a_x|^2 (-1)^popcount(x & m) for n_terms masks. */
