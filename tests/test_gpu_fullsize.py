@@ -19,14 +19,17 @@ def _uniform(s, n, rel):
     np.testing.assert_allclose(p, 2.0 ** -n, rtol=rel, atol=0)
 
 
-@pytest.mark.parametrize("n,dtype,rel", [(30, S.SIM_C64, 1e-4), (33, S.SIM_C128, 1e-10)])
-def test_qft_of_a_basis_state_is_uniform(n, dtype, rel):
+@pytest.mark.parametrize("n,dtype,rel,jit", [(30, S.SIM_C64, 1e-4, False), (30, S.SIM_C64, 1e-4, True),
+                                            (33, S.SIM_C128, 1e-10, False)])
+def test_qft_of_a_basis_state_is_uniform(n, dtype, rel, jit):
     """QFT|x> = 2^(-n/2) sum_y e^{2 pi i x y / 2^n} |y>: all magnitudes equal
-    (the 30-qubit circuit-level workload; 33 qubits in complex128)."""
+    (the 30-qubit circuit-level workload, also on the kernels specialised to
+    their programs as the bench runs it; 33 qubits in complex128)."""
     c = C.qft(n, 2)
+    opt = S.default_options(flags=S.default_options().flags | (S.SIM_F_JIT if jit else 0))
     with S.Sim(n, dtype) as s:
         s.reset(c.basis)
-        s.apply(c.gates)
+        s.apply(c.gates, opt)
         assert abs(s.norm() - 1.0) < 10 * rel
         _uniform(s, n, rel)
 
@@ -56,3 +59,22 @@ def test_layered_34_dense_blocks_inverse_returns_zero():
         s.apply(C.inverse(c).gates, opt)
         idx, p = s.top_k(2)
     assert idx[0] == 0 and abs(p[0] - 1.0) < 1e-3 and p[1] < 1e-6
+
+
+def test_diag_heavy_28_specialised_inverse_returns_basis():
+    """The 28-qubit diagonal-heavy stream in the bench's configuration (merge
+    booster, diagonal detector, chunk sweeps on the kernels specialised to
+    their programs), then its inverse on the same path: back to the basis
+    state, with the norm kept."""
+    c = C.diag_heavy(28, 500, 1)
+    opt = S.default_options(flags=S.default_options().flags | S.SIM_F_JIT)
+    with S.Sim(28, S.SIM_C64) as s:
+        s.reset(c.basis)
+        s.apply(c.gates, opt)
+        st = s.stats()
+        assert st["sweeps"] == 8 and st["diag_fused"] > 0
+        assert S.jit_info()["programs"] > 0
+        assert abs(s.norm() - 1.0) < 1e-4
+        s.apply(C.inverse(c).gates, opt)
+        idx, p = s.top_k(2)
+    assert idx[0] == c.basis and abs(p[0] - 1.0) < 1e-3 and p[1] < 1e-6
