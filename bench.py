@@ -161,46 +161,80 @@ KIND_KERNELS = {"chunk": "k_chunk (cache-blocked chunk sweep)", "diag": "k_diag 
                 "gate": "k_gate_dense (gate-by-gate)", "gate_diag": "k_gate_diag (gate-by-gate diagonal)"}
 
 
-def cpu_oracle_sample(args, budget_s: float = 15.0):
-    """Time the CPU oracle (complex128, gate by gate, all host cores) on the
-    first gates of the workload until ~budget_s of work; returns
-    (amplitude-updates/s, cores, sample description).  States above 28
-    qubits are sampled at 28 qubits (the oracle's host memory)."""
+def _cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+REF_PREFIX_GATES = 64    # gates per reference-arm step (a bounded sample of the circuit)
+
+
+def cpu_oracle_prefix(args, n_gates: int, threads: int):
+    """Time the CPU oracle (complex128, gate by gate) on the first n_gates
+    gates of the workload at min(n, 28) qubits, from its initial basis
+    state; returns (seconds, gates run, qubits)."""
     import oracle
     n = min(N_QUBITS, 28)
     c = _workload_circuit(args, n)
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    a = oracle.basis_state(n, 0)
-    oracle.run_inplace(n, a, c.gates[:1], cores)    # warm: page in the state
-    done, t0 = 0, time.perf_counter()
-    for g in c.gates[1:]:
-        oracle.run_inplace(n, a, [g], cores)
-        done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
+    a = oracle.basis_state(n, c.basis)
+    gl = c.gates[:n_gates]
+    t0 = time.perf_counter()
+    oracle.run_inplace(n, a, gl, threads)
     dt = time.perf_counter() - t0
     del a
-    return done * (1 << n) / dt, cores, \
-        f"gates 2..{done + 1} of {len(c.gates)} at {n} qubits, complex128, {dt:.1f} s (per-gate rate)"
+    return dt, len(gl), n
+
+
+def oracle_full_run(args, threads: int):
+    """The whole workload circuit on the CPU oracle (complex128, gate by gate,
+    Algorithm 1), timed: returns (state, seconds).  Only for workloads the
+    host holds in full (n <= 28: 4 GiB)."""
+    import oracle
+    c = _workload_circuit(args, N_QUBITS)
+    a = oracle.basis_state(N_QUBITS, c.basis)
+    t0 = time.perf_counter()
+    oracle.run_inplace(N_QUBITS, a, c.gates, threads)
+    return a, time.perf_counter() - t0
+
+
+def state_error(got, exp, step=1 << 24):
+    """max |got - exp|, |<exp|got>|^2 / (<got|got><exp|exp>) and the norm of
+    got, over slices (no full-size temporaries)."""
+    import numpy as np
+    err, ov, ng, ne = 0.0, 0j, 0.0, 0.0
+    for lo in range(0, exp.size, step):
+        g = got[lo:lo + step].astype(np.complex128)
+        e = exp[lo:lo + step]
+        err = max(err, float(np.max(np.abs(g - e))))
+        ov += np.vdot(e, g)
+        ng += float(np.vdot(g, g).real)
+        ne += float(np.vdot(e, e).real)
+    return err, float(abs(ov) ** 2 / (ng * ne)), ng
 
 
 def run_reference(args, rank, world):
+    """The oracle as it stands on the host cores.  One step = the first
+    REF_PREFIX_GATES gates of the workload at min(n, 28) qubits (a bounded
+    sample: the whole 528-gate circuit takes about half a minute on 16 cores,
+    and the run has 25 steps); ms_per_step is that measured time."""
     if rank != 0:
         return
-    vals = []
+    cores = _cores()
     for _ in range(args.warmup):
-        cpu_oracle_sample(args, min(5.0, args.ref_budget))
+        cpu_oracle_prefix(args, REF_PREFIX_GATES, cores)
+    times = []
     for _ in range(args.steps):
-        v, cores, sample = cpu_oracle_sample(args, args.ref_budget)
-        vals.append(v)
-    v = statistics.median(vals)
+        dt, g, n = cpu_oracle_prefix(args, REF_PREFIX_GATES, cores)
+        times.append(dt)
+    ms = 1e3 * statistics.median(times)
+    v = g * (1 << n) / (ms / 1e3)
     G = len(_workload_circuit(args, N_QUBITS).gates)
-    steps_per_s = v / (G * (1 << N_QUBITS))
+    sample = (f"each step: gates 1..{g} of the {G}-gate workload circuit at {n} qubits from its initial basis "
+              f"state, complex128, gate by gate on {cores} host threads; median of {args.steps} steps")
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000.0 / steps_per_s, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "gates": G,
-                       "seed": SEED, "l2": "state larger than L2"},
+                       "seed": SEED, "l2": "state larger than L2", "step": f"first {g} gates (bounded sample)"},
             "impl": "reference",
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -289,6 +323,8 @@ def run_gpu(args, rank, world, dist):
         ev = sim.expectation(masks)
         te.append(time.perf_counter() - t0)
     e2e_s = statistics.median(te)
+    # the fused path's final state, for the error against the oracle below
+    final_state = sim.get_state() if rank == 0 and not args.no_cpu_baseline and N_QUBITS <= 28 else None
     h2d = prof["h2d_bytes"] // max(1, args.steps)
     d2h = 64 * 16 + 16 * 8
 
@@ -307,6 +343,37 @@ def run_gpu(args, rank, world, dist):
         torch.cuda.synchronize()
         unf_ms = u0.elapsed_time(u1)
         unfused = {"ms_per_step": unf_ms, "value": G * amps / (unf_ms / 1e3), "speedup_fused_vs_unfused": unf_ms / ms}
+
+    # the oracle leg: the whole circuit on the host cores (timed), and the
+    # error of the GPU state and read-outs against it (rank 0, states the
+    # host holds in full)
+    oracle_leg = None
+    if final_state is not None:
+        import numpy as np
+        import oracle
+        got, final_state = final_state, None
+        cores = _cores()
+        exp, t_all = oracle_full_run(args, cores)
+        err, fid, ng = state_error(got, exp)
+        ref_idx, ref_p = oracle.top_k(exp, 64)
+        ref_zz = oracle.expectation_z(exp, masks)
+        del got, exp
+        t1, g1, n1 = cpu_oracle_prefix(args, 8, 1)
+        oracle_leg = {
+            "cpu_baseline": {"value": G * amps / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"the whole {G}-gate circuit at {N_QUBITS} qubits, complex128, gate by gate, "
+                                       f"{t_all:.1f} s on {cores} host threads (timed once)",
+                             "seconds": t_all,
+                             "one_thread": {"value": g1 * (1 << n1) / t1, "unit": UNIT, "cores": 1,
+                                            "sample": f"gates 1..{g1} at {n1} qubits on 1 thread, {t1:.1f} s"}},
+            "error": {"vs": "CPU oracle (complex128, gate by gate), same circuit",
+                      "state_max_abs": err, "fidelity": fid, "norm": ng,
+                      "top64_set_equal": bool(set(idx.tolist()) == set(ref_idx.tolist())),
+                      "top64_prob_max_abs": float(np.max(np.abs(np.sort(p) - np.sort(ref_p)))),
+                      "zz16_max_abs": float(np.max(np.abs(np.asarray(ev) - ref_zz))),
+                      "tolerance": {"state_max_abs": 1e-5, "fidelity": 1 - 1e-6}
+                      if dt == S.SIM_C64 else {"state_max_abs": 1e-12}},
+        }
 
     peak, peak_kind = _peaks()
     # the dominant kernel: the op kind with the most device time on the state
@@ -377,9 +444,9 @@ def run_gpu(args, rank, world, dist):
             "gpu_launches": int(gpu_launches),
             "clocks": clk,
         }
-        if not args.no_cpu_baseline:
-            v, cores, sample = cpu_oracle_sample(args, args.ref_budget)
-            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        if oracle_leg is not None:
+            line["cpu_baseline"] = oracle_leg["cpu_baseline"]
+            line["error"] = oracle_leg["error"]
         print(json.dumps(line), flush=True)
     sim.close()
 
@@ -639,7 +706,6 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--register-bits", type=int, default=0,
                     help="chunk bits per thread in the cache-blocked kernel (0 = library default)")

@@ -198,6 +198,25 @@ def test_readout_closed_forms():
         assert oracle.expectation_z(b, [m])[0] == (-1) ** bin(x & m).count("1")
 
 
+def test_fidelity_closed_forms():
+    """|<a|b>|^2 for states whose overlap has a closed form: RY(t)|0> on
+    every qubit against RY(u)|0> gives prod_q cos^2((t_q - u_q) / 2); a
+    basis state against the uniform superposition gives 2^-n; a global
+    phase changes nothing and the overlap is symmetric."""
+    n = 5
+    t = np.linspace(0.2, 2.6, n)
+    u = np.linspace(1.9, -0.4, n)
+    a = oracle.run(C.Circuit(n, [C.Gate("ry", (q,), (t[q],)) for q in range(n)]))
+    b = oracle.run(C.Circuit(n, [C.Gate("ry", (q,), (u[q],)) for q in range(n)]))
+    exp = float(np.prod(np.cos((t - u) / 2) ** 2))
+    assert abs(oracle.fidelity(a, b) - exp) <= 1e-14
+    assert abs(oracle.fidelity(b, a) - exp) <= 1e-14
+    assert abs(oracle.fidelity(a, np.exp(0.83j) * a) - 1.0) <= 1e-14
+    plus = oracle.run(C.Circuit(n, [C.Gate("h", (q,)) for q in range(n)]))
+    assert abs(oracle.fidelity(oracle.basis_state(n, 19), plus) - 2.0 ** -n) <= 1e-15
+    assert oracle.fidelity(oracle.basis_state(n, 3), oracle.basis_state(n, 4)) == 0.0
+
+
 def test_top_k_brute_force_and_ties():
     rng = np.random.default_rng(2)
     a = rng.standard_normal(64) + 1j * rng.standard_normal(64)

@@ -1,13 +1,15 @@
 """sim_expectation_noalloc: the expectation entry point for callers that
 cannot allocate device memory (it keeps its partial sums in a fixed device
 array inside the library).  Its results must match sim_expectation's, the
-allocating entry point, on consecutive calls that share that array.
+allocating entry point, on consecutive calls that share that array, and the
+oracle's <Z-string> of the oracle's own state within the same tolerance.
 
 Collected last on purpose (file name) so a run that stops at the first
 failure has already run every other test."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2604_12256_gb300 import circuits as C
 from paper_2604_12256_gb300 import svsim as S
 
@@ -22,12 +24,14 @@ def test_noalloc_matches_allocating_entry_point(dtype, tol):
     first = [(1 << 0) | (1 << 7), (1 << 3) | (1 << 14), 1 << 9, (1 << n) - 1]
     second = [(1 << 2) | (1 << 5), (1 << 11), (1 << 1) | (1 << 4) | (1 << 13), 0, 0b1010101010, 1 << 14,
               (1 << 6) | (1 << 8)]
+    ref_state = oracle.run(c)
     with S.Sim(n, dtype) as s:
         s.reset(c.basis)
         s.apply(c.gates)
         state_ptr, stream = s.device()
         for masks in (first, second):     # two calls in a row share the fixed array
             expect = s.expectation(masks)
+            ref = oracle.expectation_z(ref_state, masks)
             dm = torch.tensor(np.array(masks, dtype=np.uint64).view(np.int64), device="cuda")
             out = torch.full((len(masks),), float("nan"), dtype=torch.float64, device="cuda")
             torch.cuda.synchronize()
@@ -35,6 +39,7 @@ def test_noalloc_matches_allocating_entry_point(dtype, tol):
             s.sync()
             got = out.cpu().numpy()
             np.testing.assert_allclose(got, expect, atol=tol, rtol=0)
+            np.testing.assert_allclose(got, ref, atol=tol, rtol=0)
 
 
 def test_noalloc_rejects_bad_arguments():
