@@ -140,6 +140,23 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # SMs x FP32 lanes x FMA x
 DF_FLOPS_PER_AMP = 2 * 64 * 15 + 2 * 3                 # double-float complex128 dense block
 
 
+def _redraw(c, seed):
+    """The circuit with the same gates on the same qubits and every angle
+    (uniform in [0, 2 pi)) and Haar one-qubit matrix drawn anew."""
+    import numpy as np
+    from paper_2604_12256_gb300 import circuits as C
+    rng = np.random.default_rng(seed)
+    gs = []
+    for g in c.gates:
+        if g.kind == "u1q":
+            gs.append(C.Gate("u1q", g.qubits, matrix=C.haar_u2(rng)))
+        elif g.params:
+            gs.append(C.Gate(g.kind, g.qubits, tuple(float(rng.uniform(0, 2 * math.pi)) for _ in g.params)))
+        else:
+            gs.append(g)
+    return C.Circuit(c.n, gs, c.basis, c.name)
+
+
 def _workload_circuit(args, n):
     from paper_2604_12256_gb300 import circuits as C
     if args.workload in ("layered-dense", "layered"):
@@ -277,7 +294,16 @@ def run_gpu(args, rank, world, dist):
         sim.reset(circ.basis)
         sim.apply(ga, opt)
 
-    for _ in range(args.warmup):
+    # cold: the first apply of this circuit's structure in the process
+    # (specialised kernels generated and compiled by NVRTC on the way)
+    jit_before = S.jit_info()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    step()
+    torch.cuda.synchronize()
+    first_apply_ms = (time.perf_counter() - t0) * 1e3
+    jit_first = S.jit_info()
+    for _ in range(max(0, args.warmup - 1)):
         step()
     torch.cuda.synchronize()
     plan = sim.stats()
@@ -325,6 +351,23 @@ def run_gpu(args, rank, world, dist):
     e2e_s = statistics.median(te)
     # the fused path's final state, for the error against the oracle below
     final_state = sim.get_state() if rank == 0 and not args.no_cpu_baseline and N_QUBITS <= 28 else None
+    # fresh angles: the same circuit structure with every angle (and Haar
+    # one-qubit matrix) drawn anew, end to end through the C ABI; with
+    # specialised kernels keyed by structure no compile is expected
+    fresh = [_redraw(circ, 1000 + i) for i in range(max(3, min(args.steps, 10)))]
+    jit_f0 = S.jit_info()
+    tf = []
+    for fc in fresh:
+        t0 = time.perf_counter()
+        sim.reset(fc.basis)
+        sim.apply(fc.gates, opt)
+        sim.top_k(64)
+        sim.expectation(masks)
+        tf.append(time.perf_counter() - t0)
+    jit_f1 = S.jit_info()
+    fresh_angles = {"ms_per_step": statistics.median(tf) * 1e3, "circuits": len(fresh),
+                    "value": world * G * amps / statistics.median(tf), "unit": UNIT,
+                    "compiles": jit_f1["compiles"] - jit_f0["compiles"]}
     h2d = prof["h2d_bytes"] // max(1, args.steps)
     d2h = 64 * 16 + 16 * 8
 
@@ -431,16 +474,20 @@ def run_gpu(args, rank, world, dist):
                        "sweeps": plan["sweeps"], "chunk_ops": plan["chunk_ops"], "dense_ops": plan["dense_ops"],
                        "diag_fused": plan["diag_fused"], "plan_ms": plan["plan_ms"],
                        **({"remap": True} if args.remap else {}),
-                       "chunk_kernels": ("specialised per program at run time (NVRTC), compiled in the first "
-                                         "warm-up step and cached: %d programs, %.0f ms of compile"
-                                         % (jit["programs"], jit["compile_ms"])) if opt.flags & S.SIM_F_JIT
-                       else "interpreter"},
+                       "chunk_kernels": ("specialised per program structure at run time (NVRTC; numbers in the "
+                                         "launch's parameter block), compiled in the first warm-up step and "
+                                         "cached: %d kernels, %d compiles, %.0f ms of compile"
+                                         % (jit["programs"], jit["compiles"], jit["compile_ms"]))
+                       if opt.flags & S.SIM_F_JIT else "interpreter"},
             "hbm_gbs": total_bytes / (ms / 1e3) / 1e9,
             "hbm_frac_of_" + peak_kind: total_bytes / (ms / 1e3) / 1e9 / peak,
             "roofline": roof,
             "unfused": unfused,
             "e2e": {"value": world * G * amps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
+                    "first_apply_ms": first_apply_ms,
+                    "first_apply_compiles": jit_first["compiles"] - jit_before["compiles"],
+                    "fresh_angles": fresh_angles},
             "gpu_launches": int(gpu_launches),
             "clocks": clk,
         }

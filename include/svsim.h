@@ -93,10 +93,16 @@ enum {
                                sweeps run kernels specialised to their
                                program: ops decoded once on the host and
                                compiled (NVRTC, needs libnvrtc.so.13) into
-                               straight-line code, cached per program for the
-                               process; the first apply of a new program pays
-                               its compile (about 0.3-1 s, in parallel over a
-                               plan's programs).  Results equal the interpreter
+                               straight-line code.  A kernel holds the
+                               program's structure (op kinds, positions,
+                               layouts, table shapes); its numbers (matrix
+                               entries, phase weights) are passed per launch,
+                               so circuits that differ only in their angles
+                               share kernels.  Kernels are cached for the
+                               process (sim_jit_cache bounds how many); the
+                               first apply of a new structure pays its compile
+                               (about 0.3-1 s, in parallel over a plan's
+                               programs).  Results equal the interpreter
                                kernels' up to rounding order                  */
     SIM_F_ALL = 0x7f
 };
@@ -282,9 +288,25 @@ int sim_plan_json(int n_qubits, sim_dtype dtype, uint64_t basis_index,
 int sim_jit_check(int n_qubits, sim_dtype dtype, uint64_t basis_index, const sim_gate *gates, size_t n,
                   const sim_options *opt, int *n_programs);
 
-/* Specialised kernels compiled and cached by this process so far, and the
- * wall time their compiles took (ms). */
+/* Specialised kernels cached by this process now, and the wall time all
+ * compiles so far took (ms). */
 int sim_jit_info(uint64_t *programs, double *compile_ms);
+
+/* The specialised-kernel cache (no counterpart in the paper; a resource
+ * control).  max_kernels > 0 sets the most kernels kept loaded (default 256;
+ * least recently used first out -- an evicted kernel's module is unloaded
+ * once no launch can use it, after synchronising the devices it ran on);
+ * 0 leaves it.  *kernels: cached now; *compiles: NVRTC compiles so far. */
+int sim_jit_cache(int max_kernels, uint64_t *kernels, uint64_t *compiles);
+
+/* The generated CUDA source of every specialised sweep of the plan (as
+ * sim_plan_json plans it; no GPU needed), each after a comment line giving
+ * its parameter-block size, into buf (at most buflen bytes including the
+ * terminating NUL); *needed receives the full length + 1, SIM_ENOMEM (and
+ * nothing written) when buflen is too small.  Two circuits that differ only
+ * in their angles have equal sources. */
+int sim_jit_sources(int n_qubits, sim_dtype dtype, uint64_t basis_index, const sim_gate *gates, size_t n,
+                    const sim_options *opt, char *buf, size_t buflen, size_t *needed);
 
 /* ------------------------------------------------------------ serving */
 /* A request loop with continuous batching (not in the paper; the serving

@@ -477,21 +477,26 @@ static int execute(sim_t *s, const Plan &p, bool jit)
     }
     // specialised chunk kernels: compile the programs not cached yet (all of
     // them at once, in parallel) before the first launch
-    std::vector<char> use_jit(p.ops.size(), 0);
+    // (a program whose numbers exceed the kernel-argument space keeps the
+    // interpreter kernel: its handle has no kernel)
+    std::vector<long> jit_of(p.ops.size(), -1);
+    std::vector<JitHandle> jh;
     if (jit) {
         std::vector<JitProg> progs;
         for (size_t i = 0; i < p.ops.size(); i++) {
             const Op &o = p.ops[i];
             if (o.kind == OPK_CHUNK && jit_supported(f64, o.prog.C, o.prog.RB)) {
-                use_jit[i] = 1;
+                jit_of[i] = (long)progs.size();
                 progs.push_back({&o.words, JIT_CHUNK});
             } else if (o.kind == OPK_DIAG && jit_supported_diag(f64, (int)o.words[prog::H_RB])) {
-                use_jit[i] = 1;
+                jit_of[i] = (long)progs.size();
                 progs.push_back({&o.words, JIT_DIAG});
             }
         }
         std::string err;
-        if (!progs.empty() && !jit_prepare(progs, err)) return fail(s, SIM_ECUDA, err);
+        if (!progs.empty() && !jit_prepare(progs, jh, err)) return fail(s, SIM_ECUDA, err);
+        for (size_t i = 0; i < p.ops.size(); i++)
+            if (jit_of[i] >= 0 && !jh[(size_t)jit_of[i]].k) jit_of[i] = -1;
     }
     // 2. launches (Algorithm 5)
     for (size_t i = 0; i < p.ops.size(); i++) {
@@ -520,9 +525,9 @@ static int execute(sim_t *s, const Plan &p, bool jit)
                                  s->stream);
             break;
         case OPK_DIAG:
-            if (use_jit[i])
-                e = launch_diag_jit(a, o.n, o.words, (const uint32_t *)cst, prog::smem_bytes(o.words.data(), true),
-                                    src, s->stream);
+            if (jit_of[i] >= 0)
+                e = launch_diag_jit(jh[(size_t)jit_of[i]], a, o.n, o.words, (const uint32_t *)cst,
+                                    prog::smem_bytes(o.words.data(), true), src, s->stream);
             else
                 e = launch_diag_sweep(a, o.n, f64, (const uint32_t *)cst, prog::smem_bytes(o.words.data(), true),
                                       src, s->stream);
@@ -531,9 +536,9 @@ static int execute(sim_t *s, const Plan &p, bool jit)
             e = launch_phase_small(a, o.n, f64, (const uint64_t *)cst, (int)o.terms.size(), s->stream);
             break;
         case OPK_CHUNK:
-            if (use_jit[i])
-                e = launch_chunk_jit(a, o.n, o.words, (const uint32_t *)cst, prog::smem_bytes(o.words.data(), false),
-                                     src, s->stream);
+            if (jit_of[i] >= 0)
+                e = launch_chunk_jit(jh[(size_t)jit_of[i]], a, o.n, o.words, (const uint32_t *)cst,
+                                     prog::smem_bytes(o.words.data(), false), src, s->stream);
             else
                 e = launch_chunk(a, o.n, f64, o.prog.C, o.prog.RB, (const uint32_t *)cst,
                                  prog::smem_bytes(o.words.data(), false), src, s->stream);
@@ -723,13 +728,23 @@ int sim_plan_json(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, si
 
 int sim_jit_info(uint64_t *programs, double *compile_ms)
 {
-    const size_t n = jit_cache_size(compile_ms);
+    const size_t n = jit_cache_size(compile_ms, nullptr);
     if (programs) *programs = n;
     return SIM_OK;
 }
 
-int sim_jit_check(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_t ng, const sim_options *opt,
-                  int *n_programs)
+int sim_jit_cache(int max_kernels, uint64_t *kernels, uint64_t *compiles)
+{
+    if (max_kernels < 0) return fail(nullptr, SIM_EINVAL, "max_kernels must be >= 0");
+    if (max_kernels > 0) jit_set_cache_limit((size_t)max_kernels);
+    const size_t k = jit_cache_size(nullptr, compiles);
+    if (kernels) *kernels = k;
+    return SIM_OK;
+}
+
+// the specialised sweeps of a plan: generate (and optionally compile) each
+static int jit_plan_sources(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_t ng,
+                            const sim_options *opt, bool compile, int *n_programs, std::string *text)
 {
     int rc = check_n(n, dt);
     if (rc) return rc;
@@ -748,9 +763,15 @@ int sim_jit_check(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, si
             if (op.kind == OPK_DIAG && jit_supported_diag(dt == SIM_C128, (int)op.words[prog::H_RB])) kind = JIT_DIAG;
             if (kind < 0) continue;
             std::string src;
+            std::vector<uint32_t> vals;
             std::vector<char> cubin;
-            if (!jit_source(op.words, kind, src, err) || !jit_compile(src, cubin, err) || cubin.empty())
+            if (!jit_source(op.words, kind, src, vals, err)) return fail(nullptr, SIM_EINVAL, err);
+            if (compile && (!jit_compile(src, cubin, err) || cubin.empty()))
                 return fail(nullptr, SIM_EINVAL, err.empty() ? "empty cubin" : err);
+            if (text) {
+                *text += "// ---- specialised sweep " + std::to_string(np) + ": " + std::to_string(vals.size()) +
+                         " parameter words\n" + src;
+            }
             np++;
         }
         if (n_programs) *n_programs = np;
@@ -758,6 +779,24 @@ int sim_jit_check(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, si
         return fail(nullptr, SIM_ENOMEM, "host allocation failed while planning");
     }
     return SIM_OK;
+}
+
+int sim_jit_sources(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_t ng, const sim_options *opt,
+                    char *buf, size_t buflen, size_t *needed)
+{
+    std::string text;
+    int rc = jit_plan_sources(n, dt, basis, gates, ng, opt, false, nullptr, &text);
+    if (rc) return rc;
+    if (needed) *needed = text.size() + 1;
+    if (!buf || buflen < text.size() + 1) return fail(nullptr, SIM_ENOMEM, "buffer too small for the sources");
+    std::memcpy(buf, text.c_str(), text.size() + 1);
+    return SIM_OK;
+}
+
+int sim_jit_check(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_t ng, const sim_options *opt,
+                  int *n_programs)
+{
+    return jit_plan_sources(n, dt, basis, gates, ng, opt, true, n_programs, nullptr);
 }
 
 }  // extern "C"

@@ -675,7 +675,7 @@ template <typename T2> __device__ __forceinline__ T2 tensor_amp(const TSrc<T2> &
 // (kStages > 0: the stage count and stage layouts are compile-time).
 template <typename R, int C, int RB, typename Ops>
 __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, const uint32_t *__restrict__ gprog,
-                                            int n, TSrc<typename CT<R>::G2> src)
+                                            int n, TSrc<typename CT<R>::G2> src, const typename Ops::Params &P)
 {
     using T2 = typename CT<R>::T2;
     using G2 = typename CT<R>::G2;
@@ -889,7 +889,7 @@ __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, 
                     v[m] = sv[pm];
                 }
             }
-            Ops::template run<R, RB, T>(s, v, x0, prog, sp, cta_ph, thr_ph, nhoist, tid);
+            Ops::template run<R, RB, T>(s, v, x0, prog, sp, cta_ph, thr_ph, nhoist, tid, P);
             if (kDL && s == Ops::kStages - 1) {
                 store_direct(v, x0, s);
                 return;
@@ -941,8 +941,13 @@ __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, 
 }
 
 
+// The numbers a kernel specialised to one program reads from its parameter
+// block (jit.cpp); the interpreters read everything from the program.
+struct NoParams {};
+
 // The interpreter: the ops of stage s, as the program in shared memory lists them.
 struct InterpOps {
+    using Params = NoParams;
     static constexpr int kStages = 0;
     static constexpr bool kDirectFirst = false, kDirectLast = false;
     static __device__ __forceinline__ uint64_t roff(int, int) { return 0; }
@@ -963,7 +968,7 @@ struct InterpOps {
     template <typename R, int RB, int T>
     static __device__ __forceinline__ void run(int, typename CT<R>::T2 (&v)[1 << RB], uint64_t x0,
                                                const uint32_t *, const uint32_t *sp, const typename CT<R>::W *cta_ph,
-                                               const typename CT<R>::W *thr_ph, int nhoist, int tid)
+                                               const typename CT<R>::W *thr_ph, int nhoist, int tid, const Params &)
     {
         constexpr int NR = 1 << RB;
         const int nops = (int)ldw(sp + S_NOPS);
@@ -993,7 +998,7 @@ struct InterpOps {
 // program (jit.cpp) is generated from it.
 template <typename R, int RB, typename Ops>
 __device__ __forceinline__ void diag_sweep(typename CT<R>::G2 *__restrict__ a, const uint32_t *__restrict__ gprog,
-                                           int n, TSrc<typename CT<R>::G2> src)
+                                           int n, TSrc<typename CT<R>::G2> src, const typename Ops::Params &P)
 {
     using T2 = typename CT<R>::T2;
     using G2 = typename CT<R>::G2;
@@ -1047,7 +1052,7 @@ __device__ __forceinline__ void diag_sweep(typename CT<R>::G2 *__restrict__ a, c
                 v[m] = to_reg(tensor_amp(src, x0 + ((uint64_t)m << 7)));
             }
         }
-        Ops::template seg<R, RB, 128>(v, x0, prog, op, cta_ph, thr_ph, nhoist, tid);
+        Ops::template seg<R, RB, 128>(v, x0, prog, op, cta_ph, thr_ph, nhoist, tid, P);
 #pragma unroll
         for (int m = 0; m < NR; m++) __stcs(a + x0 + ((uint64_t)m << 7), to_glob(v[m]));
         __syncthreads();
@@ -1056,10 +1061,11 @@ __device__ __forceinline__ void diag_sweep(typename CT<R>::G2 *__restrict__ a, c
 }
 
 struct DiagInterp {
+    using Params = NoParams;
     template <typename R, int RB, int T>
     static __device__ __forceinline__ void seg(typename CT<R>::T2 (&v)[1 << RB], uint64_t x0, const uint32_t *,
                                                const uint32_t *op, const typename CT<R>::W *cta_ph,
-                                               const typename CT<R>::W *thr_ph, int nhoist, int tid)
+                                               const typename CT<R>::W *thr_ph, int nhoist, int tid, const Params &)
     {
         dseg_apply<R, RB, T>(v, x0, op, cta_ph, thr_ph, nhoist, tid);
     }

@@ -8,21 +8,29 @@
 // instantiates the same sweep templates (chunk_dev.cuh: chunk_sweep,
 // diag_sweep) with:
 // - the stage layouts and the ops as straight-line calls, register positions
-//   compile-time, 2x2 and 4x4 matrices as literals, exact identity ops
-//   dropped;
-// - phase segments generated from the program's CTA and thread tables (zero
-//   and constant sums folded on the host, only the per-chunk sums needed
-//   read, a product table over the register bits that carry a phase);
+//   compile-time, exact identity ops dropped;
+// - phase segments generated from the program's CTA and thread tables (sums
+//   without entries folded away, only the per-chunk sums needed read, a
+//   product table over the register bits that carry a phase);
 // - H-, RY- and RX-like one-qubit ops without their scalar (one packed f32x2
 //   instruction per output amplitude), the sweep's product of scalars
 //   applied once;
 // - direct first and last stages where the program's layouts allow them.
+// The source holds structure only.  Every number -- matrix entries, the
+// scaled forms' ratios, phase weights of body terms, constant phase sums and
+// factors (folded on the host in long double), the sweep's scale -- is a
+// slot of the kernel's parameter block, a __grid_constant__ kernel argument
+// (constant bank) filled per launch.  Programs that differ only in their
+// numbers (a circuit with fresh angles) therefore share one compiled kernel.
 // The arithmetic is the interpreter's up to the rounding order of those
 // rewrites; the results agree to a few float ulps.
 //
 // Compilation uses NVRTC (loaded with dlopen, so the library loads without
-// it) to a sm_103a cubin, loaded with cudaLibraryLoadData; kernels are cached
-// per program (its kind and words) for the life of the process.
+// it) to a sm_103a cubin, loaded with cudaLibraryLoadData.  Kernels are
+// cached by their source, at most jit_set_cache_limit() of them (least
+// recently used first out; an evicted kernel's library is unloaded once no
+// launch can still use it); a second map remembers each recent program's
+// source and parameter values, so a repeated program costs no generation.
 #include <cuda_runtime.h>
 #include <dlfcn.h>
 #include <nvrtc.h>
@@ -32,7 +40,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <list>
 #include <map>
+#include <unordered_map>
 #include <memory>
 #include <mutex>
 #include <sstream>
@@ -93,66 +103,72 @@ const Nvrtc &nvrtc()
     return n;
 }
 
-// exact float literal
-std::string flit(uint32_t bits)
-{
-    float f;
-    std::memcpy(&f, &bits, 4);
-    char b[48];
-    std::snprintf(b, sizeof b, "%af", (double)f);
-    return b;
-}
+// Values of a generated kernel: the parameter block's words, in the order
+// the generator reads them.  The source refers to slot k as P.w[k].
+struct PBlock {
+    std::vector<uint32_t> w;
+    std::string u(uint32_t v)
+    {
+        w.push_back(v);
+        return "P.w[" + std::to_string(w.size() - 1) + "]";
+    }
+    std::string f(float v)
+    {
+        uint32_t b;
+        std::memcpy(&b, &v, 4);
+        return "__uint_as_float(" + u(b) + ")";
+    }
+    std::string fbits(uint32_t bits) { return "__uint_as_float(" + u(bits) + ")"; }
+};
 
 constexpr const char *kKernelName = "svs_chunk_jit";
 constexpr const char *kDiagKernelName = "svs_diag_jit";
+// parameter-block words a launch may pass (kernel arguments are limited to
+// 32764 bytes; the other arguments take 40)
+constexpr size_t kMaxParamWords = 8000;
 
 // ---- phase segments
 // Where each sum of a segment comes from, read off the program's tables: a
 // slot is "dynamic" when an entry depends on the chunk (a CTA entry with a
 // mask), on the thread (a thread-table entry) or on the amplitude block (a
 // term in the body); otherwise it is the constant sum of its always-met CTA
-// entries, zero when there are none.
+// entries (a parameter), and absent when it has none.
 struct SlotSrc {
     bool cta_dyn = false;   // CTA entries with a mask: read the per-chunk sum
-    uint32_t cst = 0;       // sum of the always-met CTA entries
+    int ncst = 0;           // always-met CTA entries
+    uint32_t cst = 0;       // their sum
     bool thr = false;       // thread-table entries (hoisted segment)
-    bool dynamic() const { return cta_dyn || thr; }
 };
 
-// A complex factor while the code is generated: exactly one, a constant
-// (folded on the host in long double) or a run-time value in a variable.
+// A complex factor while the code is generated: exactly one (no entries),
+// a constant known on the host (folded in long double, passed as two
+// parameter slots) or a run-time value in a variable.
 struct Fac {
     enum Kind { ONE, CONST, VAR } kind = ONE;
     long double re = 1, im = 0;
     std::string var;
 };
 
-std::string flit_f(long double v)
-{
-    const float f = (float)v;
-    uint32_t b;
-    std::memcpy(&b, &f, 4);
-    return flit(b);
-}
-
-std::string fac_expr(const Fac &f)
+std::string fac_expr(PBlock &P, const Fac &f)
 {
     if (f.kind == Fac::VAR) return f.var;
-    return "make_float2(" + flit_f(f.re) + ", " + flit_f(f.im) + ")";
+    const std::string re = P.f((float)f.re);
+    return "make_float2(" + re + ", " + P.f((float)f.im) + ")";
 }
 
-Fac cis_const(uint32_t w)
+Fac cis_const(const SlotSrc &ss)
 {
-    const long double th = 6.283185307179586476925286766559L * (long double)w * 0x1p-32L;
     Fac f;
-    f.kind = w == 0 ? Fac::ONE : Fac::CONST;
+    if (ss.ncst == 0) return f;   // no entries: exactly one
+    const long double th = 6.283185307179586476925286766559L * (long double)ss.cst * 0x1p-32L;
+    f.kind = Fac::CONST;
     f.re = cosl(th);
     f.im = sinl(th);
     return f;
 }
 
 // a * b, emitting a run-time product into `o` (variable `name`) when needed
-Fac fac_mul(std::ostringstream &o, const Fac &a, const Fac &b, const std::string &name)
+Fac fac_mul(std::ostringstream &o, PBlock &P, const Fac &a, const Fac &b, const std::string &name)
 {
     if (a.kind == Fac::ONE) return b;
     if (b.kind == Fac::ONE) return a;
@@ -165,23 +181,25 @@ Fac fac_mul(std::ostringstream &o, const Fac &a, const Fac &b, const std::string
     }
     r.kind = Fac::VAR;
     r.var = name;
-    o << "                const float2 " << name << " = cmul(" << fac_expr(a) << ", " << fac_expr(b) << ");\n";
+    const std::string ea = fac_expr(P, a);
+    o << "                const float2 " << name << " = cmul(" << ea << ", " << fac_expr(P, b) << ");\n";
     return r;
 }
 
 // Straight-line code of one factored phase segment (no terms on several
-// register bits and other bits) of a complex64, RB = 4, T = 256 program:
-// the sums it needs, one sin/cos per run-time factor, the product table over
-// the register bits that carry a phase, and one complex product per
-// amplitude whose factor is not exactly one.
-void gen_segment(std::ostringstream &o, const std::vector<uint32_t> &w, size_t body, const std::vector<SlotSrc> &slots,
-                 int RB, int TB, int T, int SCP, long double scale)
+// register bits and other bits) of a complex64 program: the sums it needs,
+// one sin/cos per run-time factor, the product table over the register bits
+// that carry a phase, and one complex product per amplitude whose factor is
+// not exactly one.  `scaled`: the sweep's product of scalars (`scale`)
+// multiplies this segment's base factor.
+void gen_segment(std::ostringstream &o, PBlock &P, const std::vector<uint32_t> &w, size_t body,
+                 const std::vector<SlotSrc> &slots, int RB, int TB, int T, int SCP, bool scaled, long double scale)
 {
     using namespace prog;
     const uint32_t *b = &w[body];
     const int d = (int)b[D_INDEX], nb = (int)b[D_NBASE];
     const int NR = 1 << RB, S = 1 + RB;
-    const bool tabnz = (b[D_FLAGS] & 1) != 0;
+    const uint32_t tabmask = RB <= 5 ? b[D_TABMASK] : 0xffffffffu;
     o << "            {   // phase segment " << d << "\n";
     // which 128-bit words of the segment's CTA slots are read
     std::vector<char> need_q((size_t)SCP / 4, 0);
@@ -200,9 +218,9 @@ void gen_segment(std::ostringstream &o, const std::vector<uint32_t> &w, size_t b
     auto emit_sum = [&](int s, int nterm, const std::string &name) -> bool {
         const SlotSrc &ss = slots[(size_t)d * SCP + s];
         const bool thr = s < S && ss.thr;
-        if (!ss.cta_dyn && !thr && nterm == 0) return false;   // constant or zero: folded
-        o << "                uint32_t " << name << " = " << (ss.cta_dyn ? cta_val(s) : std::to_string(ss.cst) + "u")
-          << ";\n";
+        if (!ss.cta_dyn && !thr && nterm == 0) return false;   // constant or absent: folded
+        o << "                uint32_t " << name << " = "
+          << (ss.cta_dyn ? cta_val(s) : ss.ncst ? P.u(ss.cst) : std::string("0u")) << ";\n";
         if (s == 0)
             for (int i = 0; i < TB; i++)
                 if (slot_dyn(1 + RB + i))
@@ -211,7 +229,7 @@ void gen_segment(std::ostringstream &o, const std::vector<uint32_t> &w, size_t b
         for (int i = 0; i < nterm; i++, t += kTermWords) {
             const uint64_t m = (uint64_t)t[0] | ((uint64_t)t[1] << 32);
             o << "                if ((x0 & 0x" << std::hex << m << "ull) == 0x" << m << std::dec << "ull) " << name
-              << " += " << t[2] << "u;\n";
+              << " += " << P.u(t[2]) << ";\n";
         }
         return true;
     };
@@ -224,7 +242,7 @@ void gen_segment(std::ostringstream &o, const std::vector<uint32_t> &w, size_t b
         if (emit_sum(0, nb, "pb") || coef) {
             if (!(s0.cta_dyn || s0.thr || nb)) {
                 // only thread-bit coefficients: start from the constant
-                o << "                uint32_t pb = " << s0.cst << "u;\n";
+                o << "                uint32_t pb = " << (s0.ncst ? P.u(s0.cst) : std::string("0u")) << ";\n";
                 for (int i = 0; i < TB; i++)
                     if (slot_dyn(1 + RB + i))
                         o << "                if (tid & " << (1 << i) << ") pb += " << cta_val(1 + RB + i) << ";\n";
@@ -233,7 +251,7 @@ void gen_segment(std::ostringstream &o, const std::vector<uint32_t> &w, size_t b
             fb.kind = Fac::VAR;
             fb.var = "e0";
         } else {
-            fb = cis_const(s0.cst);
+            fb = cis_const(s0);
         }
     }
     std::vector<Fac> fl(RB);
@@ -244,7 +262,7 @@ void gen_segment(std::ostringstream &o, const std::vector<uint32_t> &w, size_t b
             fl[j].kind = Fac::VAR;
             fl[j].var = "e" + std::to_string(1 + j);
         } else {
-            fl[j] = cis_const(slots[(size_t)d * SCP + 1 + j].cst);
+            fl[j] = cis_const(slots[(size_t)d * SCP + 1 + j]);
         }
     }
     // product table over the register bits with a phase: tb[idx], idx the
@@ -252,12 +270,12 @@ void gen_segment(std::ostringstream &o, const std::vector<uint32_t> &w, size_t b
     std::vector<int> K;
     for (int j = 0; j < RB; j++)
         if (fl[j].kind != Fac::ONE) K.push_back(j);
-    if (scale != 1.0L) {   // the sweep's deferred scale of its scaled one-qubit ops
+    if (scaled) {   // the sweep's deferred scale of its scaled one-qubit ops
         Fac sc;
         sc.kind = Fac::CONST;
         sc.re = scale;
         sc.im = 0;
-        fb = fac_mul(o, fb, sc, "e0s");
+        fb = fac_mul(o, P, fb, sc, "e0s");
     }
     std::vector<Fac> tb(1);
     tb[0] = fb;
@@ -265,23 +283,22 @@ void gen_segment(std::ostringstream &o, const std::vector<uint32_t> &w, size_t b
         const size_t h = tb.size();
         tb.resize(2 * h);
         for (size_t i = 0; i < h; i++)
-            tb[h + i] = fac_mul(o, tb[i], fl[K[k]], "f" + std::to_string(h + i));
+            tb[h + i] = fac_mul(o, P, tb[i], fl[K[k]], "f" + std::to_string(h + i));
     }
-    const uint32_t *tab = t;   // register-only phases, then their complex factors
-    const float *ctab = (const float *)(t + 2 * NR);
+    const float *ctab = (const float *)(t + 2 * NR);   // after the register-only phases
     for (int m = 0; m < NR; m++) {
         size_t idx = 0;
         for (size_t k = 0; k < K.size(); k++)
             if ((m >> K[k]) & 1) idx |= (size_t)1 << k;
         Fac f = tb[idx];
-        if (tabnz && tab[2 * m] != 0) {
+        if ((tabmask >> m) & 1) {
             Fac c;
             c.kind = Fac::CONST;
             c.re = ctab[2 * m];   // the program's float factor, as the interpreter multiplies
             c.im = ctab[2 * m + 1];
-            f = fac_mul(o, f, c, "g" + std::to_string(m));
+            f = fac_mul(o, P, f, c, "g" + std::to_string(m));
         }
-        if (f.kind != Fac::ONE) o << "                v[" << m << "] = cmul(v[" << m << "], " << fac_expr(f) << ");\n";
+        if (f.kind != Fac::ONE) o << "                v[" << m << "] = cmul(v[" << m << "], " << fac_expr(P, f) << ");\n";
     }
     o << "            }\n";
 }
@@ -295,6 +312,10 @@ struct Scaled {
     int r0 = 0, r1 = 0;      // form 1: rows (0 x0 + x1, 1 x0 - x1, 2 x1 - x0)
 };
 
+// The form follows the op's structure (its subtype and which entries are
+// equal), not its angle: RX(t) and the real rotations of the Euler split
+// keep form 3 / 2 for every t except the measure-zero set where the pivot
+// is (nearly) zero, so circuits with fresh angles reuse their kernels.
 Scaled scaled_form(const uint32_t *b, int sub)
 {
     using namespace prog;
@@ -305,7 +326,7 @@ Scaled scaled_form(const uint32_t *b, int sub)
     };
     Scaled r;
     const long double a = f(0), d = f(6);
-    if (a == 0 || fabsl(a) < 0.125L) return r;   // keep magnitudes bounded
+    if (!(fabsl(a) >= 0x1p-24L)) return r;   // the pivot divides: keep it away from zero
     if (sub == DS_REAL) {
         const long double bb = f(2), cc = f(4);
         if (fabsl(bb) == fabsl(a) && fabsl(cc) == fabsl(a) && fabsl(d) == fabsl(a)) {
@@ -335,6 +356,31 @@ Scaled scaled_form(const uint32_t *b, int sub)
     return r;
 }
 
+// the phase slots of every segment of program w
+std::vector<SlotSrc> read_slots(const std::vector<uint32_t> &w, int RB, int SCP)
+{
+    using namespace prog;
+    const int S = 1 + RB;
+    std::vector<SlotSrc> slots((size_t)w[H_NDSEG] * SCP);
+    for (uint32_t i = 0; i < w[H_NCTA]; i++) {
+        const uint32_t *e = &w[w[H_CTA_OFF] + (size_t)i * kCtaWords];
+        SlotSrc &ss = slots[e[0]];
+        if (e[2] | e[3]) {
+            ss.cta_dyn = true;
+        } else {
+            ss.ncst++;
+            ss.cst += e[4];
+        }
+    }
+    for (uint32_t i = 0; i < w[H_NTHR]; i++) {
+        const uint32_t *e = &w[w[H_THR_OFF] + (size_t)i * kThrWords];
+        slots[(size_t)(e[0] / S) * SCP + e[0] % S].thr = true;
+    }
+    return slots;
+}
+
+const char *kParamStruct = "struct JP { uint32_t w[";
+
 }  // namespace
 
 bool jit_supported(bool f64, int C, int RB) { return !f64 && C == 12 && (RB == 4 || RB == 5); }
@@ -342,7 +388,8 @@ bool jit_supported_diag(bool f64, int RB) { return !f64 && RB == 4; }
 
 // CUDA source of the fused diagonal sweep (K3) specialised to program `w`:
 // its one phase segment as generated code, the sweep as in the interpreter.
-static bool jit_source_diag(const std::vector<uint32_t> &w, std::string &src, std::string &err)
+static bool jit_source_diag(const std::vector<uint32_t> &w, std::string &src, std::vector<uint32_t> &vals,
+                            std::string &err)
 {
     using namespace prog;
     const int C = (int)w[H_C], RB = (int)w[H_RB];
@@ -350,67 +397,52 @@ static bool jit_source_diag(const std::vector<uint32_t> &w, std::string &src, st
         err = "specialised kernels: complex64 diagonal sweeps with RB = 4 only";
         return false;
     }
-    const int TB = 7, S = 1 + RB, SCP = (int)cta_stride(RB, TB, 4);
-    const int nd = (int)w[H_NDSEG];
-    std::vector<SlotSrc> slots((size_t)nd * SCP);
-    for (uint32_t i = 0; i < w[H_NCTA]; i++) {
-        const uint32_t *e = &w[w[H_CTA_OFF] + (size_t)i * kCtaWords];
-        SlotSrc &ss = slots[e[0]];
-        if (e[2] | e[3]) ss.cta_dyn = true;
-        else ss.cst += e[4];
-    }
-    for (uint32_t i = 0; i < w[H_NTHR]; i++) {
-        const uint32_t *e = &w[w[H_THR_OFF] + (size_t)i * kThrWords];
-        slots[(size_t)(e[0] / S) * SCP + e[0] % S].thr = true;
-    }
+    const int TB = 7, SCP = (int)cta_stride(RB, TB, 4);
+    const std::vector<SlotSrc> slots = read_slots(w, RB, SCP);
     const size_t body = w[H_STAGE_OFF] + S_SIZE + O_BODY;
+    PBlock P;
+    std::ostringstream g;
+    if (w[body + D_NMULTI])
+        g << "            dseg_apply<R, RB, T, 3>(v, x0, prog + " << body << ", cta_ph, thr_ph, nhoist, tid);\n";
+    else
+        gen_segment(g, P, w, body, slots, RB, TB, 128, SCP, false, 1.0L);
+    if (P.w.empty()) P.w.push_back(0);
     std::ostringstream o;
-    o << "#include \"chunk_dev.cuh\"\nnamespace svs {\nstruct JDiag {\n"
+    o << "#include \"chunk_dev.cuh\"\nnamespace svs {\n" << kParamStruct << P.w.size() << "]; };\n"
+      << "struct JDiag {\n    using Params = JP;\n"
          "    template <typename R, int RB, int T>\n"
          "    static __device__ __forceinline__ void seg(typename CT<R>::T2 (&v)[1 << RB], uint64_t x0,\n"
          "        const uint32_t *prog, const uint32_t *, const typename CT<R>::W *cta_ph,\n"
-         "        const typename CT<R>::W *thr_ph, int nhoist, int tid)\n    {\n";
-    if (w[body + D_NMULTI])
-        o << "            dseg_apply<R, RB, T, 3>(v, x0, prog + " << body << ", cta_ph, thr_ph, nhoist, tid);\n";
-    else
-        gen_segment(o, w, body, slots, RB, TB, 128, SCP, 1.0L);
-    o << "    }\n};\n}  // namespace svs\n";
+         "        const typename CT<R>::W *thr_ph, int nhoist, int tid, const JP &P)\n    {\n"
+      << g.str() << "    }\n};\n}  // namespace svs\n";
     o << "extern \"C\" __global__ void __launch_bounds__(128) " << kDiagKernelName
       << "(svs::CT<float>::G2 *__restrict__ a, const uint32_t *__restrict__ gprog, int n, "
-         "svs::TSrc<svs::CT<float>::G2> src)\n{\n    svs::diag_sweep<float, "
-      << RB << ", svs::JDiag>(a, gprog, n, src);\n}\n";
+         "svs::TSrc<svs::CT<float>::G2> src, const __grid_constant__ svs::JP P)\n{\n    svs::diag_sweep<float, "
+      << RB << ", svs::JDiag>(a, gprog, n, src, P);\n}\n";
     src = o.str();
+    vals.swap(P.w);
     return true;
 }
 
 // CUDA source of the kernel specialised to program `w` (complex64, C = 12,
-// RB = 4).  Ops are walked as the interpreter walks them.
-bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std::string &err)
+// RB = 4 or 5) and the values of its parameter block.  Ops are walked as the
+// interpreter walks them.
+bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std::vector<uint32_t> &vals,
+                std::string &err)
 {
     using namespace prog;
-    if (kind == JIT_DIAG) return jit_source_diag(w, src, err);
+    if (kind == JIT_DIAG) return jit_source_diag(w, src, vals, err);
     const int C = (int)w[H_C], RB = (int)w[H_RB], ns = (int)w[H_NSTAGE];
     if (w[H_WBYTES] != 4 || !jit_supported(false, C, RB)) {
         err = "specialised kernels: complex64 chunk programs with C = 12, RB = 4 or 5 only";
         return false;
     }
-    const int T = 1 << (C - RB), NR = 1 << RB, TB = C - RB, S = 1 + RB;
+    const int T = 1 << (C - RB), NR = 1 << RB, TB = C - RB;
     const int SCP = (int)cta_stride(RB, TB, 4);
     // where every phase sum comes from (per segment and slot)
-    const int nd = (int)w[H_NDSEG];
-    std::vector<SlotSrc> slots((size_t)nd * SCP);
-    for (uint32_t i = 0; i < w[H_NCTA]; i++) {
-        const uint32_t *e = &w[w[H_CTA_OFF] + (size_t)i * kCtaWords];
-        SlotSrc &ss = slots[e[0]];
-        if (e[2] | e[3]) ss.cta_dyn = true;
-        else ss.cst += e[4];
-    }
-    for (uint32_t i = 0; i < w[H_NTHR]; i++) {
-        const uint32_t *e = &w[w[H_THR_OFF] + (size_t)i * kThrWords];
-        slots[(size_t)(e[0] / S) * SCP + e[0] % S].thr = true;
-    }
+    const std::vector<SlotSrc> slots = read_slots(w, RB, SCP);
+    PBlock P;
     std::ostringstream o;
-    o << "#include \"chunk_dev.cuh\"\nnamespace svs {\nstruct JOps {\n";
     o << "    static constexpr int kStages = " << ns << ";\n";
     // direct boundary stages: their register offsets in HBM
     const uint32_t direct = w[H_DIRECT];
@@ -447,12 +479,11 @@ bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std:
     o << "    template <typename R, int RB, int T>\n"
          "    static __device__ __forceinline__ void run(int s, typename CT<R>::T2 (&v)[1 << RB], uint64_t x0,\n"
          "        const uint32_t *prog, const uint32_t *, const typename CT<R>::W *cta_ph,\n"
-         "        const typename CT<R>::W *thr_ph, int nhoist, int tid)\n    {\n";
+         "        const typename CT<R>::W *thr_ph, int nhoist, int tid, const JP &P)\n    {\n";
     // pass 1: the scaled forms of one-qubit ops and the sweep's product of
     // their scalars (kept above 2^-40 so that no amplitude underflows)
     std::map<size_t, Scaled> scaled;
     long double scale = 1;
-    bool has_seg = false;
     for (int s = 0; s < ns; s++) {
         size_t op = w[H_STAGE_OFF + s] + S_SIZE;
         for (uint32_t k = 0; k < w[w[H_STAGE_OFF + s] + S_NOPS]; k++) {
@@ -464,15 +495,13 @@ bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std:
                     scaled[body] = sf;
                     scale *= sf.s;
                 }
-            } else if ((hdr & 0xff) == OP_DSEG && !w[body + D_NMULTI]) {
-                has_seg = true;
             }
             op += w[op + O_WORDS];
         }
     }
     // the scale goes into the first factored phase segment's base factor, or
     // multiplies the amplitudes at the end of the last stage
-    bool scale_done = scale == 1.0L;
+    bool scale_done = scaled.empty();
     for (int s = 0; s < ns; s++) {
         const size_t so = w[H_STAGE_OFF + s];
         o << "        if (s == " << s << ") {\n";
@@ -488,44 +517,51 @@ bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std:
                     // exactly the identity in complex64 (e.g. H H): nothing to do
                 } else if (sc != scaled.end()) {
                     const Scaled &f = sc->second;
-                    if (f.form == 1)
+                    if (f.form == 1) {
                         o << "            dense1_pm<" << NR << ", " << code << ", " << f.r0 << ", " << f.r1 << ">(v);\n";
-                    else
+                    } else {
+                        const std::string t0 = P.f(f.t0);
                         o << "            dense1_" << (f.form == 2 ? "rot<" : "rxn<") << NR << ", " << code << ">(v, "
-                          << flit_f(f.t0) << ", " << flit_f(f.t1) << ");\n";
+                          << t0 << ", " << P.f(f.t1) << ");\n";
+                    }
                 } else if (kq == 1 && sub != DS_GENERAL) {
                     const bool re = sub == DS_REAL;
-                    o << "            dense1_special_f<" << NR << ", " << code << ", " << sub << ">(v, " << flit(w[body])
-                      << ", " << flit(w[body + (re ? 2 : 3)]) << ", " << flit(w[body + (re ? 4 : 5)]) << ", "
-                      << flit(w[body + 6]) << ");\n";
+                    const std::string pa = P.fbits(w[body]), pb = P.fbits(w[body + (re ? 2 : 3)]);
+                    const std::string pc = P.fbits(w[body + (re ? 4 : 5)]), pd = P.fbits(w[body + 6]);
+                    o << "            dense1_special_f<" << NR << ", " << code << ", " << sub << ">(v, " << pa << ", "
+                      << pb << ", " << pc << ", " << pd << ");\n";
                 } else if (kq == 1) {
                     o << "            { const float m[8] = {";
-                    for (int i = 0; i < 8; i++) o << (i ? ", " : "") << flit(w[body + i]);
+                    for (int i = 0; i < 8; i++) o << (i ? ", " : "") << P.fbits(w[body + i]);
                     o << "}; dense1_general_f<" << NR << ", " << code << ">(v, m); }\n";
                 } else {
                     o << "            { const float m[32] = {";
-                    for (int i = 0; i < 32; i++) o << (i ? ", " : "") << flit(w[body + i]);
+                    for (int i = 0; i < 32; i++) o << (i ? ", " : "") << P.fbits(w[body + i]);
                     o << "}; dense2_f<" << NR << ", " << (code & 7) << ", " << ((code >> 3) & 7) << ">(v, m); }\n";
                 }
             } else if (w[body + D_NMULTI]) {
                 // terms on several register bits and other bits: the general path
                 o << "            dseg_apply<R, RB, T, 3>(v, x0, prog + " << body << ", cta_ph, thr_ph, nhoist, tid);\n";
             } else {
-                gen_segment(o, w, body, slots, RB, TB, T, SCP, scale_done ? 1.0L : scale);
+                gen_segment(o, P, w, body, slots, RB, TB, T, SCP, !scale_done, scale);
                 scale_done = true;
             }
             op += len;
         }
-        if (s == ns - 1 && !scale_done) o << "            scale_all<" << NR << ">(v, " << flit_f(scale) << ");\n";
+        if (s == ns - 1 && !scale_done) o << "            scale_all<" << NR << ">(v, " << P.f((float)scale) << ");\n";
         o << "        }\n";
     }
-    (void)has_seg;
     o << "    }\n};\n}  // namespace svs\n";
     o << "extern \"C\" __global__ void __launch_bounds__(" << T << ", 3) " << kKernelName
       << "(svs::CT<float>::G2 *__restrict__ a, const uint32_t *__restrict__ gprog, int n, "
-         "svs::TSrc<svs::CT<float>::G2> src)\n{\n    svs::chunk_sweep<float, "
-      << C << ", " << RB << ", svs::JOps>(a, gprog, n, src);\n}\n";
-    src = o.str();
+         "svs::TSrc<svs::CT<float>::G2> src, const __grid_constant__ svs::JP P)\n{\n    svs::chunk_sweep<float, "
+      << C << ", " << RB << ", svs::JOps>(a, gprog, n, src, P);\n}\n";
+    if (P.w.empty()) P.w.push_back(0);
+    std::ostringstream full;
+    full << "#include \"chunk_dev.cuh\"\nnamespace svs {\n" << kParamStruct << P.w.size() << "]; };\n"
+         << "struct JOps {\n    using Params = JP;\n" << o.str();
+    src = full.str();
+    vals.swap(P.w);
     return true;
 }
 
@@ -562,16 +598,30 @@ bool jit_compile(const std::string &src, std::vector<char> &cubin, std::string &
     return ok;
 }
 
-namespace {
-
 struct JitKernel {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kern = nullptr;
-    unsigned dev_mask = 0;    // devices whose dynamic shared-memory limit is raised
+    unsigned dev_mask = 0;    // devices it was launched on (dynamic shared-memory limit raised)
+    size_t pwords = 0;        // parameter-block words
+    int kind = JIT_CHUNK;
+    uint64_t stamp = 0;       // last use (LRU)
 };
 
+namespace {
+
 std::mutex g_mu;
-std::map<std::string, std::shared_ptr<JitKernel>> g_cache;
+// kernels by source (structure only), and recent programs by their words
+std::unordered_map<std::string, std::shared_ptr<JitKernel>> g_kernels;
+struct ProgEntry {
+    std::string src;
+    std::shared_ptr<const std::vector<uint32_t>> vals;
+    uint64_t stamp = 0;
+};
+std::unordered_map<std::string, ProgEntry> g_progs;
+std::vector<std::shared_ptr<JitKernel>> g_retired;   // evicted, unloaded when no launch can use them
+size_t g_limit = 256;
+uint64_t g_clock = 0;
+uint64_t g_compiles = 0;
 double g_compile_ms = 0;   // wall time of jit_prepare's compiles
 
 std::string key_of(const std::vector<uint32_t> &w, int kind)
@@ -579,93 +629,197 @@ std::string key_of(const std::vector<uint32_t> &w, int kind)
     return std::string(1, (char)('0' + kind)) + std::string((const char *)w.data(), w.size() * 4);
 }
 
-std::shared_ptr<JitKernel> lookup(const std::string &key)
+// Unload evicted kernels no host thread holds any more, after the devices
+// they ran on have finished all work (a launch may still be queued).
+void unload_retired_locked()
 {
-    std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_cache.find(key);
-    return it == g_cache.end() ? nullptr : it->second;
+    bool any = false;
+    for (const auto &k : g_retired) any = any || k.use_count() == 1;
+    if (!any) return;
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) return;
+    unsigned synced = 0;
+    std::vector<std::shared_ptr<JitKernel>> keep;
+    for (auto &k : g_retired) {
+        if (k.use_count() != 1) {
+            keep.push_back(k);
+            continue;
+        }
+        bool ok = true;
+        for (int d = 0; d < 32 && ok; d++)
+            if (((k->dev_mask >> d) & 1) && !((synced >> d) & 1)) {
+                ok = cudaSetDevice(d) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
+                if (ok) synced |= 1u << d;
+            }
+        if (ok && k->lib) cudaLibraryUnload(k->lib);
+        else if (!ok) keep.push_back(k);
+    }
+    cudaSetDevice(cur);
+    g_retired.swap(keep);
 }
 
-// compile and load one program's kernel into the cache
-bool build_one(const std::vector<uint32_t> &w, int kind, std::string &err)
+void evict_locked()
 {
-    const std::string key = key_of(w, kind);
-    if (lookup(key)) return true;
-    std::string src;
+    while (g_kernels.size() > g_limit) {
+        auto lru = g_kernels.begin();
+        for (auto it = g_kernels.begin(); it != g_kernels.end(); ++it)
+            if (it->second->stamp < lru->second->stamp) lru = it;
+        g_retired.push_back(lru->second);
+        g_kernels.erase(lru);
+    }
+    while (g_progs.size() > 4 * g_limit) {
+        auto lru = g_progs.begin();
+        for (auto it = g_progs.begin(); it != g_progs.end(); ++it)
+            if (it->second.stamp < lru->second.stamp) lru = it;
+        g_progs.erase(lru);
+    }
+    unload_retired_locked();
+}
+
+// compile and load one kernel
+bool build_one(const std::string &src, int kind, size_t pwords, std::shared_ptr<JitKernel> &out, std::string &err)
+{
     std::vector<char> cubin;
-    if (!jit_source(w, kind, src, err) || !jit_compile(src, cubin, err)) return false;
+    if (!jit_compile(src, cubin, err)) return false;
     auto k = std::make_shared<JitKernel>();
+    k->pwords = pwords;
+    k->kind = kind;
     cudaError_t e = cudaLibraryLoadData(&k->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (e == cudaSuccess) e = cudaLibraryGetKernel(&k->kern, k->lib, kind == JIT_DIAG ? kDiagKernelName : kKernelName);
     if (e != cudaSuccess) {
         err = std::string("loading a specialised kernel: ") + cudaGetErrorString(e);
+        if (k->lib) cudaLibraryUnload(k->lib);
         return false;
     }
-    std::lock_guard<std::mutex> lk(g_mu);
-    g_cache.emplace(key, k);   // a concurrent build of the same program keeps the first
+    out = k;
     return true;
 }
 
 }  // namespace
 
-bool jit_prepare(const std::vector<JitProg> &progs, std::string &err)
+bool jit_prepare(const std::vector<JitProg> &progs, std::vector<JitHandle> &out, std::string &err)
 {
-    std::vector<JitProg> todo;
-    for (const JitProg &p : progs)
-        if (!lookup(key_of(*p.w, p.kind))) {
-            bool dup = false;
-            for (const JitProg &x : todo) dup = dup || (x.kind == p.kind && *x.w == *p.w);
-            if (!dup) todo.push_back(p);
+    out.assign(progs.size(), JitHandle());
+    // 1. each program's source and parameter values (remembered per program)
+    std::vector<std::string> srcs(progs.size());
+    for (size_t i = 0; i < progs.size(); i++) {
+        const std::string wk = key_of(*progs[i].w, progs[i].kind);
+        {
+            std::lock_guard<std::mutex> lk(g_mu);
+            auto it = g_progs.find(wk);
+            if (it != g_progs.end()) {
+                it->second.stamp = ++g_clock;
+                srcs[i] = it->second.src;
+                out[i].vals = it->second.vals;
+                continue;
+            }
         }
-    if (todo.empty()) return true;
-    const auto t0 = std::chrono::steady_clock::now();
-    // compile in parallel (NVRTC programs are independent)
-    const size_t nt = std::min<size_t>(todo.size(), std::max(1u, std::min(8u, std::thread::hardware_concurrency())));
-    std::vector<std::string> errs(todo.size());
-    std::vector<std::thread> th;
-    for (size_t t = 0; t < nt; t++)
-        th.emplace_back([&, t] {
-            for (size_t i = t; i < todo.size(); i += nt) build_one(*todo[i].w, todo[i].kind, errs[i]);
-        });
-    for (auto &x : th) x.join();
+        std::string src;
+        auto vals = std::make_shared<std::vector<uint32_t>>();
+        if (!jit_source(*progs[i].w, progs[i].kind, src, *vals, err)) return false;
+        if (vals->size() > kMaxParamWords) {
+            srcs[i].clear();   // too many numbers for the argument space: the interpreter runs it
+            continue;
+        }
+        srcs[i] = src;
+        out[i].vals = vals;
+        std::lock_guard<std::mutex> lk(g_mu);
+        ProgEntry &pe = g_progs[wk];
+        pe.src = src;
+        pe.vals = vals;
+        pe.stamp = ++g_clock;
+    }
+    // 2. kernels: cached ones by source; compile the missing ones in parallel
+    std::vector<size_t> todo;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        g_compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        for (size_t i = 0; i < progs.size(); i++) {
+            if (srcs[i].empty()) continue;
+            auto it = g_kernels.find(srcs[i]);
+            if (it != g_kernels.end()) {
+                it->second->stamp = ++g_clock;
+                out[i].k = it->second;
+                continue;
+            }
+            bool dup = false;
+            for (size_t j : todo) dup = dup || srcs[j] == srcs[i];
+            if (!dup) todo.push_back(i);
+        }
     }
-    for (const std::string &e : errs)
-        if (!e.empty()) {
-            err = e;
+    if (!todo.empty()) {
+        const auto t0 = std::chrono::steady_clock::now();
+        const size_t nt = std::min<size_t>(todo.size(), std::max(1u, std::min(8u, std::thread::hardware_concurrency())));
+        std::vector<std::string> errs(todo.size());
+        std::vector<std::shared_ptr<JitKernel>> built(todo.size());
+        std::vector<std::thread> th;
+        for (size_t t = 0; t < nt; t++)
+            th.emplace_back([&, t] {
+                for (size_t x = t; x < todo.size(); x += nt) {
+                    const size_t i = todo[x];
+                    build_one(srcs[i], progs[i].kind, out[i].vals->size(), built[x], errs[x]);
+                }
+            });
+        for (auto &x : th) x.join();
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        for (size_t x = 0; x < todo.size(); x++) {
+            if (!built[x]) {
+                err = errs[x];
+                return false;
+            }
+            g_compiles++;
+            built[x]->stamp = ++g_clock;
+            // a concurrent build of the same source keeps the first
+            g_kernels.emplace(srcs[todo[x]], built[x]);
+        }
+        for (size_t i = 0; i < progs.size(); i++)
+            if (!srcs[i].empty() && !out[i].k) {
+                auto it = g_kernels.find(srcs[i]);
+                if (it != g_kernels.end()) out[i].k = it->second;
+            }
+        evict_locked();
+    }
+    for (size_t i = 0; i < progs.size(); i++)
+        if (!srcs[i].empty() && !out[i].k) {
+            err = "specialised kernel missing after its build";
             return false;
         }
     return true;
 }
 
-size_t jit_cache_size(double *compile_ms)
+size_t jit_cache_size(double *compile_ms, uint64_t *compiles)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     if (compile_ms) *compile_ms = g_compile_ms;
-    return g_cache.size();
+    if (compiles) *compiles = g_compiles;
+    return g_kernels.size();
 }
 
-cudaError_t launch_chunk_jit(void *a, int n, const std::vector<uint32_t> &w, const uint32_t *prog, size_t smem,
-                             TensorSrc src, cudaStream_t st)
+void jit_set_cache_limit(size_t max_kernels)
 {
-    std::shared_ptr<JitKernel> k = lookup(key_of(w, JIT_CHUNK));
-    if (!k) return cudaErrorInvalidDeviceFunction;   // jit_prepare first
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_limit = std::max<size_t>(1, max_kernels);
+    evict_locked();
+}
+
+static cudaError_t launch_jit(const JitHandle &h, void *a, int n, const uint32_t *prog, size_t smem, TensorSrc src,
+                              cudaStream_t st, int threads, int C)
+{
+    if (!h.k || !h.vals || h.vals->size() != h.k->pwords) return cudaErrorInvalidDeviceFunction;   // jit_prepare first
+    JitKernel &k = *h.k;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!((k->dev_mask >> dev) & 1)) {
-            e = cudaKernelSetAttributeForDevice(k->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024, dev);
+        if (!((k.dev_mask >> dev) & 1)) {
+            e = cudaKernelSetAttributeForDevice(k.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024, dev);
             if (e != cudaSuccess) return e;
-            k->dev_mask |= 1u << dev;
+            k.dev_mask |= 1u << dev;
         }
     }
-    const int C = (int)w[prog::H_C], RB = (int)w[prog::H_RB];
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)k->kern, 1 << (C - RB), smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)k.kern, threads, smem);
     if (e != cudaSuccess) return e;
     if (occ <= 0) return cudaErrorInvalidConfiguration;
     const int64_t work = (int64_t)1 << (n - C);
@@ -675,45 +829,26 @@ cudaError_t launch_chunk_jit(void *a, int n, const std::vector<uint32_t> &w, con
         const void *hi, *lo;
         int n_lo;
     } ts{src.hi, src.lo, src.n_lo};
-    void *args[] = {&a, (void *)&prog, &n, &ts};
-    e = cudaLaunchKernel((const void *)k->kern, dim3(grid), dim3(1 << (C - RB)), args, smem, st);
+    void *args[] = {&a, (void *)&prog, &n, &ts, (void *)h.vals->data()};
+    e = cudaLaunchKernel((const void *)k.kern, dim3(grid), dim3(threads), args, smem, st);
     return counted(e, 1);
+}
+
+// The specialised chunk sweep: persistent grid = resident CTAs x SMs.
+cudaError_t launch_chunk_jit(const JitHandle &h, void *a, int n, const std::vector<uint32_t> &w, const uint32_t *prog,
+                             size_t smem, TensorSrc src, cudaStream_t st)
+{
+    const int C = (int)w[prog::H_C], RB = (int)w[prog::H_RB];
+    return launch_jit(h, a, n, prog, smem, src, st, 1 << (C - RB), C);
 }
 
 // The specialised fused diagonal sweep: tiles of 2^(7 + RB) amplitudes, 128
 // threads, grid = resident CTAs x SMs (as launch_diag_sweep).
-cudaError_t launch_diag_jit(void *a, int n, const std::vector<uint32_t> &w, const uint32_t *prog, size_t smem,
-                            TensorSrc src, cudaStream_t st)
+cudaError_t launch_diag_jit(const JitHandle &h, void *a, int n, const std::vector<uint32_t> &w, const uint32_t *prog,
+                            size_t smem, TensorSrc src, cudaStream_t st)
 {
-    std::shared_ptr<JitKernel> k = lookup(key_of(w, JIT_DIAG));
-    if (!k) return cudaErrorInvalidDeviceFunction;   // jit_prepare first
     if (src.hi && (src.n_lo < 0 || src.n_lo > n || !src.lo)) return cudaErrorInvalidValue;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!((k->dev_mask >> dev) & 1)) {
-            e = cudaKernelSetAttributeForDevice(k->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024, dev);
-            if (e != cudaSuccess) return e;
-            k->dev_mask |= 1u << dev;
-        }
-    }
-    const int C = (int)w[prog::H_C];
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)k->kern, 128, smem);
-    if (e != cudaSuccess) return e;
-    if (occ <= 0) return cudaErrorInvalidConfiguration;
-    const int64_t work = (int64_t)1 << (n - C);
-    const int64_t g = (int64_t)device_sm_count() * occ;
-    const int grid = (int)(g < work ? g : work);
-    struct {
-        const void *hi, *lo;
-        int n_lo;
-    } ts{src.hi, src.lo, src.n_lo};
-    void *args[] = {&a, (void *)&prog, &n, &ts};
-    e = cudaLaunchKernel((const void *)k->kern, dim3(grid), dim3(128), args, smem, st);
-    return counted(e, 1);
+    return launch_jit(h, a, n, prog, smem, src, st, 128, (int)w[prog::H_C]);
 }
 
 }  // namespace svs

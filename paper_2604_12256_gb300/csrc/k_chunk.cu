@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(
                                                          const uint32_t *__restrict__ gprog, int n,
                                                          TSrc<typename CT<R>::G2> src)
 {
-    chunk_sweep<R, C, RB, InterpOps>(a, gprog, n, src);
+    chunk_sweep<R, C, RB, InterpOps>(a, gprog, n, src, NoParams{});
 }
 
 // ------------------------------------------------------------ K3 diagonal sweep (interpreter)
@@ -40,7 +40,7 @@ template <typename R, int RB>
 __global__ void __launch_bounds__(128) k_diag(typename CT<R>::G2 *__restrict__ a, const uint32_t *__restrict__ gprog,
                                               int n, TSrc<typename CT<R>::G2> src)
 {
-    diag_sweep<R, RB, DiagInterp>(a, gprog, n, src);
+    diag_sweep<R, RB, DiagInterp>(a, gprog, n, src, NoParams{});
 }
 
 // ------------------------------------------------------------ launchers

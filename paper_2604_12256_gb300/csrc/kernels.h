@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <string>
+#include <memory>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -92,27 +93,37 @@ cudaError_t launch_chunk(void *a, int n, bool is_f64, int C, int RB, const uint3
                          TensorSrc src, cudaStream_t st);
 
 // Chunk sweeps specialised to one program (jit.cpp; complex64, C = 12,
-// RB = 4): jit_prepare compiles (NVRTC) and loads the kernels of the given
-// host programs that are not cached yet, in parallel; launch_chunk_jit runs
-// the cached kernel of host program `w` (device copy `prog`), with the same
-// arguments and results as launch_chunk.
-// Fused diagonal sweeps (K3, complex64, RB = 4) likewise: launch_diag_jit
-// has launch_diag_sweep's arguments and results.
+// RB = 4 or 5): jit_prepare finds (or generates and compiles with NVRTC, in
+// parallel) the kernel of each host program and the values of its parameter
+// block; launch_chunk_jit runs it on the device copy `prog` of program `w`,
+// with the same arguments and results as launch_chunk.  Fused diagonal
+// sweeps (K3, complex64, RB = 4) likewise: launch_diag_jit has
+// launch_diag_sweep's arguments and results.  Kernels are keyed by their
+// generated source, which holds the program's structure only (its numbers
+// are parameters), and kept at most jit_set_cache_limit() at a time.
 enum { JIT_CHUNK = 0, JIT_DIAG = 1 };
 struct JitProg {
     const std::vector<uint32_t> *w;   // host program words
     int kind;                         // JIT_CHUNK or JIT_DIAG
 };
+struct JitKernel;
+struct JitHandle {
+    std::shared_ptr<JitKernel> k;                        // null: run the interpreter kernel
+    std::shared_ptr<const std::vector<uint32_t>> vals;   // the launch's parameter block
+};
 bool jit_supported(bool is_f64, int C, int RB);
 bool jit_supported_diag(bool is_f64, int RB);
-bool jit_prepare(const std::vector<JitProg> &progs, std::string &err);
-cudaError_t launch_chunk_jit(void *a, int n, const std::vector<uint32_t> &w, const uint32_t *prog, size_t smem,
-                             TensorSrc src, cudaStream_t st);
-cudaError_t launch_diag_jit(void *a, int n, const std::vector<uint32_t> &w, const uint32_t *prog, size_t smem,
-                            TensorSrc src, cudaStream_t st);
-size_t jit_cache_size(double *compile_ms);   // kernels cached, total compile wall time
-// the generated source and its NVRTC compile (no device needed)
-bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std::string &err);
+bool jit_prepare(const std::vector<JitProg> &progs, std::vector<JitHandle> &out, std::string &err);
+cudaError_t launch_chunk_jit(const JitHandle &h, void *a, int n, const std::vector<uint32_t> &w, const uint32_t *prog,
+                             size_t smem, TensorSrc src, cudaStream_t st);
+cudaError_t launch_diag_jit(const JitHandle &h, void *a, int n, const std::vector<uint32_t> &w, const uint32_t *prog,
+                            size_t smem, TensorSrc src, cudaStream_t st);
+// kernels cached now; total compiles and their wall time (ms) so far
+size_t jit_cache_size(double *compile_ms, uint64_t *compiles);
+void jit_set_cache_limit(size_t max_kernels);
+// the generated source with its parameter values, and its NVRTC compile (no device needed)
+bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std::vector<uint32_t> &vals,
+                std::string &err);
 bool jit_compile(const std::string &src, std::vector<char> &cubin, std::string &err);
 
 // Phase polynomial on small registers: one thread per amplitude sums the

@@ -369,6 +369,7 @@ static void encode_dseg(ProgWriter &pw, const std::vector<Term> &terms, const Ds
     std::vector<std::vector<Term>> lin(RB);
     std::vector<std::pair<Term, uint32_t>> multi;
     std::vector<uint64_t> tab(1u << RB, 0);
+    uint32_t tabmask = 0;   // entries of tab that register-only terms reach
     const uint32_t S = 1 + RB, SCP = prog::cta_stride(RB, cx.TB, f64 ? 8 : 4);
     auto to_tables = [&](uint32_t slot, uint64_t nonreg, uint64_t w) {
         uint64_t mt = nonreg & thrall;
@@ -416,7 +417,11 @@ static void encode_dseg(ProgWriter &pw, const std::vector<Term> &terms, const Ds
             // (a CTA-table entry whose mask is always met)
             to_tables(1 + __builtin_ctz(rm), 0, t.w);
         } else if (nonreg == 0) {
-            for (uint32_t m = 0; m < (1u << RB); m++) if ((m & rm) == rm) tab[m] += t.w;
+            for (uint32_t m = 0; m < (1u << RB); m++)
+                if ((m & rm) == rm) {
+                    tab[m] += t.w;
+                    if (RB <= 5) tabmask |= 1u << m;
+                }
         } else if (popc(rm) == 1) {
             int j = __builtin_ctz(rm);
             if (!to_tables(1 + j, nonreg, t.w)) lin[j].push_back({nonreg, t.w});
@@ -437,7 +442,7 @@ static void encode_dseg(ProgWriter &pw, const std::vector<Term> &terms, const Ds
     pw.put((uint32_t)multi.size());
     for (int j = 0; j < prog::kMaxRB; j++) pw.put(j < RB ? (uint32_t)lin[j].size() : 0);
     pw.put((uint32_t)pivot);
-    pw.put(0);
+    pw.put(RB <= 5 ? tabmask : 0xffffffffu);
     pw.put(0);
     pw.put(0);
     auto put_term = [&](const Term &t) {

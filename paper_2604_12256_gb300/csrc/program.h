@@ -131,7 +131,11 @@ enum : int {
     D_NLIN = 4,           // kMaxRB counts: terms with register bit j and other bits
     D_PIVOT = D_NLIN + kMaxRB,   // register bit present in every term, or -1:
                                  // then only amplitudes with that bit set change
-    D_TERMS = D_PIVOT + 4        // 16-byte aligned (words D_PIVOT + 1 .. + 3 are 0)
+    D_TABMASK = D_PIVOT + 1,     // bit m (RB <= 5): some register-only term has all
+                                 // its register bits in m, so entry m of the
+                                 // register-only table has terms (whatever their
+                                 // weights sum to); 0xffffffff for RB > 5
+    D_TERMS = D_PIVOT + 4        // 16-byte aligned (words D_PIVOT + 2, + 3 are 0)
 };
 static_assert(D_NLIN % 4 == 0 && D_TERMS % 4 == 0, "segment header alignment");
 // dense op subtypes (hdr bits 12..15), for k = 1

@@ -114,6 +114,10 @@ _SIGS = [
     ("sim_jit_info", ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]),
     ("sim_jit_check", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _P, ctypes.c_size_t,
                                      ctypes.POINTER(sim_options), ctypes.POINTER(ctypes.c_int)]),
+    ("sim_jit_cache", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    ("sim_jit_sources", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _P, ctypes.c_size_t,
+                                       ctypes.POINTER(sim_options), ctypes.c_char_p, ctypes.c_size_t,
+                                       ctypes.POINTER(ctypes.c_size_t)]),
 ]
 
 
@@ -215,11 +219,35 @@ def jit_check(n: int, gates, dtype: int = SIM_C64, basis: Optional[int] = 0,
 
 
 def jit_info() -> dict:
-    """Specialised kernels cached in this process and their total compile time."""
+    """Specialised kernels cached in this process now, NVRTC compiles so far
+    and their total compile time."""
     lib = load()
     n, ms = ctypes.c_uint64(0), ctypes.c_double(0)
     _check(lib.sim_jit_info(ctypes.byref(n), ctypes.byref(ms)))
-    return {"programs": n.value, "compile_ms": ms.value}
+    k, c = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(lib.sim_jit_cache(0, ctypes.byref(k), ctypes.byref(c)))
+    return {"programs": n.value, "compiles": c.value, "compile_ms": ms.value}
+
+
+def jit_cache_limit(max_kernels: int) -> None:
+    """At most max_kernels specialised kernels stay loaded (LRU)."""
+    _check(load().sim_jit_cache(int(max_kernels), None, None))
+
+
+def jit_sources(n: int, gates, dtype: int = SIM_C64, basis: Optional[int] = 0,
+                opt: Optional[sim_options] = None) -> str:
+    """The generated sources of the plan's specialised sweeps (no GPU needed)."""
+    lib = load()
+    ga = gates if isinstance(gates, GateArray) else GateArray(gates)
+    b = (1 << 64) - 1 if basis is None else basis
+    optp = ctypes.byref(opt) if opt is not None else None
+    need = ctypes.c_size_t(0)
+    rc = lib.sim_jit_sources(n, dtype, b, ga.ptr, ga.n, optp, None, 0, ctypes.byref(need))
+    if rc not in (SIM_OK, SIM_ENOMEM):
+        _check(rc)
+    buf = ctypes.create_string_buffer(need.value)
+    _check(lib.sim_jit_sources(n, dtype, b, ga.ptr, ga.n, optp, buf, need.value, ctypes.byref(need)))
+    return buf.value.decode()
 
 
 class Sim:

@@ -80,3 +80,70 @@ def test_jit_cached_and_launch_count():
     k2 = S.kernel_launches()
     assert k1 - k0 == k2 - k1
     assert np.array_equal(a, b) and np.max(np.abs(a - d)) <= 1e-6
+
+
+def _redraw(c, seed):
+    import math
+    rng = np.random.default_rng(seed)
+    gs = []
+    for g in c.gates:
+        if g.kind == "u1q":
+            gs.append(C.Gate("u1q", g.qubits, matrix=C.haar_u2(rng)))
+        elif g.params:
+            gs.append(C.Gate(g.kind, g.qubits, tuple(float(rng.uniform(0, 2 * math.pi)) for _ in g.params)))
+        else:
+            gs.append(g)
+    return C.Circuit(c.n, gs, c.basis, c.name)
+
+
+def test_fresh_angles_reuse_kernels():
+    """After a warm run of the 28-qubit diagonal-heavy stream, the same
+    stream with every angle drawn anew compiles nothing (its kernels hold
+    the structure, its numbers go in the parameter block) and still agrees
+    with the interpreter; a 22-qubit stream with fresh angles agrees with the
+    oracle."""
+    c = C.diag_heavy(28, 500, 1)
+    opt = S.default_options(flags=BASE | S.SIM_F_JIT)
+    with S.Sim(28, S.SIM_C64) as s:
+        s.reset(c.basis)
+        s.apply(c.gates, opt)
+        s.sync()
+        before = S.jit_info()["compiles"]
+        for seed in (7, 8):
+            f = _redraw(c, seed)
+            s.reset(f.basis)
+            s.apply(f.gates, opt)
+            got = s.get_state()
+            assert S.jit_info()["compiles"] == before
+            s.reset(f.basis)
+            s.apply(f.gates, S.default_options(flags=BASE, register_bits=5))
+            assert np.max(np.abs(got - s.get_state())) <= 1e-6
+    small = C.diag_heavy(22, 300, 3)
+    run(small, BASE | S.SIM_F_JIT)
+    before = S.jit_info()["compiles"]
+    f = _redraw(small, 9)
+    got, _ = run(f, BASE | S.SIM_F_JIT)
+    assert S.jit_info()["compiles"] == before
+    exp = oracle.run(f)
+    got = got.astype(np.complex128)
+    assert np.max(np.abs(got - exp)) <= 1e-5
+    assert abs(np.vdot(got, exp)) ** 2 / (np.vdot(got, got).real * np.vdot(exp, exp).real) >= 1 - 1e-6
+
+
+def test_cache_limit_evicts_and_recompiles():
+    """With room for two kernels, a plan of more programs evicts (unloading
+    the modules once the device is idle) and recompiles on its next apply;
+    results stay exact to the interpreter.  The limit is restored after."""
+    c = C.random_mixed(18, 300, 41)
+    try:
+        S.jit_cache_limit(2)
+        a, _ = run(c, BASE | S.SIM_F_JIT)
+        assert S.jit_info()["programs"] <= 2
+        before = S.jit_info()["compiles"]
+        b, _ = run(c, BASE | S.SIM_F_JIT)
+        assert S.jit_info()["compiles"] > before
+        assert np.array_equal(a, b)
+        ref, _ = run(c, BASE, register_bits=5)
+        assert np.max(np.abs(a - ref)) <= 1e-6
+    finally:
+        S.jit_cache_limit(256)

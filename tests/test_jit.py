@@ -25,3 +25,35 @@ def test_diagonal_sweep_sources_compile():
     c = C.rzz_full(14, 3)
     opt = S.default_options(flags=S.default_options().flags | S.SIM_F_JIT)
     assert S.jit_check(c.n, c.gates, S.SIM_C64, c.basis, opt) >= 1
+
+
+def _redraw(c, seed):
+    """The same circuit with every angle and one-qubit matrix drawn anew."""
+    import math
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    gs = []
+    for g in c.gates:
+        if g.kind == "u1q":
+            gs.append(C.Gate("u1q", g.qubits, matrix=C.haar_u2(rng)))
+        elif g.params:
+            gs.append(C.Gate(g.kind, g.qubits, tuple(float(rng.uniform(0, 2 * math.pi)) for _ in g.params)))
+        else:
+            gs.append(g)
+    return C.Circuit(c.n, gs, c.basis, c.name)
+
+
+@pytest.mark.parametrize("maker", [lambda: C.diag_heavy(28, 500, 1), lambda: C.layered(26, 20, 0),
+                                   lambda: C.qaoa(26, 4, 3), lambda: C.random_mixed(20, 300, 11)],
+                         ids=["diag_heavy28", "layered26", "qaoa26", "mixed20"])
+def test_sources_hold_structure_only(maker):
+    """Kernels are keyed by their generated source, which holds the program's
+    structure only: the same circuit with fresh angles (and fresh Haar
+    one-qubit matrices) generates the same sources, so it reuses the cached
+    kernels; the numbers travel in the parameter block."""
+    c = maker()
+    opt = S.default_options(flags=S.default_options().flags | S.SIM_F_JIT)
+    a = S.jit_sources(c.n, c.gates, S.SIM_C64, c.basis, opt)
+    assert "specialised sweep" in a and "P.w[" in a
+    for seed in (101, 102):
+        assert S.jit_sources(c.n, _redraw(c, seed).gates, S.SIM_C64, c.basis, opt) == a
