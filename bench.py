@@ -283,6 +283,8 @@ def run_gpu(args, rank, world, dist):
         opt.dense_precision = PRECISIONS[args.precision]
     if args.register_bits:
         opt.register_bits = args.register_bits
+    if args.chunk_qubits:
+        opt.chunk_qubits = args.chunk_qubits
     if args.jit and not dense:
         # chunk sweeps run kernels specialised to their programs, compiled
         # (NVRTC) during the first warm-up step and cached
@@ -756,6 +758,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--register-bits", type=int, default=0,
                     help="chunk bits per thread in the cache-blocked kernel (0 = library default)")
+    ap.add_argument("--chunk-qubits", type=int, default=0,
+                    help="qubits per cached chunk (0 = library default)")
     ap.add_argument("--workload", default="diag-heavy",
                     choices=["diag-heavy", "layered-dense", "layered", "rzz-full", "qft", "qaoa"],
                     help="diag-heavy: the 28-qubit gate-level stream; layered-dense: depth-20 layered "

@@ -147,7 +147,9 @@ typedef struct {
 int sim_default_options(sim_options *opt);
 
 /* Allocate a 2^n state of the given dtype on the current CUDA device, set it
- * to |0...0> and create a private stream.  SIM_ENOMEM if 2^n * bytes/amp
+ * to |0...0> and create a private stream.  The state is Eq. 1's vector
+ * |phi> = sum_{i in [0, 2^N)} a_i |i> (Section 2.1), a_i stored at index i,
+ * qubit j = bit j of i.  SIM_ENOMEM if 2^n * bytes/amp
  * exceeds free device memory. */
 int sim_create(int n_qubits, sim_dtype dtype, sim_t **out);
 
@@ -175,7 +177,9 @@ int sim_sync(sim_t *s);
 
 /* ------------------------------------------------------------ read-out */
 
-/* p_x = |a_x|^2 for all 2^n x, as doubles, into a host array of 2^n. */
+/* p_x = |a_x|^2 for all 2^n x, as doubles, into a host array of 2^n: the
+ * final probability distribution that full-state simulation yields (Section
+ * 1's motivation for full-state simulation), from Eq. 1's amplitudes. */
 int sim_probabilities(sim_t *s, double *out);
 
 /* The k (1..1024) largest probabilities, ties to the lower index, largest
@@ -186,10 +190,15 @@ int sim_probabilities(sim_t *s, double *out);
  * region, e.g. a uniform state's ties).  Synchronises the handle's stream. */
 int sim_top_k(sim_t *s, int k, uint64_t *idx, double *prob);
 
-/* <Z-string m> = sum_x |a_x|^2 (-1)^popcount(x & m) for n_terms masks. */
+/* <Z-string m> = sum_x |a_x|^2 (-1)^popcount(x & m) for n_terms masks: the
+ * expectation of the Pauli-Z product on the qubits set in m, a read-out of
+ * the probability distribution above (each qubit j in m contributes the
+ * sign of Z on bit j of the basis index, Section 2.1).  Partial sums in a
+ * fixed order, FP64 across blocks; masks with bits >= n are rejected. */
 int sim_expectation(sim_t *s, const uint64_t *z_masks, size_t n_terms, double *out);
 
-/* Squared norm sum_x |a_x|^2, accumulated in FP64. */
+/* Squared norm sum_x |a_x|^2, accumulated in FP64 (Section 2.1: the state
+ * vector has unit L2 norm; this reads how far rounding moved it). */
 int sim_norm(sim_t *s, double *out);
 
 /* <Z-string m> like sim_expectation, for callers that cannot allocate device
@@ -222,8 +231,10 @@ int sim_expectation_noalloc(const void *dev_state, int n_qubits, sim_dtype dtype
                             void *cuda_stream);
 const char *sim_noalloc_error(void);
 
-/* Copy the state out of / into host memory (bytes = 2^n * bytes/amp).
- * sim_set_state ends the product-state knowledge (no booster after it). */
+/* Copy the state out of / into host memory (bytes = 2^n * bytes/amp): Eq. 1's
+ * amplitudes a_i in index order, interleaved (re, im).  SIM_EINVAL when bytes
+ * is not the state's size.  sim_set_state ends the product-state knowledge
+ * (the merge booster of Section 4.4 needs a product state: none after it). */
 int sim_get_state(sim_t *s, void *host, size_t bytes);
 int sim_set_state(sim_t *s, const void *host, size_t bytes);
 
@@ -268,6 +279,19 @@ uint64_t sim_kernel_launches(void);
 int sim_selftest_wait_timeout(void);
 const char *sim_last_error(const sim_t *s);
 const char *sim_global_error(void);
+
+/* Host-side fault injection for tests (no counterpart in the paper).  Lets
+ * the next `skip` operations of a kind through and arms the `count` after
+ * them to fail as if the device had refused them, without touching the GPU: SIM_FAULT_ALLOC -- the library's device
+ * allocations (states, merge-booster sub-states, plan constants, read-out
+ * scratch, serving buffers) return SIM_ENOMEM without calling cudaMalloc;
+ * SIM_FAULT_LAUNCH -- sim_apply_circuit skips the launch and returns
+ * SIM_ECUDA (the state is then undefined, the handle stays usable).
+ * count = 0 disarms.  The environment variable SVSIM_FAULT = "alloc:N" or
+ * "launch:N" arms N failures (no skip) at load.  SIM_EINVAL for an unknown
+ * kind or a negative number. */
+enum { SIM_FAULT_ALLOC = 1, SIM_FAULT_LAUNCH = 2 };
+int sim_fault_inject(int kind, int skip, int count);
 
 /* ------------------------------------------------------------ planner only */
 
@@ -352,7 +376,11 @@ typedef struct {
 } srv_stats;
 
 /* Start a server on the current device.  n_streams worker streams (>= 1)
- * for full-state requests plus one batch stream. */
+ * for full-state requests plus one batch stream.  The paper has no serving
+ * loop; each request is one run of the simulator above (Algorithms 4-5 on
+ * its circuit) and its read-outs.  SIM_EINVAL for n_streams outside 1..64 or
+ * a zero budget, SIM_ENOMEM when host memory runs out, SIM_ECUDA when a
+ * stream cannot be created. */
 int srv_create(size_t hbm_budget_bytes, int n_streams, srv_t **out);
 /* Queue a request (copied).  SIM_EINVAL for malformed requests, SIM_ENOMEM
  * when its state alone exceeds the budget.  *ticket identifies it. */

@@ -122,10 +122,10 @@ static int check_n(int n, sim_dtype dt)
 static int alloc_aux(sim_t *s)
 {
     int np = reduce_partials();
-    CK(s, cudaMalloc((void **)&s->d_part, sizeof(double) * np * 16));
-    CK(s, cudaMalloc((void **)&s->d_out, sizeof(double) * 64));
-    CK(s, cudaMalloc((void **)&s->d_masks, sizeof(uint64_t) * 64));
-    CK(s, cudaMalloc((void **)&s->d_status, sizeof(int)));
+    CK(s, dev_malloc((void **)&s->d_part, sizeof(double) * np * 16));
+    CK(s, dev_malloc((void **)&s->d_out, sizeof(double) * 64));
+    CK(s, dev_malloc((void **)&s->d_masks, sizeof(uint64_t) * 64));
+    CK(s, dev_malloc((void **)&s->d_status, sizeof(int)));
     CK(s, cudaMemset(s->d_status, 0, sizeof(int)));
     CK(s, cudaEventCreateWithFlags(&s->pin_ev, cudaEventDisableTiming));
     return SIM_OK;
@@ -270,7 +270,7 @@ static int create_common(int n, sim_dtype dt, void *buf, size_t bytes, void *str
             delete s;
             return fail(nullptr, SIM_ENOMEM, "state vector does not fit in free device memory");
         }
-        e = cudaMalloc(&s->state, s->state_bytes);
+        e = dev_malloc((void **)&s->state, s->state_bytes);
         if (e != cudaSuccess) { delete s; return cuda_fail(nullptr, e, "cudaMalloc(state)"); }
         s->own_state = true;
         e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
@@ -398,7 +398,7 @@ static int ensure_sub(sim_t *s, int id, int nq)
     size_t need = ((size_t)1 << nq) * amp_bytes(s->dt);
     if (s->sub_bytes[id] < need) {
         if (s->sub[id]) { CK(s, cudaStreamSynchronize(s->stream)); CK(s, cudaFree(s->sub[id])); s->sub[id] = nullptr; }
-        CK(s, cudaMalloc(&s->sub[id], need));
+        CK(s, dev_malloc((void **)&s->sub[id], need));
         s->sub_bytes[id] = need;
     }
     return SIM_OK;
@@ -466,7 +466,7 @@ static int execute(sim_t *s, const Plan &p, bool jit)
         if (s->d_const) { CK(s, cudaStreamSynchronize(s->stream)); CK(s, cudaFree(s->d_const)); }
         s->d_const = nullptr;
         size_t nb = std::max(need, (size_t)1 << 20);
-        CK(s, cudaMalloc((void **)&s->d_const, nb));
+        CK(s, dev_malloc((void **)&s->d_const, nb));
         s->const_bytes = nb;
     }
     if (!bl.b.empty()) {
@@ -512,6 +512,7 @@ static int execute(sim_t *s, const Plan &p, bool jit)
             src.lo = buf_ptr(s, t.buf_lo);
             src.n_lo = t.n_lo;
         }
+        if (fault_launch_fails()) return cuda_fail(s, cudaErrorLaunchOutOfResources, "kernel launch (injected fault)");
         cudaError_t e = cudaSuccess;
         long pe = prof_begin(s, o.buf);
         switch (o.kind) {
@@ -631,7 +632,7 @@ int sim_top_k(sim_t *s, int k, uint64_t *idx, double *prob)
     if (s->topk_bytes < need) {
         if (s->d_topk) { CK(s, cudaStreamSynchronize(s->stream)); CK(s, cudaFree(s->d_topk)); }
         s->d_topk = nullptr;
-        CK(s, cudaMalloc(&s->d_topk, need));
+        CK(s, dev_malloc((void **)&s->d_topk, need));
         s->topk_bytes = need;
     }
     unsigned char *base = (unsigned char *)s->d_topk;

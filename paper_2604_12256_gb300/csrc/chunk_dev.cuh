@@ -836,20 +836,47 @@ __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, 
         }
     };
     constexpr bool kDF = Ops::kDirectFirst, kDL = Ops::kDirectLast;
-    // no register double buffer: without one the kernel fits in 80 registers
-    // and three CTAs per SM, whose loads overlap each other's stages
+    // Loads ahead (Ops::kPrefetch, the specialised kernels): the next chunk's
+    // amplitudes are loaded into registers (nx) as soon as this chunk's first
+    // stage has taken its own, so a whole chunk of loads stays in flight
+    // through the register stages and the store (64 registers more per
+    // thread: two CTAs per SM).  Sweeps fed by a merge-booster product compute
+    // on their loads and do not load ahead.  The interpreter has no register
+    // double buffer: it fits in 80 registers and three CTAs per SM, whose
+    // loads overlap each other's stages.
+    constexpr bool kPF = Ops::kPrefetch;
+    const bool pf_on = kPF && !src.hi;
+    T2 nx[kPF ? NR : 1];
     int64_t ch = blockIdx.x;
     uint64_t base = chunk_base(ch);
+    if constexpr (kPF) {
+        if (pf_on && ch < nchunks) {
+            if constexpr (kDF) load_direct(nx, base | s_x0[tid], 0);
+            else load_regs(nx, base);
+        }
+    }
     int cb = 0;   // CTA-table buffer of this chunk
     for (; ch < nchunks; ch += gridDim.x) {
         const W *cta_ph = cta_buf + cb * cbw;
         W *cta_next = cta_buf + (cb == 2 ? 0 : cb + 1) * cbw;
+        const int64_t nch = ch + gridDim.x;
+        const uint64_t nbase = nch < nchunks ? chunk_base(nch) : 0;
         T2 v0[NR];   // stage 0's amplitudes when it loads them itself
         if constexpr (kDF) {
-            load_direct(v0, base | s_x0[tid], 0);
+            if (kPF && pf_on) {
+#pragma unroll
+                for (int m = 0; m < NR; m++) v0[m] = nx[kPF ? m : 0];
+            } else {
+                load_direct(v0, base | s_x0[tid], 0);
+            }
         } else {
             T2 pf[NR];
-            load_regs(pf, base);
+            if (kPF && pf_on) {
+#pragma unroll
+                for (int m = 0; m < NR; m++) pf[m] = nx[kPF ? m : 0];
+            } else {
+                load_regs(pf, base);
+            }
             // ---- the chunk -> shared
 #pragma unroll
             for (int it = 0; it < NR / 2; it++) {
@@ -858,14 +885,19 @@ __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, 
                 sv[p ^ 1] = pf[2 * it + 1];
             }
         }
+        if constexpr (kPF) {
+            // the next chunk's loads, in flight through this chunk's stages
+            if (pf_on && nch < nchunks) {
+                if constexpr (kDF) load_direct(nx, nbase | s_x0[tid], 0);
+                else load_regs(nx, nbase);
+            }
+        }
         // buffer (cb + 2) mod 3: last read by the previous chunk
         cta_zero<R, T>(cta_buf + (cb == 0 ? 2 : cb - 1) * cbw, nd * SCP, tid);
         // (the chunk in shared memory; with a direct first stage nothing
         // before the first stage's own store needs a barrier: the CTA
         // buffers it reads were completed before the last chunk's barriers)
         if constexpr (!kDF) __syncthreads();
-        const int64_t nch = ch + gridDim.x;
-        const uint64_t nbase = nch < nchunks ? chunk_base(nch) : 0;
         // the next chunk's sums (its buffer was cleared during the previous chunk)
         if (nch < nchunks) cta_accum<R, T>(prog, cta_next, nbase, tid);
         // ---- register stages
@@ -949,6 +981,7 @@ struct NoParams {};
 struct InterpOps {
     using Params = NoParams;
     static constexpr int kStages = 0;
+    static constexpr bool kPrefetch = false;
     static constexpr bool kDirectFirst = false, kDirectLast = false;
     static __device__ __forceinline__ uint64_t roff(int, int) { return 0; }
     static __device__ __forceinline__ bool paired(int) { return false; }

@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "svsim.h"
 
 namespace svs {
@@ -135,6 +137,11 @@ bool make_batch_ops(int n, sim_dtype dt, const sim_gate *gates, size_t ng, std::
 int svs_rebind(sim_t *s, int n, sim_dtype dt, void *dev_buf, size_t bytes);
 
 namespace svs {
+// host-side fault injection (fault.cpp): true when the next allocation /
+// launch is to fail; dev_malloc is cudaMalloc behind that check
+bool fault_alloc_fails();
+bool fault_launch_fails();
+cudaError_t dev_malloc(void **p, size_t bytes);
 void fill_default_options(sim_options &o);
 void resolve_options(sim_options &o, int n, sim_dtype dt);
 

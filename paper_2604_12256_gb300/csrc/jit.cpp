@@ -383,7 +383,7 @@ const char *kParamStruct = "struct JP { uint32_t w[";
 
 }  // namespace
 
-bool jit_supported(bool f64, int C, int RB) { return !f64 && C == 12 && (RB == 4 || RB == 5); }
+bool jit_supported(bool f64, int C, int RB) { return !f64 && ((C == 12 && (RB == 4 || RB == 5)) || (C == 13 && RB == 5)); }
 bool jit_supported_diag(bool f64, int RB) { return !f64 && RB == 4; }
 
 // CUDA source of the fused diagonal sweep (K3) specialised to program `w`:
@@ -434,7 +434,7 @@ bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std:
     if (kind == JIT_DIAG) return jit_source_diag(w, src, vals, err);
     const int C = (int)w[H_C], RB = (int)w[H_RB], ns = (int)w[H_NSTAGE];
     if (w[H_WBYTES] != 4 || !jit_supported(false, C, RB)) {
-        err = "specialised kernels: complex64 chunk programs with C = 12, RB = 4 or 5 only";
+        err = "specialised kernels: complex64 chunk programs with C = 12, RB = 4 or 5, or C = 13, RB = 5 only";
         return false;
     }
     const int T = 1 << (C - RB), NR = 1 << RB, TB = C - RB;
@@ -444,6 +444,7 @@ bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std:
     PBlock P;
     std::ostringstream o;
     o << "    static constexpr int kStages = " << ns << ";\n";
+    o << "    static constexpr bool kPrefetch = true;\n";
     // direct boundary stages: their register offsets in HBM
     const uint32_t direct = w[H_DIRECT];
     o << "    static constexpr bool kDirectFirst = " << ((direct & DIRECT_FIRST) ? "true" : "false")
@@ -552,7 +553,8 @@ bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std:
         o << "        }\n";
     }
     o << "    }\n};\n}  // namespace svs\n";
-    o << "extern \"C\" __global__ void __launch_bounds__(" << T << ", 3) " << kKernelName
+    // registers for two CTAs of 128 threads, or one of 256
+    o << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << (T <= 128 ? 2 : 1) << ") " << kKernelName
       << "(svs::CT<float>::G2 *__restrict__ a, const uint32_t *__restrict__ gprog, int n, "
          "svs::TSrc<svs::CT<float>::G2> src, const __grid_constant__ svs::JP P)\n{\n    svs::chunk_sweep<float, "
       << C << ", " << RB << ", svs::JOps>(a, gprog, n, src, P);\n}\n";

@@ -28,7 +28,7 @@ using namespace prog;
 
 // ------------------------------------------------------------ K4 chunk sweep (interpreter)
 template <typename R, int C, int RB>
-__global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 7 ? 3 : 8) k_chunk(typename CT<R>::G2 *__restrict__ a,
+__global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 8 ? 1 : (C - RB) >= 7 ? 3 : 8) k_chunk(typename CT<R>::G2 *__restrict__ a,
                                                          const uint32_t *__restrict__ gprog, int n,
                                                          TSrc<typename CT<R>::G2> src)
 {
@@ -119,6 +119,7 @@ cudaError_t launch_chunk(void *a, int n, bool f64, int C, int RB, const uint32_t
     if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
     if (src.hi && (src.n_lo < 0 || src.n_lo > n || !src.lo)) return cudaErrorInvalidValue;
     if (!f64) {
+        if (C == 13 && RB == 5 && n >= 13) return chunk_t<float, 13, 5>(a, n, prog, smem, src, st);
         if (C == 12 && RB == 5 && n >= 12) return chunk_t<float, 12, 5>(a, n, prog, smem, src, st);
         if (C == 12 && RB == 4 && n >= 12) return chunk_t<float, 12, 4>(a, n, prog, smem, src, st);
         if (C == 10 && RB == 5 && n >= 10) return chunk_t<float, 10, 5>(a, n, prog, smem, src, st);

@@ -55,9 +55,10 @@ static bool chunk_shape(int n, sim_dtype dt, int want_c, int want_rb, int &C, in
             return true;
         }
         RB = 5;
-        int cands[2] = {12, 10};
+        // 2^13-amplitude chunks (256 threads) only when asked for
+        int cands[3] = {13, 12, 10};
         for (int c : cands)
-            if (c <= n && (want_c <= 0 || c <= want_c)) { C = c; return true; }
+            if (c <= n && (c == 13 ? want_c == 13 : (want_c <= 0 || c <= want_c))) { C = c; return true; }
     } else {
         RB = 4;
         int cands[2] = {11, 9};

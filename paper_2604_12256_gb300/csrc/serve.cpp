@@ -166,7 +166,7 @@ void batcher_loop(srv_t *s)
             if (dptr) cudaFree(dptr);
             if (hptr) cudaFreeHost(hptr);
             size_t nc = std::max(need, cap * 2);
-            cudaError_t e = cudaMalloc((void **)&dptr, nc * sizeof(*dptr));
+            cudaError_t e = dev_malloc((void **)&dptr, nc * sizeof(*dptr));
             if (e == cudaSuccess) e = cudaMallocHost((void **)&hptr, nc * sizeof(*hptr));
             cap = e == cudaSuccess ? nc : 0;
             return e;
@@ -215,45 +215,77 @@ void batcher_loop(srv_t *s)
 }
 
 // ---- full-state path: optimizer + kernels on a worker stream
+// Admission charges what the device really holds: in_use is the sum of the
+// state buffers the workers keep (each worker keeps its largest buffer for
+// the next request).  A worker may take a queued request that fits its own
+// buffer, or whose footprint fits the budget once its own buffer is given
+// back.  A worker with nothing it may take while requests wait releases its
+// buffer, so that another worker can take them.
 void worker_loop(srv_t *s)
 {
     cudaSetDevice(s->device);
     cudaStream_t st = nullptr;
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    const bool stream_ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
     void *buf = nullptr;
     size_t cap = 0;
     sim_t *h = nullptr;
+    auto release = [&] {
+        if (h) { sim_destroy(h); h = nullptr; }
+        if (buf) cudaFree(buf);
+        buf = nullptr;
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->in_use -= cap;
+        cap = 0;
+    };
     while (true) {
         Req *r = nullptr;
+        bool give_back = false;
         {
             std::unique_lock<std::mutex> lk(s->mu);
+            auto fits = [&](const Req *q) { return q->bytes <= cap || s->in_use - cap + q->bytes <= s->budget; };
             s->cv_work.wait(lk, [&] {
                 if (s->stop && s->large_q.empty()) return true;
                 for (Req *q : s->large_q)
-                    if (s->in_use + q->bytes <= s->budget) return true;
-                return false;
+                    if (fits(q)) return true;
+                return cap > 0 && !s->large_q.empty();
             });
             if (s->large_q.empty()) break;
             // admission by footprint: the first queued request that fits
             for (auto it = s->large_q.begin(); it != s->large_q.end(); ++it)
-                if (s->in_use + (*it)->bytes <= s->budget) {
+                if (fits(*it)) {
                     r = *it;
                     s->large_q.erase(it);
                     break;
                 }
-            if (!r) continue;
-            s->in_use += r->bytes;
-            s->peak = std::max(s->peak, s->in_use);
+            if (!r) {
+                give_back = true;
+            } else if (r->bytes > cap) {
+                // the buffer grows: charged now, before it is allocated
+                s->in_use += r->bytes - cap;
+                s->peak = std::max(s->peak, s->in_use);
+            }
+        }
+        if (give_back) {
+            release();
+            s->cv_work.notify_all();
+            continue;
         }
         r->t_start = Clock::now();
-        int rc = SIM_OK;
-        if (cap < r->bytes) {
+        int rc = stream_ok ? SIM_OK : SIM_ECUDA;
+        if (rc == SIM_OK && cap < r->bytes) {
+            const size_t want = r->bytes;
             if (h) { sim_destroy(h); h = nullptr; }
             if (buf) cudaFree(buf);
             buf = nullptr;
-            cap = 0;
-            if (cudaMalloc(&buf, r->bytes) == cudaSuccess) cap = r->bytes;
-            else rc = SIM_ENOMEM;
+            if (dev_malloc(&buf, want) != cudaSuccess) {
+                buf = nullptr;
+                rc = SIM_ENOMEM;
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->in_use -= want;   // charged above, not held
+                cap = 0;
+            } else {
+                cap = want;
+            }
         }
         if (rc == SIM_OK && !h) rc = sim_create_on(r->n, r->dt, buf, cap, (void *)st, &h);
         if (rc == SIM_OK) rc = svs_rebind(h, r->n, r->dt, buf, cap);
@@ -265,16 +297,11 @@ void worker_loop(srv_t *s)
         r->res.path = 1;
         r->res.n_masks = (int)r->masks.size();
         r->res.top_k = r->top_k;
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            s->in_use -= r->bytes;
-            s->cv_work.notify_all();
-        }
+        s->cv_work.notify_all();
         finish(s, r, rc);
     }
-    if (h) sim_destroy(h);
-    if (buf) cudaFree(buf);
-    cudaStreamDestroy(st);
+    release();
+    if (st) cudaStreamDestroy(st);
 }
 
 int sfail(int code) { return code; }

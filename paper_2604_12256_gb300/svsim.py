@@ -114,6 +114,7 @@ _SIGS = [
     ("sim_jit_info", ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]),
     ("sim_jit_check", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _P, ctypes.c_size_t,
                                      ctypes.POINTER(sim_options), ctypes.POINTER(ctypes.c_int)]),
+    ("sim_fault_inject", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     ("sim_jit_cache", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     ("sim_jit_sources", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _P, ctypes.c_size_t,
                                        ctypes.POINTER(sim_options), ctypes.c_char_p, ctypes.c_size_t,
@@ -227,6 +228,17 @@ def jit_info() -> dict:
     k, c = ctypes.c_uint64(0), ctypes.c_uint64(0)
     _check(lib.sim_jit_cache(0, ctypes.byref(k), ctypes.byref(c)))
     return {"programs": n.value, "compiles": c.value, "compile_ms": ms.value}
+
+
+SIM_FAULT_ALLOC = 1
+SIM_FAULT_LAUNCH = 2
+
+
+def fault_inject(kind: int, count: int, skip: int = 0) -> None:
+    """Arm host-side fault injection: after ``skip`` successful ones, the next
+    ``count`` device allocations (SIM_FAULT_ALLOC) or kernel launches
+    (SIM_FAULT_LAUNCH) fail; count 0 disarms."""
+    _check(load().sim_fault_inject(int(kind), int(skip), int(count)))
 
 
 def jit_cache_limit(max_kernels: int) -> None:

@@ -50,3 +50,13 @@ def test_errors_without_gpu_are_reported(built_lib):
     with pytest.raises(S.SimError) as e:
         S.Sim(10, S.SIM_C64)
     assert e.value.code in (S.SIM_ECUDA, S.SIM_ENOMEM)
+
+
+def test_fault_injection_arguments(built_lib):
+    from paper_2604_12256_gb300 import svsim as S
+    lib = built_lib
+    assert lib.sim_fault_inject(99, 0, 1) == S.SIM_EINVAL
+    assert lib.sim_fault_inject(S.SIM_FAULT_ALLOC, 0, -1) == S.SIM_EINVAL
+    assert lib.sim_fault_inject(S.SIM_FAULT_ALLOC, -1, 1) == S.SIM_EINVAL
+    assert lib.sim_fault_inject(S.SIM_FAULT_ALLOC, 0, 0) == S.SIM_OK
+    assert lib.sim_fault_inject(S.SIM_FAULT_LAUNCH, 0, 0) == S.SIM_OK

@@ -109,6 +109,7 @@ CASES22 = {
     "layered22": lambda: C.layered(22, 12, 1),
     "qft22_swaps": lambda: C.qft(22, 5),
     "qaoa22": lambda: C.qaoa(22, 2, 3),
+    "qaoa24p4": lambda: C.qaoa(24, 4, 7),
     "mixed22": lambda: C.random_mixed(22, 300, 11),
     "mixed23": lambda: C.random_mixed(23, 400, 12),
     "supremacy22": lambda: C.supremacy(22, 8, 13),
@@ -124,17 +125,20 @@ def _oracle(name):
     return _oracle_cache[name]
 
 
-@pytest.mark.parametrize("rb", [4, 5])
+@pytest.mark.parametrize("shape", [(12, 4), (12, 5), (13, 5)], ids=["C12RB4", "C12RB5", "C13RB5"])
 @pytest.mark.parametrize("name", sorted(CASES22))
-def test_specialised_sweeps_loop_over_chunks(name, rb):
+def test_specialised_sweeps_loop_over_chunks(name, shape):
     """svs_chunk_jit / svs_diag_jit against the oracle and the interpreter
-    where a CTA processes several chunks (tiles) per launch."""
+    where a CTA processes several chunks (tiles) per launch: chunks of 2^12
+    amplitudes on 128 or 256 threads (two or three CTAs per SM) and of 2^13
+    on 256 threads (one CTA per SM)."""
+    cq, rb = shape
     c, exp = _oracle(name)
-    assert (1 << (c.n - 12)) > 3 * _sm_count()   # more chunks than resident CTAs
-    got, st = _run(c, S.SIM_C64, S.default_options(flags=BASE | S.SIM_F_JIT, register_bits=rb))
+    assert (1 << (c.n - cq)) > 3 * _sm_count()   # more chunks than resident CTAs
+    got, st = _run(c, S.SIM_C64, S.default_options(flags=BASE | S.SIM_F_JIT, register_bits=rb, chunk_qubits=cq))
     assert st["chunk_ops"] + st["diag_ops"] > 0
     _check64(got, exp)
-    ref, st_ref = _run(c, S.SIM_C64, S.default_options(flags=BASE, register_bits=rb))
+    ref, st_ref = _run(c, S.SIM_C64, S.default_options(flags=BASE, register_bits=rb, chunk_qubits=cq))
     st.pop("plan_ms"), st_ref.pop("plan_ms")
     assert st == st_ref
     assert float(np.max(np.abs(got - ref))) <= 1e-6

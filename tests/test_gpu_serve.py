@@ -94,3 +94,23 @@ def test_admission_timeout_and_errors():
         assert srv.poll(t, -1)["status"] == 0
         with pytest.raises(S.SimError):
             srv.poll(t, 0)                                 # released
+
+
+def test_admission_charges_retained_buffers():
+    """Workers keep their state buffer for the next request, and admission
+    charges those buffers: with a budget of one 22-qubit state, 20-qubit
+    requests on four workers leave buffers behind, and a 22-qubit request
+    queued behind them is still served (idle workers give their buffers
+    back); the peak of the buffers held never exceeds the budget."""
+    budget = (1 << 22) * 8
+    reqs = [C.diag_heavy(20, 60, s) for s in range(6)] + [C.diag_heavy(22, 80, 9)] + \
+           [C.diag_heavy(21, 60, s) for s in range(10, 13)]
+    with S.Server(budget, n_streams=4) as srv:
+        tickets = [srv.submit(c, 8, [3]) for c in reqs]
+        res = [srv.poll(t, 60000) for t in tickets]
+        st = srv.stats()
+    assert all(r["status"] == 0 and r["path"] == 1 for r in res)
+    assert 0 < st["hbm_peak"] <= budget
+    big = reqs[6]
+    eidx, ep = oracle.top_k(oracle.run(big), 8)
+    np.testing.assert_allclose(res[6]["top_p"], ep, atol=2e-5)
