@@ -481,10 +481,20 @@ bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std:
          "    static __device__ __forceinline__ void run(int s, typename CT<R>::T2 (&v)[1 << RB], uint64_t x0,\n"
          "        const uint32_t *prog, const uint32_t *, const typename CT<R>::W *cta_ph,\n"
          "        const typename CT<R>::W *thr_ph, int nhoist, int tid, const JP &P)\n    {\n";
-    // pass 1: the scaled forms of one-qubit ops and the sweep's product of
-    // their scalars (kept above 2^-40 so that no amplitude underflows)
+    // pass 1: the scaled forms of one-qubit ops (their form follows the op's
+    // structure) and where their scalars are applied.  The product of the
+    // scalars since the last factored phase segment is folded into the next
+    // one (its base factor, free) or, after the last, multiplies the
+    // amplitudes at the end of the last stage: each product is applied right
+    // after the growth it undoes (no amplitude is scaled down before it has
+    // grown).  A group's product is kept above 2^-60, so that magnitudes stay
+    // below 2^60 times their own: an op whose scalar would push it lower
+    // (angles within about 2^-30 of the rotation's zero, in practice never)
+    // keeps its unscaled form.
     std::map<size_t, Scaled> scaled;
-    long double scale = 1;
+    std::map<size_t, long double> fold;   // factored segment body -> product folded into it
+    long double grp = 1;
+    bool grp_open = false;
     for (int s = 0; s < ns; s++) {
         size_t op = w[H_STAGE_OFF + s] + S_SIZE;
         for (uint32_t k = 0; k < w[w[H_STAGE_OFF + s] + S_NOPS]; k++) {
@@ -492,17 +502,19 @@ bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std:
             const size_t body = op + O_BODY;
             if ((hdr & 0xff) == OP_DENSE && ((hdr >> 8) & 0xf) == 1) {
                 const Scaled sf = scaled_form(&w[body], (hdr >> 12) & 0xf);
-                if (sf.form && fabsl(scale * sf.s) >= 0x1p-40L) {
+                if (sf.form && fabsl(grp * sf.s) >= 0x1p-60L) {
                     scaled[body] = sf;
-                    scale *= sf.s;
+                    grp *= sf.s;
+                    grp_open = true;
                 }
+            } else if ((hdr & 0xff) == OP_DSEG && !w[body + D_NMULTI] && grp_open) {
+                fold[body] = grp;
+                grp = 1;
+                grp_open = false;
             }
             op += w[op + O_WORDS];
         }
     }
-    // the scale goes into the first factored phase segment's base factor, or
-    // multiplies the amplitudes at the end of the last stage
-    bool scale_done = scaled.empty();
     for (int s = 0; s < ns; s++) {
         const size_t so = w[H_STAGE_OFF + s];
         o << "        if (s == " << s << ") {\n";
@@ -544,12 +556,12 @@ bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std:
                 // terms on several register bits and other bits: the general path
                 o << "            dseg_apply<R, RB, T, 3>(v, x0, prog + " << body << ", cta_ph, thr_ph, nhoist, tid);\n";
             } else {
-                gen_segment(o, P, w, body, slots, RB, TB, T, SCP, !scale_done, scale);
-                scale_done = true;
+                const auto fd = fold.find(body);
+                gen_segment(o, P, w, body, slots, RB, TB, T, SCP, fd != fold.end(), fd != fold.end() ? fd->second : 1.0L);
             }
             op += len;
         }
-        if (s == ns - 1 && !scale_done) o << "            scale_all<" << NR << ">(v, " << P.f((float)scale) << ");\n";
+        if (s == ns - 1 && grp_open) o << "            scale_all<" << NR << ">(v, " << P.f((float)grp) << ");\n";
         o << "        }\n";
     }
     o << "    }\n};\n}  // namespace svs\n";

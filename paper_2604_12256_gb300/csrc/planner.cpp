@@ -119,50 +119,93 @@ static std::vector<cd> expand(const std::vector<cd> &M, int k, const int *pos, i
 }
 
 // ------------------------------------------------------------ diagonal detector
-// Algorithm 8 with readings (i)-(iv) above.  Fused groups become one gate
-// whose phase polynomial is the sum of the members' polynomials.
+// Section 4.5 (Algorithm 8), restated from the rule it rests on: a diagonal
+// gate commutes with every other diagonal gate and with every gate on other
+// qubits.  A diagonal gate may therefore move back past any run of gates
+// that holds no non-diagonal gate on one of its qubits, and merge with a
+// diagonal group there; the fused group is one gate whose phase polynomial
+// is the sum of its members' polynomials (diagonals multiply).
+//
+// One pass builds the output.  Each diagonal group in it records its
+// "walls": the qubits of the non-diagonal gates emitted after it.  Walls only
+// grow, and an older group's walls contain a newer one's, so the groups a
+// gate can reach are the newest ones.  A diagonal gate joins the oldest group
+// whose walls miss its qubits and whose qubit set stays within D (D = 0: no
+// bound, reading (iii)); otherwise it starts a group.  A group of one gate is
+// emitted as that gate (reading (i)).  Non-diagonal gates keep their order,
+// and no gate passes a gate it does not commute with (reading (ii)).
+namespace {
+struct DiagGroup {
+    size_t slot;            // its place in the output
+    uint64_t qubits = 0;    // qubits of its members
+    uint64_t walls = 0;     // qubits of non-diagonal gates emitted after it
+    std::vector<size_t> members;
+};
+}  // namespace
+
 static std::vector<PGate> diagonal_detector(const std::vector<PGate> &G, int D, uint64_t &absorbed)
 {
+    // output slots: a gate of G (>= 0) or a group (-1 - group index)
+    std::vector<long> slots;
+    std::vector<DiagGroup> groups;
+    size_t live = 0;   // groups before this index can no longer be reached
+    slots.reserve(G.size());
+    uint64_t all = 0;   // every qubit the circuit touches
+    for (const PGate &x : G) all |= x.qmask;
+    for (size_t t = 0; t < G.size(); t++) {
+        const PGate &g = G[t];
+        if (!g.diag) {
+            slots.push_back((long)t);
+            for (size_t k = live; k < groups.size(); k++) groups[k].walls |= g.qmask;
+            // the oldest live groups whose walls already hold every qubit of
+            // the circuit can take nothing more
+            while (live < groups.size() && (groups[live].walls & all) == all) live++;
+            continue;
+        }
+        bool joined = false;
+        for (size_t k = live; k < groups.size() && !joined; k++) {
+            DiagGroup &grp = groups[k];
+            if (grp.walls & g.qmask) continue;
+            if (D > 0 && popc(grp.qubits | g.qmask) > D) continue;
+            grp.qubits |= g.qmask;
+            grp.members.push_back(t);
+            joined = true;
+        }
+        if (!joined) {
+            DiagGroup grp;
+            grp.slot = slots.size();
+            grp.qubits = g.qmask;
+            grp.members.push_back(t);
+            slots.push_back(-1 - (long)groups.size());
+            groups.push_back(std::move(grp));
+        }
+    }
     std::vector<PGate> res;
-    res.reserve(G.size());
-    size_t i = 0;
+    res.reserve(slots.size());
     absorbed = 0;
-    while (i < G.size()) {
-        if (!G[i].diag) { res.push_back(G[i]); i++; continue; }
-        std::vector<size_t> diagList{i}, uList;
-        uint64_t stop = 0, dep = G[i].qmask, fused = G[i].qmask;
-        size_t j = i + 1;
-        for (; j < G.size(); j++) {
-            const PGate &h = G[j];
-            if (!h.diag) {
-                if ((h.qmask & dep) || (h.qmask & stop)) { stop |= h.qmask; uList.push_back(j); }
-                else res.push_back(h);
-            } else {
-                if ((h.qmask & stop) || (D > 0 && popc(fused | h.qmask) > D)) break;
-                dep |= h.qmask;
-                fused |= h.qmask;
-                diagList.push_back(j);
-            }
+    for (long sl : slots) {
+        if (sl >= 0) {
+            res.push_back(G[(size_t)sl]);
+            continue;
         }
-        if (diagList.size() == 1) {
-            res.push_back(G[i]);
-        } else {
-            PGate f;
-            f.kind = kFusedDiag;
-            f.diag = true;
-            f.qmask = fused;
-            f.k = popc(fused);
-            f.n_src = 0;
-            for (size_t d : diagList) {
-                f.terms.insert(f.terms.end(), G[d].terms.begin(), G[d].terms.end());
-                f.n_src += G[d].n_src;
-            }
-            normalize_terms(f.terms);
-            absorbed += diagList.size() - 1;
-            res.push_back(std::move(f));
+        const DiagGroup &grp = groups[(size_t)(-1 - sl)];
+        if (grp.members.size() == 1) {
+            res.push_back(G[grp.members[0]]);
+            continue;
         }
-        for (size_t u : uList) res.push_back(G[u]);
-        i = j;
+        PGate f;
+        f.kind = kFusedDiag;
+        f.diag = true;
+        f.qmask = grp.qubits;
+        f.k = popc(grp.qubits);
+        f.n_src = 0;
+        for (size_t m : grp.members) {
+            f.terms.insert(f.terms.end(), G[m].terms.begin(), G[m].terms.end());
+            f.n_src += G[m].n_src;
+        }
+        normalize_terms(f.terms);
+        absorbed += grp.members.size() - 1;
+        res.push_back(std::move(f));
     }
     return res;
 }

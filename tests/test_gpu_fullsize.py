@@ -72,7 +72,7 @@ def test_diag_heavy_28_specialised_inverse_returns_basis():
         s.reset(c.basis)
         s.apply(c.gates, opt)
         st = s.stats()
-        assert st["sweeps"] == 8 and st["diag_fused"] > 0
+        assert st["sweeps"] == 7 and st["diag_fused"] > 0
         assert S.jit_info()["programs"] > 0
         assert abs(s.norm() - 1.0) < 1e-4
         s.apply(C.inverse(c).gates, opt)

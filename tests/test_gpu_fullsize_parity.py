@@ -174,7 +174,7 @@ def test_config1_28q_specialised_against_oracle(config1):
     32 amplitudes per thread): every amplitude against the oracle."""
     c, exp = config1
     got, st = _run(c, S.SIM_C64, S.default_options(flags=BASE | S.SIM_F_JIT))
-    assert st["sweeps"] == 8 and st["diag_fused"] > 0
+    assert st["sweeps"] == 7 and st["diag_fused"] > 0
     _chunked_check(got, exp, TOL64, FID64)
 
 

@@ -166,9 +166,11 @@ def test_remap_plans_are_exact(name):
 
 
 def test_remap_cuts_sweeps_on_layered_circuits():
+    """With 32 amplitudes per thread (the specialised kernels' shape) the
+    qubit frame saves sweeps on the layered circuit (13 -> 11 at 28 qubits)."""
     c = C.layered(28, 20, 0)
-    base = S.default_options()
-    rm = S.default_options(flags=base.flags | S.SIM_F_REMAP)
+    base = S.default_options(register_bits=5)
+    rm = S.default_options(flags=base.flags | S.SIM_F_REMAP, register_bits=5)
     s0 = S.plan_json(c.n, c.gates, S.SIM_C64, 0, base)["stats"]["sweeps"]
     s1 = S.plan_json(c.n, c.gates, S.SIM_C64, 0, rm)["stats"]["sweeps"]
     assert s1 < s0
@@ -191,10 +193,10 @@ def test_euler_split_real_rotations_and_exact():
 
 
 @pytest.mark.parametrize("name,make,max_sweeps", [
-    ("diag-heavy 28", lambda: C.diag_heavy(28, 500, 1), 8),
+    ("diag-heavy 28", lambda: C.diag_heavy(28, 500, 1), 7),
     ("qaoa 30", lambda: C.qaoa(30, 4, 3), 13),
     ("qft 30", lambda: C.qft(30, 2), 4),
-    ("layered 30", lambda: C.layered(30, 20, 0), 33),
+    ("layered 30", lambda: C.layered(30, 20, 0), 15),
 ])
 def test_benchmark_workloads_sweep_budget(name, make, max_sweeps):
     """The full-state passes of the benchmarked workloads, with the options
