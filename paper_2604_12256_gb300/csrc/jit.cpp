@@ -565,8 +565,9 @@ bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std:
         o << "        }\n";
     }
     o << "    }\n};\n}  // namespace svs\n";
-    // registers for two CTAs of 128 threads, or one of 256
-    o << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << (T <= 128 ? 2 : 1) << ") " << kKernelName
+    // registers for two CTAs per SM (2^12-amplitude chunks: 128 threads of
+    // 32 amplitudes or 256 of 16), or one of 256 threads (2^13 amplitudes)
+    o << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << (C == 13 ? 1 : 2) << ") " << kKernelName
       << "(svs::CT<float>::G2 *__restrict__ a, const uint32_t *__restrict__ gprog, int n, "
          "svs::TSrc<svs::CT<float>::G2> src, const __grid_constant__ svs::JP P)\n{\n    svs::chunk_sweep<float, "
       << C << ", " << RB << ", svs::JOps>(a, gprog, n, src, P);\n}\n";

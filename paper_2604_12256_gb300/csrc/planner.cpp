@@ -23,7 +23,9 @@
 #include <chrono>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <sstream>
+#include <unordered_map>
 
 #include "internal.h"
 #include "program.h"
@@ -1827,6 +1829,71 @@ static std::vector<PGate> euler_split(const std::vector<PGate> &G, int n, uint64
     return out;
 }
 
+// ------------------------------------------------------------ chunk shape
+// Complex64 plans for the specialised kernels, with no shape asked for,
+// choose between chunks of 2^12 amplitudes and of 2^13 (one more qubit per
+// sweep, so often fewer sweeps) by planning both.  The choice is kept per
+// circuit structure (gate kinds and qubits, options; not the angles), so
+// repeated applies of a structure plan once.
+static bool auto_chunk_shape(int n, sim_dtype dt, const sim_options &o)
+{
+    return dt == SIM_C64 && n >= 16 && (o.flags & SIM_F_JIT) && (o.flags & SIM_F_BLOCK) && !(o.flags & SIM_F_TC) &&
+           o.chunk_qubits == 0 && (o.register_bits == 0 || o.register_bits == 5);
+}
+
+static uint64_t shape_key(int n, sim_dtype dt, const sim_options &o, bool product_state, const sim_gate *gates,
+                          size_t ng)
+{
+    uint64_t h = 1469598103934665603ull;   // FNV-1a, 64 bit
+    auto mix = [&](uint64_t v) {
+        for (int i = 0; i < 8; i++) {
+            h ^= (v >> (8 * i)) & 255;
+            h *= 1099511628211ull;
+        }
+    };
+    mix((uint64_t)n);
+    mix((uint64_t)dt);
+    mix(o.flags);
+    mix((uint64_t)(uint32_t)o.max_fuse_qubits | (uint64_t)(uint32_t)o.max_diag_qubits << 32);
+    mix((uint64_t)(uint32_t)o.max_stages | (uint64_t)(uint32_t)o.booster_div << 32);
+    mix(product_state ? 1 : 0);
+    mix(ng);
+    for (size_t i = 0; i < ng; i++) {
+        const sim_gate &g = gates[i];
+        mix((uint64_t)g.kind | (uint64_t)g.nq << 32);
+        for (uint32_t j = 0; j < g.nq && j < 6; j++) mix(g.q[j]);
+    }
+    return h;
+}
+
+static std::mutex g_shape_mu;
+static std::unordered_map<uint64_t, int> g_shapes;
+
+static int cached_shape(uint64_t key)
+{
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    auto it = g_shapes.find(key);
+    return it == g_shapes.end() ? 0 : it->second;
+}
+
+static void remember_shape(uint64_t key, int cq)
+{
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    if (g_shapes.size() >= 4096) g_shapes.clear();
+    g_shapes[key] = cq;
+}
+
+// passes over the whole state in a plan
+static size_t full_sweeps(const Plan &p)
+{
+    size_t k = 0;
+    for (const Op &o : p.ops)
+        if (o.buf == 0 && (o.kind == OPK_GATE || o.kind == OPK_GATE_DIAG || o.kind == OPK_DIAG || o.kind == OPK_CHUNK ||
+                           o.kind == OPK_DENSE_TC))
+            k++;
+    return k;
+}
+
 bool make_plan(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_t ng, const sim_options &opt_in,
                Plan &plan, std::string &err)
 {
@@ -1859,7 +1926,32 @@ bool make_plan(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_
         G = diagonal_detector(G, opt.max_diag_qubits, absorbed);
         plan.stats.diag_fused += absorbed;
     }
-    schedule(G, n, opt, dt, 0, plan);
+    if (auto_chunk_shape(n, dt, opt)) {
+        // the full state's chunk shape: 2^12 or 2^13 amplitudes, whichever
+        // the cost model says is cheaper for this circuit's structure
+        const uint64_t key = shape_key(n, dt, opt, basis != UINT64_MAX, gates, ng);
+        int cq = cached_shape(key);
+        if (cq) {
+            sim_options o = opt;
+            o.chunk_qubits = cq;
+            schedule(G, n, o, dt, 0, plan);
+        } else {
+            Plan p12 = plan, p13 = plan;
+            sim_options o12 = opt, o13 = opt;
+            o12.chunk_qubits = 12;
+            o13.chunk_qubits = 13;
+            schedule(G, n, o12, dt, 0, p12);
+            schedule(G, n, o13, dt, 0, p13);
+            // a sweep of 2^13-amplitude chunks (one CTA of 256 threads per
+            // SM) takes about 1.1 times as long as one of 2^12 (two CTAs of
+            // 128): measured 1.06-1.14 on the benchmarked workloads
+            cq = full_sweeps(p13) * 11 < full_sweeps(p12) * 10 ? 13 : 12;
+            remember_shape(key, cq);
+            plan = cq == 13 ? std::move(p13) : std::move(p12);
+        }
+    } else {
+        schedule(G, n, opt, dt, 0, plan);
+    }
     finalize_words(plan);
     // a tensor product that only feeds the next sweep of the same buffer is
     // computed by that sweep's loads: one write-only pass instead of a write

@@ -48,8 +48,8 @@ CASES = {
 def test_jit_equals_interpreter(name, rb):
     """Same plan (explicit register bits), both kernels."""
     c = CASES[name]()
-    ref, st_ref = run(c, BASE, register_bits=rb)
-    got, st = run(c, BASE | S.SIM_F_JIT, register_bits=rb)
+    ref, st_ref = run(c, BASE, register_bits=rb, chunk_qubits=12)
+    got, st = run(c, BASE | S.SIM_F_JIT, register_bits=rb, chunk_qubits=12)
     assert st["chunk_ops"] + st["diag_ops"] > 0
     st.pop("plan_ms"), st_ref.pop("plan_ms")
     assert st == st_ref   # same plan
