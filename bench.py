@@ -135,7 +135,7 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-PRECISIONS = {"tf32x3": 0, "fp32": 1, "fp64": 2}
+PRECISIONS = {"tf32x3": 0, "fp32": 1, "fp64": 2, "df": 3}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # SMs x FP32 lanes x FMA x max SM clock
 DF_FLOPS_PER_AMP = 2 * 64 * 15 + 2 * 3                 # double-float complex128 dense block
 
@@ -615,6 +615,113 @@ def run_readouts(args, rank, world, dist):
         print(json.dumps(line), flush=True)
 
 
+FP64_PEAK_TFLOPS = 1.25    # nominal dense FP64 of a GB300 (no measured figure on this machine)
+
+
+def run_precision(args, rank, world, dist):
+    """Config 3's precision study: the depth-20 random layered circuit fused
+    into dense 5-qubit blocks, run in every arithmetic arm, each timed (CUDA
+    events around the whole apply, one run after a smaller warm-up circuit)
+    and compared with a complex128 GPU reference state on the device: true
+    FP64 blocks at n <= 30, double-float above (the FP64 run grows to minutes
+    there; double-float agrees with it to about 1e-14, tests/test_gpu_dense).
+    Both reference arms are checked against the CPU oracle at <= 24 qubits by
+    the GPU tests.  Error = max |a - a_ref| and |<a_ref|a>|^2 / norms, in FP64
+    over slices of the states (no full-size temporaries)."""
+    import torch
+    from paper_2604_12256_gb300 import build as B
+    from paper_2604_12256_gb300 import circuits as C
+    from paper_2604_12256_gb300 import svsim as S
+
+    B.build()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    n = args.qubits or 33
+    circ = C.layered(n, 20, 0)
+    ga = S.GateArray(circ.gates)
+    warm = S.GateArray(C.layered(n, 1, 1).gates)
+    stream = torch.cuda.current_stream()
+    amps = 1 << n
+    ref_prec = "fp64" if n <= 30 else "double-float"
+    arms = [("c128", ref_prec)] + [("c128", "double-float")] * (ref_prec == "fp64") + \
+           [("c64", "tf32x3"), ("c64", "fp32")]
+    code = {"tf32x3": S.SIM_DENSE_SPLIT_TF32, "fp32": S.SIM_DENSE_FP32, "fp64": S.SIM_DENSE_FP64,
+            "double-float": S.SIM_DENSE_DOUBLE_FLOAT}
+    clocks = Clocks(dev)
+    clocks.start()
+    ref = None
+    out = []
+    for dt_name, prec in arms:
+        c128 = dt_name == "c128"
+        buf = torch.empty(2 * amps, dtype=torch.float64 if c128 else torch.float32, device="cuda")
+        sim = S.Sim(n, S.SIM_C128 if c128 else S.SIM_C64, dev_buf=buf.data_ptr(),
+                    nbytes=buf.numel() * buf.element_size(), stream=stream.cuda_stream)
+        opt = S.default_options(flags=S.SIM_F_TC | S.SIM_F_DIAG, dense_precision=code[prec])
+        sim.reset(0)
+        sim.apply(warm, opt)
+        sim.profile_enable(True, state_only=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.reset(0)
+        sim.apply(ga, opt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        prof = sim.profile_read()
+        st = sim.stats()
+        sim.close()
+        cv = buf.view(torch.complex128 if c128 else torch.complex64)
+        d = prof["dense"]
+        sweep_ms = d["ms"] / max(1, d["launches"])
+        if prec == "tf32x3":
+            roof = {"bound": "hbm", "achieved": 16.0 * amps / (sweep_ms / 1e3) / 1e9, "peak": _peaks()[0],
+                    "unit": "GB/s", "kernel": "k_dense5_tc"}
+        elif prec == "fp32":
+            roof = {"bound": "alu", "achieved": 256.0 * amps / (sweep_ms / 1e3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "kernel": "k_dense5_fma<float>",
+                    "flop_per_amp": 256, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+        elif prec == "double-float":
+            roof = {"bound": "alu", "achieved": DF_FLOPS_PER_AMP * amps / (sweep_ms / 1e3) / 1e12,
+                    "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "kernel": "k_dense5_df",
+                    "flop_per_amp": DF_FLOPS_PER_AMP,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (FP32 operations of the "
+                                   "double-float arithmetic)"}
+        else:
+            roof = {"bound": "alu", "achieved": 256.0 * amps / (sweep_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "kernel": "k_dense5_fma<double>", "flop_per_amp": 256,
+                    "peak_source": "nominal FP64 of a GB300"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        row = {"dtype": dt_name, "arith": prec, "ms": ms, "block_sweeps": st["dense_ops"],
+               "ms_per_block_sweep": sweep_ms, "amplitude_updates_per_s": len(circ.gates) * amps / (ms / 1e3),
+               "roofline": roof}
+        if ref is None:
+            ref, ref_buf = cv, buf
+            row["error"] = "reference"
+        else:
+            err, ov, ng, ne = 0.0, 0j, 0.0, 0.0
+            step = 1 << 26
+            for lo in range(0, amps, step):
+                a = cv[lo:lo + step].to(torch.complex128)
+                r = ref[lo:lo + step]
+                err = max(err, float((a - r).abs().max()))
+                ov += complex(torch.vdot(r, a))
+                ng += float(torch.vdot(a, a).real)
+                ne += float(torch.vdot(r, r).real)
+            row["error"] = {"max_abs": err, "fidelity": abs(ov) ** 2 / (ng * ne), "norm": ng,
+                            "vs": f"complex128 {ref_prec} GPU state"}
+            del cv, buf
+            torch.cuda.empty_cache()
+        out.append(row)
+    clk = clocks.stop()
+    if rank == 0:
+        line = {"metric": "precision study: time, roofline and error of the dense 5-qubit block arms (config 3)",
+                "n_qubits": n, "workload": f"{n}-qubit random layered circuit, depth 20, dense 5-qubit blocks",
+                "gates": len(circ.gates), "data": "synthetic", "reference": f"complex128 {ref_prec} on the GPU",
+                "arms": out, "clocks": clk}
+        print(json.dumps(line), flush=True)
+
+
 def _pct(xs, q):
     xs = sorted(xs)
     return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))] if xs else None
@@ -783,6 +890,9 @@ def main():
     ap.add_argument("--families", action="store_true",
                     help="per-gate time of the BV / HS / QV / SC / VC families: gate by gate, optimized, "
                          "optimized with the merge booster")
+    ap.add_argument("--precision-study", action="store_true",
+                    help="config 3: the layered circuit in dense 5-qubit blocks in every arithmetic arm (split-TF32, "
+                         "FP32, double-float, FP64), each timed and compared with a complex128 GPU reference")
     ap.add_argument("--serve", action="store_true",
                     help="time the serving loop on a Poisson request stream instead")
     ap.add_argument("--requests", type=int, default=1000)
@@ -831,7 +941,7 @@ def main():
         dist = dist_
     try:
         (run_serve if args.serve else run_families if args.families else run_readouts if args.readouts
-         else run_gpu)(args, rank, world, dist)
+         else run_precision if args.precision_study else run_gpu)(args, rank, world, dist)
     finally:
         if dist is not None:
             dist.destroy_process_group()

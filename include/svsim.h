@@ -38,7 +38,14 @@ extern "C" {
 
 typedef struct sim_t sim_t;
 
-/* Amplitude type of a state vector.  The paper runs complex128 (Section 5.1). */
+/* Amplitude type of a state vector.  The paper runs complex128 (Section 5.1).
+ * SIM_C64: float (re, im) pairs; sweeps compute in FP32, with FP64 for fused
+ * matrix composition and every reduction.  SIM_C128: double (re, im) pairs in
+ * memory and at the ABI; the cache-blocked, phase and dense-block kernels
+ * compute in double-float -- each real as an unevaluated sum of two floats,
+ * about 48 significant bits (this GPU's FP64 rate is 1/64 of its FP32 rate)
+ * -- except dense blocks asked for SIM_DENSE_FP64 (true FP64), the
+ * gate-by-gate kernels and the reductions, which run FP64. */
 typedef enum { SIM_C64 = 0, SIM_C128 = 1 } sim_dtype;
 
 typedef enum {
@@ -107,10 +114,13 @@ enum {
     SIM_F_ALL = 0x7f
 };
 
-/* Precision of dense fused blocks on complex64 states (complex128 states
- * compute their blocks in double-float, pairs of FP32 numbers with about 48
- * significant bits, whatever this field says). */
-enum { SIM_DENSE_SPLIT_TF32 = 0, SIM_DENSE_FP32 = 1, SIM_DENSE_FP64 = 2 };
+/* Arithmetic of dense fused 5-qubit blocks (SIM_F_TC).  complex64 states:
+ * SIM_DENSE_SPLIT_TF32 on the tensor cores (three TF32 products, FP32
+ * accumulation) or SIM_DENSE_FP32 on the CUDA cores (the other two values run
+ * FP32 too).  complex128 states: SIM_DENSE_FP64 runs true FP64 on the FP64
+ * pipe; every other value runs double-float on the FP32 pipe (about 48
+ * significant bits, several times faster here). */
+enum { SIM_DENSE_SPLIT_TF32 = 0, SIM_DENSE_FP32 = 1, SIM_DENSE_FP64 = 2, SIM_DENSE_DOUBLE_FLOAT = 3 };
 
 /* The environment of Section 4.1 (N comes from the handle, R is 0: one GPU). */
 typedef struct {

@@ -11,7 +11,9 @@
 //     as D(128 x 64) = A(128 x 64) B(64 x 64)^T with A = X^T of a 128-column
 //     tile (one CTA thread per column) and B = the 64 x 64 embedding.
 //   * k_dense5_fma<float>: FP32 CUDA cores (complex64 states).
-//   * k_dense5_df: double-float on the FP32 pipe (complex128 states).
+//   * k_dense5_df: double-float on the FP32 pipe (complex128 states, default).
+//   * k_dense5_fma<double>: FP64 on the FP64 pipe (complex128 states asked
+//     for SIM_DENSE_FP64; this GPU's FP64 rate is 1/64 of its FP32 rate).
 #include <cstdint>
 
 #include "dfloat.h"
@@ -379,7 +381,10 @@ cudaError_t launch_dense5(void *a, int n, bool f64, int precision, const int *q,
     const int64_t ncol = (int64_t)1 << (n - 5);
     if (f64) {
         int grid = (int)std::min<int64_t>((ncol + 127) / 128, (int64_t)device_sm_count() * 8);
-        k_dense5_df<<<grid, 128, 0, st>>>((double2 *)a, n, g, (const double2 *)U64);
+        if (precision == 2)   // true FP64 on the FP64 pipe
+            k_dense5_fma<double><<<grid, 128, 0, st>>>((double2 *)a, n, g, (const double2 *)U64);
+        else
+            k_dense5_df<<<grid, 128, 0, st>>>((double2 *)a, n, g, (const double2 *)U64);
         return counted(cudaGetLastError(), 1);
     }
     if (precision == 0) {   // split-TF32 on the tensor cores

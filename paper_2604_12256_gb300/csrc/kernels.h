@@ -133,8 +133,8 @@ cudaError_t launch_phase_small(void *a, int n, bool is_f64, const uint64_t *term
 // Dense 5-qubit block (K6): q = the 5 qubits (local bit i <-> q[i]), U64 =
 // device 32 x 32 row-major complex matrix in FP64.  precision: 0 split-TF32
 // on the tensor cores, 1 FP32 CUDA cores (complex64 states); complex128
-// states always use double-float on the FP32 pipe (about 48 significant
-// bits).  status: device int set to 1 when a bounded wait
+// states: 2 FP64 on the FP64 pipe, anything else double-float on the FP32
+// pipe (about 48 significant bits).  status: device int set to 1 when a bounded wait
 // of the tensor-core kernel gave up.
 cudaError_t launch_dense5(void *a, int n, bool is_f64, int precision, const int *q, const void *U64, int *status,
                           cudaStream_t st);

@@ -1399,7 +1399,12 @@ static void schedule_dense_blocks(const std::vector<PGate> &G, int n, int precis
 static void schedule(const std::vector<PGate> &G, int n, const sim_options &opt, sim_dtype dt, int buf, Plan &plan)
 {
     if ((opt.flags & SIM_F_TC) && n >= 5) {
-        schedule_dense_blocks(G, n, dt == SIM_C128 ? SIM_DENSE_FP64 : opt.dense_precision, buf, plan);
+        // complex64: split-TF32 or FP32 (FP64 and double-float asks run FP32);
+        // complex128: true FP64, or double-float for every other ask
+        int prec = opt.dense_precision;
+        if (dt == SIM_C64) prec = prec == SIM_DENSE_SPLIT_TF32 ? SIM_DENSE_SPLIT_TF32 : SIM_DENSE_FP32;
+        else prec = prec == SIM_DENSE_FP64 ? SIM_DENSE_FP64 : SIM_DENSE_DOUBLE_FLOAT;
+        schedule_dense_blocks(G, n, prec, buf, plan);
         return;
     }
     int C = 0, RB = 0;

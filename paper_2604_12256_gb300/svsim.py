@@ -23,7 +23,7 @@ SIM_C64, SIM_C128 = 0, 1
 SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_ETIMEOUT, SIM_EBUSY, SIM_EUNSUPPORTED = range(7)
 SIM_F_DIAG, SIM_F_BOOST, SIM_F_BLOCK, SIM_F_FUSE, SIM_F_TC, SIM_F_REMAP, SIM_F_JIT = 1, 2, 4, 8, 16, 32, 64
 SIM_F_ALL = 0x7F
-SIM_DENSE_SPLIT_TF32, SIM_DENSE_FP32, SIM_DENSE_FP64 = 0, 1, 2
+SIM_DENSE_SPLIT_TF32, SIM_DENSE_FP32, SIM_DENSE_FP64, SIM_DENSE_DOUBLE_FLOAT = 0, 1, 2, 3
 
 KIND = {"h": 0, "x": 1, "y": 2, "z": 3, "s": 4, "t": 5, "rx": 6, "ry": 7, "rz": 8, "p": 9,
         "cx": 10, "cz": 11, "cp": 12, "rzz": 13, "swap": 14, "u1q": 15, "unitary": 16, "diag": 17}

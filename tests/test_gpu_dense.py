@@ -1,6 +1,6 @@
 """Dense 5-qubit fused blocks (tensor-core GEMM path) against the oracle:
 split-TF32 on the tensor cores and FP32 CUDA cores for complex64 states,
-FP64 for complex128 states."""
+double-float (about 48 bits) and true FP64 for complex128 states."""
 import numpy as np
 import pytest
 
@@ -11,7 +11,7 @@ from paper_2604_12256_gb300 import svsim as S
 pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("built_lib")]
 
 PRECISIONS = [(S.SIM_C64, S.SIM_DENSE_SPLIT_TF32, 1e-5), (S.SIM_C64, S.SIM_DENSE_FP32, 1e-5),
-              (S.SIM_C128, S.SIM_DENSE_FP64, 1e-12)]
+              (S.SIM_C128, S.SIM_DENSE_DOUBLE_FLOAT, 1e-12), (S.SIM_C128, S.SIM_DENSE_FP64, 1e-12)]
 
 
 def fid(a, b):
@@ -27,7 +27,7 @@ def run_tc(c, dtype, prec):
         return s.get_state().astype(np.complex128), st
 
 
-@pytest.mark.parametrize("dtype,prec,tol", PRECISIONS, ids=["tf32x3", "fp32", "fp64"])
+@pytest.mark.parametrize("dtype,prec,tol", PRECISIONS, ids=["tf32x3", "fp32", "double-float", "fp64"])
 @pytest.mark.parametrize("targets", [(0, 1, 2, 3, 4), (3, 7, 9, 11, 14), (10, 11, 12, 13, 14), (13, 1, 6, 12, 5)])
 def test_single_block(dtype, prec, tol, targets):
     rng = np.random.default_rng(sum(targets))
@@ -47,7 +47,7 @@ def test_single_block(dtype, prec, tol, targets):
     assert err <= tol * 0.1, err
 
 
-@pytest.mark.parametrize("dtype,prec,tol", PRECISIONS, ids=["tf32x3", "fp32", "fp64"])
+@pytest.mark.parametrize("dtype,prec,tol", PRECISIONS, ids=["tf32x3", "fp32", "double-float", "fp64"])
 @pytest.mark.parametrize("maker", [lambda: C.layered(14, 8, 3), lambda: C.random_mixed(13, 150, 9, max_k=3),
                                    lambda: C.qft(12, 5), lambda: C.layered(20, 6, 4)],
                          ids=["layered14", "mixed13", "qft12", "layered20"])
@@ -91,3 +91,13 @@ def test_bounded_wait_times_out_and_recovers():
         got = s.get_state()
     exp = oracle.run(c)
     assert np.abs(got - exp).max() < 1e-5
+
+
+def test_fp64_and_double_float_agree():
+    """The two complex128 arms on a 20-qubit layered circuit: true FP64 (the
+    reference of the precision study) and double-float agree far inside the
+    complex128 tolerance."""
+    c = C.layered(20, 8, 21)
+    a, _ = run_tc(c, S.SIM_C128, S.SIM_DENSE_FP64)
+    b, _ = run_tc(c, S.SIM_C128, S.SIM_DENSE_DOUBLE_FLOAT)
+    assert np.max(np.abs(a - b)) <= 1e-13

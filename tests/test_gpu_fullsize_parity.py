@@ -188,10 +188,10 @@ def test_config1_28q_complex128_against_oracle(config1):
 
 # ---------------------------------------------------------------- dense blocks
 DENSE = [(S.SIM_C64, S.SIM_DENSE_SPLIT_TF32, TOL64), (S.SIM_C64, S.SIM_DENSE_FP32, TOL64),
-         (S.SIM_C128, S.SIM_DENSE_FP64, TOL128)]
+         (S.SIM_C128, S.SIM_DENSE_DOUBLE_FLOAT, TOL128), (S.SIM_C128, S.SIM_DENSE_FP64, TOL128)]
 
 
-@pytest.mark.parametrize("dtype,prec,tol", DENSE, ids=["tf32x3", "fp32", "double-float"])
+@pytest.mark.parametrize("dtype,prec,tol", DENSE, ids=["tf32x3", "fp32", "double-float", "fp64"])
 def test_dense_blocks_loop_over_tiles(dtype, prec, tol):
     """Dense 5-qubit blocks at 24 qubits: 2^19 columns, so each tensor-core
     CTA runs about 13 tiles (mbarrier phase flips, TMEM reuse, the prefetched
@@ -209,7 +209,7 @@ def test_dense_blocks_loop_over_tiles(dtype, prec, tol):
         assert _fid(exp, got) >= FID64
 
 
-@pytest.mark.parametrize("dtype,prec,tol", DENSE, ids=["tf32x3", "fp32", "double-float"])
+@pytest.mark.parametrize("dtype,prec,tol", DENSE, ids=["tf32x3", "fp32", "double-float", "fp64"])
 def test_single_dense_block_22q(dtype, prec, tol):
     """One Haar-random 32x32 block on scattered qubits of a random 22-qubit
     state (1024 tensor-core tiles on 2 x SMs CTAs)."""
