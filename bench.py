@@ -42,9 +42,9 @@ WORKLOAD = "28-qubit diagonal-heavy gate-level stream (500 gates, 80% RZ/CP/RZZ,
 # A sweep's traffic grows with the amplitudes it processes, so a capture on a
 # smaller state scales to the full one (profiles/ has the captures).
 TRAFFIC_PER_AMP = {
-    # profiles/svs_chunk_jit_diagheavy_25q.md: 475.97 MB per 2^25-amplitude sweep
+    # profiles/svs_chunk_jit_diagheavy_25q.md: 477.45 MB per 2^25-amplitude sweep
     # (the specialised kernel: keyed by its device templates and generator)
-    ("diag-heavy", "chunk-jit", "359062f70d7e6966f803d6dcbb4c08f0795e984a9309e29795f9a2ea43905579"): 475.97e6 / 2 ** 25,
+    ("diag-heavy", "chunk-jit", "64c99e642ad2d86e4eab5fb10ad0006408612f54b2ef585dab4697c801503c8c"): 477.45e6 / 2 ** 25,
     # profiles/k_chunk_diagheavy_25q.md: 476.05 MB per 2^25-amplitude sweep (interpreter)
     ("diag-heavy", "chunk", "8f96366b3d7184491700fbf33588aba4d28412cc874eee7e00ed69b7789963a2"): 476.05e6 / 2 ** 25,
     # profiles/k_dense5_tc_layered_26q.md: 1011.84 MB per 2^26-amplitude block sweep
@@ -895,7 +895,7 @@ def main():
                          "FP32, double-float, FP64), each timed and compared with a complex128 GPU reference")
     ap.add_argument("--serve", action="store_true",
                     help="time the serving loop on a Poisson request stream instead")
-    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--requests", type=int, default=10000, help="serving requests (config 4: 10,000)")
     ap.add_argument("--streams", type=int, default=4, help="serving worker streams")
     ap.add_argument("--budget-gib", type=float, default=32.0, help="serving HBM budget for admitted states")
     ap.add_argument("--qubits", type=int, default=0,
