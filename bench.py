@@ -347,8 +347,7 @@ def run_gpu(args, rank, world, dist):
         t0 = time.perf_counter()
         sim.reset(circ.basis)
         sim.apply(circ.gates, opt)      # marshal from the Python gate list each step
-        idx, p = sim.top_k(64)
-        ev = sim.expectation(masks)
+        idx, p, ev = sim.top_k_expectation(64, masks)   # both read-outs, concurrently, one sync
         te.append(time.perf_counter() - t0)
     e2e_s = statistics.median(te)
     # the fused path's final state, for the error against the oracle below
@@ -363,8 +362,7 @@ def run_gpu(args, rank, world, dist):
         t0 = time.perf_counter()
         sim.reset(fc.basis)
         sim.apply(fc.gates, opt)
-        sim.top_k(64)
-        sim.expectation(masks)
+        sim.top_k_expectation(64, masks)
         tf.append(time.perf_counter() - t0)
     jit_f1 = S.jit_info()
     fresh_angles = {"ms_per_step": statistics.median(tf) * 1e3, "circuits": len(fresh),
@@ -582,7 +580,8 @@ def run_readouts(args, rank, world, dist):
     sim.apply(circ.gates, opt)
     torch.cuda.synchronize()
     masks = [(1 << a) | (1 << ((a * 7 + 3) % n)) for a in range(16)]
-    calls = {"top64": lambda: sim.top_k(64), "zz16": lambda: sim.expectation(masks), "norm": lambda: sim.norm()}
+    calls = {"top64": lambda: sim.top_k(64), "zz16": lambda: sim.expectation(masks), "norm": lambda: sim.norm(),
+             "top64+zz16 (one call, concurrent)": lambda: sim.top_k_expectation(64, masks)}
     peak, peak_kind = _peaks()
     state_bytes = (1 << n) * 8
     clocks = Clocks(dev)

@@ -207,6 +207,16 @@ int sim_top_k(sim_t *s, int k, uint64_t *idx, double *prob);
  * fixed order, FP64 across blocks; masks with bits >= n are rejected. */
 int sim_expectation(sim_t *s, const uint64_t *z_masks, size_t n_terms, double *out);
 
+/* Both read-outs above in one call: the k largest probabilities (as
+ * sim_top_k) and n_terms <Z-string> values (as sim_expectation, 16 strings
+ * per pass; out may be NULL when n_terms = 0).  The top-k and the first 16 strings'
+ * sums run concurrently on the handle's stream and a second stream the
+ * handle creates on first use, and one synchronisation waits for both; the
+ * results equal those of the two separate calls.  Synchronises the handle's
+ * stream. */
+int sim_top_k_expectation(sim_t *s, int k, uint64_t *idx, double *prob, const uint64_t *z_masks, size_t n_terms,
+                          double *out);
+
 /* Squared norm sum_x |a_x|^2, accumulated in FP64 (Section 2.1: the state
  * vector has unit L2 norm; this reads how far rounding moved it). */
 int sim_norm(sim_t *s, double *out);

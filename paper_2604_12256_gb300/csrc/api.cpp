@@ -42,6 +42,8 @@ struct sim_t {
     size_t pin_bytes = 0;
     cudaEvent_t pin_ev = nullptr;
     bool pin_pending = false;
+    cudaStream_t aux = nullptr;         // second stream of the combined read-out
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<void *> sub;            // booster sub-state buffers
     std::vector<size_t> sub_bytes;
     std::string err;
@@ -146,6 +148,9 @@ static void free_all(sim_t *s)
     if (s->pin_ev) cudaEventDestroy(s->pin_ev);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     for (void *p : s->sub) if (p) cudaFree(p);
+    if (s->aux) { cudaStreamSynchronize(s->aux); cudaStreamDestroy(s->aux); }
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }
@@ -622,12 +627,8 @@ int sim_probabilities(sim_t *s, double *out)
     return check_status(s);
 }
 
-int sim_top_k(sim_t *s, int k, uint64_t *idx, double *prob)
+static int topk_scratch(sim_t *s)
 {
-    if (!s || !idx || !prob) return fail(s, SIM_EINVAL, "null argument");
-    if (k < 1 || k > 1024) return fail(s, SIM_EINVAL, "k must be in 1..1024");
-    if (int rc = materialize(s)) return rc;
-    int kk = (int)std::min<uint64_t>((uint64_t)k, (uint64_t)1 << s->n);
     size_t need = topk_scratch_bytes(1024) + 2 * 1024 * 8;
     if (s->topk_bytes < need) {
         if (s->d_topk) { CK(s, cudaStreamSynchronize(s->stream)); CK(s, cudaFree(s->d_topk)); }
@@ -635,6 +636,17 @@ int sim_top_k(sim_t *s, int k, uint64_t *idx, double *prob)
         CK(s, dev_malloc((void **)&s->d_topk, need));
         s->topk_bytes = need;
     }
+    return SIM_OK;
+}
+
+// Top-k of the state into host idx/prob.  `join`: an event recorded on
+// another stream (the combined read-out's <Z> sums, nz values at dz) that
+// the handle's stream waits for before the first copies, so both run while
+// one synchronisation waits for both; the sums are copied to zout.
+static int top_k_into(sim_t *s, int k, uint64_t *idx, double *prob, cudaEvent_t join, double *zout,
+                      const double *dz, int nz)
+{
+    int kk = (int)std::min<uint64_t>((uint64_t)k, (uint64_t)1 << s->n);
     unsigned char *base = (unsigned char *)s->d_topk;
     uint64_t *di = (uint64_t *)(base + topk_scratch_bytes(1024));
     double *dp = (double *)(di + 1024);
@@ -645,12 +657,59 @@ int sim_top_k(sim_t *s, int k, uint64_t *idx, double *prob)
     for (int pass = 0; pass < 2; pass++) {
         CK(s, launch_topk(s->state, s->n, s->dt == SIM_C128, kk, base, di, dp, s->stream, pass ? 0 : keep,
                           pass ? nullptr : &slice));
+        if (join && pass == 0) {
+            CK(s, cudaStreamWaitEvent(s->stream, join, 0));
+            CK(s, cudaMemcpyAsync(zout, dz, sizeof(double) * nz, cudaMemcpyDeviceToHost, s->stream));
+        }
         CK(s, cudaMemcpyAsync(idx, di, sizeof(uint64_t) * kk, cudaMemcpyDeviceToHost, s->stream));
         CK(s, cudaMemcpyAsync(prob, dp, sizeof(double) * kk, cudaMemcpyDeviceToHost, s->stream));
         CK(s, cudaStreamSynchronize(s->stream));
         if (pass || !topk_warp_suspect(idx, kk, slice, keep)) break;
     }
     for (int i = kk; i < k; i++) { idx[i] = UINT64_MAX; prob[i] = -1.0; }
+    return SIM_OK;
+}
+
+int sim_top_k(sim_t *s, int k, uint64_t *idx, double *prob)
+{
+    if (!s || !idx || !prob) return fail(s, SIM_EINVAL, "null argument");
+    if (k < 1 || k > 1024) return fail(s, SIM_EINVAL, "k must be in 1..1024");
+    if (int rc = materialize(s)) return rc;
+    if (int rc = topk_scratch(s)) return rc;
+    return top_k_into(s, k, idx, prob, nullptr, nullptr, nullptr, 0);
+}
+
+int sim_top_k_expectation(sim_t *s, int k, uint64_t *idx, double *prob, const uint64_t *masks, size_t nt,
+                          double *out)
+{
+    if (!s || !idx || !prob || (nt && (!masks || !out))) return fail(s, SIM_EINVAL, "null argument");
+    if (k < 1 || k > 1024) return fail(s, SIM_EINVAL, "k must be in 1..1024");
+    for (size_t i = 0; i < nt; i++)
+        if (s->n < 64 && (masks[i] >> s->n)) return fail(s, SIM_EINVAL, "Z mask has bits above n");
+    if (int rc = materialize(s)) return rc;
+    if (int rc = topk_scratch(s)) return rc;
+    if (nt == 0) return top_k_into(s, k, idx, prob, nullptr, nullptr, nullptr, 0);
+    if (!s->aux) {
+        CK(s, cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking));
+        CK(s, cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+        CK(s, cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
+    }
+    // the first 16 strings' sums on the second stream, beside the top-k
+    const int c0 = (int)std::min<size_t>(16, nt);
+    CK(s, cudaEventRecord(s->ev_fork, s->stream));
+    CK(s, cudaStreamWaitEvent(s->aux, s->ev_fork, 0));
+    CK(s, cudaMemcpyAsync(s->d_masks, masks, sizeof(uint64_t) * c0, cudaMemcpyHostToDevice, s->aux));
+    CK(s, launch_expect_z(s->state, s->n, s->dt == SIM_C128, s->d_masks, c0, s->d_part, s->d_out, s->aux));
+    CK(s, cudaEventRecord(s->ev_join, s->aux));
+    if (int rc = top_k_into(s, k, idx, prob, s->ev_join, out, s->d_out, c0)) return rc;
+    // further strings, 16 at a time, after
+    for (size_t b = 16; b < nt; b += 16) {
+        int cnt = (int)std::min<size_t>(16, nt - b);
+        CK(s, cudaMemcpyAsync(s->d_masks, masks + b, sizeof(uint64_t) * cnt, cudaMemcpyHostToDevice, s->stream));
+        CK(s, launch_expect_z(s->state, s->n, s->dt == SIM_C128, s->d_masks, cnt, s->d_part, s->d_out, s->stream));
+        CK(s, cudaMemcpyAsync(out + b, s->d_out, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s->stream));
+        CK(s, cudaStreamSynchronize(s->stream));
+    }
     return SIM_OK;
 }
 

@@ -291,8 +291,11 @@ void worker_loop(srv_t *s)
         if (rc == SIM_OK) rc = svs_rebind(h, r->n, r->dt, buf, cap);
         if (rc == SIM_OK) rc = sim_reset(h, r->basis);
         if (rc == SIM_OK) rc = sim_apply_circuit(h, r->gates.data(), r->gates.size(), nullptr);
-        if (rc == SIM_OK && !r->masks.empty()) rc = sim_expectation(h, r->masks.data(), r->masks.size(), r->res.expect);
-        if (rc == SIM_OK && r->top_k > 0) rc = sim_top_k(h, r->top_k, r->res.top_idx, r->res.top_p);
+        if (rc == SIM_OK && r->top_k > 0)
+            rc = sim_top_k_expectation(h, r->top_k, r->res.top_idx, r->res.top_p, r->masks.data(), r->masks.size(),
+                                       r->res.expect);
+        else if (rc == SIM_OK && !r->masks.empty())
+            rc = sim_expectation(h, r->masks.data(), r->masks.size(), r->res.expect);
         if (rc == SIM_OK) rc = sim_sync(h);
         r->res.path = 1;
         r->res.n_masks = (int)r->masks.size();

@@ -115,6 +115,7 @@ _SIGS = [
     ("sim_jit_check", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _P, ctypes.c_size_t,
                                      ctypes.POINTER(sim_options), ctypes.POINTER(ctypes.c_int)]),
     ("sim_fault_inject", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    ("sim_top_k_expectation", ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_size_t, _P]),
     ("sim_jit_cache", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     ("sim_jit_sources", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _P, ctypes.c_size_t,
                                        ctypes.POINTER(sim_options), ctypes.c_char_p, ctypes.c_size_t,
@@ -346,6 +347,17 @@ class Sim:
         out = np.empty(len(m), np.float64)
         _check(self.lib.sim_expectation(self.h, m.ctypes.data, len(m), out.ctypes.data), self.h)
         return out
+
+    def top_k_expectation(self, k: int, masks: Iterable[int]):
+        """(top-k indices, probabilities, <Z-string> values) in one call: the
+        two read-outs run concurrently (sim_top_k_expectation)."""
+        idx = np.empty(k, np.uint64)
+        p = np.empty(k, np.float64)
+        m = np.ascontiguousarray(np.array(list(masks), dtype=np.uint64))
+        out = np.empty(max(1, len(m)), np.float64)
+        _check(self.lib.sim_top_k_expectation(self.h, k, idx.ctypes.data, p.ctypes.data, m.ctypes.data if len(m) else None,
+                                              len(m), out.ctypes.data), self.h)
+        return idx, p, out[:len(m)]
 
     def get_state(self) -> np.ndarray:
         dt = np.complex64 if self.dtype == SIM_C64 else np.complex128

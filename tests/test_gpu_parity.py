@@ -311,3 +311,25 @@ def test_expectation_on_larger_states(n):
         back = s.get_state()
     exp = oracle.expectation_z(back.astype(np.complex128), masks)
     np.testing.assert_allclose(got, exp, atol=2e-6, rtol=0)
+
+
+@pytest.mark.parametrize("nmask", [0, 5, 16, 21])
+def test_combined_readout_equals_separate_calls(nmask):
+    """sim_top_k_expectation runs the top-k and the <Z> sums concurrently
+    on two streams: the results are bit-equal to the two separate calls,
+    and equal the oracle's within the complex64 tolerance."""
+    c = C.diag_heavy(20, 150, 17)
+    rng = np.random.default_rng(nmask)
+    masks = [int(rng.integers(1, 1 << 20)) for _ in range(nmask)]
+    with S.Sim(20, S.SIM_C64) as s:
+        s.reset(c.basis)
+        s.apply(c.gates)
+        i1, p1 = s.top_k(64)
+        e1 = s.expectation(masks) if nmask else np.zeros(0)
+        for _ in range(2):   # twice: the second stream and events are reused
+            i2, p2, e2 = s.top_k_expectation(64, masks)
+            assert np.array_equal(i1, i2) and np.array_equal(p1, p2) and np.array_equal(e1, e2)
+    exp = oracle.run(c)
+    if nmask:
+        np.testing.assert_allclose(e2, oracle.expectation_z(exp, masks), atol=2e-5)
+    np.testing.assert_allclose(p2, oracle.top_k(exp, 64)[1], atol=2e-5)
