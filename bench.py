@@ -228,6 +228,49 @@ def state_error(got, exp, step=1 << 24):
     return err, float(abs(ov) ** 2 / (ng * ne)), ng
 
 
+def error_without_oracle(args, sim, buf, circ, opt, dt):
+    """The error of a final state too large for the host oracle.  QFT and the
+    full-connectivity RZZ stream have closed forms (QFT|x> = 2^(-n/2)
+    sum_y e^{2 pi i x y / 2^n} |y>; RZZ after H on every qubit: 2^(-n/2)
+    exp(-i/2 sum_{a<b} theta_ab s_a s_b), s_q = 1 - 2 x_q), compared on 2^16
+    seeded random indices and a run of 2^16; other circuits are followed by
+    their inverse and the distance from the initial basis state is reported."""
+    import numpy as np
+    import torch
+    from paper_2604_12256_gb300 import circuits as C
+    from paper_2604_12256_gb300 import svsim as S
+    n = circ.n
+    rng = np.random.default_rng(7)
+    idx = np.unique(np.concatenate([rng.integers(0, 1 << n, 1 << 16, dtype=np.int64),
+                                    np.arange(1 << 20, (1 << 20) + (1 << 16), dtype=np.int64)]))
+    if args.workload in ("qft", "rzz-full"):
+        torch.cuda.synchronize()
+        cv = buf.view(torch.complex128 if dt == S.SIM_C128 else torch.complex64)
+        got = cv[torch.as_tensor(idx, device="cuda")].cpu().numpy().astype(np.complex128)
+        amp = 2.0 ** (-n / 2)
+        if args.workload == "qft":
+            x = circ.basis
+            ph = ((np.uint64(x) * idx.astype(np.uint64)) & np.uint64((1 << n) - 1)).astype(np.float64) / float(1 << n)
+            exp = amp * np.exp(2j * np.pi * ph)
+        else:
+            theta = np.zeros((n, n))
+            for g in circ.gates:
+                if g.kind == "rzz":
+                    theta[g.qubits[0], g.qubits[1]] += g.params[0]
+            sgn = 1.0 - 2.0 * ((idx[:, None] >> np.arange(n)[None, :]) & 1).astype(np.float64)
+            exp = amp * np.exp(-0.5j * np.einsum("ia,ab,ib->i", sgn, theta, sgn))
+        err = float(np.max(np.abs(got - exp)))
+        return {"vs": "closed form on %d sampled amplitudes" % idx.size, "state_max_abs": err,
+                "state_max_rel": err / amp,
+                "tolerance": {"state_max_abs": 1e-5 if dt == S.SIM_C64 else 1e-12}}
+    inv = C.inverse(circ)
+    sim.apply(inv.gates, opt)
+    ti, tp = sim.top_k(2)
+    return {"vs": "the inverse circuit applied after the circuit: distance from the initial basis state",
+            "one_minus_p_initial": float(1.0 - tp[0]) if int(ti[0]) == circ.basis else 1.0,
+            "largest_other_p": float(tp[1]), "norm": sim.norm()}
+
+
 def run_reference(args, rank, world):
     """The oracle as it stands on the host cores.  One step = the first
     REF_PREFIX_GATES gates of the workload at min(n, 28) qubits (a bounded
@@ -352,6 +395,11 @@ def run_gpu(args, rank, world, dist):
     e2e_s = statistics.median(te)
     # the fused path's final state, for the error against the oracle below
     final_state = sim.get_state() if rank == 0 and not args.no_cpu_baseline and N_QUBITS <= 28 else None
+    # states the host oracle does not hold: closed forms on sampled
+    # amplitudes, or the inverse circuit's return to the initial state
+    big_error = None
+    if rank == 0 and N_QUBITS > 28:
+        big_error = error_without_oracle(args, sim, buf, circ, opt, dt)
     # fresh angles: the same circuit structure with every angle (and Haar
     # one-qubit matrix) drawn anew, end to end through the C ABI; with
     # specialised kernels keyed by structure no compile is expected
@@ -494,6 +542,8 @@ def run_gpu(args, rank, world, dist):
         if oracle_leg is not None:
             line["cpu_baseline"] = oracle_leg["cpu_baseline"]
             line["error"] = oracle_leg["error"]
+        elif big_error is not None:
+            line["error"] = big_error
         print(json.dumps(line), flush=True)
     sim.close()
 

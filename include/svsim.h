@@ -108,9 +108,12 @@ enum {
                                share kernels.  Kernels are cached for the
                                process (sim_jit_cache bounds how many); the
                                first apply of a new structure pays its compile
-                               (about 0.3-1 s, in parallel over a plan's
-                               programs).  Results equal the interpreter
-                               kernels' up to rounding order                  */
+                               (1-3 s for 25-40-op sweeps, up to tens of
+                               seconds for the largest, in parallel over a
+                               plan's programs; the environment variable
+                               SVSIM_JIT_FAST_COMPILE=min|mid|max trades run
+                               time for compile time).  Results equal the
+                               interpreter kernels' up to rounding order      */
     SIM_F_ALL = 0x7f
 };
 

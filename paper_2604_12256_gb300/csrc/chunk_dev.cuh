@@ -668,6 +668,26 @@ template <typename T2> __device__ __forceinline__ T2 tensor_amp(const TSrc<T2> &
     return cmul(h, l);
 }
 
+// The sweep's helper lambdas are always inlined (their arrays must stay in
+// registers), also when a kernel is compiled with reduced optimisation.
+#define SVS_INLINE_LAMBDA __attribute__((always_inline))
+
+// A compile-time stage index: kernels specialised to a program run each
+// register stage as its own instantiation (Ops::run_s<..., S>), so the
+// compiler never sees one stage's ops inlined into another's.
+template <int S> struct StageIdx {
+    static constexpr int value = S;
+};
+__device__ __forceinline__ constexpr int stage_of(int s) { return s; }
+template <int S> __device__ __forceinline__ constexpr int stage_of(StageIdx<S>) { return S; }
+template <int S, int N, typename F> __device__ __forceinline__ void for_stages(F &f)
+{
+    if constexpr (S < N) {
+        f(StageIdx<S>{});
+        for_stages<S + 1, N>(f);
+    }
+}
+
 // ------------------------------------------------------------ K4 chunk sweep
 // The sweep over all chunks; `Ops` supplies the register stages' op
 // sequence: InterpOps walks the program in shared memory, a run-time
@@ -766,14 +786,14 @@ __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, 
     const int64_t nchunks = (int64_t)1 << (n - C);
     // chunk base: spread the chunk number over the free (non-chunk) qubits
     // (deposit is linear over disjoint input bytes: three 256-entry tables)
-    auto chunk_base = [&](int64_t chn) {
+    auto chunk_base = [&](int64_t chn) SVS_INLINE_LAMBDA {
         const uint64_t c = (uint64_t)chn;
         return s_dep[c & 255] | s_dep[256 + ((c >> 8) & 255)] | s_dep[512 + ((c >> 16) & 255)];
     };
     if (blockIdx.x < nchunks) cta_accum<R, T>(prog, cta_buf, chunk_base(blockIdx.x), tid);
     __syncthreads();
     // coalesced loads of one chunk's amplitude pairs into registers
-    auto load_regs = [&](T2 (&dst)[NR], uint64_t b) {
+    auto load_regs = [&](T2 (&dst)[NR], uint64_t b) SVS_INLINE_LAMBDA {
         if (src.hi) {
 #pragma unroll
             for (int it = 0; it < NR / 2; it++) {
@@ -799,7 +819,7 @@ __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, 
     // a direct stage (program.h: specialised kernels only) moves its own
     // amplitudes between HBM and registers: register index m of the thread
     // whose stage-s thread bits are at xb is amplitude xb | Ops::roff(s, m)
-    auto load_direct = [&](T2 (&dst)[NR], uint64_t xb, int s) {
+    auto load_direct = [&](T2 (&dst)[NR], uint64_t xb, int s) SVS_INLINE_LAMBDA {
 #pragma unroll
         for (int m = 0; m < NR; m++) {
             const uint64_t g = xb | Ops::roff(s, m);
@@ -819,7 +839,7 @@ __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, 
             }
         }
     };
-    auto store_direct = [&](const T2 (&val)[NR], uint64_t xb, int s) {
+    auto store_direct = [&](const T2 (&val)[NR], uint64_t xb, int s) SVS_INLINE_LAMBDA {
 #pragma unroll
         for (int m = 0; m < NR; m++) {
             const uint64_t g = xb | Ops::roff(s, m);
@@ -901,7 +921,8 @@ __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, 
         // the next chunk's sums (its buffer was cleared during the previous chunk)
         if (nch < nchunks) cta_accum<R, T>(prog, cta_next, nbase, tid);
         // ---- register stages
-        auto stage = [&](int s) {
+        auto stage = [&](auto si) SVS_INLINE_LAMBDA {
+            const int s = stage_of(si);
             const uint32_t *sp = prog + Ops::stage_off(prog, s);
             uint32_t pv[(RB + 3) & ~3];
             Ops::template stage_pv<RB>(sp, s, pv);
@@ -921,7 +942,10 @@ __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, 
                     v[m] = sv[pm];
                 }
             }
-            Ops::template run<R, RB, T>(s, v, x0, prog, sp, cta_ph, thr_ph, nhoist, tid, P);
+            if constexpr (Ops::kStages > 0)
+                Ops::template run_s<R, RB, T, decltype(si)::value>(v, x0, prog, sp, cta_ph, thr_ph, nhoist, tid, P);
+            else
+                Ops::template run<R, RB, T>(s, v, x0, prog, sp, cta_ph, thr_ph, nhoist, tid, P);
             if (kDL && s == Ops::kStages - 1) {
                 store_direct(v, x0, s);
                 return;
@@ -946,8 +970,7 @@ __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, 
             __syncthreads();
         };
         if constexpr (Ops::kStages > 0) {
-#pragma unroll
-            for (int s = 0; s < Ops::kStages; s++) stage(s);
+            for_stages<0, Ops::kStages>(stage);
         } else {
             for (int s = 0; s < nst; s++) stage(s);
         }

@@ -477,8 +477,9 @@ bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std:
         o << " }\n";
     }
     o << "    }\n";
-    o << "    template <typename R, int RB, int T>\n"
-         "    static __device__ __forceinline__ void run(int s, typename CT<R>::T2 (&v)[1 << RB], uint64_t x0,\n"
+    // one instantiation per stage (S compile-time): each holds its own ops only
+    o << "    template <typename R, int RB, int T, int S>\n"
+         "    static __device__ __forceinline__ void run_s(typename CT<R>::T2 (&v)[1 << RB], uint64_t x0,\n"
          "        const uint32_t *prog, const uint32_t *, const typename CT<R>::W *cta_ph,\n"
          "        const typename CT<R>::W *thr_ph, int nhoist, int tid, const JP &P)\n    {\n";
     // pass 1: the scaled forms of one-qubit ops (their form follows the op's
@@ -517,7 +518,7 @@ bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std:
     }
     for (int s = 0; s < ns; s++) {
         const size_t so = w[H_STAGE_OFF + s];
-        o << "        if (s == " << s << ") {\n";
+        o << "        " << (s ? "else " : "") << "if constexpr (S == " << s << ") {\n";
         size_t op = so + S_SIZE;
         for (uint32_t k = 0; k < w[so + S_NOPS]; k++) {
             const uint32_t hdr = w[op], len = w[op + O_WORDS];
@@ -594,8 +595,15 @@ bool jit_compile(const std::string &src, std::vector<char> &cubin, std::string &
         err = "NVRTC: create failed";
         return false;
     }
-    const char *opts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", "-lineinfo"};
-    const nvrtcResult r = nv.compile(p, 4, opts);
+    // SVSIM_JIT_FAST_COMPILE = 0 | min | mid | max: NVRTC's --Ofast-compile
+    // level (compile time against run time; the sweep's helpers stay inlined)
+    static const std::string fast = [] {
+        const char *e = getenv("SVSIM_JIT_FAST_COMPILE");
+        const std::string v = e ? e : "0";
+        return (v == "min" || v == "mid" || v == "max") ? "--Ofast-compile=" + v : std::string();
+    }();
+    const char *opts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", "-lineinfo", fast.c_str()};
+    const nvrtcResult r = nv.compile(p, fast.empty() ? 4 : 5, opts);
     bool ok = r == NVRTC_SUCCESS;
     if (!ok) {
         size_t ls = 0;

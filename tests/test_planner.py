@@ -208,3 +208,28 @@ def test_benchmark_workloads_sweep_budget(name, make, max_sweeps):
     st = S.plan_json(c.n, c.gates, S.SIM_C64, c.basis, opt)["stats"]
     assert st["sweeps"] <= max_sweeps, (name, st)
     assert st["chunk_ops"] + st["diag_ops"] >= 1
+
+
+@pytest.mark.parametrize("name", ["mixed", "diagheavy", "qft", "qaoa", "layered"])
+def test_plans_with_13_qubit_chunks_are_exact(name):
+    """Chunks of 2^13 amplitudes (256 threads of 32 amplitudes, the shape
+    the cost model picks for QAOA and layered circuits): plans at 15 qubits,
+    run by the plan interpreter, equal the oracle's gate-by-gate state."""
+    c = CIRCUITS[name](15 if name != "qaoa" else 14)
+    opt = S.default_options(chunk_qubits=13, register_bits=5, flags=S.default_options().flags | S.SIM_F_JIT)
+    plan = S.plan_json(c.n, c.gates, S.SIM_C64, c.basis, opt)
+    assert any(o["op"] == "chunk" and o["C"] == 13 for o in plan["ops"])
+    np.testing.assert_allclose(interpret(plan, basis=c.basis), oracle.run(c), atol=2e-7, rtol=0)
+
+
+def test_chunk_shape_chosen_by_cost():
+    """With no shape asked for, the specialised kernels' plans take 2^13-
+    amplitude chunks only where they save enough sweeps (QAOA 30 q: 13 -> 9)
+    and keep 2^12 where they do not (the 28-qubit diagonal-heavy stream)."""
+    opt = S.default_options(flags=S.default_options().flags | S.SIM_F_JIT)
+    q = C.qaoa(30, 4, 3)
+    pq = S.plan_json(q.n, q.gates, S.SIM_C64, q.basis, opt)
+    assert {o["C"] for o in pq["ops"] if o["op"] == "chunk" and o["n"] == 30} == {13}
+    d = C.diag_heavy(28, 500, 1)
+    pd = S.plan_json(d.n, d.gates, S.SIM_C64, d.basis, opt)
+    assert {o["C"] for o in pd["ops"] if o["op"] == "chunk" and o["n"] == 28} == {12}
