@@ -27,8 +27,10 @@ namespace svs {
 using namespace prog;
 
 // ------------------------------------------------------------ K4 chunk sweep (interpreter)
+// Registers for three CTAs per SM (2^12 chunks: 256 threads of 16 amplitudes
+// fit in 80 registers), one for 2^13 chunks.
 template <typename R, int C, int RB>
-__global__ void __launch_bounds__(1 << (C - RB), (C - RB) >= 8 ? 1 : (C - RB) >= 7 ? 3 : 8) k_chunk(typename CT<R>::G2 *__restrict__ a,
+__global__ void __launch_bounds__(1 << (C - RB), C >= 13 ? 1 : (C - RB) >= 7 ? 3 : 8) k_chunk(typename CT<R>::G2 *__restrict__ a,
                                                          const uint32_t *__restrict__ gprog, int n,
                                                          TSrc<typename CT<R>::G2> src)
 {
