@@ -42,9 +42,9 @@ WORKLOAD = "28-qubit diagonal-heavy gate-level stream (500 gates, 80% RZ/CP/RZZ,
 # A sweep's traffic grows with the amplitudes it processes, so a capture on a
 # smaller state scales to the full one (profiles/ has the captures).
 TRAFFIC_PER_AMP = {
-    # profiles/svs_chunk_jit_diagheavy_25q.md: 477.45 MB per 2^25-amplitude sweep
+    # profiles/svs_chunk_jit_diagheavy_25q.md: 477.19 MB per 2^25-amplitude sweep
     # (the specialised kernel: keyed by its device templates and generator)
-    ("diag-heavy", "chunk-jit", "64c99e642ad2d86e4eab5fb10ad0006408612f54b2ef585dab4697c801503c8c"): 477.45e6 / 2 ** 25,
+    ("diag-heavy", "chunk-jit", "6054a1651d667797596900ce8ad4b7590004329bf6d837cfade35485f886521e"): 477.19e6 / 2 ** 25,
     # profiles/k_chunk_diagheavy_25q.md: 476.05 MB per 2^25-amplitude sweep (interpreter)
     ("diag-heavy", "chunk", "8f96366b3d7184491700fbf33588aba4d28412cc874eee7e00ed69b7789963a2"): 476.05e6 / 2 ** 25,
     # profiles/k_dense5_tc_layered_26q.md: 1011.84 MB per 2^26-amplitude block sweep
