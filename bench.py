@@ -137,6 +137,21 @@ class Clocks:
 
 PRECISIONS = {"tf32x3": 0, "fp32": 1, "fp64": 2, "df": 3}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # SMs x FP32 lanes x FMA x max SM clock
+TF32_PER_BF16 = 1.1 / 2.25                             # nominal dense TF32 / BF16 tensor rates of a GB300
+TF32_FLOPS_PER_AMP_BLOCK = 3 * 2 * 64 * 64 / 32        # split-TF32: three 64 x 64 real products per 32 amplitudes
+
+
+def _tf32_peak(sustained=True):
+    """Dense TF32 tensor peak: the measured cuBLAS bf16 figure (sustained for
+    a kernel timed inside a long step) times the nominal TF32/BF16 ratio."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        key = "bf16_tflops_sustained" if sustained and "bf16_tflops_sustained" in d else "bf16_tflops"
+        if key in d:
+            return d[key] * TF32_PER_BF16, f"measured {key} x {TF32_PER_BF16:.3f} (nominal TF32/BF16)"
+    return (1700.0 if sustained else 1900.0) * TF32_PER_BF16, "fallback bf16 x nominal TF32/BF16"
 DF_FLOPS_PER_AMP = 2 * 64 * 15 + 2 * 3                 # double-float complex128 dense block
 
 
@@ -322,8 +337,11 @@ def run_gpu(args, rank, world, dist):
     sim = S.Sim(N_QUBITS, dt, dev_buf=buf.data_ptr(), nbytes=buf.numel() * 4, stream=stream.cuda_stream)
     opt = S.default_options()
     if dense:
-        opt.flags = S.SIM_F_TC | S.SIM_F_DIAG
+        # split-TF32 complex64 blocks run cache-blocked (several per sweep on
+        # the tensor cores) unless --dense-separate asks for one sweep each
+        opt.flags = S.SIM_F_TC | S.SIM_F_DIAG | (0 if args.dense_separate else S.SIM_F_BLOCK)
         opt.dense_precision = PRECISIONS[args.precision]
+    fused_dense = dense and dt == S.SIM_C64 and args.precision == "tf32x3" and not args.dense_separate
     if args.register_bits:
         opt.register_bits = args.register_bits
     if args.chunk_qubits:
@@ -485,8 +503,8 @@ def run_gpu(args, rank, world, dist):
     if jit_on:
         kname = ("svs_chunk_jit (cache-blocked chunk sweep specialised to its program)" if kind == "chunk" else
                  "svs_diag_jit (fused-diagonal sweep specialised to its program)")
-    if (dense and args.precision != "tf32x3") or args.dtype != "c64":
-        tpa = None   # captured on complex64 (and the tensor-core variant) only
+    if (dense and (args.precision != "tf32x3" or fused_dense)) or args.dtype != "c64":
+        tpa = None   # captured on complex64 (and the one-block-per-sweep tensor-core kernel) only
     traffic = tpa * amps if tpa is not None else None
     if kind == "dense" and dt == S.SIM_C128:
         # double-float on the FP32 pipe: per amplitude 2 components x 64 real
@@ -503,6 +521,20 @@ def run_gpu(args, rank, world, dist):
         roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    elif kind == "dense" and fused_dense:
+        # several blocks per sweep: the tensor pipe (three TF32 products of
+        # 64 x 64 per 32 amplitudes and block) against the HBM round trip
+        kname = "k_dense_chunk_tc (dense 5-qubit blocks inside the cache-blocked sweep, tcgen05 split-TF32)"
+        tpeak, tsrc = _tf32_peak(sustained=True)
+        tflops = TF32_FLOPS_PER_AMP_BLOCK * amps * plan["dense_ops"] * args.steps / (kp["ms"] / 1e3) / 1e12
+        gbs = bytes_per_launch / (avg_ms / 1e3) / 1e9
+        tc = {"achieved": tflops, "peak": tpeak, "unit": "TFLOP/s", "frac": tflops / tpeak, "peak_source": tsrc,
+              "flop_per_amp_per_block": TF32_FLOPS_PER_AMP_BLOCK,
+              "blocks_per_sweep": plan["dense_ops"] / max(1, plan["sweeps"])}
+        hb = {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "peak_source": peak_kind}
+        main = tc if tc["frac"] >= hb["frac"] else hb
+        roof = {"bound": "tensor" if main is tc else "hbm", "kernel": kname, **main, "traffic": traffic,
+                "tensor": tc, "hbm": hb}
     else:
         achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9 if kp["ms"] > 0 else None
         roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -692,20 +724,22 @@ def run_precision(args, rank, world, dist):
     stream = torch.cuda.current_stream()
     amps = 1 << n
     ref_prec = "fp64" if n <= 30 else "double-float"
-    arms = [("c128", ref_prec)] + [("c128", "double-float")] * (ref_prec == "fp64") + \
-           [("c64", "tf32x3"), ("c64", "fp32")]
+    # (dtype, arithmetic, cache-blocked block sweeps): split-TF32 both ways
+    arms = [("c128", ref_prec, False)] + [("c128", "double-float", False)] * (ref_prec == "fp64") + \
+           [("c64", "tf32x3", True), ("c64", "tf32x3", False), ("c64", "fp32", False)]
     code = {"tf32x3": S.SIM_DENSE_SPLIT_TF32, "fp32": S.SIM_DENSE_FP32, "fp64": S.SIM_DENSE_FP64,
             "double-float": S.SIM_DENSE_DOUBLE_FLOAT}
     clocks = Clocks(dev)
     clocks.start()
     ref = None
     out = []
-    for dt_name, prec in arms:
+    for dt_name, prec, blocked in arms:
         c128 = dt_name == "c128"
         buf = torch.empty(2 * amps, dtype=torch.float64 if c128 else torch.float32, device="cuda")
         sim = S.Sim(n, S.SIM_C128 if c128 else S.SIM_C64, dev_buf=buf.data_ptr(),
                     nbytes=buf.numel() * buf.element_size(), stream=stream.cuda_stream)
-        opt = S.default_options(flags=S.SIM_F_TC | S.SIM_F_DIAG, dense_precision=code[prec])
+        opt = S.default_options(flags=S.SIM_F_TC | S.SIM_F_DIAG | (S.SIM_F_BLOCK if blocked else 0),
+                                dense_precision=code[prec])
         sim.reset(0)
         sim.apply(warm, opt)
         sim.profile_enable(True, state_only=True)
@@ -723,7 +757,14 @@ def run_precision(args, rank, world, dist):
         cv = buf.view(torch.complex128 if c128 else torch.complex64)
         d = prof["dense"]
         sweep_ms = d["ms"] / max(1, d["launches"])
-        if prec == "tf32x3":
+        if prec == "tf32x3" and blocked:
+            tpeak, tsrc = _tf32_peak(sustained=True)
+            roof = {"bound": "tensor",
+                    "achieved": TF32_FLOPS_PER_AMP_BLOCK * amps * st["dense_ops"] / (d["ms"] / 1e3) / 1e12,
+                    "peak": tpeak, "unit": "TFLOP/s", "peak_source": tsrc, "kernel": "k_dense_chunk_tc",
+                    "flop_per_amp_per_block": TF32_FLOPS_PER_AMP_BLOCK,
+                    "hbm_frac": 16.0 * amps / (sweep_ms / 1e3) / 1e9 / _peaks()[0]}
+        elif prec == "tf32x3":
             roof = {"bound": "hbm", "achieved": 16.0 * amps / (sweep_ms / 1e3) / 1e9, "peak": _peaks()[0],
                     "unit": "GB/s", "kernel": "k_dense5_tc"}
         elif prec == "fp32":
@@ -741,9 +782,9 @@ def run_precision(args, rank, world, dist):
                     "unit": "TFLOP/s", "kernel": "k_dense5_fma<double>", "flop_per_amp": 256,
                     "peak_source": "nominal FP64 of a GB300"}
         roof["frac"] = roof["achieved"] / roof["peak"]
-        row = {"dtype": dt_name, "arith": prec, "ms": ms, "block_sweeps": st["dense_ops"],
-               "ms_per_block_sweep": sweep_ms, "amplitude_updates_per_s": len(circ.gates) * amps / (ms / 1e3),
-               "roofline": roof}
+        row = {"dtype": dt_name, "arith": prec, "ms": ms, "blocks": st["dense_ops"], "sweeps": st["sweeps"],
+               "cache_blocked": blocked, "ms_per_sweep": sweep_ms,
+               "amplitude_updates_per_s": len(circ.gates) * amps / (ms / 1e3), "roofline": roof}
         if ref is None:
             ref, ref_buf = cv, buf
             row["error"] = "reference"
@@ -924,6 +965,8 @@ def main():
                          "(the last three: 34 qubits complex64 / 33 complex128 by default); qft, qaoa: "
                          "the 30-qubit circuit-level pair (QFT with the reversal SWAPs on a random basis "
                          "state; QAOA p = 4 on a random 3-regular graph)")
+    ap.add_argument("--dense-separate", action="store_true",
+                    help="layered-dense: one sweep per dense block instead of cache-blocked block sweeps")
     ap.add_argument("--precision", default="tf32x3", choices=sorted(PRECISIONS),
                     help="dense-block arithmetic for --workload layered-dense")
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])

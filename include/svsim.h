@@ -292,13 +292,14 @@ int sim_profile_read(sim_t *s, sim_profile *out);
  * servers and threads (a launch that failed to enqueue is not counted).  A
  * diagnostic with no counterpart in the paper; never fails. */
 uint64_t sim_kernel_launches(void);
-/* Self-test of the tensor-core block kernel's bounded waits, on the current
- * device.  It runs the kernel with its MMA issue suppressed, so that every
+/* Self-test of the bounded waits of the two tensor-core kernels (the dense
+ * block sweep and the cache-blocked dense-block sweep), on the current
+ * device.  It runs each kernel with its MMA issue suppressed, so that every
  * mbarrier wait gives up after a few thousand polls, and checks three things:
  * the kernel sets its status word, leaves the state untouched and frees its
- * tensor memory; and a normal block launch afterwards still works.  SIM_OK
- * when all hold; otherwise the failing check is in sim_global_error().
- * Allocates a few KB of device memory.  No counterpart in the paper. */
+ * tensor memory; and a normal launch afterwards still works.  SIM_OK when all
+ * hold; otherwise the failing check is in sim_global_error().  Allocates
+ * about 100 KB of device memory.  No counterpart in the paper. */
 int sim_selftest_wait_timeout(void);
 const char *sim_last_error(const sim_t *s);
 const char *sim_global_error(void);

@@ -243,9 +243,60 @@ int sim_selftest_wait_timeout(void)
             }
         }
     }
+    // 3-4. the same two checks for the cache-blocked dense-block sweep, on one
+    // 2^12-amplitude chunk with one block (X on qubit 0)
+    const int n2 = 12;
+    const size_t N2 = (size_t)1 << n2;
+    std::vector<float2> h2(N2), back2(N2);
+    for (size_t i = 0; i < N2; i++) h2[i] = make_float2(0.0002f * (float)i, 0.0001f * (float)(N2 - i));
+    float2 *d_a2 = nullptr;
+    uint32_t *d_prog = nullptr;
+    std::vector<uint32_t> words;
+    {
+        PGate g;
+        g.kind = kFusedDense;
+        g.k = 5;
+        for (int i = 0; i < 5; i++) g.q[i] = i;
+        g.qmask = 31;
+        g.M.assign(32 * 32, cd(0, 0));
+        for (int r = 0; r < 32; r++) g.M[(size_t)r * 32 + (r ^ 1)] = 1;
+        int cq[16];
+        for (int i = 0; i < 12; i++) cq[i] = i;
+        words = encode_dense_chunk(n2, cq, std::vector<PGate>{g});
+    }
+    if (rc == SIM_OK && ck(cudaMalloc((void **)&d_a2, N2 * sizeof(float2)), "malloc") &&
+        ck(cudaMalloc((void **)&d_prog, words.size() * 4), "malloc") &&
+        ck(cudaMemcpy(d_a2, h2.data(), N2 * sizeof(float2), cudaMemcpyHostToDevice), "copy") &&
+        ck(cudaMemcpy(d_prog, words.data(), words.size() * 4, cudaMemcpyHostToDevice), "copy") &&
+        ck(cudaMemset(d_st, 0, sizeof(int)), "memset") &&
+        ck(launch_dense_chunk_wait_selftest(d_a2, n2, d_prog, d_st, 1u << 12, st), "self-test launch") &&
+        ck(cudaStreamSynchronize(st), "self-test sync") &&
+        ck(cudaMemcpy(&flag, d_st, sizeof(int), cudaMemcpyDeviceToHost), "status read") &&
+        ck(cudaMemcpy(back2.data(), d_a2, N2 * sizeof(float2), cudaMemcpyDeviceToHost), "state read")) {
+        if (flag != 1) { rc = SIM_EINVAL; msg = "the timed-out dense-block sweep did not set the status word"; }
+        for (size_t i = 0; rc == SIM_OK && i < N2; i++)
+            if (back2[i].x != h2[i].x || back2[i].y != h2[i].y) { rc = SIM_EINVAL; msg = "the aborted sweep wrote the state"; }
+    }
+    if (rc == SIM_OK && ck(cudaMemset(d_st, 0, sizeof(int)), "memset") &&
+        ck(launch_dense_chunk(d_a2, n2, d_prog, d_st, st), "sweep launch") &&
+        ck(cudaStreamSynchronize(st), "sweep sync") &&
+        ck(cudaMemcpy(&flag, d_st, sizeof(int), cudaMemcpyDeviceToHost), "status read") &&
+        ck(cudaMemcpy(back2.data(), d_a2, N2 * sizeof(float2), cudaMemcpyDeviceToHost), "state read")) {
+        if (flag != 0) { rc = SIM_ETIMEOUT; msg = "a normal dense-block sweep timed out after the self-test"; }
+        for (size_t i = 0; rc == SIM_OK && i < N2; i++) {
+            const float2 want = h2[i ^ 1];
+            if (std::fabs(back2[i].x - want.x) > 1e-6f * (1.f + std::fabs(want.x)) ||
+                std::fabs(back2[i].y - want.y) > 1e-6f * (1.f + std::fabs(want.y))) {
+                rc = SIM_EINVAL;
+                msg = "the dense-block sweep after the self-test is wrong";
+            }
+        }
+    }
     if (st) cudaStreamSynchronize(st);
     if (d_a) cudaFree(d_a);
     if (d_u) cudaFree(d_u);
+    if (d_a2) cudaFree(d_a2);
+    if (d_prog) cudaFree(d_prog);
     if (d_st) cudaFree(d_st);
     if (st) cudaStreamDestroy(st);
     if (!msg.empty()) return fail(nullptr, rc, msg);
@@ -450,7 +501,7 @@ static int execute(sim_t *s, const Plan &p, bool jit)
             for (const Term &t : o.terms) { tw.push_back(t.mask); tw.push_back(t.w); }
             if (tw.empty()) tw.assign(2, 0);
             off[i] = bl.add(tw.data(), tw.size() * 8);
-        } else if (o.kind == OPK_CHUNK || o.kind == OPK_DIAG) {
+        } else if (o.kind == OPK_CHUNK || o.kind == OPK_DIAG || o.kind == OPK_DENSE_CHUNK) {
             off[i] = bl.add(o.words.data(), o.words.size() * 4);
         }
     }
@@ -552,11 +603,15 @@ static int execute(sim_t *s, const Plan &p, bool jit)
         case OPK_TENSOR:
             e = launch_tensor(a, buf_ptr(s, o.buf_hi), o.n_hi, buf_ptr(s, o.buf_lo), o.n_lo, f64, s->stream);
             break;
+        case OPK_DENSE_CHUNK:
+            e = f64 ? cudaErrorInvalidValue
+                    : launch_dense_chunk(a, o.n, (const uint32_t *)cst, s->d_status, s->stream);
+            break;
         }
         if (e != cudaSuccess) return cuda_fail(s, e, "kernel launch");
         double amps = (double)((uint64_t)1 << o.n), sz = f64 ? 16.0 : 8.0;
         double by = (o.kind == OPK_TENSOR || o.kind == OPK_INIT_BASIS || fed) ? amps * sz : 2.0 * amps * sz;
-        prof_end(s, pe, (int)o.kind + (o.buf ? 8 : 0), by);
+        prof_end(s, pe, profile_kind(o.kind) + (o.buf ? 8 : 0), by);
     }
     if (s->prof_on) s->prof.h2d_bytes += bl.b.size();
     return SIM_OK;

@@ -67,6 +67,7 @@ enum OpKind {
     OPK_TENSOR = 5,      // tensor product of two sub-states (Algorithm 5, first branch)
     OPK_DENSE_TC = 6,    // dense 5-qubit block as a tensor-core GEMM
     OPK_PHASE_SMALL = 7, // fused diagonal on a register too small for the sweep kernels
+    OPK_DENSE_CHUNK = 8, // dense 5-qubit blocks inside a cache-blocked sweep (tensor cores)
 };
 
 // A chunk program: one cached chunk of C qubits passes through a sequence of
@@ -106,9 +107,15 @@ struct Op {
     ChunkProg prog;                // CHUNK
     int buf_lo = 0, buf_hi = 0, n_lo = 0, n_hi = 0;   // TENSOR: buf <- hi (x) lo
     bool fused = false;            // TENSOR: computed by the next op's loads, not launched
-    std::vector<uint32_t> words;   // CHUNK / DIAG: encoded device program
+    std::vector<uint32_t> words;   // CHUNK / DIAG / DENSE_CHUNK: encoded device program
     int precision = 0;             // DENSE_TC: SIM_DENSE_* arithmetic
+    std::vector<PGate> blocks;     // DENSE_CHUNK: the 5-qubit blocks, in order
+    int cq[16] = {0};              // DENSE_CHUNK: chunk qubits, ascending
 };
+
+// Profile slot (sim_profile index) of an op kind: a dense-block sweep counts
+// as a dense block, whether it holds one block or several.
+inline int profile_kind(int kind) { return kind == OPK_DENSE_CHUNK ? OPK_DENSE_TC : kind; }
 
 struct Plan {
     int n = 0;
@@ -123,6 +130,9 @@ struct Plan {
 bool make_plan(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_t ng,
                const sim_options &opt, Plan &plan, std::string &err);
 std::string plan_json(const Plan &p);
+// Device program of a cache-blocked dense-block sweep (dense_prog.h): chunk
+// qubits cq[0..11] ascending with qubits 0..3 first, 5-qubit blocks in order.
+std::vector<uint32_t> encode_dense_chunk(int n, const int *cq, const std::vector<PGate> &blocks);
 
 // Serving: ops of the one-CTA batch kernel (batch.h) for a small circuit --
 // the diagonal detector's fused phases and dense gates of <= 3 qubits.

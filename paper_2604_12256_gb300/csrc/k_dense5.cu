@@ -18,6 +18,7 @@
 
 #include "dfloat.h"
 #include "kernels.h"
+#include "tc_dev.cuh"
 
 namespace svs {
 
@@ -123,58 +124,6 @@ __global__ void __launch_bounds__(128) k_dense5_fma(typename D5T<R>::T2 *__restr
 }
 
 // ------------------------------------------------------------ tensor cores
-// Shared-memory operand layout: K-major, no swizzle.  A "core matrix" is 8
-// rows x 16 bytes (4 TF32), stored as 128 contiguous bytes; core matrices are
-// ordered with the row (M or N) direction fastest, so the row-direction step
-// (SBO) is 128 B and the K-direction step (LBO) is rows/8 * 128 B.
-__device__ __forceinline__ uint32_t kmajor_off(int row, int k, int rows)
-{
-    return (uint32_t)(((k >> 2) * (rows >> 3) + (row >> 3)) * 128 + (row & 7) * 16 + (k & 3) * 4);
-}
-
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;          // descriptor version for tcgen05
-    // base offset 0, lbo mode 0, layout type 0 (no swizzle)
-    return d;
-}
-
-__device__ __forceinline__ uint32_t tf32_of(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t phase)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(addr), "r"(phase)
-        : "memory");
-    return ok != 0;
-}
-
-// 32 consecutive TMEM columns of this warp's 32 lanes -> 32 registers
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&y)[32])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(y[0]), "=r"(y[1]), "=r"(y[2]), "=r"(y[3]), "=r"(y[4]), "=r"(y[5]), "=r"(y[6]), "=r"(y[7]),
-          "=r"(y[8]), "=r"(y[9]), "=r"(y[10]), "=r"(y[11]), "=r"(y[12]), "=r"(y[13]), "=r"(y[14]), "=r"(y[15]),
-          "=r"(y[16]), "=r"(y[17]), "=r"(y[18]), "=r"(y[19]), "=r"(y[20]), "=r"(y[21]), "=r"(y[22]),
-          "=r"(y[23]), "=r"(y[24]), "=r"(y[25]), "=r"(y[26]), "=r"(y[27]), "=r"(y[28]), "=r"(y[29]),
-          "=r"(y[30]), "=r"(y[31])
-        : "r"(taddr));
-}
-
 constexpr int kTcCols = 128;                  // columns per tile (MMA M)
 constexpr int kTmemCols = 64;                 // columns of one accumulator (MMA N)
 constexpr int kTmemAlloc = 128;               // two accumulators: hi.hi and the hi.lo + lo.hi corrections

@@ -138,6 +138,14 @@ cudaError_t launch_phase_small(void *a, int n, bool is_f64, const uint64_t *term
 // of the tensor-core kernel gave up.
 cudaError_t launch_dense5(void *a, int n, bool is_f64, int precision, const int *q, const void *U64, int *status,
                           cudaStream_t st);
+// Cache-blocked dense-block sweep (K6 inside K4, complex64, split-TF32 on the
+// tensor cores): the blocks of the device program `prog` (dense_prog.h, in
+// device memory, 16-byte aligned) applied chunk by chunk in one pass over the
+// 2^n state.  status: device int set to 1 when a bounded wait gave up.
+cudaError_t launch_dense_chunk(void *a, int n, const uint32_t *prog, int *status, cudaStream_t st);
+// Self-test only: the same kernel with its MMA issue suppressed.
+cudaError_t launch_dense_chunk_wait_selftest(void *a, int n, const uint32_t *prog, int *status, uint32_t wait_limit,
+                                             cudaStream_t st);
 // Self-test only: the tensor-core block kernel with its MMA issue suppressed,
 // so that its bounded waits (wait_limit polls each) run out; *status -> 1.
 cudaError_t launch_dense5_wait_selftest(void *a, int n, const void *U64, int *status, uint32_t wait_limit,

@@ -27,6 +27,7 @@
 #include <sstream>
 #include <unordered_map>
 
+#include "dense_prog.h"
 #include "internal.h"
 #include "program.h"
 
@@ -1275,6 +1276,13 @@ static void account(Plan &p)
             s.state_updates += (uint64_t)amps;
             s.flops += amps * 8.0 * 32;
             break;
+        case OPK_DENSE_CHUNK:
+            s.dense_ops += o.blocks.size();
+            if (o.buf == 0) s.sweeps++;
+            s.bytes += (uint64_t)(2 * amps * sz);
+            s.state_updates += (uint64_t)(amps * o.blocks.size());
+            s.flops += amps * 8.0 * 32 * o.blocks.size();
+            break;
         }
     }
 }
@@ -1396,6 +1404,155 @@ static void schedule_dense_blocks(const std::vector<PGate> &G, int n, int precis
     }
 }
 
+// TF32 operand rounding (the conversion the kernels use for their A operand,
+// cvt.rna: to nearest, ties away from zero, 10 stored mantissa bits): half a
+// unit of the 13 dropped bits added to the magnitude, then cleared.
+static uint32_t tf32_bits(float x)
+{
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return u;
+    return (u + 0x1000u) & 0xffffe000u;
+}
+
+static float float_of_bits(uint32_t u)
+{
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// Device program of a cache-blocked dense-block sweep (dense_prog.h): chunk
+// qubits, per block its target bits, row order and swizzled offsets, and its
+// 64 x 64 real embedding split into TF32 hi + lo, stacked as one 128-row MMA
+// operand (K-major core matrices of 8 rows x 4 elements, rows fastest).
+std::vector<uint32_t> encode_dense_chunk(int n, const int *cq, const std::vector<PGate> &blocks)
+{
+    using namespace dprog;
+    const int nb = (int)blocks.size();
+    std::vector<uint32_t> w((size_t)H_SIZE + (size_t)nb * kBlkWords, 0);
+    const size_t boff = (w.size() + 31) & ~(size_t)31;
+    w.resize(boff + (size_t)nb * kBImgWords, 0);
+    w[H_MAGIC] = kMagic;
+    w[H_N] = (uint32_t)n;
+    w[H_NBLK] = (uint32_t)nb;
+    w[H_BOFF] = (uint32_t)boff;
+    w[H_WORDS] = (uint32_t)w.size();
+    uint64_t cm = 0;
+    int cbit[64];
+    for (int i = 0; i < 64; i++) cbit[i] = -1;
+    for (int i = 0; i < kC; i++) {
+        w[H_QIN + i] = (uint32_t)cq[i];
+        cm |= 1ull << cq[i];
+        cbit[cq[i]] = i;
+    }
+    const uint64_t fm = (n >= 64 ? ~0ull : (1ull << n) - 1) & ~cm;
+    w[H_FREE_LO] = (uint32_t)fm;
+    w[H_FREE_HI] = (uint32_t)(fm >> 32);
+    for (int b = 0; b < nb; b++) {
+        const PGate &g = blocks[(size_t)b];
+        uint32_t *r = &w[(size_t)H_SIZE + (size_t)b * kBlkWords];
+        int T[5];
+        uint32_t tmask = 0;
+        for (int i = 0; i < 5; i++) {
+            T[i] = cbit[g.q[i]];
+            tmask |= 1u << T[i];
+        }
+        r[B_TMASK] = tmask;
+        // row bits: lanes 0..3 of a warp take chunk bits of distinct residues
+        // mod 4 where the block leaves them (conflict-free half-warp accesses
+        // under the swizzle), then the remaining bits in ascending order
+        int rows[7], nr = 0;
+        uint32_t taken = 0, resid = 0;
+        for (int i = 0; i < kC && nr < 4; i++)
+            if (!((tmask >> i) & 1) && !((resid >> (i & 3)) & 1)) {
+                rows[nr++] = i;
+                taken |= 1u << i;
+                resid |= 1u << (i & 3);
+            }
+        for (int i = 0; i < kC; i++)
+            if (!((tmask >> i) & 1) && !((taken >> i) & 1)) rows[nr++] = i;
+        for (int i = 0; i < 7; i++) r[B_ROWSLOT + i] = slot(1u << rows[i]);
+        for (int j = 0; j < 32; j++) {
+            uint32_t x = 0;
+            for (int i = 0; i < 5; i++)
+                if ((j >> i) & 1) x |= 1u << T[i];
+            r[B_TOFF + j] = slot(x);
+        }
+        // B[nn][kk]: output real nn (re 0..31, im 32..63) from input real kk
+        uint32_t *bi = &w[boff + (size_t)b * kBImgWords];
+        for (int nn = 0; nn < 64; nn++)
+            for (int kk = 0; kk < 64; kk++) {
+                const cd u = g.M[(size_t)(nn & 31) * 32 + (kk & 31)];
+                const double v = nn < 32 ? (kk < 32 ? u.real() : -u.imag()) : (kk < 32 ? u.imag() : u.real());
+                const uint32_t hi = tf32_bits((float)v);
+                const uint32_t lo = tf32_bits((float)(v - (double)float_of_bits(hi)));
+                // one operand of 128 rows: hi in rows 0..63, lo in rows 64..127
+                auto word = [](int row, int k) {
+                    return (size_t)(((k >> 2) * 16 + (row >> 3)) * 32 + (row & 7) * 4 + (k & 3));
+                };
+                bi[word(nn, kk)] = hi;
+                bi[word(64 + nn, kk)] = lo;
+            }
+    }
+    return w;
+}
+
+// Cache blocking of dense blocks (K6 inside K4): the 5-qubit blocks of a run
+// share one sweep while their qubits, with qubits 0..3, fit a 2^12-amplitude
+// chunk.  Greedy in dependency order like the block search itself: a block
+// joins the open sweep unless it shares a qubit with a block left out before
+// it (blocks on disjoint qubits commute).
+static void group_dense_chunks(Plan &plan, size_t first, int n)
+{
+    using dprog::kC;
+    std::vector<Op> in;
+    for (size_t i = first; i < plan.ops.size(); i++) in.push_back(std::move(plan.ops[i]));
+    plan.ops.resize(first);
+    size_t i = 0;
+    while (i < in.size()) {
+        if (in[i].kind != OPK_DENSE_TC) {
+            plan.ops.push_back(std::move(in[i]));
+            i++;
+            continue;
+        }
+        size_t j = i;
+        while (j < in.size() && in[j].kind == OPK_DENSE_TC) j++;
+        std::vector<char> done(j - i, 0);
+        size_t left = j - i, head = 0;
+        while (left) {
+            while (done[head]) head++;
+            Op o;
+            o.kind = OPK_DENSE_CHUNK;
+            o.buf = in[i].buf;
+            o.n = n;
+            o.precision = SIM_DENSE_SPLIT_TF32;
+            uint64_t S = 0xF, blocked = 0;
+            for (size_t k = head; k < j - i && (int)o.blocks.size() < dprog::kMaxBlocks; k++) {
+                if (done[k]) continue;
+                const uint64_t m = in[i + k].gate.qmask;
+                if (m & blocked) {
+                    blocked |= m;
+                } else if (popc(S | m) <= kC) {
+                    S |= m;
+                    o.blocks.push_back(std::move(in[i + k].gate));
+                    done[k] = 1;
+                    left--;
+                } else {
+                    blocked |= m;
+                }
+            }
+            for (int p = 0; p < n && popc(S) < kC; p++) S |= 1ull << p;
+            int c = 0;
+            for (int p = 0; p < n; p++)
+                if ((S >> p) & 1) o.cq[c++] = p;
+            o.words = encode_dense_chunk(n, o.cq, o.blocks);
+            plan.ops.push_back(std::move(o));
+        }
+        i = j;
+    }
+}
+
 static void schedule(const std::vector<PGate> &G, int n, const sim_options &opt, sim_dtype dt, int buf, Plan &plan)
 {
     if ((opt.flags & SIM_F_TC) && n >= 5) {
@@ -1404,7 +1561,12 @@ static void schedule(const std::vector<PGate> &G, int n, const sim_options &opt,
         int prec = opt.dense_precision;
         if (dt == SIM_C64) prec = prec == SIM_DENSE_SPLIT_TF32 ? SIM_DENSE_SPLIT_TF32 : SIM_DENSE_FP32;
         else prec = prec == SIM_DENSE_FP64 ? SIM_DENSE_FP64 : SIM_DENSE_DOUBLE_FLOAT;
+        const size_t first = plan.ops.size();
         schedule_dense_blocks(G, n, prec, buf, plan);
+        // split-TF32 blocks of a state of >= 2^12 amplitudes: cache-blocked,
+        // several blocks per sweep (without SIM_F_BLOCK: one sweep per block)
+        if (prec == SIM_DENSE_SPLIT_TF32 && dt == SIM_C64 && (opt.flags & SIM_F_BLOCK) && n >= dprog::kC)
+            group_dense_chunks(plan, first, n);
         return;
     }
     int C = 0, RB = 0;
@@ -1840,6 +2002,47 @@ static std::vector<PGate> euler_split(const std::vector<PGate> &G, int n, uint64
 // sweep, so often fewer sweeps) by planning both.  The choice is kept per
 // circuit structure (gate kinds and qubits, options; not the angles), so
 // repeated applies of a structure plan once.
+// The checks the dense-block sweep kernel relies on: header, chunk qubits
+// (qubits 0..3 first, ascending, below n), five distinct target bits per
+// block, row bits and offsets that cover the chunk exactly once, B images
+// inside the program and 16-byte aligned.
+static bool validate_dense_chunk(const std::vector<uint32_t> &w, int n, std::string &err)
+{
+    using namespace dprog;
+    auto bad = [&](const char *m) { err = std::string("internal: invalid dense-block program: ") + m; return false; };
+    if (w.size() < (size_t)H_SIZE || w[H_MAGIC] != kMagic || w[H_WORDS] != w.size()) return bad("header");
+    if ((int)w[H_N] != n || n < kC || n > 40) return bad("n");
+    const size_t nb = w[H_NBLK], boff = w[H_BOFF];
+    if (nb < 1 || nb > (size_t)kMaxBlocks) return bad("block count");
+    if (boff % 32 != 0 || boff < (size_t)H_SIZE + nb * kBlkWords || boff + nb * kBImgWords != w.size())
+        return bad("B images");
+    uint64_t cm = 0;
+    for (int i = 0; i < kC; i++) {
+        const uint32_t q = w[H_QIN + i];
+        if ((int)q >= n || (i < 4 && q != (uint32_t)i) || (i > 0 && q <= w[H_QIN + i - 1])) return bad("chunk qubits");
+        cm |= 1ull << q;
+    }
+    const uint64_t fm = (uint64_t)w[H_FREE_LO] | ((uint64_t)w[H_FREE_HI] << 32);
+    if (fm != (((1ull << n) - 1) & ~cm)) return bad("free mask");
+    std::vector<char> seen(1u << kC);
+    for (size_t b = 0; b < nb; b++) {
+        const uint32_t *r = &w[H_SIZE + b * kBlkWords];
+        if (popc(r[B_TMASK]) != 5 || (r[B_TMASK] >> kC) != 0) return bad("targets");
+        std::fill(seen.begin(), seen.end(), 0);
+        for (uint32_t t = 0; t < (uint32_t)kCols; t++) {
+            uint32_t rb = 0;
+            for (int i = 0; i < 7; i++)
+                if ((t >> i) & 1) rb ^= r[B_ROWSLOT + i];
+            for (int j = 0; j < 32; j++) {
+                const uint32_t sl = rb ^ r[B_TOFF + j];
+                if (sl >= (1u << kC) || seen[sl]) return bad("chunk cover");
+                seen[sl] = 1;
+            }
+        }
+    }
+    return true;
+}
+
 static bool auto_chunk_shape(int n, sim_dtype dt, const sim_options &o)
 {
     return dt == SIM_C64 && n >= 16 && (o.flags & SIM_F_JIT) && (o.flags & SIM_F_BLOCK) && !(o.flags & SIM_F_TC) &&
@@ -1894,7 +2097,7 @@ static size_t full_sweeps(const Plan &p)
     size_t k = 0;
     for (const Op &o : p.ops)
         if (o.buf == 0 && (o.kind == OPK_GATE || o.kind == OPK_GATE_DIAG || o.kind == OPK_DIAG || o.kind == OPK_CHUNK ||
-                           o.kind == OPK_DENSE_TC))
+                           o.kind == OPK_DENSE_TC || o.kind == OPK_DENSE_CHUNK))
             k++;
     return k;
 }
@@ -1926,6 +2129,34 @@ bool make_plan(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_
         uint64_t nsplit = 0;
         G = euler_split(G, n, nsplit);
     }
+    // cache-blocked dense blocks: the blocks absorb diagonal gates anyway, and
+    // the detector's fused diagonals can split runs of blocks; plan with and
+    // without it and keep the cheaper (a sweep costs about as much as 2.5
+    // blocks of tensor-core work on this GPU)
+    const bool dense_blocked = (opt.flags & SIM_F_TC) && (opt.flags & SIM_F_BLOCK) && dt == SIM_C64 &&
+                               opt.dense_precision == SIM_DENSE_SPLIT_TF32 && n >= dprog::kC;
+    if ((opt.flags & SIM_F_DIAG) && dense_blocked) {
+        uint64_t absorbed = 0;
+        std::vector<PGate> Gd = diagonal_detector(G, opt.max_diag_qubits, absorbed);
+        Plan pd = plan, pn = plan;
+        schedule(Gd, n, opt, dt, 0, pd);
+        schedule(G, n, opt, dt, 0, pn);
+        auto cost = [](const Plan &p) {
+            size_t sw = 0, bl = 0;
+            for (const Op &o : p.ops) {
+                if (o.buf != 0) continue;
+                if (o.kind == OPK_DENSE_CHUNK) { sw++; bl += o.blocks.size(); }
+                else if (o.kind != OPK_INIT_BASIS && o.kind != OPK_TENSOR) { sw++; bl++; }
+            }
+            return 5.0 * (double)sw + 2.0 * (double)bl;
+        };
+        if (cost(pd) <= cost(pn)) {
+            plan = std::move(pd);
+            plan.stats.diag_fused += absorbed;
+        } else {
+            plan = std::move(pn);
+        }
+    } else {
     if (opt.flags & SIM_F_DIAG) {
         uint64_t absorbed = 0;
         G = diagonal_detector(G, opt.max_diag_qubits, absorbed);
@@ -1957,6 +2188,7 @@ bool make_plan(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_
     } else {
         schedule(G, n, opt, dt, 0, plan);
     }
+    }
     finalize_words(plan);
     // a tensor product that only feeds the next sweep of the same buffer is
     // computed by that sweep's loads: one write-only pass instead of a write
@@ -1975,6 +2207,7 @@ bool make_plan(int n, sim_dtype dt, uint64_t basis, const sim_gate *gates, size_
             err = "internal: bad dense gate op";
             return false;
         }
+        if (o.kind == OPK_DENSE_CHUNK && !validate_dense_chunk(o.words, o.n, err)) return false;
     }
     account(plan);
     plan.stats.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -2094,6 +2327,20 @@ std::string plan_json(const Plan &p)
             for (int i = 0; i < o.gate.k; i++) os << (i ? "," : "") << o.gate.q[i];
             os << "],\"matrix\":";
             jmat(os, o.gate.M);
+            break;
+        case OPK_DENSE_CHUNK:
+            os << "\"op\":\"dense_chunk\",\"qin\":[";
+            for (int i = 0; i < dprog::kC; i++) os << (i ? "," : "") << o.cq[i];
+            os << "],\"words\":" << o.words.size() << ",\"blocks\":[";
+            for (size_t b = 0; b < o.blocks.size(); b++) {
+                const PGate &g = o.blocks[b];
+                os << (b ? "," : "") << "{\"qubits\":[";
+                for (int i = 0; i < g.k; i++) os << (i ? "," : "") << g.q[i];
+                os << "],\"matrix\":";
+                jmat(os, g.M);
+                os << "}";
+            }
+            os << "]";
             break;
         }
         os << "}";

@@ -89,6 +89,13 @@ def interpret(plan, init_state=None, basis=0):
                     else:
                         a = a * phase_factors(nb, x["phase"], wbits)
             a = permute(a, nb, op["qin"], op["qout"])
+        elif kind == "dense_chunk":
+            # a cache-blocked sweep of dense blocks: each block is a matrix on
+            # its qubits, applied in order (the chunk changes no labels)
+            for blk in op["blocks"]:
+                q = blk["qubits"]
+                dim = 1 << len(q)
+                a = apply_matrix(a, nb, q, _matrix(blk["matrix"]).reshape(dim, dim))
         elif kind == "tensor":
             a = np.kron(bufs[op["hi"]], bufs[op["lo"]])
         else:

@@ -139,6 +139,44 @@ def test_dense_block_plans_are_exact(maker):
     np.testing.assert_allclose(interpret(p, basis=c.basis), oracle.run(c), atol=1e-12)
 
 
+@pytest.mark.parametrize("maker", [lambda: C.layered(12, 6, 1), lambda: C.layered(16, 8, 2),
+                                   lambda: C.random_mixed(14, 150, 3, max_k=3), lambda: C.qft(13, 2),
+                                   lambda: C.diag_heavy(15, 120, 4)],
+                         ids=["layered12", "layered16", "mixed14", "qft13", "diag15"])
+def test_cache_blocked_dense_plans_are_exact(maker):
+    """Complex64 split-TF32 blocks with cache blocking: runs of 5-qubit
+    blocks share sweeps (dense_chunk ops) whose chunk holds qubits 0..3 and
+    every block's qubits; the plan is exact and has no more sweeps than one
+    sweep per block."""
+    c = maker()
+    base = S.SIM_F_TC | S.SIM_F_DIAG
+    p = S.plan_json(c.n, c.gates, S.SIM_C64, c.basis, S.default_options(flags=base | S.SIM_F_BLOCK))
+    sep = S.plan_json(c.n, c.gates, S.SIM_C64, c.basis, S.default_options(flags=base))
+    chunks = [op for op in p["ops"] if op["op"] == "dense_chunk"]
+    assert chunks and not any(op["op"] == "gate" and len(op["qubits"]) == 5 for op in p["ops"])
+    for op in chunks:
+        assert op["qin"][:4] == [0, 1, 2, 3] and op["qin"] == sorted(set(op["qin"])) and len(op["qin"]) == 12
+        for blk in op["blocks"]:
+            assert len(blk["qubits"]) == 5 and set(blk["qubits"]) <= set(op["qin"])
+    # the blocked plan keeps the diagonal detector's output only when that is
+    # cheaper, so its block count may differ from the one-sweep-per-block plan
+    assert sum(len(op["blocks"]) for op in chunks) == p["stats"]["dense_ops"] <= sep["stats"]["dense_ops"] + 4
+    assert p["stats"]["sweeps"] <= sep["stats"]["sweeps"]
+    np.testing.assert_allclose(interpret(p, basis=c.basis), oracle.run(c), atol=1e-12)
+
+
+def test_cache_blocked_dense_needs_a_full_chunk():
+    """Below 12 qubits, complex128 states and the FP32 arm keep one sweep per
+    block."""
+    c = C.layered(11, 4, 1)
+    opt = S.default_options(flags=S.SIM_F_TC | S.SIM_F_DIAG | S.SIM_F_BLOCK)
+    assert not any(op["op"] == "dense_chunk" for op in S.plan_json(11, c.gates, S.SIM_C64, 0, opt)["ops"])
+    c = C.layered(14, 4, 1)
+    assert not any(op["op"] == "dense_chunk" for op in S.plan_json(14, c.gates, S.SIM_C128, 0, opt)["ops"])
+    opt.dense_precision = S.SIM_DENSE_FP32
+    assert not any(op["op"] == "dense_chunk" for op in S.plan_json(14, c.gates, S.SIM_C64, 0, opt)["ops"])
+
+
 def test_swap_network_is_a_relabelling():
     """A qubit permutation given as SWAP gates (Eq. 4) costs no extra sweep
     per SWAP: the chunk stores apply it as a relabelling, a few sweeps for a
