@@ -6,19 +6,20 @@
 //   4. gate-block search (GBSA mode 0, Algorithm 2's cache blocking) fused
 //      with register-stage scheduling, lazy placement of diagonal phases and
 //      cost-based gate fusion (GBSA mode 1);
-//   5. encoding of each block as a device program (program.h).
+//   5. encoding of each block as a device program (program.h), and of runs
+//      of dense 5-qubit blocks as cache-blocked tensor-core sweeps
+//      (dense_prog.h).
 //
-// Readings of Algorithm 8 (the pseudocode leaves these open):
-//   (i)   a lone diagonal gate (diagSize == 1) is emitted unchanged;
-//   (ii)  a non-diagonal gate goes to uList when it overlaps depSet OR a
-//         qubit already held by uList (else it would jump ahead of that gate);
-//   (iii) the D bound of Section 4.1 stops the fusion (a break) when the fused
-//         qubit set would exceed D (D = 0: unbounded, the phase-polynomial
-//         form needs no table);
-//   (iv)  a diagonal gate that meets a stopped qubit ends the group and starts
-//         the next one.
+// Readings of the diagonal detector (Algorithm 8), restated from the
+// commutation rule it rests on (see diagonal_detector):
+//   (i)   a group of one diagonal gate is emitted unchanged;
+//   (ii)  no gate passes a gate it does not commute with;
+//   (iii) the D bound of Section 4.1 caps a group's qubit set (D = 0:
+//         unbounded, the phase-polynomial form needs no table);
+//   (iv)  a diagonal gate joins the oldest group it can reach.
 // GBSA itself is unspecified (Section 4.2 builds on prior simulators); ours is
-// a greedy scan in dependency order, see schedule_blocked().
+// a greedy scan in dependency order (Scheduler, and group_dense_chunks for
+// dense blocks).
 #include <algorithm>
 #include <chrono>
 #include <cstring>
