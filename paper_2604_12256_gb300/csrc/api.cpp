@@ -543,7 +543,8 @@ static int execute(sim_t *s, const Plan &p, bool jit)
             const Op &o = p.ops[i];
             if (o.kind == OPK_CHUNK && jit_supported(f64, o.prog.C, o.prog.RB)) {
                 jit_of[i] = (long)progs.size();
-                progs.push_back({&o.words, JIT_CHUNK});
+                const bool fed = i > 0 && p.ops[i - 1].fused;
+                progs.push_back({&o.words, fed ? JIT_CHUNK_FED : JIT_CHUNK});
             } else if (o.kind == OPK_DIAG && jit_supported_diag(f64, (int)o.words[prog::H_RB])) {
                 jit_of[i] = (long)progs.size();
                 progs.push_back({&o.words, JIT_DIAG});
@@ -872,9 +873,11 @@ static int jit_plan_sources(int n, sim_dtype dt, uint64_t basis, const sim_gate 
     try {
         if (!make_plan(n, dt, basis, gates, ng, o, p, err)) return fail(nullptr, SIM_EINVAL, err);
         int np = 0;
-        for (const Op &op : p.ops) {
+        for (size_t i = 0; i < p.ops.size(); i++) {
+            const Op &op = p.ops[i];
             int kind = -1;
-            if (op.kind == OPK_CHUNK && jit_supported(dt == SIM_C128, op.prog.C, op.prog.RB)) kind = JIT_CHUNK;
+            if (op.kind == OPK_CHUNK && jit_supported(dt == SIM_C128, op.prog.C, op.prog.RB))
+                kind = i > 0 && p.ops[i - 1].fused ? JIT_CHUNK_FED : JIT_CHUNK;
             if (op.kind == OPK_DIAG && jit_supported_diag(dt == SIM_C128, (int)op.words[prog::H_RB])) kind = JIT_DIAG;
             if (kind < 0) continue;
             std::string src;

@@ -792,9 +792,12 @@ __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, 
     };
     if (blockIdx.x < nchunks) cta_accum<R, T>(prog, cta_buf, chunk_base(blockIdx.x), tid);
     __syncthreads();
+    // Ops::kFed: 1 the sweep's input is a merge-booster product (src.hi set),
+    // 0 it is the state, -1 decided by src.hi at run time (the interpreter)
+    const bool fed = Ops::kFed < 0 ? src.hi != nullptr : Ops::kFed > 0;
     // coalesced loads of one chunk's amplitude pairs into registers
     auto load_regs = [&](T2 (&dst)[NR], uint64_t b) SVS_INLINE_LAMBDA {
-        if (src.hi) {
+        if (fed) {
 #pragma unroll
             for (int it = 0; it < NR / 2; it++) {
                 const uint64_t g = b | g_tid | s_git[it];
@@ -823,7 +826,7 @@ __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, 
 #pragma unroll
         for (int m = 0; m < NR; m++) {
             const uint64_t g = xb | Ops::roff(s, m);
-            if (src.hi) {
+            if (fed) {
                 dst[m] = to_reg(tensor_amp(src, g));
             } else if constexpr (sizeof(R) == 4) {
                 if (Ops::paired(s)) {   // m, m + 1 adjacent: one 16-byte load
@@ -860,12 +863,13 @@ __device__ __forceinline__ void chunk_sweep(typename CT<R>::G2 *__restrict__ a, 
     // amplitudes are loaded into registers (nx) as soon as this chunk's first
     // stage has taken its own, so a whole chunk of loads stays in flight
     // through the register stages and the store (64 registers more per
-    // thread: two CTAs per SM).  Sweeps fed by a merge-booster product compute
-    // on their loads and do not load ahead.  The interpreter has no register
-    // double buffer: it fits in 80 registers and three CTAs per SM, whose
-    // loads overlap each other's stages.
+    // thread: two CTAs per SM).  A sweep fed by a merge-booster product runs a
+    // kernel of its own (Ops::kFed = 1) that computes the next chunk's
+    // products ahead the same way.  The interpreter has no register double
+    // buffer: it fits in 80 registers and three CTAs per SM, whose loads
+    // overlap each other's stages.
     constexpr bool kPF = Ops::kPrefetch;
-    const bool pf_on = kPF && !src.hi;
+    const bool pf_on = kPF;
     T2 nx[kPF ? NR : 1];
     int64_t ch = blockIdx.x;
     uint64_t base = chunk_base(ch);
@@ -1005,6 +1009,7 @@ struct InterpOps {
     using Params = NoParams;
     static constexpr int kStages = 0;
     static constexpr bool kPrefetch = false;
+    static constexpr int kFed = -1;   // fed by a product or not: decided at run time
     static constexpr bool kDirectFirst = false, kDirectLast = false;
     static __device__ __forceinline__ uint64_t roff(int, int) { return 0; }
     static __device__ __forceinline__ bool paired(int) { return false; }

@@ -445,6 +445,8 @@ bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std:
     std::ostringstream o;
     o << "    static constexpr int kStages = " << ns << ";\n";
     o << "    static constexpr bool kPrefetch = true;\n";
+    // fed by a merge-booster product or not, fixed per kernel
+    o << "    static constexpr int kFed = " << (kind == JIT_CHUNK_FED ? 1 : 0) << ";\n";
     // direct boundary stages: their register offsets in HBM
     const uint32_t direct = w[H_DIRECT];
     o << "    static constexpr bool kDirectFirst = " << ((direct & DIRECT_FIRST) ? "true" : "false")
@@ -862,6 +864,10 @@ cudaError_t launch_chunk_jit(const JitHandle &h, void *a, int n, const std::vect
                              size_t smem, TensorSrc src, cudaStream_t st)
 {
     const int C = (int)w[prog::H_C], RB = (int)w[prog::H_RB];
+    // a kernel built for a fed sweep reads only the product's factors, one
+    // built for a plain sweep only the state
+    if (h.k && (h.k->kind == JIT_CHUNK_FED) != (src.hi != nullptr)) return cudaErrorInvalidValue;
+    if (src.hi && (src.n_lo < 0 || src.n_lo > n || !src.lo)) return cudaErrorInvalidValue;
     return launch_jit(h, a, n, prog, smem, src, st, 1 << (C - RB), C);
 }
 

@@ -101,10 +101,12 @@ cudaError_t launch_chunk(void *a, int n, bool is_f64, int C, int RB, const uint3
 // launch_diag_sweep's arguments and results.  Kernels are keyed by their
 // generated source, which holds the program's structure only (its numbers
 // are parameters), and kept at most jit_set_cache_limit() at a time.
-enum { JIT_CHUNK = 0, JIT_DIAG = 1 };
+// JIT_CHUNK_FED: a chunk program whose sweep computes its input from a fused
+// merge-booster product (it must be launched with that product's factors).
+enum { JIT_CHUNK = 0, JIT_DIAG = 1, JIT_CHUNK_FED = 2 };
 struct JitProg {
     const std::vector<uint32_t> *w;   // host program words
-    int kind;                         // JIT_CHUNK or JIT_DIAG
+    int kind;                         // JIT_CHUNK, JIT_DIAG or JIT_CHUNK_FED
 };
 struct JitKernel;
 struct JitHandle {
