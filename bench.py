@@ -42,9 +42,9 @@ WORKLOAD = "28-qubit diagonal-heavy gate-level stream (500 gates, 80% RZ/CP/RZZ,
 # A sweep's traffic grows with the amplitudes it processes, so a capture on a
 # smaller state scales to the full one (profiles/ has the captures).
 TRAFFIC_PER_AMP = {
-    # profiles/svs_chunk_jit_diagheavy_25q.md: 477.19 MB per 2^25-amplitude sweep
+    # profiles/svs_chunk_jit_diagheavy_25q.md: 477.10 MB per 2^25-amplitude sweep
     # (the specialised kernel: keyed by its device templates and generator)
-    ("diag-heavy", "chunk-jit", "6054a1651d667797596900ce8ad4b7590004329bf6d837cfade35485f886521e"): 477.19e6 / 2 ** 25,
+    ("diag-heavy", "chunk-jit", "1b4f4a03973c98809a91fc71c554d608ae040372d49c9921a0ca0b30153cffe7"): 477.10e6 / 2 ** 25,
     # profiles/k_chunk_diagheavy_25q.md: 476.05 MB per 2^25-amplitude sweep (interpreter)
     ("diag-heavy", "chunk", "8f96366b3d7184491700fbf33588aba4d28412cc874eee7e00ed69b7789963a2"): 476.05e6 / 2 ** 25,
     # profiles/k_dense5_tc_layered_26q.md: 1011.84 MB per 2^26-amplitude block sweep
@@ -153,6 +153,7 @@ def _tf32_peak(sustained=True):
             return d[key] * TF32_PER_BF16, f"measured {key} x {TF32_PER_BF16:.3f} (nominal TF32/BF16)"
     return (1700.0 if sustained else 1900.0) * TF32_PER_BF16, "fallback bf16 x nominal TF32/BF16"
 DF_FLOPS_PER_AMP = 2 * 64 * 15 + 2 * 3                 # double-float complex128 dense block
+DF_OPS_PER_FLOP = 7.5                                  # FP32 operations per double-float flop (15 per multiply-add)
 
 
 def _redraw(c, seed):
@@ -521,6 +522,17 @@ def run_gpu(args, rank, world, dist):
         roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    elif kind == "chunk" and dt == S.SIM_C128:
+        # double-float chunk sweeps are bound by FP32 issue, not HBM: the plan's
+        # flops (8 per complex multiply-add of a gate, 6 per phase product) at
+        # 7.5 FP32 operations each (a double-float multiply-add issues about 15)
+        achieved = plan["flops"] * DF_OPS_PER_FLOP * args.steps / (kp["ms"] / 1e3) / 1e12
+        gbs = bytes_per_launch / (avg_ms / 1e3) / 1e9
+        roof = {"bound": "alu", "kernel": kname + ", double-float", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "flop_per_amp": plan["flops"] / amps, "fp32_ops_per_flop": DF_OPS_PER_FLOP,
+                "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak}}
     elif kind == "dense" and fused_dense:
         # several blocks per sweep: the tensor pipe (three TF32 products of
         # 64 x 64 per 32 amplitudes and block) against the HBM round trip
@@ -597,9 +609,13 @@ def run_families(args, rank, world, dist):
     buf = torch.empty(2 << n, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     sim = S.Sim(n, S.SIM_C64, dev_buf=buf.data_ptr(), nbytes=buf.numel() * 4, stream=stream.cuda_stream)
+    # interpreter kernels, then the kernels specialised to each sweep's
+    # structure (compiled in the warm-up runs)
     configs = {"naive": S.default_options(flags=0),
                "ours": S.default_options(flags=S.SIM_F_DIAG | S.SIM_F_BLOCK | S.SIM_F_FUSE),
-               "ours_b": S.default_options()}
+               "ours_b": S.default_options(),
+               "ours_jit": S.default_options(flags=S.SIM_F_DIAG | S.SIM_F_BLOCK | S.SIM_F_FUSE | S.SIM_F_JIT),
+               "ours_b_jit": S.default_options(flags=S.default_options().flags | S.SIM_F_JIT)}
     clocks = Clocks(dev)
     clocks.start()
     out = {}
@@ -626,6 +642,8 @@ def run_families(args, rank, world, dist):
             row[key] = {"ms": ms, "ms_per_gate": ms / len(c.gates), "sweeps": st["sweeps"], "ops": st["ops"]}
         row["speedup_ours_vs_naive"] = row["naive"]["ms"] / row["ours"]["ms"]
         row["speedup_booster"] = row["ours"]["ms"] / row["ours_b"]["ms"]
+        row["speedup_booster_jit"] = row["ours_jit"]["ms"] / row["ours_b_jit"]["ms"]
+        row["speedup_jit_vs_naive"] = row["naive"]["ms"] / row["ours_b_jit"]["ms"]
         out[fam] = row
     clk = clocks.stop()
     sim.close()
