@@ -119,6 +119,20 @@ struct PBlock {
         return "__uint_as_float(" + u(b) + ")";
     }
     std::string fbits(uint32_t bits) { return "__uint_as_float(" + u(bits) + ")"; }
+    // a constant factor as the two packed operands (re, re), (-im, im) of the
+    // f32x2 complex product, 8-byte aligned in the block
+    std::string pk(float re, float im)
+    {
+        if (w.size() & 1) w.push_back(0);
+        const size_t k = w.size();
+        const float q[4] = {re, re, -im, im};
+        for (float x : q) {
+            uint32_t b;
+            std::memcpy(&b, &x, 4);
+            w.push_back(b);
+        }
+        return "*(const u64 *)&P.w[" + std::to_string(k) + "], *(const u64 *)&P.w[" + std::to_string(k + 2) + "]";
+    }
 };
 
 constexpr const char *kKernelName = "svs_chunk_jit";
@@ -190,7 +204,7 @@ Fac fac_mul(std::ostringstream &o, PBlock &P, const Fac &a, const Fac &b, const 
 // register bits and other bits) of a complex64 program: the sums it needs,
 // one sin/cos per run-time factor, the product table over the register bits
 // that carry a phase, and one complex product per amplitude whose factor is
-// not exactly one.  `scaled`: the sweep's product of scalars (`scale`)
+// not exactly one (packed f32x2: cmul_f, or cmul_pk for a constant).  `scaled`: the sweep's product of scalars (`scale`)
 // multiplies this segment's base factor.
 void gen_segment(std::ostringstream &o, PBlock &P, const std::vector<uint32_t> &w, size_t body,
                  const std::vector<SlotSrc> &slots, int RB, int TB, int T, int SCP, bool scaled, long double scale)
@@ -298,7 +312,12 @@ void gen_segment(std::ostringstream &o, PBlock &P, const std::vector<uint32_t> &
             c.im = ctab[2 * m + 1];
             f = fac_mul(o, P, f, c, "g" + std::to_string(m));
         }
-        if (f.kind != Fac::ONE) o << "                v[" << m << "] = cmul(v[" << m << "], " << fac_expr(P, f) << ");\n";
+        // the amplitude's product in packed form (cmul_f, cmul_pk): a
+        // constant factor comes as its two packed operands
+        if (f.kind == Fac::CONST)
+            o << "                v[" << m << "] = cmul_pk(v[" << m << "], " << P.pk((float)f.re, (float)f.im) << ");\n";
+        else if (f.kind == Fac::VAR)
+            o << "                v[" << m << "] = cmul_f(v[" << m << "], " << f.var << ");\n";
     }
     o << "            }\n";
 }
@@ -379,7 +398,7 @@ std::vector<SlotSrc> read_slots(const std::vector<uint32_t> &w, int RB, int SCP)
     return slots;
 }
 
-const char *kParamStruct = "struct JP { uint32_t w[";
+const char *kParamStruct = "struct __align__(8) JP { uint32_t w[";
 
 }  // namespace
 
@@ -407,6 +426,7 @@ static bool jit_source_diag(const std::vector<uint32_t> &w, std::string &src, st
     else
         gen_segment(g, P, w, body, slots, RB, TB, 128, SCP, false, 1.0L);
     if (P.w.empty()) P.w.push_back(0);
+    if (P.w.size() & 1) P.w.push_back(0);   // the block is 8-byte aligned: whole 8-byte units
     std::ostringstream o;
     o << "#include \"chunk_dev.cuh\"\nnamespace svs {\n" << kParamStruct << P.w.size() << "]; };\n"
       << "struct JDiag {\n    using Params = JP;\n"
@@ -576,6 +596,7 @@ bool jit_source(const std::vector<uint32_t> &w, int kind, std::string &src, std:
       << C << ", " << RB << ", svs::JOps>(a, gprog, n, src, P);\n}\n";
     if (P.w.empty()) P.w.push_back(0);
     std::ostringstream full;
+    if (P.w.size() & 1) P.w.push_back(0);   // the block is 8-byte aligned: whole 8-byte units
     full << "#include \"chunk_dev.cuh\"\nnamespace svs {\n" << kParamStruct << P.w.size() << "]; };\n"
          << "struct JOps {\n    using Params = JP;\n" << o.str();
     src = full.str();
