@@ -310,6 +310,15 @@ void gen_segment(std::ostringstream &o, PBlock &P, const std::vector<uint32_t> &
             c.kind = Fac::CONST;
             c.re = ctab[2 * m];   // the program's float factor, as the interpreter multiplies
             c.im = ctab[2 * m + 1];
+            if (f.kind == Fac::VAR) {
+                // two packed products (the constant's, then the table entry's,
+                // which other amplitudes share) instead of a scalar product of
+                // the two factors that would then be packed for this one use
+                o << "                v[" << m << "] = cmul_pk(v[" << m << "], " << P.pk((float)c.re, (float)c.im)
+                  << ");\n";
+                o << "                v[" << m << "] = cmul_f(v[" << m << "], " << f.var << ");\n";
+                continue;
+            }
             f = fac_mul(o, P, f, c, "g" + std::to_string(m));
         }
         // the amplitude's product in packed form (cmul_f, cmul_pk): a

@@ -57,3 +57,31 @@ def test_sources_hold_structure_only(maker):
     assert "specialised sweep" in a and "P.w[" in a
     for seed in (101, 102):
         assert S.jit_sources(c.n, _redraw(c, seed).gates, S.SIM_C64, c.basis, opt) == a
+
+
+@pytest.mark.parametrize("maker", [lambda: C.diag_heavy(28, 500, 1), lambda: C.layered(26, 20, 0),
+                                   lambda: C.qft(24, 2), lambda: C.rzz_full(14, 3)],
+                         ids=["diag_heavy28", "layered26", "qft24", "rzz14"])
+def test_parameter_blocks_hold_aligned_packed_constants(maker):
+    """A specialised kernel reads each constant phase factor as two 64-bit
+    packed operands of its parameter block: every such read starts on an
+    even word (8-byte aligned, the block being declared 8-byte aligned) and
+    lies inside the block, and every block is a whole number of 8-byte units
+    (the launch passes exactly its words)."""
+    import re
+    c = maker()
+    opt = S.default_options(flags=S.default_options().flags | S.SIM_F_JIT)
+    src = S.jit_sources(c.n, c.gates, S.SIM_C64, c.basis, opt)
+    parts = [p for p in re.split(r"(?=// ---- specialised sweep)", src) if p.startswith("// ---- specialised")]
+    assert parts
+    packed = 0
+    for p in parts:
+        words = int(re.match(r"// ---- specialised sweep \d+: (\d+) parameter words", p).group(1))
+        assert words % 2 == 0
+        assert "struct __align__(8) JP { uint32_t w[%d]; };" % words in p
+        for k in map(int, re.findall(r"\*\(const u64 \*\)&P\.w\[(\d+)\]", p)):
+            assert k % 2 == 0 and k + 1 < words
+            packed += 1
+        # the amplitudes' phase products are packed (no scalar product of an amplitude)
+        assert not re.search(r"v\[\d+\] = cmul\(v\[", p)
+    assert packed > 0   # each of these circuits has constant phase factors
