@@ -42,11 +42,11 @@ WORKLOAD = "28-qubit diagonal-heavy gate-level stream (500 gates, 80% RZ/CP/RZZ,
 # A sweep's traffic grows with the amplitudes it processes, so a capture on a
 # smaller state scales to the full one (profiles/ has the captures).
 TRAFFIC_PER_AMP = {
-    # profiles/svs_chunk_jit_diagheavy_28q.md: 3.9242 GB per launch, the mean of
+    # profiles/svs_chunk_jit_diagheavy_28q.md: 3.9241 GB per launch, the mean of
     # one step's seven 2^28-amplitude sweeps (six read + write, one write-only)
     # at this workload's own size, as `achieved` averages the algorithmic bytes
     # (the specialised kernel: keyed by its device templates and generator)
-    ("diag-heavy", "chunk-jit", "71880ec277eb61e83993d152f97fd715e9714f575de4e7b9596512422c3feaf7"): 3.92419e9 / 2 ** 28,
+    ("diag-heavy", "chunk-jit", "b550109b50cf382e660da46a21662018df0103984dbd8174814aed752c456a33"): 3.92412e9 / 2 ** 28,
     # profiles/k_chunk_diagheavy_25q.md: 476.05 MB per 2^25-amplitude sweep (interpreter)
     ("diag-heavy", "chunk", "8f96366b3d7184491700fbf33588aba4d28412cc874eee7e00ed69b7789963a2"): 476.05e6 / 2 ** 25,
     # profiles/k_dense5_tc_layered_26q.md: 1011.84 MB per 2^26-amplitude block sweep
