@@ -505,6 +505,16 @@ static void encode_dseg(ProgWriter &pw, const std::vector<Term> &terms, const Ds
     // of evaluating a sin/cos per amplitude)
     for (uint32_t m = 0; m < (1u << RB); m++) {
         const uint64_t q = qweight(tab[m], f64);
+        if (q == 0) {   // cis(0) = (1, +0) exactly: no long-double sin/cos
+            if (f64) {
+                put_df(pw, 1.0L);
+                put_df(pw, 0.0L);
+            } else {
+                pw.put(0x3f800000u);   // 1.0f
+                pw.put(0u);            // +0.0f
+            }
+            continue;
+        }
         const long double th = 6.283185307179586476925286766559L *
                                (f64 ? (long double)q * 0x1p-64L : (long double)(uint32_t)q * 0x1p-32L);
         if (f64) {
